@@ -1,0 +1,26 @@
+"""FP64 CPU oracle for the Wilson-Dirac fermion matrix (test infrastructure only).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg import
+this package. It shares no code with the CUDA library; both sides take their
+inputs from the seeded generators in paper_1112_5280_gb300.synth.
+
+Contents
+  * ctypes bindings to the C oracle (wilson_oracle.c): hopping term, M, Mhat,
+    CG on the normal equations, even-odd CG and BiCGStab.
+  * dense.py: brute-force dense matrices for tiny lattices (pure Python loops),
+    the free-field closed forms and the FFT solve of the free field.
+"""
+from .wilson import (  # noqa: F401
+    apply_M,
+    apply_Mhat,
+    get_threads,
+    hop,
+    hop_eo,
+    hop_sites,
+    set_threads,
+    solve,
+    true_residual,
+    METHOD_CG_FULL,
+    METHOD_CG_EO,
+    METHOD_BICGSTAB_EO,
+)
