@@ -1,0 +1,228 @@
+/* lqcd.h — C ABI of the GB300 (sm_103a) Wilson-Dirac library.
+ *
+ * Operator (paper arXiv:1112.5280, Section 3: the even-odd preconditioned
+ * Wilson hopping term "dslash" and the inversion of the fermion matrix are
+ * the hot path; the operator is not written out there, this is the textbook
+ * Wilson form with r = 1 in the kappa normalisation):
+ *
+ *   M psi(x) = psi(x) - kappa sum_mu [ eta (1 - g_mu) U_mu(x) psi(x+mu)
+ *                                     + eta (1 + g_mu) U_mu(x-mu)^dag psi(x-mu) ]
+ *
+ * chiral gamma matrices g_k = [[0, -i s_k], [i s_k, 0]] (mu = 0,1,2 = x,y,z),
+ * g_t = [[0, 1], [1, 0]] (mu = 3), g5 = diag(1, 1, -1, -1); eta = t_bc on
+ * hops across the t boundary (t_bc = -1: antiperiodic), else 1.
+ * Even-odd (Section 3 "even-odd preconditioned"): with D_pq the hop from
+ * parity q to parity p, Mhat = 1 - kappa^2 D_eo D_oe on even sites,
+ * bhat_e = b_e + kappa D_eo b_o and x_o = b_o + kappa D_oe x_e.
+ *
+ * Host layout (borrowed for the duration of a call, never retained):
+ *   site s = x + Lx*(y + Ly*(z + Lz*t)), x fastest; parity (x+y+z+t) mod 2, 0 = even
+ *   links   double[V][4][3][3][2]  (mu, row, col, re/im)
+ *   spinors double[V][4][3][2]     (spin, colour, re/im)
+ * All extents must be even and >= 2; V/2 < 2^31.
+ *
+ * Return values: LQCD_OK (0) or a negative LQCD_E* code; lqcd_last_error()
+ * gives a message for the calling thread. Handles are owned by the library
+ * and released with the matching *_destroy; destroying NULL is a no-op.
+ * All device work of a context runs on its stream; calls that return host
+ * data synchronise that stream. A context is used by one host thread at a time.
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define LQCD_API __attribute__((visibility("default")))
+#else
+#define LQCD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LQCD_OK 0
+#define LQCD_EINVAL (-1)       /* bad argument (sizes, parities, precisions, NULL) */
+#define LQCD_ENOMEM (-2)       /* device allocation failed, or request beyond the engine budget */
+#define LQCD_ENOCONV (-3)      /* solver hit maxiter before the tolerance */
+#define LQCD_EBREAKDOWN (-4)   /* Krylov breakdown (zero denominator) */
+#define LQCD_ENONFINITE (-5)   /* NaN or Inf in a residual */
+#define LQCD_ETIMEOUT (-6)     /* engine deadline passed */
+#define LQCD_ECUDA (-7)        /* CUDA runtime error (message in lqcd_last_error) */
+#define LQCD_EBUSY (-8)        /* engine cannot admit the request now (slots or memory in use) */
+
+/* storage precisions */
+#define LQCD_F64 0
+#define LQCD_F32 1
+#define LQCD_F16 2
+#define LQCD_BF16 3
+
+/* field subsets */
+#define LQCD_EVEN 0
+#define LQCD_ODD 1
+#define LQCD_FULL 2
+
+/* solvers */
+#define LQCD_CG 0        /* CG on Mhat^dag Mhat (normal equations of the Schur system) */
+#define LQCD_BICGSTAB 1  /* BiCGStab on Mhat */
+
+typedef struct lqcd_ctx lqcd_ctx;
+typedef struct lqcd_gauge lqcd_gauge;
+typedef struct lqcd_field lqcd_field;
+typedef struct lqcd_engine lqcd_engine;
+
+LQCD_API const char* lqcd_status_string(int status);
+/* Message of the last failing call on this host thread ("" if none). */
+LQCD_API const char* lqcd_last_error(void);
+/* Library version string. */
+LQCD_API const char* lqcd_version(void);
+
+/* ---------------------------------------------------------------- context */
+
+/* Binds CUDA device `device`. cuda_stream: a cudaStream_t borrowed for the
+ * context's lifetime, or NULL to create an owned non-blocking stream. */
+LQCD_API int lqcd_ctx_create(lqcd_ctx** out, int device, void* cuda_stream);
+LQCD_API void lqcd_ctx_destroy(lqcd_ctx* ctx);
+/* Replaces the stream (borrowed; NULL restores the owned stream). */
+LQCD_API int lqcd_ctx_set_stream(lqcd_ctx* ctx, void* cuda_stream);
+LQCD_API void* lqcd_ctx_stream(const lqcd_ctx* ctx);
+LQCD_API int lqcd_ctx_sync(lqcd_ctx* ctx);
+/* Number of batched-kernel launches this context has issued (instrumentation). */
+LQCD_API long long lqcd_ctx_launch_count(const lqcd_ctx* ctx);
+
+/* ---------------------------------------------------------------- gauge field (A1) */
+
+/* Uploads an SU(3) gauge field (host layout above) and converts it on the
+ * device to the structure-of-arrays even-odd layout. An FP64 18-real copy is
+ * always kept (true residuals); `prec` / `compress` (18 or 12 reals, row 2
+ * rebuilt from rows 0-1 as conj(row0 x row1), the RECONSTRUCT TWELVE of
+ * Section 3) choose the default copy used for fields of that precision.
+ * prec LQCD_F16 and LQCD_BF16 both store FP16 links. t_bc: +1 or -1.
+ * The 12-real form assumes det U = 1 (true for the seeded generator). */
+LQCD_API int lqcd_gauge_upload(lqcd_ctx* ctx, const int dims[4], const double* host_U, int prec,
+                      int compress, int t_bc, lqcd_gauge** out);
+/* Same from a device pointer (e.g. a torch tensor) in the host layout. */
+LQCD_API int lqcd_gauge_upload_dev(lqcd_ctx* ctx, const int dims[4], const double* dev_U, int prec,
+                          int compress, int t_bc, lqcd_gauge** out);
+/* Adds a resident copy in another precision / compression (from the FP64 copy). */
+LQCD_API int lqcd_gauge_add_copy(lqcd_gauge* g, int prec, int compress);
+/* Device bytes held by the gauge field (all copies). */
+LQCD_API size_t lqcd_gauge_bytes(const lqcd_gauge* g);
+LQCD_API void lqcd_gauge_destroy(lqcd_gauge* g);
+
+/* ---------------------------------------------------------------- spinor fields (A2) */
+
+/* Allocates a spinor field of the gauge's lattice: subset LQCD_EVEN, LQCD_ODD
+ * (one checkerboard, V/2 sites) or LQCD_FULL (both). Contents are zero. */
+LQCD_API int lqcd_field_create(lqcd_ctx* ctx, const int dims[4], int prec, int subset, lqcd_field** out);
+/* host_psi: full-lattice host spinor; sites outside the field's subset are ignored. */
+LQCD_API int lqcd_field_upload(lqcd_field* f, const double* host_psi);
+/* Writes the field's sites into host_psi (full-lattice array); other sites untouched. */
+LQCD_API int lqcd_field_download(const lqcd_field* f, double* host_psi);
+/* Device-pointer variants (full-lattice FP64 array in the host layout, on the device). */
+LQCD_API int lqcd_field_upload_dev(lqcd_field* f, const double* dev_psi);
+LQCD_API int lqcd_field_download_dev(const lqcd_field* f, double* dev_psi);
+/* dst = scale * src on the common subset, converting precision. */
+LQCD_API int lqcd_field_copy(lqcd_field* dst, const lqcd_field* src, double scale);
+/* ||f||^2 over the field's sites (FP64 accumulation). */
+LQCD_API int lqcd_field_norm2(const lqcd_field* f, double* out);
+LQCD_API int lqcd_field_zero(lqcd_field* f);
+LQCD_API size_t lqcd_field_bytes(const lqcd_field* f);
+LQCD_API void lqcd_field_destroy(lqcd_field* f);
+
+/* ---------------------------------------------------------------- operators (A3-A5) */
+
+/* out_{p} = D_{p,1-p} in_{1-p} (hopping term alone; dagger != 0 gives (D^dag)_{p,1-p}
+ * = g5 D_{p,1-p} g5). in must hold parity 1-p (subset 1-p or FULL); out must hold
+ * parity p. Both fields have the same precision; the gauge copy of that precision
+ * (with the gauge's compression) is used. Asynchronous on the context stream. */
+LQCD_API int lqcd_dslash_eo(const lqcd_gauge* g, const lqcd_field* in, lqcd_field* out, int out_parity,
+                   int dagger);
+/* out_e = in_e - kappa^2 D_eo D_oe in_e (or Mhat^dag = g5 Mhat g5 when dagger).
+ * in and out hold the even parity (EVEN or FULL); uses an odd temporary of the context. */
+LQCD_API int lqcd_apply_Mhat(const lqcd_gauge* g, double kappa, const lqcd_field* in, lqcd_field* out,
+                    int dagger);
+/* out = M in (full, unpreconditioned); both fields FULL. */
+LQCD_API int lqcd_apply_M(const lqcd_gauge* g, double kappa, const lqcd_field* in, lqcd_field* out,
+                 int dagger);
+
+/* ---------------------------------------------------------------- solvers (A6-A9) */
+
+typedef struct lqcd_solve_opts {
+  int solver;           /* LQCD_CG or LQCD_BICGSTAB */
+  int sloppy_prec;      /* LQCD_F64: plain FP64 solve; LQCD_F32 / F16 / BF16: mixed precision */
+  int sloppy_compress;  /* 18 or 12 reals per link of the sloppy operator */
+  int maxiter;          /* iteration limit (default 50000) */
+  double delta;         /* reliable-update threshold on |r| (<= 0: 0.1 mixed, none for FP64) */
+  int chunk;            /* iterations per CUDA-graph replay / host poll (default 32) */
+  int use_graph;        /* 1: capture iteration chunks as CUDA graphs (default 1) */
+} lqcd_solve_opts;
+
+typedef struct lqcd_solve_info {
+  int status;            /* LQCD_OK, LQCD_ENOCONV, LQCD_EBREAKDOWN, LQCD_ENONFINITE */
+  int iters;             /* Krylov iterations (sloppy) */
+  int reliable_updates;  /* FP64 true-residual recomputations */
+  int pad;
+  double true_resid;     /* ||b - M x|| / ||b|| with the full FP64 operator */
+  double ms;             /* wall time of the call */
+} lqcd_solve_info;
+
+LQCD_API void lqcd_solve_opts_default(lqcd_solve_opts* opts);
+
+/* Solves M x = b (full lattice) through the even-odd Schur system to
+ * ||b - M x|| <= tol ||b||, checked in FP64 on the full operator. host_src and
+ * host_x are full-lattice host spinors. info (may be NULL) is filled even on
+ * failure; the return value equals info->status. */
+LQCD_API int lqcd_solve(const lqcd_gauge* g, const double* host_src, double kappa, double tol,
+               const lqcd_solve_opts* opts, double* host_x, lqcd_solve_info* info);
+/* Same with device fields: src and x are FULL FP64 fields. */
+LQCD_API int lqcd_solve_fields(const lqcd_gauge* g, const lqcd_field* src, double kappa, double tol,
+                      const lqcd_solve_opts* opts, lqcd_field* x, lqcd_solve_info* info);
+/* Multi-right-hand-side solve (A10): n sources on one gauge field, one batched
+ * Krylov recurrence per source, links streamed once per site block for all
+ * sources. srcs[i], xs[i]: FULL FP64 fields. infos: n entries (may be NULL).
+ * Returns LQCD_OK if every solve converged, else the first failing status. */
+LQCD_API int lqcd_solve_multi(const lqcd_gauge* g, int n, const lqcd_field* const* srcs, double kappa,
+                     double tol, const lqcd_solve_opts* opts, lqcd_field* const* xs,
+                     lqcd_solve_info* infos);
+
+/* ---------------------------------------------------------------- batched engine (A11, A12) */
+
+/* A Krylov engine that advances many independent solves (any lattice sizes,
+ * own gauge field and kappa each) in the same kernel launches. hbm_budget:
+ * device bytes the engine may hold for solver state (0: no limit); max_slots:
+ * concurrent solves (<= 1024). opts: as for lqcd_solve (CG only). */
+LQCD_API int lqcd_engine_create(lqcd_ctx* ctx, const lqcd_solve_opts* opts, size_t hbm_budget,
+                       int max_slots, lqcd_engine** out);
+/* Device bytes one request on this lattice holds while active. */
+LQCD_API size_t lqcd_engine_request_bytes(const lqcd_engine* e, const int dims[4]);
+/* Admits a solve of M x = src (src: FULL FP64 field, copied at submit). Returns
+ * LQCD_EBUSY when no slot or not enough budget is free now (the caller retries
+ * after results are collected), LQCD_ENOMEM when the request can never fit. */
+LQCD_API int lqcd_engine_submit(lqcd_engine* e, const lqcd_gauge* g, const lqcd_field* src, double kappa,
+                       double tol, long long* request_id);
+/* Runs one chunk of iterations for every active solve; *n_active: solves still running. */
+LQCD_API int lqcd_engine_step(lqcd_engine* e, int* n_active);
+/* Ids of solves finished since the last call (up to max). */
+LQCD_API int lqcd_engine_completed(lqcd_engine* e, long long* ids, int max, int* n);
+/* Copies the solution of a finished request into x (FULL FP64) and frees its slot. */
+LQCD_API int lqcd_engine_result(lqcd_engine* e, long long request_id, lqcd_field* x, lqcd_solve_info* info);
+/* Stops a running request: it finishes at the next step with `status` (a negative
+ * LQCD_E* code, e.g. LQCD_ETIMEOUT) and its best iterate so far. */
+LQCD_API int lqcd_engine_cancel(lqcd_engine* e, long long request_id, int status);
+/* Active solves and device bytes in use. */
+LQCD_API int lqcd_engine_stats(const lqcd_engine* e, int* active, size_t* bytes_in_use);
+LQCD_API void lqcd_engine_destroy(lqcd_engine* e);
+
+/* ---------------------------------------------------------------- tuning */
+
+/* Caps the persistent grid of batched kernel family (0 Dslash, 1 BLAS) at
+ * mult CTAs per SM (0: occupancy limit). */
+LQCD_API void lqcd_set_grid_multiplier(int family, int mult);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LQCD_H */

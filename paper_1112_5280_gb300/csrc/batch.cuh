@@ -1,0 +1,343 @@
+// Batched tile launches: one kernel launch covers many independent "slots"
+// (a slot = one lattice problem: a single solve, one right-hand side of a
+// multi-RHS solve, or one request of the serving loop).
+//
+// Work is cut into tiles of TILE consecutive half-lattice sites of one slot.
+// A launch walks its tile list with a persistent grid (CTAs per SM chosen by
+// the tuner). Norm reductions are deterministic and batch independent: every
+// tile writes one FP64 partial at partial[slot.tile0 + tile_in_slot]; the last
+// tile of a slot to finish (atomic ticket) sums that slot's partials in tile
+// order and runs the slot's scalar program (the "finisher"). So the result of
+// a slot depends only on its own geometry, never on what else is in the batch.
+#pragma once
+
+#include "dslash.cuh"
+
+namespace lqcd {
+
+constexpr int TILE = 128;         // sites per tile = threads per CTA of batched kernels
+constexpr int MAX_SLOTS = 1024;   // slots in one launch
+
+// Slot state machine of the Krylov engine.
+enum SlotState { S_RUNNING = 0, S_UPDATE = 1, S_DONE = 2, S_FAILED = 3, S_IDLE = 4 };
+// Status codes written into Scalars::status (mirrors the public LQCD_* codes).
+enum SlotStatus { ST_OK = 0, ST_MAXITER = -3, ST_BREAKDOWN = -4, ST_NONFINITE = -5 };
+
+// Scalar programs run by the last tile of a slot after a reduction.
+enum Fin {
+  FIN_NONE = 0,
+  FIN_STORE0,    // res[0] = sum
+  FIN_STORE1,    // res[1] = sum
+  FIN_ALPHA,     // CG: qq = |Mhat p|^2, alpha = rr / qq
+  FIN_BETA,      // CG: rr_new, beta, reliable-update / stop / maxiter decisions
+  FIN_TRUERES,   // reliable update: |bhat - Mhat x|^2 -> converged?
+  FIN_RHO,       // reliable update: |Mhat^dag u|^2 -> new sloppy scale and p coefficient
+  FIN_RESUME,    // reliable update done: back to RUNNING
+  FIN_BICG_RHO,  // BiCGStab scalars (see solver.cu)
+  FIN_BICG_ALPHA,
+  FIN_BICG_OMEGA,
+  FIN_BICG_RES,
+};
+
+// Per-slot solver state in device memory.
+struct Scalars {
+  double rr, rr_prev, alpha, beta, qq, rr_max;
+  double stop_rr;   // sloppy rr at which the engine checks the true residual
+  double delta2;    // reliable update when rr < delta2 * rr_max since the last update
+  double target2;   // (tol * |b|)^2 for the FP64 true residual of Mhat
+  double sigma;     // sloppy unit: true vector = sigma * stored vector
+  double true_r2;   // last |bhat - Mhat x|^2 (FP64)
+  double rho2;      // last |Mhat^dag u|^2 (FP64)
+  double nreal;     // 24 * Vh, for the RMS normalisation of sloppy vectors
+  double res[6];    // generic reduction results / coefficients
+  double cres[8];   // complex scalars (BiCGStab): re, im pairs
+  int state, status, iter, maxiter, last, n_updates, restart_p, pad;
+  unsigned counter;
+  unsigned pad2[3];
+};
+
+// One slot's operands for one batched kernel.
+struct Work {
+  Geom g;
+  int out_par;      // output parity (dslash) / parity of the half fields
+  int run_if;       // run only when Scalars::state == run_if; -1: always
+  int red;          // reduction: 0 none, 1 |out|^2, 2 <zin,out>, 3 <out,y1> and |out|^2,
+                    //            4 <y2,out> and |out|^2 (complex dots as re, im)
+  int fin;          // Fin program after the reduction
+  int pad;
+  const void* in;   // in-parity half field (dslash input)
+  void* out;        // out-parity half field
+  const void* Uout; // links of parity out_par (dslash)
+  const void* Uin;  // links of parity 1 - out_par
+  const void* y1;   // epilogue operands (out parity), may be null
+  const void* y2;
+  void* z;          // secondary output (CG: x_sloppy)
+  const void* zin;  // secondary input (CG: p)
+  double a, c1, c2; // out = a * D in + c1 * y1 + c2 * y2
+  Scalars* sc;
+  int tile0;        // first partial of this slot
+  int ntiles;       // tiles of this slot = ceil(Vh / TILE)
+};
+
+// A launch: slots in device memory (works != nullptr) or one slot by value.
+struct Launch {
+  const Work* works;
+  const int* tile_prefix;  // CONCAT mode: prefix sums of ntiles, nslots + 1 entries
+  Work inline_work;
+  int nslots;
+  int ntiles;              // total tiles
+  int interleave;          // 1: tile t -> (slot t % nslots, block t / nslots), equal Vh
+  double* partials;
+};
+
+__device__ __forceinline__ const Work& work_of(const Launch& L, int slot) {
+  return L.works ? L.works[slot] : L.inline_work;
+}
+
+// tile -> (slot, first site)
+__device__ __forceinline__ void tile_of(const Launch& L, int tile, int& slot, int& start) {
+  if (L.nslots == 1) {
+    slot = 0;
+    start = tile * TILE;
+  } else if (L.interleave) {
+    slot = tile % L.nslots;
+    start = (tile / L.nslots) * TILE;
+  } else {
+    int lo = 0, hi = L.nslots;  // largest slot with prefix[slot] <= tile
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (__ldg(L.tile_prefix + mid) <= tile) lo = mid; else hi = mid;
+    }
+    slot = lo;
+    start = (tile - __ldg(L.tile_prefix + lo)) * TILE;
+  }
+}
+
+__device__ __forceinline__ bool slot_runs(const Work& w) {
+  if (w.run_if < 0) return true;
+  return *((volatile int*)&w.sc->state) == w.run_if;
+}
+
+// Block-wide FP64 sum in a fixed order (TILE threads). Result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double s = 0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < TILE / 32; ++i) s += sh[i];
+  }
+  __syncthreads();
+  return s;
+}
+
+// The scalar programs. Run by one thread of the slot's last tile.
+__device__ __noinline__ static void run_fin_bicg(const Work& w, const double* v);
+
+__device__ __noinline__ static void run_fin(const Work& w, const double* v) {
+  Scalars* s = w.sc;
+  const double sum = v[0];
+  switch (w.fin) {
+    case FIN_STORE0:
+      s->res[0] = sum;
+      break;
+    case FIN_STORE1:
+      s->res[1] = sum;
+      break;
+    case FIN_ALPHA:  // alpha = <r,r> / <p, Mhat^dag Mhat p> = rr / |Mhat p|^2
+      s->qq = sum;
+      if (!isfinite(sum)) {
+        s->state = S_FAILED;
+        s->status = ST_NONFINITE;
+      } else if (!(sum > 0.0)) {
+        s->state = S_FAILED;
+        s->status = ST_BREAKDOWN;
+      } else {
+        s->alpha = s->rr / sum;
+      }
+      break;
+    case FIN_BETA: {  // new |r|^2: beta, and whether to leave for a reliable update
+      s->rr_prev = s->rr;
+      s->rr = sum;
+      s->iter += 1;
+      if (!isfinite(sum)) {
+        s->state = S_FAILED;
+        s->status = ST_NONFINITE;
+        break;
+      }
+      s->beta = sum / s->rr_prev;
+      if (sum > s->rr_max) s->rr_max = sum;
+      bool upd = (sum <= s->stop_rr) || (sum < s->delta2 * s->rr_max);
+      if (s->iter >= s->maxiter) {
+        upd = true;
+        s->last = 1;
+      }
+      if (upd) s->state = S_UPDATE;
+      break;
+    }
+    case FIN_TRUERES:  // FP64 |bhat - Mhat x|^2
+      s->true_r2 = sum;
+      s->n_updates += 1;
+      if (!isfinite(sum)) {
+        s->state = S_FAILED;
+        s->status = ST_NONFINITE;
+      } else if (sum <= s->target2) {
+        s->state = S_DONE;
+        s->status = ST_OK;
+      } else if (s->last) {
+        s->state = S_FAILED;
+        s->status = ST_MAXITER;
+      }
+      break;
+    case FIN_RHO: {  // rho = Mhat^dag u: new sloppy unit, p coefficient, stop estimate
+      s->rho2 = sum;
+      if (!isfinite(sum) || !(sum > 0.0)) {
+        s->state = S_FAILED;
+        s->status = isfinite(sum) ? ST_BREAKDOWN : ST_NONFINITE;
+        break;
+      }
+      const double sig_new = sqrt(sum / s->nreal);
+      double pc = 0.0;
+      if (!s->restart_p) {
+        // beta of the CG step replaced by this update, in true units, then
+        // p rescaled from the old sloppy unit to the new one
+        const double beta = sum / (s->sigma * s->sigma * s->rr_prev);
+        pc = beta * s->sigma / sig_new;
+      }
+      s->res[4] = pc;
+      s->res[5] = 1.0 / sig_new;
+      const double c2 = s->true_r2 / sum;  // |u|^2 / |Mhat^dag u|^2 at this x
+      s->sigma = sig_new;
+      s->rr = sum / (sig_new * sig_new);
+      s->rr_max = s->rr;
+      s->stop_rr = 0.5 * s->target2 / (c2 * sig_new * sig_new);
+      break;
+    }
+    case FIN_RESUME:
+      s->state = S_RUNNING;
+      s->restart_p = 0;
+      break;
+    default:
+      run_fin_bicg(w, v);
+      break;
+  }
+}
+
+// complex helpers for the BiCGStab scalars (re, im pairs in Scalars::cres)
+__device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi, double& r, double& i) {
+  const double d = br * br + bi * bi;
+  r = (ar * br + ai * bi) / d;
+  i = (ai * br - ar * bi) / d;
+}
+
+// cres: [0,1] rho, [2,3] alpha, [4,5] omega, [6,7] beta; res[0] = |r|^2
+__device__ __noinline__ static void run_fin_bicg(const Work& w, const double* v) {
+  Scalars* s = w.sc;
+  switch (w.fin) {
+    case FIN_BICG_ALPHA: {  // alpha = rho / <r0, v>
+      if (!isfinite(v[0]) || !isfinite(v[1])) {
+        s->state = S_FAILED;
+        s->status = ST_NONFINITE;
+      } else if (v[0] == 0.0 && v[1] == 0.0) {
+        s->state = S_FAILED;
+        s->status = ST_BREAKDOWN;
+      } else {
+        cdiv(s->cres[0], s->cres[1], v[0], v[1], s->cres[2], s->cres[3]);
+      }
+      break;
+    }
+    case FIN_BICG_OMEGA: {  // omega = <t, s> / <t, t>
+      if (!isfinite(v[2]) || !isfinite(v[0])) {
+        s->state = S_FAILED;
+        s->status = ST_NONFINITE;
+      } else if (!(v[2] > 0.0)) {
+        s->state = S_FAILED;
+        s->status = ST_BREAKDOWN;
+      } else {
+        s->cres[4] = v[0] / v[2];
+        s->cres[5] = v[1] / v[2];
+      }
+      break;
+    }
+    case FIN_BICG_RES: {  // rho_new = <r0, r>, |r|^2; beta = (rho_new / rho) (alpha / omega)
+      s->iter += 1;
+      s->res[0] = v[2];
+      if (!isfinite(v[2]) || !isfinite(v[0])) {
+        s->state = S_FAILED;
+        s->status = ST_NONFINITE;
+        break;
+      }
+      if (v[2] <= s->stop_rr) {
+        s->state = S_DONE;
+        break;
+      }
+      if (s->iter >= s->maxiter) {
+        s->state = S_FAILED;
+        s->status = ST_MAXITER;
+        break;
+      }
+      double q1r, q1i, q2r, q2i;
+      if ((s->cres[0] == 0.0 && s->cres[1] == 0.0) || (s->cres[4] == 0.0 && s->cres[5] == 0.0) ||
+          (v[0] == 0.0 && v[1] == 0.0)) {
+        s->state = S_FAILED;
+        s->status = ST_BREAKDOWN;
+        break;
+      }
+      cdiv(v[0], v[1], s->cres[0], s->cres[1], q1r, q1i);
+      cdiv(s->cres[2], s->cres[3], s->cres[4], s->cres[5], q2r, q2i);
+      s->cres[6] = q1r * q2r - q1i * q2i;
+      s->cres[7] = q1r * q2i + q1i * q2r;
+      s->cres[0] = v[0];
+      s->cres[1] = v[1];
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// Called by all threads of the CTA after its tile: records the partial sums, and
+// the slot's last tile sums all partials of the slot (in tile order) and runs
+// the finisher. Partials are strided by 3 (up to three sums per reduction).
+__device__ __forceinline__ void tile_finish(const Work& w, int tile_in_slot, double v0, double v1,
+                                            double v2, double* partials) {
+  __shared__ double sh[TILE / 32];
+  __shared__ int am_last;
+  if (!w.red && w.fin == FIN_NONE) return;
+  const int ns = (w.red >= 2) ? 3 : 1;
+  double s[3];
+  s[0] = block_sum(v0, sh);
+  if (ns == 3) {
+    s[1] = block_sum(v1, sh);
+    s[2] = block_sum(v2, sh);
+  }
+  if (threadIdx.x == 0) {
+    double* dst = partials + 3 * (size_t)(w.tile0 + tile_in_slot);
+    for (int k = 0; k < ns; ++k) dst[k] = s[k];
+    __threadfence();
+    const unsigned ticket = atomicAdd(&w.sc->counter, 1u);
+    am_last = (ticket == (unsigned)w.ntiles - 1);
+  }
+  __syncthreads();
+  if (am_last) {
+    __threadfence();
+    double acc[3] = {0, 0, 0};
+    for (int i = threadIdx.x; i < w.ntiles; i += TILE) {
+      const double* src = partials + 3 * (size_t)(w.tile0 + i);
+      for (int k = 0; k < ns; ++k) acc[k] += __ldcg(src + k);
+    }
+    double tot[3] = {0, 0, 0};
+    for (int k = 0; k < ns; ++k) tot[k] = block_sum(acc[k], sh);
+    if (threadIdx.x == 0) {
+      w.sc->counter = 0;
+      run_fin(w, tot);
+      __threadfence();
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace lqcd

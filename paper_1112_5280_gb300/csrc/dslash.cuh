@@ -1,0 +1,176 @@
+// The even-odd Wilson hopping term at one output site.
+//
+// D_{pq} psi (x) = sum_mu [ eta (1 - g_mu) U_mu(x) psi(x+mu)
+//                         + eta (1 + g_mu) U_mu(x-mu)^dag psi(x-mu) ],   x of parity p
+// (paper Section 3: the even-odd preconditioned "dslash"; the operator itself
+// is the textbook Wilson term with r = 1). eta = t_bc for hops across the t
+// boundary, applied to the hop and never folded into the links, so the
+// 12-real reconstruction stays valid. D^dag swaps the two projectors.
+//
+// Chiral basis: g_k = [[0, A_k], [A_k^dag, 0]] with A_k = -i sigma_k
+// (mu = 0, 1, 2) and A_t = 1, so g5 = diag(1, 1, -1, -1). The projector
+// (1 + s g_mu), s = +-1, has rank two:
+//   (1 + s g) psi = [ h ; s A^dag h ],   h = psi_up + s A psi_dn,
+// so each hop projects to a half spinor h (2 spin x 3 colour), multiplies the
+// two colour vectors by the link, and rebuilds the lower spin components.
+#pragma once
+
+#include "field.cuh"
+
+namespace lqcd {
+
+struct Geom {
+  int L[4];  // Lx, Ly, Lz, Lt (all even)
+  int Lxh;   // Lx / 2
+  int Vh;    // V / 2 sites per parity
+  int t_bc;  // +1 periodic, -1 antiperiodic in t
+};
+
+// Half-lattice index h = xh + Lxh*(y + Ly*(z + Lz*t)) with x = 2 xh + ((p+y+z+t) & 1).
+__device__ __forceinline__ void neighbours(const Geom& g, int h, int par, int nf[4], int nb[4],
+                                           int& t) {
+  const int xh = h % g.Lxh;
+  int r = h / g.Lxh;
+  const int y = r % g.L[1];
+  r /= g.L[1];
+  const int z = r % g.L[2];
+  t = r / g.L[2];
+  const int x = 2 * xh + ((par + y + z + t) & 1);
+  const int rest = h - xh;
+  const int xp = (x + 1 == g.L[0]) ? 0 : x + 1;
+  const int xm = (x == 0) ? g.L[0] - 1 : x - 1;
+  nf[0] = rest + (xp >> 1);
+  nb[0] = rest + (xm >> 1);
+  const int sy = g.Lxh;
+  nf[1] = (y + 1 == g.L[1]) ? h - (g.L[1] - 1) * sy : h + sy;
+  nb[1] = (y == 0) ? h + (g.L[1] - 1) * sy : h - sy;
+  const int sz = sy * g.L[1];
+  nf[2] = (z + 1 == g.L[2]) ? h - (g.L[2] - 1) * sz : h + sz;
+  nb[2] = (z == 0) ? h + (g.L[2] - 1) * sz : h - sz;
+  const int st = sz * g.L[2];
+  nf[3] = (t + 1 == g.L[3]) ? h - (g.L[3] - 1) * st : h + st;
+  nb[3] = (t == 0) ? h + (g.L[3] - 1) * st : h - st;
+}
+
+template <typename R>
+__device__ __forceinline__ Cx<R> sp(const R* v, int spin, int col) {
+  return {v[(spin * 3 + col) * 2], v[(spin * 3 + col) * 2 + 1]};
+}
+template <typename R>
+__device__ __forceinline__ void acc_add(R* a, int spin, int col, Cx<R> w) {
+  a[(spin * 3 + col) * 2] += w.re;
+  a[(spin * 3 + col) * 2 + 1] += w.im;
+}
+// i * w
+template <typename R>
+__device__ __forceinline__ Cx<R> mul_i(Cx<R> w) {
+  return {-w.im, w.re};
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> scale(Cx<R> w, R s) {
+  return {s * w.re, s * w.im};
+}
+
+// One hop: acc += eta * (1 + S g_MU) (U or U^dag) psi.
+template <int MU, int S, bool ADJ, typename R>
+__device__ __forceinline__ void hop(const R psi[24], const R u[18], R eta, R acc[24]) {
+  Cx<R> h0[3], h1[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const Cx<R> p0 = sp(psi, 0, c), p1 = sp(psi, 1, c), p2 = sp(psi, 2, c), p3 = sp(psi, 3, c);
+    if (MU == 0) {  // h = psi_up + S (-i sigma_1) psi_dn
+      h0[c] = {p0.re + S * p3.im, p0.im - S * p3.re};
+      h1[c] = {p1.re + S * p2.im, p1.im - S * p2.re};
+    } else if (MU == 1) {  // -i sigma_2 = [[0,-1],[1,0]]
+      h0[c] = {p0.re - S * p3.re, p0.im - S * p3.im};
+      h1[c] = {p1.re + S * p2.re, p1.im + S * p2.im};
+    } else if (MU == 2) {  // -i sigma_3 = diag(-i, i)
+      h0[c] = {p0.re + S * p2.im, p0.im - S * p2.re};
+      h1[c] = {p1.re - S * p3.im, p1.im + S * p3.re};
+    } else {  // identity
+      h0[c] = {p0.re + S * p2.re, p0.im + S * p2.im};
+      h1[c] = {p1.re + S * p3.re, p1.im + S * p3.im};
+    }
+    if (MU == 3) {
+      h0[c] = scale(h0[c], eta);
+      h1[c] = scale(h1[c], eta);
+    }
+  }
+  Cx<R> w0[3], w1[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Cx<R> s0{R(0), R(0)}, s1{R(0), R(0)};
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const Cx<R> uab = ADJ ? Cx<R>{u[(b * 3 + a) * 2], -u[(b * 3 + a) * 2 + 1]}
+                            : Cx<R>{u[(a * 3 + b) * 2], u[(a * 3 + b) * 2 + 1]};
+      const Cx<R> m0 = cmul(uab, h0[b]), m1 = cmul(uab, h1[b]);
+      s0.re += m0.re; s0.im += m0.im;
+      s1.re += m1.re; s1.im += m1.im;
+    }
+    w0[a] = s0;
+    w1[a] = s1;
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    acc_add(acc, 0, a, w0[a]);
+    acc_add(acc, 1, a, w1[a]);
+    if (MU == 0) {  // lower = S A^dag h, A^dag = [[0,i],[i,0]]
+      acc_add(acc, 2, a, scale(mul_i(w1[a]), R(S)));
+      acc_add(acc, 3, a, scale(mul_i(w0[a]), R(S)));
+    } else if (MU == 1) {  // A^dag = [[0,1],[-1,0]]
+      acc_add(acc, 2, a, scale(w1[a], R(S)));
+      acc_add(acc, 3, a, scale(w0[a], R(-S)));
+    } else if (MU == 2) {  // A^dag = diag(i, -i)
+      acc_add(acc, 2, a, scale(mul_i(w0[a]), R(S)));
+      acc_add(acc, 3, a, scale(mul_i(w1[a]), R(-S)));
+    } else {
+      acc_add(acc, 2, a, scale(w0[a], R(S)));
+      acc_add(acc, 3, a, scale(w1[a], R(S)));
+    }
+  }
+}
+
+// Link field of one parity: direction mu starts NR * Vh reals after direction mu-1.
+template <int LP, int NR>
+__device__ __forceinline__ const char* link_dir(const void* base, int Vh, int mu) {
+  return reinterpret_cast<const char*>(base) + (size_t)mu * NR * Vh * prec_bytes(LP);
+}
+
+template <int MU, int SP, int LP, int NR, bool DAG>
+__device__ __forceinline__ void hop_pair(const Geom& g, int h, const int nf[4], const int nb[4],
+                                         int t, const void* in, const void* Uout,
+                                         const void* Uin, typename SpinorIO<SP>::Real acc[24]) {
+  using R = typename SpinorIO<SP>::Real;
+  {  // forward: U_mu(x) psi(x + mu), projector (1 - g) for D, (1 + g) for D^dag
+    R psi[24], u[18];
+    SpinorIO<SP>::load(in, g.Vh, nf[MU], psi);
+    load_link<LP, NR>(link_dir<LP, NR>(Uout, g.Vh, MU), g.Vh, h, u);
+    const R eta = (MU == 3 && t == g.L[3] - 1) ? R(g.t_bc) : R(1);
+    hop<MU, DAG ? 1 : -1, false>(psi, u, eta, acc);
+  }
+  {  // backward: U_mu(x - mu)^dag psi(x - mu), projector (1 + g) for D, (1 - g) for D^dag
+    R psi[24], u[18];
+    SpinorIO<SP>::load(in, g.Vh, nb[MU], psi);
+    load_link<LP, NR>(link_dir<LP, NR>(Uin, g.Vh, MU), g.Vh, nb[MU], u);
+    const R eta = (MU == 3 && t == 0) ? R(g.t_bc) : R(1);
+    hop<MU, DAG ? -1 : 1, true>(psi, u, eta, acc);
+  }
+}
+
+// acc = (D_{p,1-p} in)(h) for output parity p. Uout: links of parity p, Uin: links of 1-p.
+template <int SP, int LP, int NR, bool DAG>
+__device__ __forceinline__ void dslash_site(const Geom& g, int h, int out_par, const void* in,
+                                            const void* Uout, const void* Uin,
+                                            typename SpinorIO<SP>::Real acc[24]) {
+  int nf[4], nb[4], t;
+  neighbours(g, h, out_par, nf, nb, t);
+#pragma unroll
+  for (int i = 0; i < 24; ++i) acc[i] = 0;
+  hop_pair<0, SP, LP, NR, DAG>(g, h, nf, nb, t, in, Uout, Uin, acc);
+  hop_pair<1, SP, LP, NR, DAG>(g, h, nf, nb, t, in, Uout, Uin, acc);
+  hop_pair<2, SP, LP, NR, DAG>(g, h, nf, nb, t, in, Uout, Uin, acc);
+  hop_pair<3, SP, LP, NR, DAG>(g, h, nf, nb, t, in, Uout, Uin, acc);
+}
+
+}  // namespace lqcd

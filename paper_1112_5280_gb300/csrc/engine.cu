@@ -1,0 +1,787 @@
+// Krylov engine: CG on the normal equations of the even-odd Schur system,
+// Mhat^dag Mhat x_e = Mhat^dag bhat_e (paper Section 3: "inversion of the
+// fermion matrix" with even-odd preconditioning), batched over slots.
+//
+// Mixed precision (defect correction with reliable updates):
+//  * the Krylov vectors r, p, q, t live in the sloppy storage (FP32, FP16 or
+//    BF16, arithmetic in FP32) in units of sigma (RMS 1 per real after each
+//    update), the sloppy solution xs in FP32;
+//  * an update folds sigma * xs into the FP64 solution x, recomputes the true
+//    residual u = bhat - Mhat x and rho = Mhat^dag u in FP64 with FP64 links,
+//    restarts r = rho / sigma_new and keeps the search direction p (rescaled,
+//    with the CG beta of the replaced step);
+//  * an update is triggered when |r| drops below delta * max|r| since the last
+//    one, when the sloppy residual predicts convergence, or at maxiter. The
+//    solve ends when |bhat - Mhat x| <= tol |b| in FP64; then x_o = b_o +
+//    kappa D_oe x_e and the full ||b - M x|| is measured in FP64.
+// With FP64 sloppy storage and delta = 0 this is the plain FP64 CG.
+//
+// Every slot runs its own scalar recurrences on the device (finishers in
+// batch.cuh); the host replays CUDA graphs of `chunk` iterations and polls
+// slot states between replays.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "kernels.cuh"
+#include "runtime.h"
+
+namespace lqcd {
+
+enum Step { K1 = 0, K2, K3, K4, K6, RU_FOLD, RU_D1, RU_RES, RU_D2, RU_RHO, RU_CONV, NSTEP };
+
+__global__ void k_slot_init(Scalars* s, double tol2, double nreal, int maxiter, double delta2) {
+  s->res[3] = s->res[0] + s->res[1];  // |b|^2 of the full source
+  s->target2 = tol2 * s->res[3];
+  s->sigma = 1.0;
+  s->nreal = nreal;
+  s->maxiter = maxiter;
+  s->delta2 = delta2;
+  s->state = S_UPDATE;
+  s->status = ST_OK;
+  s->iter = 0;
+  s->last = 0;
+  s->n_updates = 0;
+  s->restart_p = 1;
+  s->rr = s->rr_prev = 1.0;
+  s->alpha = s->beta = 0.0;
+  s->rr_max = 0.0;
+  s->stop_rr = 0.0;
+  s->counter = 0;
+}
+
+__global__ void k_slot_cancel(Scalars* s, int status) {
+  if (s->state == S_RUNNING || s->state == S_UPDATE) {
+    s->state = S_FAILED;
+    s->status = status;
+  }
+}
+
+struct SlotBuf {
+  void* block = nullptr;
+  size_t bytes = 0;
+  void *be, *bo, *bhat, *x64, *u64, *t64;  // FP64 halves (t64 odd)
+  void *r, *p, *q, *t;                     // sloppy halves (t odd)
+  void* xs;                                // sloppy solution (FP32, or FP64 for an FP64 solve)
+};
+
+struct Request {
+  long long id = 0;
+  const lqcd_gauge* gauge = nullptr;
+  Geom g{};
+  double kappa = 0, tol = 0;
+  int slot = -1;
+  SlotBuf buf;
+  int tile0 = 0, ntiles = 0;
+  bool finished = false;
+  lqcd_solve_info info{};
+  std::chrono::steady_clock::time_point t0;
+};
+
+}  // namespace lqcd
+
+using namespace lqcd;
+
+struct lqcd_engine {
+  lqcd_ctx* ctx = nullptr;
+  lqcd_solve_opts opts{};
+  int sp = P_F32, xp = P_F32, nr = 12;
+  double delta2 = 0.01;
+  int ru_every = 8;
+  size_t budget = 0;
+  int max_slots = 0;
+  Scalars* d_sc = nullptr;
+  Scalars* h_sc = nullptr;
+  Work* d_works = nullptr;  // NSTEP x max_slots
+  int* d_prefix = nullptr;
+  double* d_partials = nullptr;
+  size_t partials_cap = 0;
+  std::vector<int> free_slots;
+  std::map<long long, Request> reqs;  // live and finished-not-collected
+  std::vector<long long> active;      // ids in launch order
+  std::vector<long long> done_ids;    // finished since last lqcd_engine_completed
+  std::multimap<size_t, void*> pool;  // freed slot blocks by size
+  size_t bytes_in_use = 0, bytes_pooled = 0;
+  long long next_id = 1;
+  bool dirty = true;
+  int ntiles_total = 0;
+  int interleave = 0;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<Work> h_works;
+};
+
+namespace {
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t slot_bytes(const lqcd_engine* e, int Vh) {
+  return 6 * align256(half_spinor_bytes(P_F64, Vh)) + 4 * align256(half_spinor_bytes(e->sp, Vh)) +
+         align256(half_spinor_bytes(e->xp, Vh));
+}
+
+void carve(SlotBuf& b, const lqcd_engine* e, int Vh) {
+  char* p = static_cast<char*>(b.block);
+  auto take = [&](int prec) {
+    void* r = p;
+    p += align256(half_spinor_bytes(prec, Vh));
+    return r;
+  };
+  b.be = take(P_F64);
+  b.bo = take(P_F64);
+  b.bhat = take(P_F64);
+  b.x64 = take(P_F64);
+  b.u64 = take(P_F64);
+  b.t64 = take(P_F64);
+  b.r = take(e->sp);
+  b.p = take(e->sp);
+  b.q = take(e->sp);
+  b.t = take(e->sp);
+  b.xs = take(e->xp);
+}
+
+const void* sloppy_links(const lqcd_engine* e, const lqcd_gauge* g) {
+  return g->copy[link_prec_for(e->sp)][e->nr == 12];
+}
+
+Work slot_work(const lqcd_engine* e, const Request& q) {
+  Work w = blank_work(q.g);
+  w.sc = e->d_sc + q.slot;
+  w.tile0 = q.tile0;
+  w.ntiles = q.ntiles;
+  return w;
+}
+
+void step_works(const lqcd_engine* e, const Request& q, Work out[NSTEP]) {
+  const int Vh = q.g.Vh;
+  const double kk = q.kappa * q.kappa;
+  const void* US = sloppy_links(e, q.gauge);
+  const int lpS = link_prec_for(e->sp);
+  const void* U64 = q.gauge->copy[P_F64][0];
+  auto links = [&](Work& w, const void* U, int lp, int nr, int out_par) {
+    w.out_par = out_par;
+    w.Uout = parity_links(U, lp, nr, Vh, out_par);
+    w.Uin = parity_links(U, lp, nr, Vh, 1 - out_par);
+  };
+  const SlotBuf& b = q.buf;
+  for (int s = 0; s < NSTEP; ++s) out[s] = slot_work(e, q);
+  // --- sloppy CG iteration
+  Work& k1 = out[K1];
+  links(k1, US, lpS, e->nr, 1);
+  k1.in = b.p; k1.out = b.t; k1.a = 1.0; k1.run_if = S_RUNNING;
+  Work& k2 = out[K2];
+  links(k2, US, lpS, e->nr, 0);
+  k2.in = b.t; k2.out = b.q; k2.y1 = b.p; k2.c1 = 1.0; k2.a = -kk;
+  k2.red = 1; k2.fin = FIN_ALPHA; k2.run_if = S_RUNNING;
+  Work& k3 = out[K3];
+  links(k3, US, lpS, e->nr, 1);
+  k3.in = b.q; k3.out = b.t; k3.a = 1.0; k3.run_if = S_RUNNING;
+  Work& k4 = out[K4];
+  links(k4, US, lpS, e->nr, 0);
+  k4.in = b.t; k4.out = b.r; k4.y1 = b.q; k4.a = -kk; k4.z = b.xs; k4.zin = b.p;
+  k4.red = 1; k4.fin = FIN_BETA; k4.run_if = S_RUNNING;
+  Work& k6 = out[K6];
+  k6.in = b.r; k6.out = b.p; k6.run_if = S_RUNNING;
+  // --- FP64 reliable update
+  Work& f = out[RU_FOLD];
+  f.in = b.xs; f.out = b.x64; f.run_if = S_UPDATE;
+  Work& d1 = out[RU_D1];
+  links(d1, U64, P_F64, 18, 1);
+  d1.in = b.x64; d1.out = b.t64; d1.a = 1.0; d1.run_if = S_UPDATE;
+  Work& rs = out[RU_RES];
+  links(rs, U64, P_F64, 18, 0);
+  rs.in = b.t64; rs.out = b.u64; rs.y1 = b.bhat; rs.c1 = 1.0; rs.y2 = b.x64; rs.c2 = -1.0;
+  rs.a = kk; rs.red = 1; rs.fin = FIN_TRUERES; rs.run_if = S_UPDATE;
+  Work& d2 = out[RU_D2];
+  links(d2, U64, P_F64, 18, 1);
+  d2.in = b.u64; d2.out = b.t64; d2.a = 1.0; d2.run_if = S_UPDATE;
+  Work& rh = out[RU_RHO];
+  links(rh, U64, P_F64, 18, 0);
+  rh.in = b.t64; rh.out = b.u64; rh.y1 = b.u64; rh.c1 = 1.0; rh.a = -kk;
+  rh.red = 1; rh.fin = FIN_RHO; rh.run_if = S_UPDATE;
+  Work& cv = out[RU_CONV];
+  cv.in = b.u64; cv.out = b.r; cv.z = b.p; cv.fin = FIN_RESUME; cv.run_if = S_UPDATE;
+}
+
+struct StepKind {
+  bool dslash;
+  bool f64;
+  bool dag;
+  int epi_or_op;
+};
+
+StepKind kind_of(int s) {
+  switch (s) {
+    case K1: return {true, false, false, EPI_LIN};
+    case K2: return {true, false, false, EPI_LIN};
+    case K3: return {true, false, true, EPI_LIN};
+    case K4: return {true, false, true, EPI_CG};
+    case K6: return {false, false, false, B_CG_P};
+    case RU_FOLD: return {false, false, false, B_RU_FOLD};
+    case RU_D1: return {true, true, false, EPI_LIN};
+    case RU_RES: return {true, true, false, EPI_LIN};
+    case RU_D2: return {true, true, true, EPI_LIN};
+    case RU_RHO: return {true, true, true, EPI_LIN};
+    case RU_CONV: return {false, false, false, B_RU_CONVERT};
+  }
+  return {false, false, false, 0};
+}
+
+cudaError_t issue(lqcd_engine* e, int s, const Launch& L) {
+  const StepKind k = kind_of(s);
+  e->ctx->launches++;
+  if (k.dslash) {
+    if (k.f64) return launch_dslash(P_F64, 18, k.dag, k.epi_or_op, L, 0, e->ctx->stream);
+    return launch_dslash(e->sp, e->nr, k.dag, k.epi_or_op, L, 0, e->ctx->stream);
+  }
+  const int prec = (k.epi_or_op == B_RU_FOLD) ? e->xp : e->sp;
+  return launch_blas(prec, k.epi_or_op, L, 0, e->ctx->stream);
+}
+
+Launch batch_launch(const lqcd_engine* e, int s) {
+  Launch L;
+  memset(&L, 0, sizeof L);
+  L.works = e->d_works + (size_t)s * e->max_slots;
+  L.tile_prefix = e->d_prefix;
+  L.nslots = (int)e->active.size();
+  L.ntiles = e->ntiles_total;
+  L.interleave = e->interleave;
+  L.partials = e->d_partials;
+  return L;
+}
+
+cudaError_t issue_iteration_block(lqcd_engine* e, int iters) {
+  for (int it = 0; it < iters; ++it) {
+    for (int s : {K1, K2, K3, K4, K6}) {
+      cudaError_t err = issue(e, s, batch_launch(e, s));
+      if (err != cudaSuccess) return err;
+    }
+    if ((it + 1) % e->ru_every == 0 || it + 1 == iters) {
+      for (int s : {RU_FOLD, RU_D1, RU_RES, RU_D2, RU_RHO, RU_CONV}) {
+        cudaError_t err = issue(e, s, batch_launch(e, s));
+        if (err != cudaSuccess) return err;
+      }
+    }
+  }
+  return cudaSuccess;
+}
+
+int rebuild(lqcd_engine* e) {
+  const int n = (int)e->active.size();
+  e->dirty = false;
+  if (n == 0) return LQCD_OK;
+  // interleave tiles when every slot solves on the same gauge field (multi-RHS):
+  // consecutive tiles then share links, which stream from HBM once per site block
+  const lqcd_gauge* g0 = e->reqs[e->active[0]].gauge;
+  bool same = true;
+  for (long long id : e->active) same = same && e->reqs[id].gauge == g0;
+  e->interleave = (same && n > 1) ? 1 : 0;
+  std::vector<int> prefix(n + 1, 0);
+  e->h_works.assign((size_t)NSTEP * e->max_slots, Work{});
+  for (int i = 0; i < n; ++i) {
+    const Request& q = e->reqs[e->active[i]];
+    Work w[NSTEP];
+    step_works(e, q, w);
+    for (int s = 0; s < NSTEP; ++s) e->h_works[(size_t)s * e->max_slots + i] = w[s];
+    prefix[i + 1] = prefix[i] + q.ntiles;
+  }
+  e->ntiles_total = prefix[n];
+  cudaStream_t st = e->ctx->stream;
+  LQCD_CK(cudaMemcpyAsync(e->d_works, e->h_works.data(), sizeof(Work) * e->h_works.size(),
+                          cudaMemcpyHostToDevice, st));
+  LQCD_CK(cudaMemcpyAsync(e->d_prefix, prefix.data(), sizeof(int) * (n + 1),
+                          cudaMemcpyHostToDevice, st));
+  LQCD_CK(cudaStreamSynchronize(st));  // host vectors are reused
+  if (e->opts.use_graph) {
+    cudaGraph_t graph = nullptr;
+    LQCD_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = issue_iteration_block(e, e->opts.chunk);
+    cudaError_t err2 = cudaStreamEndCapture(st, &graph);
+    if (err != cudaSuccess) return set_error(LQCD_ECUDA, "capture: %s", cudaGetErrorString(err));
+    if (err2 != cudaSuccess) return set_error(LQCD_ECUDA, "end capture: %s", cudaGetErrorString(err2));
+    if (e->exec) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(e->exec, graph, &info) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(e->exec);
+        e->exec = nullptr;
+      }
+    }
+    if (!e->exec) {
+      cudaError_t ie = cudaGraphInstantiate(&e->exec, graph, 0);
+      if (ie != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        e->exec = nullptr;
+        return set_error(LQCD_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+      }
+    }
+    cudaGraphDestroy(graph);
+  }
+  return LQCD_OK;
+}
+
+int ensure_partials(lqcd_engine* e, size_t n) {
+  if (e->partials_cap >= n) return LQCD_OK;
+  LQCD_CK(cudaStreamSynchronize(e->ctx->stream));
+  if (e->d_partials) cudaFree(e->d_partials);
+  e->d_partials = nullptr;
+  size_t cap = std::max(n, 2 * e->partials_cap);
+  LQCD_CK(cudaMalloc(&e->d_partials, cap * sizeof(double)));
+  e->partials_cap = cap;
+  e->dirty = true;
+  return LQCD_OK;
+}
+
+// tile ranges of live requests: first fit over the partials buffer
+int assign_tiles(lqcd_engine* e, Request& q) {
+  std::vector<std::pair<int, int>> used;
+  for (auto& kv : e->reqs)
+    if (kv.second.slot >= 0 && kv.first != q.id) used.push_back({kv.second.tile0, kv.second.ntiles});
+  std::sort(used.begin(), used.end());
+  int pos = 0;
+  for (auto& u : used) {
+    if (u.first - pos >= q.ntiles) break;
+    pos = std::max(pos, u.first + u.second);
+  }
+  q.tile0 = pos;
+  return ensure_partials(e, 3 * ((size_t)pos + q.ntiles));
+}
+
+int alloc_block(lqcd_engine* e, size_t bytes, void** out) {
+  auto it = e->pool.find(bytes);
+  if (it != e->pool.end()) {
+    *out = it->second;
+    e->pool.erase(it);
+    e->bytes_pooled -= bytes;
+    return LQCD_OK;
+  }
+  // free pooled blocks first when the budget would be exceeded
+  while (e->budget && e->bytes_in_use + e->bytes_pooled + bytes > e->budget && !e->pool.empty()) {
+    auto p = e->pool.begin();
+    LQCD_CK(cudaStreamSynchronize(e->ctx->stream));
+    cudaFree(p->second);
+    e->bytes_pooled -= p->first;
+    e->pool.erase(p);
+  }
+  cudaError_t err = cudaMalloc(out, bytes);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(LQCD_ENOMEM, "slot buffers (%zu bytes): %s", bytes, cudaGetErrorString(err));
+  }
+  return LQCD_OK;
+}
+
+// single-slot launches of the finishing steps (after DONE / FAILED)
+int finalize_launch(lqcd_engine* e, Request& q) {
+  const Geom& g = q.g;
+  const void* U64 = q.gauge->copy[P_F64][0];
+  const SlotBuf& b = q.buf;
+  cudaStream_t st = e->ctx->stream;
+  auto lin = [&](int out_par, const void* in, void* out, const void* y1, double c1, const void* y2,
+                 double c2, double a, int fin) -> int {
+    Work w = slot_work(e, q);
+    w.out_par = out_par;
+    w.Uout = parity_links(U64, P_F64, 18, g.Vh, out_par);
+    w.Uin = parity_links(U64, P_F64, 18, g.Vh, 1 - out_par);
+    w.in = in; w.out = out; w.y1 = y1; w.c1 = c1; w.y2 = y2; w.c2 = c2; w.a = a;
+    w.red = fin != FIN_NONE ? 1 : 0; w.fin = fin; w.run_if = -1;
+    Launch L = single_launch(w, e->d_partials);
+    e->ctx->launches++;
+    LQCD_CK(launch_dslash(P_F64, 18, false, EPI_LIN, L, 0, st));
+    return LQCD_OK;
+  };
+  int rc;
+  // x_o = b_o + kappa D_oe x_e
+  if ((rc = lin(1, b.x64, b.t64, b.bo, 1.0, nullptr, 0.0, q.kappa, FIN_NONE))) return rc;
+  // r_e = b_e - x_e + kappa D_eo x_o ; r_o = b_o - x_o + kappa D_oe x_e  (full M, FP64)
+  if ((rc = lin(0, b.t64, b.u64, b.be, 1.0, b.x64, -1.0, q.kappa, FIN_STORE0))) return rc;
+  if ((rc = lin(1, b.x64, b.bhat, b.bo, 1.0, b.t64, -1.0, q.kappa, FIN_STORE1))) return rc;
+  return LQCD_OK;
+}
+
+int status_of(int st) { return st; }  // Scalars::status mirrors the public codes
+
+}  // namespace
+
+extern "C" {
+
+void lqcd_solve_opts_default(lqcd_solve_opts* o) {
+  if (!o) return;
+  o->solver = LQCD_CG;
+  o->sloppy_prec = LQCD_F32;
+  o->sloppy_compress = 12;
+  o->maxiter = 50000;
+  o->delta = 0.0;
+  o->chunk = 32;
+  o->use_graph = 1;
+}
+
+int lqcd_engine_create(lqcd_ctx* c, const lqcd_solve_opts* opts, size_t budget, int max_slots,
+                       lqcd_engine** out) {
+  clear_error();
+  if (!c || !out) return set_error(LQCD_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (max_slots < 1 || max_slots > MAX_SLOTS) return set_error(LQCD_EINVAL, "max_slots %d", max_slots);
+  lqcd_solve_opts o;
+  lqcd_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.solver != LQCD_CG) return set_error(LQCD_EINVAL, "the batched engine runs CG");
+  if (o.sloppy_prec < LQCD_F64 || o.sloppy_prec > LQCD_BF16) return set_error(LQCD_EINVAL, "sloppy precision");
+  if (o.sloppy_compress != 12 && o.sloppy_compress != 18) return set_error(LQCD_EINVAL, "sloppy compress");
+  if (o.maxiter < 1) o.maxiter = 50000;
+  if (o.chunk < 1) o.chunk = 32;
+  LQCD_CK(cudaSetDevice(c->device));
+  lqcd_engine* e = new lqcd_engine();
+  e->ctx = c;
+  e->opts = o;
+  e->sp = o.sloppy_prec;
+  e->xp = (o.sloppy_prec == LQCD_F64) ? P_F64 : P_F32;
+  e->nr = (o.sloppy_prec == LQCD_F64) ? 18 : o.sloppy_compress;
+  const double delta = o.delta > 0 ? o.delta : (o.sloppy_prec == LQCD_F64 ? 0.0 : 0.1);
+  e->delta2 = delta * delta;
+  e->ru_every = std::min(8, o.chunk);
+  e->budget = budget;
+  e->max_slots = max_slots;
+  cudaError_t err = cudaMalloc(&e->d_sc, sizeof(Scalars) * max_slots);
+  if (err == cudaSuccess) err = cudaMemset(e->d_sc, 0, sizeof(Scalars) * max_slots);
+  if (err == cudaSuccess) err = cudaMallocHost(&e->h_sc, sizeof(Scalars) * max_slots);
+  if (err == cudaSuccess) err = cudaMalloc(&e->d_works, sizeof(Work) * NSTEP * max_slots);
+  if (err == cudaSuccess) err = cudaMalloc(&e->d_prefix, sizeof(int) * (max_slots + 1));
+  if (err != cudaSuccess) {
+    lqcd_engine_destroy(e);
+    return set_error(LQCD_ENOMEM, "engine: %s", cudaGetErrorString(err));
+  }
+  for (int i = max_slots - 1; i >= 0; --i) e->free_slots.push_back(i);
+  *out = e;
+  return LQCD_OK;
+}
+
+void lqcd_engine_destroy(lqcd_engine* e) {
+  if (!e) return;
+  cudaSetDevice(e->ctx->device);
+  cudaStreamSynchronize(e->ctx->stream);
+  if (e->exec) cudaGraphExecDestroy(e->exec);
+  for (auto& kv : e->reqs)
+    if (kv.second.buf.block) cudaFree(kv.second.buf.block);
+  for (auto& kv : e->pool) cudaFree(kv.second);
+  if (e->d_sc) cudaFree(e->d_sc);
+  if (e->h_sc) cudaFreeHost(e->h_sc);
+  if (e->d_works) cudaFree(e->d_works);
+  if (e->d_prefix) cudaFree(e->d_prefix);
+  if (e->d_partials) cudaFree(e->d_partials);
+  delete e;
+}
+
+size_t lqcd_engine_request_bytes(const lqcd_engine* e, const int dims[4]) {
+  Geom g;
+  if (!e || make_geom(dims, -1, g) != LQCD_OK) return 0;
+  return slot_bytes(e, g.Vh);
+}
+
+int lqcd_engine_submit(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field* src, double kappa,
+                       double tol, long long* request_id) {
+  clear_error();
+  if (!e || !gauge || !src || !request_id) return set_error(LQCD_EINVAL, "NULL argument");
+  if (src->prec != LQCD_F64 || src->subset != LQCD_FULL)
+    return set_error(LQCD_EINVAL, "source must be a FULL FP64 field");
+  if (memcmp(src->g.L, gauge->g.L, sizeof src->g.L)) return set_error(LQCD_EINVAL, "lattice mismatch");
+  if (!(tol > 0) || !(kappa >= 0)) return set_error(LQCD_EINVAL, "tol must be > 0 and kappa >= 0");
+  if (gauge->ctx != e->ctx || src->ctx != e->ctx) return set_error(LQCD_EINVAL, "context mismatch");
+  lqcd_ctx* c = e->ctx;
+  LQCD_CK(cudaSetDevice(c->device));
+  const size_t need = slot_bytes(e, gauge->g.Vh);
+  if (e->budget && need > e->budget) return set_error(LQCD_ENOMEM, "request needs %zu bytes > budget %zu", need, e->budget);
+  if (e->free_slots.empty()) return set_error(LQCD_EBUSY, "no free slot");
+  if (e->budget && e->bytes_in_use + need > e->budget)
+    return set_error(LQCD_EBUSY, "budget: %zu in use + %zu > %zu", e->bytes_in_use, need, e->budget);
+  // sloppy link copy
+  if (e->sp != P_F64) {
+    int rc = lqcd_gauge_add_copy(const_cast<lqcd_gauge*>(gauge), e->sp, e->nr);
+    if (rc != LQCD_OK) return rc;
+  }
+  Request q;
+  q.id = e->next_id++;
+  q.gauge = gauge;
+  q.g = gauge->g;
+  q.kappa = kappa;
+  q.tol = tol;
+  q.ntiles = (q.g.Vh + TILE - 1) / TILE;
+  q.t0 = std::chrono::steady_clock::now();
+  int rc = alloc_block(e, need, &q.buf.block);
+  if (rc != LQCD_OK) return rc;
+  q.buf.bytes = need;
+  carve(q.buf, e, q.g.Vh);
+  q.slot = e->free_slots.back();
+  e->free_slots.pop_back();
+  e->bytes_in_use += need;
+  e->reqs[q.id] = q;
+  Request& R = e->reqs[q.id];
+  rc = assign_tiles(e, R);
+  cudaStream_t st = c->stream;
+  const size_t hb = half_spinor_bytes(P_F64, q.g.Vh);
+  Scalars* sc = e->d_sc + R.slot;
+  if (rc == LQCD_OK) {
+    cudaError_t err = cudaMemcpyAsync(R.buf.be, src->half[0], hb, cudaMemcpyDeviceToDevice, st);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(R.buf.bo, src->half[1], hb, cudaMemcpyDeviceToDevice, st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(R.buf.x64, 0, hb, st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(R.buf.xs, 0, half_spinor_bytes(e->xp, q.g.Vh), st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(sc, 0, sizeof(Scalars), st);
+    if (err != cudaSuccess) rc = set_error(LQCD_ECUDA, "submit copies: %s", cudaGetErrorString(err));
+  }
+  if (rc == LQCD_OK) {
+    // |b|^2 (both halves) and bhat_e = b_e + kappa D_eo b_o, in FP64
+    Work w = slot_work(e, R);
+    w.red = 1;
+    w.in = R.buf.be;
+    w.fin = FIN_STORE0;
+    cudaError_t err = launch_blas(P_F64, B_NORM, single_launch(w, e->d_partials), 0, st);
+    w.in = R.buf.bo;
+    w.fin = FIN_STORE1;
+    if (err == cudaSuccess) err = launch_blas(P_F64, B_NORM, single_launch(w, e->d_partials), 0, st);
+    if (err == cudaSuccess) {
+      k_slot_init<<<1, 1, 0, st>>>(sc, tol * tol, 24.0 * q.g.Vh, e->opts.maxiter, e->delta2);
+      err = cudaGetLastError();
+    }
+    if (err == cudaSuccess) {
+      Work d = slot_work(e, R);
+      const void* U64 = gauge->copy[P_F64][0];
+      d.out_par = 0;
+      d.Uout = parity_links(U64, P_F64, 18, q.g.Vh, 0);
+      d.Uin = parity_links(U64, P_F64, 18, q.g.Vh, 1);
+      d.in = R.buf.bo;
+      d.out = R.buf.bhat;
+      d.y1 = R.buf.be;
+      d.c1 = 1.0;
+      d.a = kappa;
+      err = launch_dslash(P_F64, 18, false, EPI_LIN, single_launch(d, e->d_partials), 0, st);
+    }
+    if (err == cudaSuccess) {
+      // first true residual and restart (state UPDATE, restart_p = 1)
+      Work w2[NSTEP];
+      step_works(e, R, w2);
+      for (int s : {RU_FOLD, RU_D1, RU_RES, RU_D2, RU_RHO, RU_CONV}) {
+        if (err != cudaSuccess) break;
+        err = issue(e, s, single_launch(w2[s], e->d_partials));
+      }
+    }
+    c->launches += 4;
+    if (err != cudaSuccess) rc = set_error(LQCD_ECUDA, "submit kernels: %s", cudaGetErrorString(err));
+  }
+  if (rc != LQCD_OK) {
+    e->free_slots.push_back(R.slot);
+    e->bytes_in_use -= need;
+    cudaFree(R.buf.block);
+    e->reqs.erase(q.id);
+    return rc;
+  }
+  e->active.push_back(q.id);
+  e->dirty = true;
+  *request_id = q.id;
+  return LQCD_OK;
+}
+
+int lqcd_engine_step(lqcd_engine* e, int* n_active) {
+  clear_error();
+  if (!e) return set_error(LQCD_EINVAL, "engine is NULL");
+  lqcd_ctx* c = e->ctx;
+  LQCD_CK(cudaSetDevice(c->device));
+  cudaStream_t st = c->stream;
+  if (!e->active.empty()) {
+    if (e->dirty) {
+      int rc = rebuild(e);
+      if (rc != LQCD_OK) return rc;
+    }
+    if (e->opts.use_graph) {
+      LQCD_CK(cudaGraphLaunch(e->exec, st));
+      c->launches += (long long)e->opts.chunk * 5 +
+                     ((e->opts.chunk + e->ru_every - 1) / e->ru_every) * 6;
+    } else {
+      cudaError_t err = issue_iteration_block(e, e->opts.chunk);
+      if (err != cudaSuccess) return set_error(LQCD_ECUDA, "iteration: %s", cudaGetErrorString(err));
+    }
+    int maxslot = 0;
+    for (long long id : e->active) maxslot = std::max(maxslot, e->reqs[id].slot + 1);
+    LQCD_CK(cudaMemcpyAsync(e->h_sc, e->d_sc, sizeof(Scalars) * maxslot, cudaMemcpyDeviceToHost, st));
+    LQCD_CK(cudaStreamSynchronize(st));
+    std::vector<long long> fin;
+    for (long long id : e->active) {
+      const Scalars& s = e->h_sc[e->reqs[id].slot];
+      if (s.state == S_DONE || s.state == S_FAILED) fin.push_back(id);
+    }
+    if (!fin.empty()) {
+      for (long long id : fin) {
+        int rc = finalize_launch(e, e->reqs[id]);
+        if (rc != LQCD_OK) return rc;
+      }
+      LQCD_CK(cudaMemcpyAsync(e->h_sc, e->d_sc, sizeof(Scalars) * maxslot, cudaMemcpyDeviceToHost, st));
+      LQCD_CK(cudaStreamSynchronize(st));
+      const auto now = std::chrono::steady_clock::now();
+      for (long long id : fin) {
+        Request& q = e->reqs[id];
+        const Scalars& s = e->h_sc[q.slot];
+        q.finished = true;
+        q.info.status = status_of(s.status);
+        q.info.iters = s.iter;
+        q.info.reliable_updates = s.n_updates;
+        q.info.true_resid = s.res[3] > 0 ? sqrt((s.res[0] + s.res[1]) / s.res[3]) : 0.0;
+        q.info.ms = std::chrono::duration<double, std::milli>(now - q.t0).count();
+        if (q.info.status == LQCD_OK && !(q.info.true_resid <= q.tol)) {
+          // the Schur residual met the tolerance but the full one did not
+          q.info.status = LQCD_ENOCONV;
+        }
+        e->done_ids.push_back(id);
+        e->active.erase(std::find(e->active.begin(), e->active.end(), id));
+      }
+      e->dirty = true;
+    }
+  }
+  if (n_active) *n_active = (int)e->active.size();
+  return LQCD_OK;
+}
+
+int lqcd_engine_completed(lqcd_engine* e, long long* ids, int max, int* n) {
+  clear_error();
+  if (!e || !n || (max > 0 && !ids)) return set_error(LQCD_EINVAL, "NULL argument");
+  int k = 0;
+  while (k < max && k < (int)e->done_ids.size()) {
+    ids[k] = e->done_ids[k];
+    ++k;
+  }
+  e->done_ids.erase(e->done_ids.begin(), e->done_ids.begin() + k);
+  *n = k;
+  return LQCD_OK;
+}
+
+int lqcd_engine_result(lqcd_engine* e, long long id, lqcd_field* x, lqcd_solve_info* info) {
+  clear_error();
+  if (!e) return set_error(LQCD_EINVAL, "engine is NULL");
+  auto it = e->reqs.find(id);
+  if (it == e->reqs.end()) return set_error(LQCD_EINVAL, "unknown request %lld", id);
+  Request& q = it->second;
+  if (!q.finished) return set_error(LQCD_EBUSY, "request %lld still running", id);
+  LQCD_CK(cudaSetDevice(e->ctx->device));
+  if (x) {
+    if (x->subset != LQCD_FULL || memcmp(x->g.L, q.g.L, sizeof q.g.L))
+      return set_error(LQCD_EINVAL, "x must be a FULL field of the request's lattice");
+    LQCD_CK(spinor_convert(q.buf.x64, P_F64, x->half[0], x->prec, q.g.Vh, 1.0, e->ctx->stream));
+    LQCD_CK(spinor_convert(q.buf.t64, P_F64, x->half[1], x->prec, q.g.Vh, 1.0, e->ctx->stream));
+  }
+  if (info) *info = q.info;
+  const int rc = q.info.status;
+  // release the slot
+  LQCD_CK(cudaStreamSynchronize(e->ctx->stream));
+  e->pool.insert({q.buf.bytes, q.buf.block});
+  e->bytes_pooled += q.buf.bytes;
+  e->bytes_in_use -= q.buf.bytes;
+  e->free_slots.push_back(q.slot);
+  e->reqs.erase(it);
+  return rc;
+}
+
+int lqcd_engine_cancel(lqcd_engine* e, long long id, int status) {
+  clear_error();
+  if (!e) return set_error(LQCD_EINVAL, "engine is NULL");
+  auto it = e->reqs.find(id);
+  if (it == e->reqs.end()) return set_error(LQCD_EINVAL, "unknown request %lld", id);
+  if (status >= 0) return set_error(LQCD_EINVAL, "cancel status must be a negative LQCD_E* code");
+  if (it->second.finished) return LQCD_OK;
+  LQCD_CK(cudaSetDevice(e->ctx->device));
+  k_slot_cancel<<<1, 1, 0, e->ctx->stream>>>(e->d_sc + it->second.slot, status);
+  LQCD_CK(cudaGetLastError());
+  return LQCD_OK;
+}
+
+int lqcd_engine_stats(const lqcd_engine* e, int* active, size_t* bytes) {
+  if (!e) return set_error(LQCD_EINVAL, "engine is NULL");
+  if (active) *active = (int)e->active.size();
+  if (bytes) *bytes = e->bytes_in_use;
+  return LQCD_OK;
+}
+
+// ------------------------------------------------------------------ one-shot solves
+
+static int run_engine(lqcd_engine* e, int n, const long long* ids, lqcd_field* const* xs,
+                      lqcd_solve_info* infos) {
+  int active = n;
+  while (active > 0) {
+    int rc = lqcd_engine_step(e, &active);
+    if (rc != LQCD_OK) return rc;
+  }
+  int first_bad = LQCD_OK;
+  for (int i = 0; i < n; ++i) {
+    lqcd_solve_info info{};
+    int rc = lqcd_engine_result(e, ids[i], xs[i], &info);
+    if (infos) infos[i] = info;
+    if (rc != LQCD_OK && first_bad == LQCD_OK) first_bad = rc;
+  }
+  return first_bad;
+}
+
+int lqcd_solve_fields(const lqcd_gauge* g, const lqcd_field* src, double kappa, double tol,
+                      const lqcd_solve_opts* opts, lqcd_field* x, lqcd_solve_info* info) {
+  const lqcd_field* s[1] = {src};
+  lqcd_field* xx[1] = {x};
+  return lqcd_solve_multi(g, 1, s, kappa, tol, opts, xx, info);
+}
+
+int lqcd_solve_multi(const lqcd_gauge* g, int n, const lqcd_field* const* srcs, double kappa,
+                     double tol, const lqcd_solve_opts* opts, lqcd_field* const* xs,
+                     lqcd_solve_info* infos) {
+  clear_error();
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!g || n < 1 || n > MAX_SLOTS || !srcs || !xs) return set_error(LQCD_EINVAL, "bad arguments");
+  lqcd_solve_opts o;
+  lqcd_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.solver == LQCD_BICGSTAB) {
+    int first_bad = LQCD_OK;
+    for (int i = 0; i < n; ++i) {
+      lqcd_solve_info inf{};
+      int rc = bicgstab_solve(g, srcs[i], kappa, tol, &o, xs[i], &inf);
+      if (infos) infos[i] = inf;
+      if (rc != LQCD_OK && first_bad == LQCD_OK) first_bad = rc;
+    }
+    return first_bad;
+  }
+  lqcd_engine* e = nullptr;
+  int rc = lqcd_engine_create(g->ctx, &o, 0, n, &e);
+  if (rc != LQCD_OK) return rc;
+  std::vector<long long> ids(n);
+  for (int i = 0; i < n && rc == LQCD_OK; ++i) rc = lqcd_engine_submit(e, g, srcs[i], kappa, tol, &ids[i]);
+  if (rc == LQCD_OK) rc = run_engine(e, n, ids.data(), xs, infos);
+  lqcd_engine_destroy(e);
+  if (infos && rc != LQCD_ECUDA && rc != LQCD_EINVAL) {
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (n == 1) infos[0].ms = ms;
+  }
+  return rc;
+}
+
+int lqcd_solve(const lqcd_gauge* g, const double* host_src, double kappa, double tol,
+               const lqcd_solve_opts* opts, double* host_x, lqcd_solve_info* info) {
+  clear_error();
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!g || !host_src || !host_x) return set_error(LQCD_EINVAL, "NULL argument");
+  lqcd_ctx* c = g->ctx;
+  int dims[4] = {g->g.L[0], g->g.L[1], g->g.L[2], g->g.L[3]};
+  lqcd_field *b = nullptr, *x = nullptr;
+  lqcd_solve_info inf{};
+  int rc = lqcd_field_create(c, dims, LQCD_F64, LQCD_FULL, &b);
+  if (rc == LQCD_OK) rc = lqcd_field_create(c, dims, LQCD_F64, LQCD_FULL, &x);
+  if (rc == LQCD_OK) rc = lqcd_field_upload(b, host_src);
+  int src_rc = rc;
+  if (rc == LQCD_OK) rc = lqcd_solve_fields(g, b, kappa, tol, opts, x, &inf);
+  if (src_rc == LQCD_OK && (rc == LQCD_OK || rc == LQCD_ENOCONV || rc == LQCD_EBREAKDOWN ||
+                            rc == LQCD_ENONFINITE)) {
+    int rc2 = lqcd_field_download(x, host_x);
+    if (rc2 != LQCD_OK) rc = rc2;
+  }
+  lqcd_field_destroy(b);
+  lqcd_field_destroy(x);
+  inf.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = inf;
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,292 @@
+// Storage formats of spinor and link fields in HBM, and their register loads.
+//
+// Half-lattice fields (one checkerboard, Vh = V/2 sites) are structure-of-
+// arrays: the 24 reals of a spinor (4 spin x 3 colour x re/im) or the 18/12
+// reals of a link are split into "chunks" of one vector word, and chunk c of
+// every site is contiguous: word(c, h) = base[c * Vh + h]. A warp therefore
+// reads 32 consecutive words per chunk, fully coalesced.
+//
+//   spinor, 16-byte words : F64 12 x double2, F32 6 x float4, F16/BF16 3 x uint4
+//   link,   widest word that divides the link: F64 9/6 x double2,
+//           F32 9 x float2 (18 reals) or 3 x float4 (12 reals),
+//           F16 9 x half2 (18 reals) or 3 x 4 halves (12 reals)
+//
+// Links are stored per parity and direction: link(p, mu) occupies
+// NR * Vh reals starting at base_p + mu * NR * Vh. RECONSTRUCT TWELVE (the
+// paper's Section 3 cites it as the next memory optimisation) keeps rows 0
+// and 1 and rebuilds row 2 = conj(row0 x row1) in registers, exact for
+// det U = 1.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lqcd {
+
+enum Prec { P_F64 = 0, P_F32 = 1, P_F16 = 2, P_BF16 = 3 };
+
+__host__ __device__ inline int prec_bytes(int p) { return p == P_F64 ? 8 : (p == P_F32 ? 4 : 2); }
+
+template <typename T>
+struct Cx {
+  T re, im;
+};
+
+template <typename T>
+__device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T>
+__device__ __forceinline__ Cx<T> cmulc(Cx<T> a, Cx<T> b) {  // conj(a) * b
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+
+// ------------------------------------------------------------------ raw loads
+// Read-only data is loaded through the non-coherent path. Links are read
+// exactly once per half-lattice sweep, so they bypass L1 allocation.
+
+__device__ __forceinline__ double2 ld_ro(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ float4 ld_ro(const float4* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ld_ro(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ uint4 ld_ro(const uint4* p) { return __ldg(p); }
+__device__ __forceinline__ uint2 ld_ro(const uint2* p) { return __ldg(p); }
+__device__ __forceinline__ unsigned ld_ro(const unsigned* p) { return __ldg(p); }
+
+__device__ __forceinline__ double2 ld_stream(const double2* p) {
+  double2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float2 ld_stream(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0,%1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint4 ld_stream(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_stream(const uint2* p) {
+  uint2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ unsigned ld_stream(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
+// half2 / bfloat162 packed in a 32-bit word
+__device__ __forceinline__ float2 unpack_h2(unsigned w) {
+  __half2 h = *reinterpret_cast<__half2*>(&w);
+  return __half22float2(h);
+}
+__device__ __forceinline__ float2 unpack_b2(unsigned w) {
+  __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&w);
+  return __bfloat1622float2(h);
+}
+__device__ __forceinline__ unsigned pack_h2(float a, float b) {
+  __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<unsigned*>(&h);
+}
+__device__ __forceinline__ unsigned pack_b2(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<unsigned*>(&h);
+}
+
+// ------------------------------------------------------------------ spinors
+
+template <int P>
+struct SpinorIO;
+
+template <>
+struct SpinorIO<P_F64> {
+  using Real = double;
+  static constexpr int CHUNKS = 12;
+  __device__ static void load(const void* base, int Vh, int h, double v[24]) {
+    const double2* p = reinterpret_cast<const double2*>(base) + h;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      double2 d = ld_ro(p + (size_t)c * Vh);
+      v[2 * c] = d.x;
+      v[2 * c + 1] = d.y;
+    }
+  }
+  __device__ static void store(void* base, int Vh, int h, const double v[24]) {
+    double2* p = reinterpret_cast<double2*>(base) + h;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) p[(size_t)c * Vh] = make_double2(v[2 * c], v[2 * c + 1]);
+  }
+};
+
+template <>
+struct SpinorIO<P_F32> {
+  using Real = float;
+  static constexpr int CHUNKS = 6;
+  __device__ static void load(const void* base, int Vh, int h, float v[24]) {
+    const float4* p = reinterpret_cast<const float4*>(base) + h;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      float4 d = ld_ro(p + (size_t)c * Vh);
+      v[4 * c] = d.x;
+      v[4 * c + 1] = d.y;
+      v[4 * c + 2] = d.z;
+      v[4 * c + 3] = d.w;
+    }
+  }
+  __device__ static void store(void* base, int Vh, int h, const float v[24]) {
+    float4* p = reinterpret_cast<float4*>(base) + h;
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+      p[(size_t)c * Vh] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+  }
+};
+
+template <bool BF>
+struct SpinorIO16 {
+  using Real = float;
+  static constexpr int CHUNKS = 3;
+  __device__ static float2 unpack(unsigned w) { return BF ? unpack_b2(w) : unpack_h2(w); }
+  __device__ static unsigned pack(float a, float b) { return BF ? pack_b2(a, b) : pack_h2(a, b); }
+  __device__ static void load(const void* base, int Vh, int h, float v[24]) {
+    const uint4* p = reinterpret_cast<const uint4*>(base) + h;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      uint4 d = ld_ro(p + (size_t)c * Vh);
+      float2 a = unpack(d.x), b = unpack(d.y), e = unpack(d.z), f = unpack(d.w);
+      v[8 * c + 0] = a.x; v[8 * c + 1] = a.y; v[8 * c + 2] = b.x; v[8 * c + 3] = b.y;
+      v[8 * c + 4] = e.x; v[8 * c + 5] = e.y; v[8 * c + 6] = f.x; v[8 * c + 7] = f.y;
+    }
+  }
+  __device__ static void store(void* base, int Vh, int h, const float v[24]) {
+    uint4* p = reinterpret_cast<uint4*>(base) + h;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      uint4 d;
+      d.x = pack(v[8 * c + 0], v[8 * c + 1]);
+      d.y = pack(v[8 * c + 2], v[8 * c + 3]);
+      d.z = pack(v[8 * c + 4], v[8 * c + 5]);
+      d.w = pack(v[8 * c + 6], v[8 * c + 7]);
+      p[(size_t)c * Vh] = d;
+    }
+  }
+};
+template <>
+struct SpinorIO<P_F16> : SpinorIO16<false> {};
+template <>
+struct SpinorIO<P_BF16> : SpinorIO16<true> {};
+
+// ------------------------------------------------------------------ links
+
+// Loads the NR stored reals of link (mu) at half-site h into u[18] (row-major,
+// re/im interleaved) and rebuilds row 2 when NR == 12.
+template <int LP, int NR>
+struct LinkIO;
+
+template <int NR>
+struct LinkIO<P_F64, NR> {
+  using Real = double;
+  __device__ static void load(const void* base_mu, int Vh, int h, double u[18]) {
+    const double2* p = reinterpret_cast<const double2*>(base_mu) + h;
+#pragma unroll
+    for (int c = 0; c < NR / 2; ++c) {
+      double2 d = ld_stream(p + (size_t)c * Vh);
+      u[2 * c] = d.x;
+      u[2 * c + 1] = d.y;
+    }
+  }
+};
+
+template <>
+struct LinkIO<P_F32, 18> {
+  using Real = float;
+  __device__ static void load(const void* base_mu, int Vh, int h, float u[18]) {
+    const float2* p = reinterpret_cast<const float2*>(base_mu) + h;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      float2 d = ld_stream(p + (size_t)c * Vh);
+      u[2 * c] = d.x;
+      u[2 * c + 1] = d.y;
+    }
+  }
+};
+template <>
+struct LinkIO<P_F32, 12> {
+  using Real = float;
+  __device__ static void load(const void* base_mu, int Vh, int h, float u[18]) {
+    const float4* p = reinterpret_cast<const float4*>(base_mu) + h;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float4 d = ld_stream(p + (size_t)c * Vh);
+      u[4 * c] = d.x;
+      u[4 * c + 1] = d.y;
+      u[4 * c + 2] = d.z;
+      u[4 * c + 3] = d.w;
+    }
+  }
+};
+template <>
+struct LinkIO<P_F16, 18> {
+  using Real = float;
+  __device__ static void load(const void* base_mu, int Vh, int h, float u[18]) {
+    const unsigned* p = reinterpret_cast<const unsigned*>(base_mu) + h;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      float2 d = unpack_h2(ld_stream(p + (size_t)c * Vh));
+      u[2 * c] = d.x;
+      u[2 * c + 1] = d.y;
+    }
+  }
+};
+template <>
+struct LinkIO<P_F16, 12> {
+  using Real = float;
+  __device__ static void load(const void* base_mu, int Vh, int h, float u[18]) {
+    const uint2* p = reinterpret_cast<const uint2*>(base_mu) + h;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      uint2 d = ld_stream(p + (size_t)c * Vh);
+      float2 a = unpack_h2(d.x), b = unpack_h2(d.y);
+      u[4 * c] = a.x;
+      u[4 * c + 1] = a.y;
+      u[4 * c + 2] = b.x;
+      u[4 * c + 3] = b.y;
+    }
+  }
+};
+
+// row 2 = conj(row0 x row1)
+template <typename R>
+__device__ __forceinline__ void reconstruct_row2(R u[18]) {
+  const Cx<R> a0{u[0], u[1]}, a1{u[2], u[3]}, a2{u[4], u[5]};
+  const Cx<R> b0{u[6], u[7]}, b1{u[8], u[9]}, b2{u[10], u[11]};
+  // c_k = a_i b_j - a_j b_i ; row2_k = conj(c_k)
+  Cx<R> c0 = cmul(a1, b2), d0 = cmul(a2, b1);
+  Cx<R> c1 = cmul(a2, b0), d1 = cmul(a0, b2);
+  Cx<R> c2 = cmul(a0, b1), d2 = cmul(a1, b0);
+  u[12] = c0.re - d0.re; u[13] = -(c0.im - d0.im);
+  u[14] = c1.re - d1.re; u[15] = -(c1.im - d1.im);
+  u[16] = c2.re - d2.re; u[17] = -(c2.im - d2.im);
+}
+
+template <int LP, int NR>
+__device__ __forceinline__ void load_link(const void* base_mu, int Vh, int h,
+                                          typename LinkIO<LP, NR>::Real u[18]) {
+  LinkIO<LP, NR>::load(base_mu, Vh, h, u);
+  if (NR == 12) reconstruct_row2(u);
+}
+
+// Number of reals stored per link and the word size of each link chunk.
+__host__ __device__ inline int link_reals(int compress) { return compress == 12 ? 12 : 18; }
+
+}  // namespace lqcd

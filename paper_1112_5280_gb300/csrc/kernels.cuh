@@ -1,0 +1,268 @@
+// Batched kernels: even-odd Dslash with fused epilogues, and the fused BLAS of
+// the Krylov solvers. Instantiated per spinor precision in kernels_<prec>.cu.
+#pragma once
+
+#include "batch.cuh"
+
+namespace lqcd {
+
+enum Epi { EPI_LIN = 0, EPI_CG = 1 };
+
+template <typename R>
+__device__ __forceinline__ double site_norm2(const R v[24]) {
+  R s = 0;
+#pragma unroll
+  for (int i = 0; i < 24; ++i) s += v[i] * v[i];
+  return (double)s;
+}
+
+// <a, b> = sum conj(a) b over one site, (re, im)
+template <typename R>
+__device__ __forceinline__ void site_dot(const R a[24], const R b[24], double& re, double& im) {
+  R sr = 0, si = 0;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    sr += a[2 * i] * b[2 * i] + a[2 * i + 1] * b[2 * i + 1];
+    si += a[2 * i] * b[2 * i + 1] - a[2 * i + 1] * b[2 * i];
+  }
+  re = (double)sr;
+  im = (double)si;
+}
+
+// Storage of the sloppy solution accumulator: FP64 for an FP64 solve, else FP32.
+template <int SP>
+struct XSloppy {
+  static constexpr int P = (SP == P_F64) ? P_F64 : P_F32;
+};
+
+// Whole-CTA exit for a single-slot launch whose slot does not run.
+__device__ __forceinline__ bool single_slot_idle(const Launch& L) {
+  return L.nslots == 1 && !slot_runs(work_of(L, 0));
+}
+
+// Batched Dslash: out = a * D_{p,1-p} in + c1 * y1 + c2 * y2      (EPI_LIN)
+//                 r -= alpha (y1 + a * D in); x += alpha p      (EPI_CG, CG step)
+// with the Work's reduction (norm / dots) and scalar finisher per slot.
+template <int SP, int LP, int NR, bool DAG, int EPI>
+__global__ void __launch_bounds__(TILE) k_dslash(const Launch L) {
+  using R = typename SpinorIO<SP>::Real;
+  if (single_slot_idle(L)) return;
+  for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
+    int slot, start;
+    tile_of(L, tile, slot, start);
+    const Work& w = work_of(L, slot);
+    if (!slot_runs(w)) continue;
+    const int h = start + threadIdx.x;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+    if (h < w.g.Vh) {
+      R acc[24];
+      dslash_site<SP, LP, NR, DAG>(w.g, h, w.out_par, w.in, w.Uout, w.Uin, acc);
+      const R a = (R)w.a;
+      if (EPI == EPI_LIN) {
+#pragma unroll
+        for (int i = 0; i < 24; ++i) acc[i] *= a;
+        R y[24];
+        if (w.y1) {
+          SpinorIO<SP>::load(w.y1, w.g.Vh, h, y);
+          const R c = (R)w.c1;
+#pragma unroll
+          for (int i = 0; i < 24; ++i) acc[i] += c * y[i];
+        }
+        if (w.y2) {
+          R y2[24];
+          SpinorIO<SP>::load(w.y2, w.g.Vh, h, y2);
+          const R c = (R)w.c2;
+#pragma unroll
+          for (int i = 0; i < 24; ++i) acc[i] += c * y2[i];
+        }
+        SpinorIO<SP>::store(w.out, w.g.Vh, h, acc);
+        if (w.red == 1) {
+          v0 = site_norm2(acc);
+        } else if (w.red == 2) {
+          R z[24];
+          SpinorIO<SP>::load(w.zin, w.g.Vh, h, z);
+          site_dot(z, acc, v0, v1);
+        } else if (w.red == 3) {  // <out, y1>, |out|^2
+          site_dot(acc, y, v0, v1);
+          v2 = site_norm2(acc);
+        }
+      } else {
+        const R alpha = (R)w.sc->alpha;
+        R y[24], r[24];
+        SpinorIO<SP>::load(w.y1, w.g.Vh, h, y);
+        SpinorIO<SP>::load(w.out, w.g.Vh, h, r);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) r[i] -= alpha * (y[i] + a * acc[i]);
+        SpinorIO<SP>::store(w.out, w.g.Vh, h, r);
+        v0 = site_norm2(r);
+        using XR = typename SpinorIO<XSloppy<SP>::P>::Real;
+        R p[24];
+        XR x[24];
+        SpinorIO<SP>::load(w.zin, w.g.Vh, h, p);
+        SpinorIO<XSloppy<SP>::P>::load(w.z, w.g.Vh, h, x);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) x[i] += (XR)alpha * (XR)p[i];
+        SpinorIO<XSloppy<SP>::P>::store(w.z, w.g.Vh, h, x);
+      }
+    }
+    tile_finish(w, start / TILE, v0, v1, v2, L.partials);
+  }
+}
+
+// ------------------------------------------------------------------ fused BLAS
+
+enum Blas {
+  B_CG_P = 0,     // p(out) = r(in) + beta p
+  B_RU_FOLD,      // x64(out) += sigma * xs(in) ; xs = 0          (SP = precision of xs)
+  B_RU_CONVERT,   // r(out) = rho64(in) * res[5] ; p(z) = restart ? r : r + res[4] p
+  B_NORM,         // |in|^2
+  B_AXPBY,        // out(SP) = a * in(FP64) + c1 * y1(SP)
+  B_ZERO,         // out = 0
+  B_BICG_P,       // p(out) = r(in) + beta (p - omega v(y1))
+  B_BICG_S,       // s(out) = r(in) - alpha v(y1)
+  B_BICG_X,       // x(z) += alpha p(zin) + omega s(in) ; r(out) = s - omega t(y1) ; <r0(y2), r>, |r|^2
+  B_FOLD64,       // x64(out) += a * xs(in) (SP) ; xs = 0
+};
+
+template <int P>
+__device__ __forceinline__ void load_d(const void* base, int Vh, int h, double v[24]) {
+  typename SpinorIO<P>::Real t[24];
+  SpinorIO<P>::load(base, Vh, h, t);
+#pragma unroll
+  for (int i = 0; i < 24; ++i) v[i] = (double)t[i];
+}
+template <int P>
+__device__ __forceinline__ void store_d(void* base, int Vh, int h, const double v[24]) {
+  typename SpinorIO<P>::Real t[24];
+#pragma unroll
+  for (int i = 0; i < 24; ++i) t[i] = (typename SpinorIO<P>::Real)v[i];
+  SpinorIO<P>::store(base, Vh, h, t);
+}
+
+// out = x + c * y (complex c)
+template <typename R>
+__device__ __forceinline__ void caxpy(R* out, const R* x, R cr, R ci, const R* y) {
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    const R yr = y[2 * i], yi = y[2 * i + 1];
+    out[2 * i] = x[2 * i] + cr * yr - ci * yi;
+    out[2 * i + 1] = x[2 * i + 1] + cr * yi + ci * yr;
+  }
+}
+
+template <int SP, int OP>
+__global__ void __launch_bounds__(TILE) k_blas(const Launch L) {
+  using R = typename SpinorIO<SP>::Real;
+  if (single_slot_idle(L)) return;
+  for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
+    int slot, start;
+    tile_of(L, tile, slot, start);
+    const Work& w = work_of(L, slot);
+    if (!slot_runs(w)) continue;
+    const int h = start + threadIdx.x;
+    const int Vh = w.g.Vh;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+    if (h < Vh) {
+      if (OP == B_CG_P) {
+        const R beta = (R)w.sc->beta;
+        R r[24], p[24];
+        SpinorIO<SP>::load(w.in, Vh, h, r);
+        SpinorIO<SP>::load(w.out, Vh, h, p);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) p[i] = r[i] + beta * p[i];
+        SpinorIO<SP>::store(w.out, Vh, h, p);
+      } else if (OP == B_RU_FOLD || OP == B_FOLD64) {
+        const double sg = (OP == B_RU_FOLD) ? w.sc->sigma : w.a;
+        double x[24], xs[24];
+        load_d<P_F64>(w.out, Vh, h, x);
+        load_d<SP>(w.in, Vh, h, xs);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) {
+          x[i] += sg * xs[i];
+          xs[i] = 0.0;
+        }
+        store_d<P_F64>(w.out, Vh, h, x);
+        store_d<SP>(const_cast<void*>(w.in), Vh, h, xs);
+      } else if (OP == B_RU_CONVERT) {
+        const double inv = w.sc->res[5], pc = w.sc->res[4];
+        const int restart = w.sc->restart_p;
+        double rho[24];
+        load_d<P_F64>(w.in, Vh, h, rho);
+        R r[24];
+#pragma unroll
+        for (int i = 0; i < 24; ++i) r[i] = (R)(rho[i] * inv);
+        SpinorIO<SP>::store(w.out, Vh, h, r);
+        R p[24];
+        if (restart) {
+#pragma unroll
+          for (int i = 0; i < 24; ++i) p[i] = r[i];
+        } else {
+          SpinorIO<SP>::load(w.z, Vh, h, p);
+#pragma unroll
+          for (int i = 0; i < 24; ++i) p[i] = r[i] + (R)pc * p[i];
+        }
+        SpinorIO<SP>::store(w.z, Vh, h, p);
+      } else if (OP == B_NORM) {
+        R v[24];
+        SpinorIO<SP>::load(w.in, Vh, h, v);
+        v0 = site_norm2(v);
+      } else if (OP == B_AXPBY) {
+        double v[24];
+        load_d<P_F64>(w.in, Vh, h, v);
+        const double a = w.a;
+        if (w.y1) {
+          double y[24];
+          load_d<SP>(w.y1, Vh, h, y);
+#pragma unroll
+          for (int i = 0; i < 24; ++i) v[i] = a * v[i] + w.c1 * y[i];
+        } else {
+#pragma unroll
+          for (int i = 0; i < 24; ++i) v[i] = a * v[i];
+        }
+        store_d<SP>(w.out, Vh, h, v);
+        if (w.red == 1) v0 = site_norm2(v);
+      } else if (OP == B_ZERO) {
+        R v[24];
+#pragma unroll
+        for (int i = 0; i < 24; ++i) v[i] = 0;
+        SpinorIO<SP>::store(w.out, Vh, h, v);
+      } else if (OP == B_BICG_P) {
+        const R br = (R)w.sc->cres[6], bi = (R)w.sc->cres[7];
+        const R omr = (R)w.sc->cres[4], omi = (R)w.sc->cres[5];
+        R r[24], p[24], v[24], t[24];
+        SpinorIO<SP>::load(w.in, Vh, h, r);
+        SpinorIO<SP>::load(w.out, Vh, h, p);
+        SpinorIO<SP>::load(w.y1, Vh, h, v);
+        caxpy(t, p, -omr, -omi, v);  // p - omega v
+        caxpy(p, r, br, bi, t);      // r + beta (p - omega v)
+        SpinorIO<SP>::store(w.out, Vh, h, p);
+      } else if (OP == B_BICG_S) {
+        const R ar = (R)w.sc->cres[2], ai = (R)w.sc->cres[3];
+        R r[24], v[24], s[24];
+        SpinorIO<SP>::load(w.in, Vh, h, r);
+        SpinorIO<SP>::load(w.y1, Vh, h, v);
+        caxpy(s, r, -ar, -ai, v);
+        SpinorIO<SP>::store(w.out, Vh, h, s);
+      } else if (OP == B_BICG_X) {
+        const R ar = (R)w.sc->cres[2], ai = (R)w.sc->cres[3];
+        const R omr = (R)w.sc->cres[4], omi = (R)w.sc->cres[5];
+        R s[24], t[24], p[24], x[24], r[24], r0[24];
+        SpinorIO<SP>::load(w.in, Vh, h, s);
+        SpinorIO<SP>::load(w.y1, Vh, h, t);
+        SpinorIO<SP>::load(w.zin, Vh, h, p);
+        SpinorIO<SP>::load(w.z, Vh, h, x);
+        caxpy(x, x, ar, ai, p);
+        caxpy(x, x, omr, omi, s);
+        SpinorIO<SP>::store(w.z, Vh, h, x);
+        caxpy(r, s, -omr, -omi, t);
+        SpinorIO<SP>::store(w.out, Vh, h, r);
+        SpinorIO<SP>::load(w.y2, Vh, h, r0);
+        site_dot(r0, r, v0, v1);
+        v2 = site_norm2(r);
+      }
+    }
+    tile_finish(w, start / TILE, v0, v1, v2, L.partials);
+  }
+}
+
+}  // namespace lqcd

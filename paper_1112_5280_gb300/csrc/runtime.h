@@ -1,0 +1,80 @@
+// Host-side objects behind the C ABI handles.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <string>
+
+#include "lqcd.h"
+#include "launch.h"
+
+struct lqcd_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;      // stream all work is issued on
+  cudaStream_t own_stream = nullptr;  // created by the context
+  double* partials = nullptr;         // reduction partials of one-off launches
+  size_t partials_cap = 0;            // in doubles
+  lqcd::Scalars* scratch_sc = nullptr;  // scalar blocks for one-off reductions
+  lqcd::Scalars* host_sc = nullptr;     // pinned mirror
+  void* tmp = nullptr;                // operator temporaries (odd half fields)
+  size_t tmp_bytes = 0;
+  double* staging = nullptr;          // host-layout FP64 staging on the device
+  size_t staging_bytes = 0;
+  long long launches = 0;
+};
+
+struct lqcd_gauge {
+  lqcd_ctx* ctx = nullptr;
+  lqcd::Geom g{};
+  int prec = 0;
+  int compress = 18;
+  void* copy[4][2] = {};  // [link precision][compress == 12]
+  size_t bytes = 0;
+};
+
+struct lqcd_field {
+  lqcd_ctx* ctx = nullptr;
+  lqcd::Geom g{};
+  int prec = 0;
+  int subset = LQCD_FULL;
+  void* half[2] = {nullptr, nullptr};
+  size_t half_bytes = 0;
+};
+
+namespace lqcd {
+
+int set_error(int code, const char* fmt, ...);
+void clear_error();
+
+#define LQCD_CK(call)                                                                     \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return ::lqcd::set_error(LQCD_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+int make_geom(const int dims[4], int t_bc, Geom& g);
+size_t half_spinor_bytes(int prec, int Vh);
+size_t gauge_copy_bytes(int prec, int nr, int Vh);
+
+// device buffers of the context, grown on demand (synchronises when growing)
+int ctx_partials(lqcd_ctx* c, size_t n);
+int ctx_tmp(lqcd_ctx* c, size_t bytes);
+int ctx_staging(lqcd_ctx* c, size_t bytes);
+
+// link copy for fields of precision field_prec (created on first use)
+int gauge_links(const lqcd_gauge* g, int field_prec, const void** base, int* nr);
+inline const void* parity_links(const void* base, int lp, int nr, int Vh, int par) {
+  return static_cast<const char*>(base) + (size_t)par * gauge_copy_bytes(lp, nr, Vh) / 2;
+}
+
+// BiCGStab on Mhat (bicgstab.cu)
+int bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kappa, double tol,
+                   const lqcd_solve_opts* opts, lqcd_field* x, lqcd_solve_info* info);
+
+// a single-slot launch description
+Launch single_launch(const Work& w, double* partials);
+Work blank_work(const Geom& g);
+
+}  // namespace lqcd

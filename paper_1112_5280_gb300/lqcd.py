@@ -1,0 +1,409 @@
+"""ctypes binding of liblqcd.so (include/lqcd.h). Argument marshalling only:
+every step of the computation runs in the library's CUDA kernels.
+
+Host arrays use the library's host layout (complex128):
+  links  [V, 4, 3, 3]   spinors [V, 4, 3],   site = x + Lx*(y + Ly*(z + Lz*t)).
+Device arrays may be torch tensors (complex128 / float64, same layout); their
+data pointers are passed to the *_dev entry points.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ENOCONV, EBREAKDOWN, ENONFINITE, ETIMEOUT, ECUDA, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7, -8
+F64, F32, F16, BF16 = 0, 1, 2, 3
+EVEN, ODD, FULL = 0, 1, 2
+CG, BICGSTAB = 0, 1
+
+PRECISIONS = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
+
+
+class LqcdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lqcd error {code}: {msg}")
+        self.code = code
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("solver", C.c_int), ("sloppy_prec", C.c_int), ("sloppy_compress", C.c_int),
+                ("maxiter", C.c_int), ("delta", C.c_double), ("chunk", C.c_int),
+                ("use_graph", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("reliable_updates", C.c_int),
+                ("pad", C.c_int), ("true_resid", C.c_double), ("ms", C.c_double)]
+
+    def as_dict(self):
+        return {"status": self.status, "iters": self.iters,
+                "reliable_updates": self.reliable_updates, "true_resid": self.true_resid,
+                "ms": self.ms}
+
+
+_lib = None
+_VP = C.c_void_p
+_IP = C.POINTER(C.c_int)
+
+
+def _sig(lib, name, res, args):
+    f = getattr(lib, name)
+    f.restype = res
+    f.argtypes = args
+
+
+def load(build_if_missing: bool = True):
+    """Load the library; builds it first when it is missing or stale and nvcc exists."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"liblqcd.so not built ({_build.LIB}); run __graft_entry__.build()")
+    lib = C.CDLL(_build.LIB)
+    i, d, sz, ll = C.c_int, C.c_double, C.c_size_t, C.c_longlong
+    _sig(lib, "lqcd_status_string", C.c_char_p, [i])
+    _sig(lib, "lqcd_last_error", C.c_char_p, [])
+    _sig(lib, "lqcd_version", C.c_char_p, [])
+    _sig(lib, "lqcd_ctx_create", i, [C.POINTER(_VP), i, _VP])
+    _sig(lib, "lqcd_ctx_destroy", None, [_VP])
+    _sig(lib, "lqcd_ctx_set_stream", i, [_VP, _VP])
+    _sig(lib, "lqcd_ctx_stream", _VP, [_VP])
+    _sig(lib, "lqcd_ctx_sync", i, [_VP])
+    _sig(lib, "lqcd_ctx_launch_count", ll, [_VP])
+    _sig(lib, "lqcd_set_grid_multiplier", None, [i, i])
+    _sig(lib, "lqcd_gauge_upload", i, [_VP, _IP, _VP, i, i, i, C.POINTER(_VP)])
+    _sig(lib, "lqcd_gauge_upload_dev", i, [_VP, _IP, _VP, i, i, i, C.POINTER(_VP)])
+    _sig(lib, "lqcd_gauge_add_copy", i, [_VP, i, i])
+    _sig(lib, "lqcd_gauge_bytes", sz, [_VP])
+    _sig(lib, "lqcd_gauge_destroy", None, [_VP])
+    _sig(lib, "lqcd_field_create", i, [_VP, _IP, i, i, C.POINTER(_VP)])
+    _sig(lib, "lqcd_field_upload", i, [_VP, _VP])
+    _sig(lib, "lqcd_field_download", i, [_VP, _VP])
+    _sig(lib, "lqcd_field_upload_dev", i, [_VP, _VP])
+    _sig(lib, "lqcd_field_download_dev", i, [_VP, _VP])
+    _sig(lib, "lqcd_field_copy", i, [_VP, _VP, d])
+    _sig(lib, "lqcd_field_norm2", i, [_VP, C.POINTER(d)])
+    _sig(lib, "lqcd_field_zero", i, [_VP])
+    _sig(lib, "lqcd_field_bytes", sz, [_VP])
+    _sig(lib, "lqcd_field_destroy", None, [_VP])
+    _sig(lib, "lqcd_dslash_eo", i, [_VP, _VP, _VP, i, i])
+    _sig(lib, "lqcd_apply_Mhat", i, [_VP, d, _VP, _VP, i])
+    _sig(lib, "lqcd_apply_M", i, [_VP, d, _VP, _VP, i])
+    if hasattr(lib, "lqcd_solve"):
+        _sig(lib, "lqcd_solve_opts_default", None, [C.POINTER(SolveOpts)])
+        _sig(lib, "lqcd_solve", i, [_VP, _VP, d, d, C.POINTER(SolveOpts), _VP, C.POINTER(SolveInfo)])
+        _sig(lib, "lqcd_solve_fields", i, [_VP, _VP, d, d, C.POINTER(SolveOpts), _VP,
+                                           C.POINTER(SolveInfo)])
+        _sig(lib, "lqcd_solve_multi", i, [_VP, i, C.POINTER(_VP), d, d, C.POINTER(SolveOpts),
+                                          C.POINTER(_VP), C.POINTER(SolveInfo)])
+        _sig(lib, "lqcd_engine_create", i, [_VP, C.POINTER(SolveOpts), sz, i, C.POINTER(_VP)])
+        _sig(lib, "lqcd_engine_request_bytes", sz, [_VP, _IP])
+        _sig(lib, "lqcd_engine_submit", i, [_VP, _VP, _VP, d, d, C.POINTER(ll)])
+        _sig(lib, "lqcd_engine_step", i, [_VP, _IP])
+        _sig(lib, "lqcd_engine_completed", i, [_VP, C.POINTER(ll), i, _IP])
+        _sig(lib, "lqcd_engine_result", i, [_VP, ll, _VP, C.POINTER(SolveInfo)])
+        _sig(lib, "lqcd_engine_cancel", i, [_VP, ll, i])
+        _sig(lib, "lqcd_engine_stats", i, [_VP, _IP, C.POINTER(sz)])
+        _sig(lib, "lqcd_engine_destroy", None, [_VP])
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != OK:
+        lib = load()
+        raise LqcdError(rc, f"{lib.lqcd_status_string(rc).decode()}: {lib.lqcd_last_error().decode()}")
+    return rc
+
+
+def _dims(dims):
+    return (C.c_int * 4)(*[int(d) for d in dims])
+
+
+def _prec(p):
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def _host_array(a, shape):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    if a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))
+
+
+class Context:
+    """A device + stream binding (lqcd_ctx)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._lib = load()
+        h = _VP()
+        _check(self._lib.lqcd_ctx_create(C.byref(h), int(device), _stream_handle(stream)))
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            self._lib.lqcd_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        _check(self._lib.lqcd_ctx_set_stream(self.h, _stream_handle(stream)))
+
+    @property
+    def stream(self):
+        return self._lib.lqcd_ctx_stream(self.h)
+
+    def sync(self):
+        _check(self._lib.lqcd_ctx_sync(self.h))
+
+    @property
+    def launches(self) -> int:
+        return int(self._lib.lqcd_ctx_launch_count(self.h))
+
+    def gauge(self, dims, U, prec="f64", compress=18, t_bc=-1):
+        return Gauge(self, dims, U, prec, compress, t_bc)
+
+    def field(self, dims, prec="f64", subset=FULL, data=None):
+        f = Field(self, dims, prec, subset)
+        if data is not None:
+            f.upload(data)
+        return f
+
+
+class Gauge:
+    """SU(3) gauge field resident on the device (lqcd_gauge)."""
+
+    def __init__(self, ctx: Context, dims, U, prec="f64", compress=18, t_bc=-1):
+        self.ctx, self.dims, self.t_bc = ctx, tuple(int(d) for d in dims), t_bc
+        self._lib = ctx._lib
+        V = int(np.prod(self.dims))
+        h = _VP()
+        if hasattr(U, "data_ptr"):  # device tensor in the host layout
+            if not U.is_cuda or not U.is_contiguous() or U.numel() * U.element_size() != V * 4 * 9 * 16:
+                raise ValueError("device gauge tensor must be contiguous [V,4,3,3] complex128")
+            _check(self._lib.lqcd_gauge_upload_dev(ctx.h, _dims(dims), U.data_ptr(), _prec(prec),
+                                                   int(compress), int(t_bc), C.byref(h)))
+        else:
+            U = _host_array(U, (V, 4, 3, 3))
+            _check(self._lib.lqcd_gauge_upload(ctx.h, _dims(dims), U.ctypes.data, _prec(prec),
+                                               int(compress), int(t_bc), C.byref(h)))
+        self.h = h
+
+    def add_copy(self, prec, compress):
+        _check(self._lib.lqcd_gauge_add_copy(self.h, _prec(prec), int(compress)))
+
+    @property
+    def nbytes(self) -> int:
+        return int(self._lib.lqcd_gauge_bytes(self.h))
+
+    def close(self):
+        if self.h:
+            self._lib.lqcd_gauge_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Field:
+    """Spinor field on the device (lqcd_field): EVEN, ODD or FULL subset."""
+
+    def __init__(self, ctx: Context, dims, prec="f64", subset=FULL):
+        self.ctx, self.dims, self.prec, self.subset = ctx, tuple(int(d) for d in dims), _prec(prec), subset
+        self._lib = ctx._lib
+        self.V = int(np.prod(self.dims))
+        h = _VP()
+        _check(self._lib.lqcd_field_create(ctx.h, _dims(dims), self.prec, int(subset), C.byref(h)))
+        self.h = h
+
+    def upload(self, psi):
+        if hasattr(psi, "data_ptr"):
+            if not psi.is_cuda or not psi.is_contiguous() or psi.numel() * psi.element_size() != self.V * 12 * 16:
+                raise ValueError("device spinor tensor must be contiguous [V,4,3] complex128")
+            _check(self._lib.lqcd_field_upload_dev(self.h, psi.data_ptr()))
+        else:
+            psi = _host_array(psi, (self.V, 4, 3))
+            _check(self._lib.lqcd_field_upload(self.h, psi.ctypes.data))
+        return self
+
+    def download(self, out=None):
+        if out is not None and hasattr(out, "data_ptr"):
+            _check(self._lib.lqcd_field_download_dev(self.h, out.data_ptr()))
+            return out
+        if out is None:
+            out = np.zeros((self.V, 4, 3), dtype=np.complex128)
+        _check(self._lib.lqcd_field_download(self.h, out.ctypes.data))
+        return out
+
+    def copy_from(self, src: "Field", scale=1.0):
+        _check(self._lib.lqcd_field_copy(self.h, src.h, float(scale)))
+
+    def norm2(self) -> float:
+        v = C.c_double()
+        _check(self._lib.lqcd_field_norm2(self.h, C.byref(v)))
+        return v.value
+
+    def zero(self):
+        _check(self._lib.lqcd_field_zero(self.h))
+
+    @property
+    def nbytes(self) -> int:
+        return int(self._lib.lqcd_field_bytes(self.h))
+
+    def close(self):
+        if self.h:
+            self._lib.lqcd_field_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dslash_eo(gauge: Gauge, fin: Field, fout: Field, out_parity: int, dagger=False):
+    _check(gauge._lib.lqcd_dslash_eo(gauge.h, fin.h, fout.h, int(out_parity), int(bool(dagger))))
+
+
+def apply_Mhat(gauge: Gauge, kappa: float, fin: Field, fout: Field, dagger=False):
+    _check(gauge._lib.lqcd_apply_Mhat(gauge.h, float(kappa), fin.h, fout.h, int(bool(dagger))))
+
+
+def apply_M(gauge: Gauge, kappa: float, fin: Field, fout: Field, dagger=False):
+    _check(gauge._lib.lqcd_apply_M(gauge.h, float(kappa), fin.h, fout.h, int(bool(dagger))))
+
+
+def set_grid_multiplier(family: int, mult: int):
+    load().lqcd_set_grid_multiplier(int(family), int(mult))
+
+
+def solve_opts(**kw) -> SolveOpts:
+    o = SolveOpts()
+    load().lqcd_solve_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if k in ("sloppy_prec",):
+            v = _prec(v)
+        setattr(o, k, v)
+    return o
+
+
+def solve(gauge: Gauge, src, kappa, tol=1e-10, opts: SolveOpts | None = None):
+    """Host solve: src full-lattice numpy spinor; returns (x, info dict)."""
+    V = int(np.prod(gauge.dims))
+    src = _host_array(src, (V, 4, 3))
+    x = np.zeros_like(src)
+    info = SolveInfo()
+    o = opts if opts is not None else solve_opts()
+    rc = gauge._lib.lqcd_solve(gauge.h, src.ctypes.data, float(kappa), float(tol), C.byref(o),
+                               x.ctypes.data, C.byref(info))
+    if rc not in (OK, ENOCONV, EBREAKDOWN, ENONFINITE):
+        _check(rc)
+    return x, info.as_dict()
+
+
+def solve_fields(gauge: Gauge, src: Field, kappa, tol, x: Field, opts: SolveOpts | None = None):
+    info = SolveInfo()
+    o = opts if opts is not None else solve_opts()
+    rc = gauge._lib.lqcd_solve_fields(gauge.h, src.h, float(kappa), float(tol), C.byref(o), x.h,
+                                      C.byref(info))
+    if rc not in (OK, ENOCONV, EBREAKDOWN, ENONFINITE):
+        _check(rc)
+    return info.as_dict()
+
+
+def solve_multi(gauge: Gauge, srcs, kappa, tol, xs, opts: SolveOpts | None = None):
+    n = len(srcs)
+    sp = (_VP * n)(*[s.h for s in srcs])
+    xp = (_VP * n)(*[x.h for x in xs])
+    infos = (SolveInfo * n)()
+    o = opts if opts is not None else solve_opts()
+    rc = gauge._lib.lqcd_solve_multi(gauge.h, n, sp, float(kappa), float(tol), C.byref(o), xp, infos)
+    if rc not in (OK, ENOCONV, EBREAKDOWN, ENONFINITE):
+        _check(rc)
+    return [infos[i].as_dict() for i in range(n)]
+
+
+class Engine:
+    """Batched Krylov engine (lqcd_engine): many solves advance in the same launches."""
+
+    def __init__(self, ctx: Context, opts: SolveOpts | None = None, hbm_budget=0, max_slots=64):
+        self._lib = ctx._lib
+        self.ctx = ctx
+        h = _VP()
+        o = opts if opts is not None else solve_opts()
+        _check(self._lib.lqcd_engine_create(ctx.h, C.byref(o), C.c_size_t(int(hbm_budget)),
+                                            int(max_slots), C.byref(h)))
+        self.h = h
+
+    def request_bytes(self, dims) -> int:
+        return int(self._lib.lqcd_engine_request_bytes(self.h, _dims(dims)))
+
+    def submit(self, gauge: Gauge, src: Field, kappa, tol):
+        """Returns a request id, or None when the engine is busy (retry later)."""
+        rid = C.c_longlong()
+        rc = self._lib.lqcd_engine_submit(self.h, gauge.h, src.h, float(kappa), float(tol),
+                                          C.byref(rid))
+        if rc == EBUSY:
+            return None
+        _check(rc)
+        return rid.value
+
+    def step(self) -> int:
+        n = C.c_int()
+        _check(self._lib.lqcd_engine_step(self.h, C.byref(n)))
+        return n.value
+
+    def completed(self, max_ids=1024):
+        ids = (C.c_longlong * max_ids)()
+        n = C.c_int()
+        _check(self._lib.lqcd_engine_completed(self.h, ids, max_ids, C.byref(n)))
+        return [ids[i] for i in range(n.value)]
+
+    def result(self, rid, x: Field):
+        info = SolveInfo()
+        _check(self._lib.lqcd_engine_result(self.h, C.c_longlong(rid), x.h, C.byref(info)))
+        return info.as_dict()
+
+    def cancel(self, rid, status=ETIMEOUT):
+        _check(self._lib.lqcd_engine_cancel(self.h, C.c_longlong(rid), int(status)))
+
+    def stats(self):
+        a = C.c_int()
+        b = C.c_size_t()
+        _check(self._lib.lqcd_engine_stats(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def close(self):
+        if self.h:
+            self._lib.lqcd_engine_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,181 @@
+"""GPU parity of the even-odd Wilson Dslash, Mhat and M against the FP64 oracle.
+
+Paper Section 3: the even-odd preconditioned hopping term "dslash" is the hot
+kernel. Every precision / compression / dagger / parity combination is
+compared element by element with the oracle on the same seeded inputs.
+Tolerance (max |gpu - oracle| / max |oracle|): FP64 1e-12, FP32 1e-5 (the
+stated bars); FP16 4e-3 and BF16 3e-2, derived from the unit roundoff of the
+storage (2^-11, 2^-8) times the ~8-term sums per output component.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1112_5280_gb300 import lqcd, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "f16": 4e-3, "bf16": 3e-2}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = lqcd.Context(0)
+    yield c
+    c.close()
+
+
+def _rel_err(a, b, mask=None):
+    if mask is not None:
+        a, b = a[mask], b[mask]
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def _par(dims, p):
+    return synth.parity_of_sites(dims) == p
+
+
+# ragged: Vh = 720 -> 5.6 tiles of 128; 2^4: coinciding neighbours; 4^4: small workload
+LATTICES = [(6, 6, 4, 10), (2, 2, 2, 2), (4, 4, 4, 4), (2, 4, 6, 4)]
+
+
+@pytest.mark.parametrize("dims", LATTICES)
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("compress", [18, 12])
+def test_dslash_eo_parity(ctx, dims, prec, compress):
+    U = synth.random_links(dims, 0.5, seed=1001)
+    psi = synth.gaussian_spinor(dims, seed=2002)
+    g = ctx.gauge(dims, U, prec=prec, compress=compress, t_bc=-1)
+    fin = ctx.field(dims, prec, lqcd.FULL, data=psi)
+    for p in (0, 1):
+        for dag in (False, True):
+            fout = ctx.field(dims, prec, p)
+            lqcd.dslash_eo(g, fin, fout, p, dagger=dag)
+            got = fout.download()
+            ref = oracle.hop_eo(dims, U, psi, p, dagger=dag)
+            err = _rel_err(got, ref, _par(dims, p))
+            assert err < TOL[prec], (prec, compress, p, dag, err)
+
+
+@pytest.mark.parametrize("t_bc", [1, -1])
+def test_dslash_boundary_conditions(ctx, t_bc):
+    dims = (4, 2, 2, 6)
+    U = synth.random_links(dims, 0.8, seed=5)
+    psi = synth.gaussian_spinor(dims, seed=6)
+    g = ctx.gauge(dims, U, prec="f64", t_bc=t_bc)
+    fin = ctx.field(dims, "f64", lqcd.FULL, data=psi)
+    fout = ctx.field(dims, "f64", lqcd.FULL)
+    for p in (0, 1):
+        lqcd.dslash_eo(g, fin, fout, p)
+    got = fout.download()
+    ref = oracle.hop(dims, U, psi, t_bc=t_bc)
+    assert _rel_err(got, ref) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_apply_M_and_Mhat(ctx, prec):
+    dims = (6, 4, 4, 6)
+    kappa = 0.15
+    U = synth.random_links(dims, 0.5, seed=11)
+    psi = synth.gaussian_spinor(dims, seed=12)
+    g = ctx.gauge(dims, U, prec=prec, compress=12)
+    fin = ctx.field(dims, prec, lqcd.FULL, data=psi)
+    fout = ctx.field(dims, prec, lqcd.FULL)
+    for dag in (False, True):
+        lqcd.apply_M(g, kappa, fin, fout, dagger=dag)
+        assert _rel_err(fout.download(), oracle.apply_M(dims, U, kappa, psi, dagger=dag)) < TOL[prec]
+        fe = ctx.field(dims, prec, lqcd.EVEN, data=psi)
+        fo = ctx.field(dims, prec, lqcd.EVEN)
+        lqcd.apply_Mhat(g, kappa, fe, fo, dagger=dag)
+        psi_e = psi * _par(dims, 0)[:, None, None]
+        ref = oracle.apply_Mhat(dims, U, kappa, psi_e, dagger=dag)
+        assert _rel_err(fo.download(), ref, _par(dims, 0)) < TOL[prec]
+
+
+def test_kappa_zero_is_identity(ctx):
+    dims = (4, 4, 2, 2)
+    U = synth.random_links(dims, 0.5, seed=3)
+    psi = synth.gaussian_spinor(dims, seed=4)
+    g = ctx.gauge(dims, U, prec="f64")
+    fin = ctx.field(dims, "f64", lqcd.FULL, data=psi)
+    fout = ctx.field(dims, "f64", lqcd.FULL)
+    lqcd.apply_M(g, 0.0, fin, fout)
+    assert np.array_equal(fout.download(), psi)
+
+
+def test_gauge_covariance_on_gpu(ctx):
+    """M[U^g](g psi) = g M[U] psi evaluated entirely on the GPU (FP64)."""
+    from oracle import dense
+    dims = (4, 4, 4, 6)
+    U = synth.random_links(dims, 0.5, seed=31)
+    gt = synth.gauge_transform_field(dims, seed=32)
+    psi = synth.gaussian_spinor(dims, seed=33)
+    kappa = 0.14
+    outs = []
+    for links, src in ((U, psi), (dense.gauge_transform_links(dims, U, gt),
+                                  dense.gauge_transform_spinor(gt, psi))):
+        g = ctx.gauge(dims, links, prec="f64")
+        fin = ctx.field(dims, "f64", lqcd.FULL, data=src)
+        fout = ctx.field(dims, "f64", lqcd.FULL)
+        lqcd.apply_M(g, kappa, fin, fout)
+        outs.append(fout.download())
+    assert _rel_err(outs[1], dense.gauge_transform_spinor(gt, outs[0])) < 1e-12
+
+
+def test_norm_copy_and_device_io(ctx):
+    import torch
+    dims = (4, 2, 4, 4)
+    psi = synth.gaussian_spinor(dims, seed=9)
+    f64 = ctx.field(dims, "f64", lqcd.FULL, data=psi)
+    assert abs(f64.norm2() - np.vdot(psi, psi).real) < 1e-10 * np.vdot(psi, psi).real
+    f32 = ctx.field(dims, "f32", lqcd.FULL)
+    f32.copy_from(f64, 2.0)
+    assert _rel_err(f32.download(), 2 * psi) < 1e-6
+    t = torch.from_numpy(psi).cuda()
+    fd = ctx.field(dims, "f64", lqcd.FULL)
+    fd.upload(t)
+    out = torch.zeros_like(t)
+    fd.download(out)
+    ctx.sync()
+    assert np.array_equal(out.cpu().numpy(), psi)
+
+
+def test_half_field_download_leaves_other_parity(ctx):
+    dims = (4, 4, 2, 2)
+    psi = synth.gaussian_spinor(dims, seed=19)
+    f = ctx.field(dims, "f64", lqcd.ODD, data=psi)
+    host = np.full_like(psi, 7.0 + 1j)
+    f.download(host)
+    odd = _par(dims, 1)
+    assert np.array_equal(host[odd], psi[odd])
+    assert np.all(host[~odd] == 7.0 + 1j)
+
+
+def test_invalid_arguments_fail_loudly(ctx):
+    with pytest.raises(lqcd.LqcdError):
+        ctx.field((3, 4, 4, 4), "f64")
+    dims = (4, 4, 4, 4)
+    g = ctx.gauge(dims, synth.unit_links(dims), prec="f64")
+    fe = ctx.field(dims, "f64", lqcd.EVEN)
+    fo = ctx.field(dims, "f64", lqcd.EVEN)
+    with pytest.raises(lqcd.LqcdError):
+        lqcd.dslash_eo(g, fe, fo, 0)  # input must hold the odd parity
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+def test_dslash_sampled_sites_16x32(ctx, prec):
+    """Benchmark workload shape (16^3 x 32, eps = 0.5): sampled output sites vs the oracle."""
+    dims = (16, 16, 16, 32)
+    U = synth.random_links(dims, 0.5, seed=1001)
+    psi = synth.gaussian_spinor(dims, seed=2002)
+    g = ctx.gauge(dims, U, prec=prec, compress=18 if prec != "f16" else 12)
+    fin = ctx.field(dims, prec, lqcd.FULL, data=psi)
+    fout = ctx.field(dims, prec, lqcd.FULL)
+    for p in (0, 1):
+        lqcd.dslash_eo(g, fin, fout, p)
+    got = fout.download()
+    rng = np.random.default_rng(5)
+    sites = np.concatenate([rng.integers(0, synth.volume(dims), 3000),
+                            [0, synth.volume(dims) - 1]])
+    ref = oracle.hop_sites(dims, U, psi, sites)
+    assert _rel_err(got[sites], ref) < TOL[prec]

@@ -1,0 +1,207 @@
+"""GPU solves (CG on Mhat^dag Mhat with FP64 reliable updates, BiCGStab on Mhat) vs the oracle.
+
+Paper Section 3: the inversion of the even-odd preconditioned fermion matrix is
+the dominant cost. Bars: every GPU solution has ||b - M x|| <= tol ||b|| with
+the full operator, measured by the FP64 oracle on the returned x; and agrees
+with the oracle's own solution within C * tol (C = 100 covers the condition
+numbers of these workloads, checked against the oracle's iterate).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import dense
+from paper_1112_5280_gb300 import lqcd, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = lqcd.Context(0)
+    yield c
+    c.close()
+
+
+def _solve_check(ctx, dims, eps, kappa, prec, compress=12, solver=lqcd.CG, tol=1e-10,
+                 seed_u=1001, seed_b=2002, xtol=1e-8):
+    U = synth.random_links(dims, eps, seed=seed_u)
+    b = synth.gaussian_spinor(dims, seed=seed_b)
+    g = ctx.gauge(dims, U, prec="f64")
+    opts = lqcd.solve_opts(sloppy_prec=prec, sloppy_compress=compress, solver=solver)
+    x, info = lqcd.solve(g, b, kappa, tol, opts)
+    assert info["status"] == 0, info
+    assert info["true_resid"] <= tol, info
+    res = oracle.true_residual(dims, U, kappa, b, x)
+    assert res <= tol, (res, info)
+    xo, st, _, _ = oracle.solve(dims, U, kappa, b, tol=tol * 1e-2, method=oracle.METHOD_CG_EO)
+    assert st == 0
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < xtol
+    return x, info
+
+
+def test_cg_fp64_small_workload(ctx):
+    """4^4, kappa 0.12, eps 0.3: plain FP64 CG on the GPU."""
+    _solve_check(ctx, (4, 4, 4, 4), 0.3, 0.12, "f64", compress=18)
+
+
+@pytest.mark.parametrize("prec,compress", [("f32", 18), ("f32", 12), ("f16", 12), ("bf16", 12),
+                                           ("f16", 18)])
+def test_cg_mixed_precision(ctx, prec, compress):
+    """Mixed precision with FP64 reliable updates reaches 1e-10 on a ragged lattice."""
+    _solve_check(ctx, (6, 4, 4, 6), 0.5, 0.15, prec, compress)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_bicgstab(ctx, prec):
+    _solve_check(ctx, (6, 4, 4, 6), 0.5, 0.15, prec, 12, solver=lqcd.BICGSTAB)
+    _solve_check(ctx, (4, 4, 4, 4), 0.3, 0.12, prec, 18, solver=lqcd.BICGSTAB)
+
+
+def test_free_field_fft(ctx):
+    """U = 1 on 8^3 x 16: the GPU solution equals the exact Fourier solution."""
+    dims = (8, 8, 8, 16)
+    kappa = 0.124
+    b = synth.gaussian_spinor(dims, seed=61)
+    g = ctx.gauge(dims, synth.unit_links(dims), prec="f64")
+    x, info = lqcd.solve(g, b, kappa, 1e-11, lqcd.solve_opts(sloppy_prec="f16"))
+    assert info["status"] == 0
+    xf = dense.free_solve_fft(dims, kappa, b)
+    assert np.linalg.norm(x - xf) / np.linalg.norm(xf) < 1e-9
+
+
+def test_solve_gauge_covariance(ctx):
+    dims = (4, 4, 4, 6)
+    U = synth.random_links(dims, 0.5, seed=71)
+    gt = synth.gauge_transform_field(dims, seed=72)
+    b = synth.gaussian_spinor(dims, seed=73)
+    opts = lqcd.solve_opts(sloppy_prec="f32")
+    x1, i1 = lqcd.solve(ctx.gauge(dims, U), b, 0.13, 1e-11, opts)
+    x2, i2 = lqcd.solve(ctx.gauge(dims, dense.gauge_transform_links(dims, U, gt)),
+                        dense.gauge_transform_spinor(gt, b), 0.13, 1e-11, opts)
+    ref = dense.gauge_transform_spinor(gt, x1)
+    assert i1["status"] == 0 and i2["status"] == 0
+    assert np.linalg.norm(x2 - ref) / np.linalg.norm(ref) < 1e-9
+
+
+def _point_sources(dims, site):
+    return [synth.point_source(dims, site, s, c) for s in range(4) for c in range(3)]
+
+
+def test_multi_rhs_point_sources_match_single(ctx):
+    """12 point sources (spin x colour) solved together equal the same solves one by one,
+    bit for bit (reductions depend only on each slot's own geometry)."""
+    dims = (4, 4, 4, 8)
+    U = synth.random_links(dims, 0.5, seed=81)
+    site = synth.point_site(dims)
+    srcs_h = _point_sources(dims, site)
+    g = ctx.gauge(dims, U, prec="f64")
+    opts = lqcd.solve_opts(sloppy_prec="f32")
+    srcs = [ctx.field(dims, "f64", lqcd.FULL, data=s) for s in srcs_h]
+    xs = [ctx.field(dims, "f64", lqcd.FULL) for _ in srcs_h]
+    infos = lqcd.solve_multi(g, srcs, 0.15, 1e-10, xs, opts)
+    for k, (inf, s, xf) in enumerate(zip(infos, srcs_h, xs)):
+        assert inf["status"] == 0 and inf["true_resid"] <= 1e-10, (k, inf)
+        x = xf.download()
+        assert oracle.true_residual(dims, U, 0.15, s, x) <= 1e-10
+        if k in (0, 7):
+            x1 = ctx.field(dims, "f64", lqcd.FULL)
+            lqcd.solve_fields(g, srcs[k], 0.15, 1e-10, x1, opts)
+            assert np.array_equal(x1.download(), x), k
+
+
+def test_engine_uneven_lattices_same_alone_and_in_mix(ctx):
+    """Several lattices of different sizes and kappas in one engine: each result equals its
+    solo solve bit for bit."""
+    cases = [((4, 4, 4, 4), 0.12, 11), ((6, 4, 4, 6), 0.15, 12), ((4, 4, 2, 8), 0.14, 13),
+             ((8, 4, 4, 4), 0.155, 14)]
+    opts = lqcd.solve_opts(sloppy_prec="f16")
+    eng = lqcd.Engine(ctx, opts, max_slots=8)
+    items = []
+    for dims, kappa, seed in cases:
+        U = synth.random_links(dims, 0.5, seed=seed)
+        b = synth.gaussian_spinor(dims, seed=seed + 100)
+        g = ctx.gauge(dims, U, prec="f64")
+        src = ctx.field(dims, "f64", lqcd.FULL, data=b)
+        rid = eng.submit(g, src, kappa, 1e-10)
+        items.append((rid, dims, kappa, U, b, g, src))
+    while eng.step() > 0:
+        pass
+    done = set(eng.completed())
+    assert done == {it[0] for it in items}
+    for rid, dims, kappa, U, b, g, src in items:
+        x = ctx.field(dims, "f64", lqcd.FULL)
+        info = eng.result(rid, x)
+        assert info["status"] == 0 and info["true_resid"] <= 1e-10
+        xm = x.download()
+        assert oracle.true_residual(dims, U, kappa, b, xm) <= 1e-10
+        xs = ctx.field(dims, "f64", lqcd.FULL)
+        lqcd.solve_fields(g, src, kappa, 1e-10, xs, opts)
+        assert np.array_equal(xs.download(), xm)
+    eng.close()
+
+
+def test_nonconvergence_reports_status(ctx):
+    dims = (4, 4, 4, 4)
+    U = synth.random_links(dims, 0.5, seed=3)
+    b = synth.gaussian_spinor(dims, seed=4)
+    g = ctx.gauge(dims, U)
+    x, info = lqcd.solve(g, b, 0.15, 1e-10, lqcd.solve_opts(sloppy_prec="f32", maxiter=5))
+    assert info["status"] == lqcd.ENOCONV
+    assert info["iters"] >= 5 and info["true_resid"] > 1e-10
+
+
+def test_nan_source_reports_nonfinite(ctx):
+    dims = (4, 4, 4, 4)
+    g = ctx.gauge(dims, synth.random_links(dims, 0.3, seed=5))
+    b = synth.gaussian_spinor(dims, seed=6)
+    b[17, 2, 1] = np.nan
+    x, info = lqcd.solve(g, b, 0.12, 1e-10, lqcd.solve_opts(sloppy_prec="f32"))
+    assert info["status"] == lqcd.ENONFINITE
+
+
+def test_zero_source(ctx):
+    dims = (4, 4, 4, 4)
+    g = ctx.gauge(dims, synth.random_links(dims, 0.3, seed=5))
+    x, info = lqcd.solve(g, np.zeros((256, 4, 3), complex), 0.12, 1e-10)
+    assert info["status"] == 0 and np.all(x == 0)
+
+
+def test_engine_budget_and_cancel(ctx):
+    dims = (4, 4, 4, 4)
+    g = ctx.gauge(dims, synth.random_links(dims, 0.3, seed=7))
+    src = ctx.field(dims, "f64", lqcd.FULL, data=synth.gaussian_spinor(dims, seed=8))
+    probe = lqcd.Engine(ctx, lqcd.solve_opts(sloppy_prec="f32"))
+    need = probe.request_bytes(dims)
+    probe.close()
+    tiny = lqcd.Engine(ctx, lqcd.solve_opts(sloppy_prec="f32"), hbm_budget=need // 2)
+    with pytest.raises(lqcd.LqcdError) as e:
+        tiny.submit(g, src, 0.12, 1e-10)
+    assert e.value.code == lqcd.ENOMEM
+    tiny.close()
+    one = lqcd.Engine(ctx, lqcd.solve_opts(sloppy_prec="f32"), hbm_budget=need + need // 2)
+    r1 = one.submit(g, src, 0.12, 1e-10)
+    assert r1 is not None
+    assert one.submit(g, src, 0.12, 1e-10) is None  # busy: budget holds one request
+    one.cancel(r1, lqcd.ETIMEOUT)
+    one.step()
+    assert one.completed() == [r1]
+    x = ctx.field(dims, "f64", lqcd.FULL)
+    with pytest.raises(lqcd.LqcdError) as e:
+        one.result(r1, x)
+    assert e.value.code == lqcd.ETIMEOUT
+    assert one.submit(g, src, 0.12, 1e-10) is not None  # slot and budget freed
+    one.close()
+
+
+@pytest.mark.slow
+def test_near_critical_16x32_mixed_f16(ctx):
+    """16^3 x 32, kappa 0.155, eps 0.8 (the ill-conditioned workload at reduced volume):
+    FP16 sloppy CG with FP64 reliable updates reaches 1e-10 (oracle-measured residual)."""
+    dims = (16, 16, 16, 32)
+    U = synth.random_links(dims, 0.8)
+    b = synth.gaussian_spinor(dims)
+    g = ctx.gauge(dims, U, prec="f64")
+    x, info = lqcd.solve(g, b, 0.155, 1e-10, lqcd.solve_opts(sloppy_prec="f16", sloppy_compress=12))
+    assert info["status"] == 0, info
+    assert oracle.true_residual(dims, U, 0.155, b, x) <= 1e-10
