@@ -81,8 +81,11 @@ LQCD_API const char* lqcd_version(void);
 
 /* ---------------------------------------------------------------- context */
 
-/* Binds CUDA device `device`. cuda_stream: a cudaStream_t borrowed for the
- * context's lifetime, or NULL to create an owned non-blocking stream. */
+/* Binds CUDA device `device`. cuda_stream: a cudaStream_t borrowed by the
+ * context (it must stay valid until the context and every object made from it
+ * are destroyed), or NULL to create an owned non-blocking stream.
+ * lqcd_ctx_destroy releases the handle; the context's device resources are
+ * freed once its last gauge field, spinor field and engine are destroyed too. */
 LQCD_API int lqcd_ctx_create(lqcd_ctx** out, int device, void* cuda_stream);
 LQCD_API void lqcd_ctx_destroy(lqcd_ctx* ctx);
 /* Replaces the stream (borrowed; NULL restores the owned stream). */

@@ -180,6 +180,17 @@ int lqcd_ctx_create(lqcd_ctx** out, int device, void* stream) {
 
 void lqcd_ctx_destroy(lqcd_ctx* c) {
   if (!c) return;
+  ctx_release(c);
+}
+
+}  // extern "C"
+
+namespace lqcd {
+
+void ctx_retain(lqcd_ctx* c) { c->refs.fetch_add(1); }
+
+void ctx_release(lqcd_ctx* c) {
+  if (c->refs.fetch_sub(1) != 1) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->partials) cudaFree(c->partials);
@@ -190,6 +201,10 @@ void lqcd_ctx_destroy(lqcd_ctx* c) {
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
 }
+
+}  // namespace lqcd
+
+extern "C" {
 
 int lqcd_ctx_set_stream(lqcd_ctx* c, void* stream) {
   clear_error();
@@ -235,6 +250,7 @@ static int gauge_upload_impl(lqcd_ctx* c, const int dims[4], const double* U, bo
   }
   lqcd_gauge* gg = new lqcd_gauge();
   gg->ctx = c;
+  ctx_retain(c);
   gg->g = g;
   gg->prec = prec;
   gg->compress = compress;
@@ -303,7 +319,9 @@ void lqcd_gauge_destroy(lqcd_gauge* g) {
   for (auto& row : g->copy)
     for (auto& p : row)
       if (p) cudaFree(p);
+  lqcd_ctx* c = g->ctx;
   delete g;
+  ctx_release(c);
 }
 
 // ------------------------------------------------------------------ fields
@@ -319,6 +337,7 @@ int lqcd_field_create(lqcd_ctx* c, const int dims[4], int prec, int subset, lqcd
   LQCD_TRY(ctx_set_device(c));
   lqcd_field* f = new lqcd_field();
   f->ctx = c;
+  ctx_retain(c);
   f->g = g;
   f->prec = prec;
   f->subset = subset;
@@ -346,7 +365,9 @@ void lqcd_field_destroy(lqcd_field* f) {
   cudaStreamSynchronize(f->ctx->stream);
   for (auto& p : f->half)
     if (p) cudaFree(p);
+  lqcd_ctx* c = f->ctx;
   delete f;
+  ctx_release(c);
 }
 
 static int field_upload_impl(lqcd_field* f, const double* psi, bool dev) {

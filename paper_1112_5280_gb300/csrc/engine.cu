@@ -434,6 +434,7 @@ int lqcd_engine_create(lqcd_ctx* c, const lqcd_solve_opts* opts, size_t budget, 
   LQCD_CK(cudaSetDevice(c->device));
   lqcd_engine* e = new lqcd_engine();
   e->ctx = c;
+  ctx_retain(c);
   e->opts = o;
   e->sp = o.sloppy_prec;
   e->xp = (o.sloppy_prec == LQCD_F64) ? P_F64 : P_F32;
@@ -470,7 +471,9 @@ void lqcd_engine_destroy(lqcd_engine* e) {
   if (e->d_works) cudaFree(e->d_works);
   if (e->d_prefix) cudaFree(e->d_prefix);
   if (e->d_partials) cudaFree(e->d_partials);
+  lqcd_ctx* c = e->ctx;
   delete e;
+  ctx_release(c);
 }
 
 size_t lqcd_engine_request_bytes(const lqcd_engine* e, const int dims[4]) {

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <string>
 
@@ -22,6 +23,10 @@ struct lqcd_ctx {
   double* staging = nullptr;          // host-layout FP64 staging on the device
   size_t staging_bytes = 0;
   long long launches = 0;
+  // The context handle and every gauge, field and engine made from it hold one
+  // reference; lqcd_ctx_destroy drops the handle's and the context is freed
+  // when the last object goes, so objects may outlive the handle.
+  std::atomic<int> refs{1};
 };
 
 struct lqcd_gauge {
@@ -45,6 +50,8 @@ struct lqcd_field {
 namespace lqcd {
 
 int set_error(int code, const char* fmt, ...);
+void ctx_retain(lqcd_ctx* c);
+void ctx_release(lqcd_ctx* c);
 void clear_error();
 
 #define LQCD_CK(call)                                                                     \

@@ -154,6 +154,7 @@ class Context:
         _check(self._lib.lqcd_ctx_create(C.byref(h), int(device), _stream_handle(stream)))
         self.h = h
         self.device = device
+        self._stream = stream  # a borrowed stream must outlive the context's objects
 
     def close(self):
         if self.h:

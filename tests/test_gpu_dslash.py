@@ -179,3 +179,20 @@ def test_dslash_sampled_sites_16x32(ctx, prec):
                             [0, synth.volume(dims) - 1]])
     ref = oracle.hop_sites(dims, U, psi, sites)
     assert _rel_err(got[sites], ref) < TOL[prec]
+
+
+def test_objects_outlive_context_handle():
+    """Destroying the context handle first is safe: its fields and gauge keep it alive."""
+    c = lqcd.Context(0)
+    dims = (4, 4, 4, 4)
+    psi = synth.gaussian_spinor(dims, seed=1)
+    g = c.gauge(dims, synth.random_links(dims, 0.3, seed=2), prec="f64")
+    f = c.field(dims, "f64", lqcd.FULL, data=psi)
+    o = c.field(dims, "f64", lqcd.FULL)
+    c.close()
+    for p in (0, 1):
+        lqcd.dslash_eo(g, f, o, p)
+    assert np.abs(o.download() - oracle.hop(dims, synth.random_links(dims, 0.3, seed=2), psi)).max() < 1e-12 * 100
+    f.close()
+    o.close()
+    g.close()
