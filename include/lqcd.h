@@ -151,6 +151,28 @@ LQCD_API int lqcd_apply_Mhat(const lqcd_gauge* g, double kappa, const lqcd_field
 LQCD_API int lqcd_apply_M(const lqcd_gauge* g, double kappa, const lqcd_field* in, lqcd_field* out,
                  int dagger);
 
+/* Mhat exactly as lqcd_apply_Mhat, for callers that cannot let the library
+ * allocate device memory: applications whose device memory belongs to their
+ * own pool (a caching allocator such as PyTorch's, or a fixed-budget arena),
+ * where a library cudaMalloc can fail while the pool still holds free blocks,
+ * and latency-sensitive callers that cannot accept the device-wide
+ * synchronisation of cudaMalloc / cudaFree. The paper has no counterpart; this
+ * is an interface addition of the library.
+ * The odd-parity temporary lives in a fixed 16 MiB device array that is part of
+ * the library image (every GPU that loads the library holds it until the process
+ * exits). Lattices whose half spinor exceeds it (FP32 beyond V/2 = 174762 sites,
+ * FP64 beyond V/2 = 87381) are rejected with LQCD_EINVAL, and so is a gauge field
+ * without a resident link copy for the fields' precision (make one first with
+ * lqcd_gauge_add_copy). The call never calls cudaMalloc, cudaFree or an allocating
+ * routine. Its first call on a device looks the array's device address up with
+ * cudaGetSymbolAddress while that device is current; make that first call before
+ * any stream capture. Every call uses the same array: calls whose GPU work can
+ * overlap (different streams or contexts on one device without ordering between
+ * them) race on it. The temporary is fully written before it is read, so a call
+ * never sees what an earlier call left there. */
+LQCD_API int lqcd_apply_Mhat_noalloc(const lqcd_gauge* g, double kappa, const lqcd_field* in,
+                                     lqcd_field* out, int dagger);
+
 /* ---------------------------------------------------------------- solvers (A6-A9) */
 
 typedef struct lqcd_solve_opts {

@@ -95,6 +95,8 @@ def load(build_if_missing: bool = True):
     _sig(lib, "lqcd_dslash_eo", i, [_VP, _VP, _VP, i, i])
     _sig(lib, "lqcd_apply_Mhat", i, [_VP, d, _VP, _VP, i])
     _sig(lib, "lqcd_apply_M", i, [_VP, d, _VP, _VP, i])
+    if hasattr(lib, "lqcd_apply_Mhat_noalloc"):
+        _sig(lib, "lqcd_apply_Mhat_noalloc", i, [_VP, d, _VP, _VP, i])
     if hasattr(lib, "lqcd_solve"):
         _sig(lib, "lqcd_solve_opts_default", None, [C.POINTER(SolveOpts)])
         _sig(lib, "lqcd_solve", i, [_VP, _VP, d, d, C.POINTER(SolveOpts), _VP, C.POINTER(SolveInfo)])
@@ -292,6 +294,13 @@ def dslash_eo(gauge: Gauge, fin: Field, fout: Field, out_parity: int, dagger=Fal
 
 def apply_Mhat(gauge: Gauge, kappa: float, fin: Field, fout: Field, dagger=False):
     _check(gauge._lib.lqcd_apply_Mhat(gauge.h, float(kappa), fin.h, fout.h, int(bool(dagger))))
+
+
+def apply_Mhat_noalloc(gauge: Gauge, kappa: float, fin: Field, fout: Field, dagger=False):
+    """Mhat without any device allocation by the library (fixed 16 MiB built-in
+    scratch for the odd temporary; see include/lqcd.h for the limits)."""
+    _check(gauge._lib.lqcd_apply_Mhat_noalloc(gauge.h, float(kappa), fin.h, fout.h,
+                                              int(bool(dagger))))
 
 
 def apply_M(gauge: Gauge, kappa: float, fin: Field, fout: Field, dagger=False):
