@@ -72,6 +72,7 @@ typedef struct lqcd_ctx lqcd_ctx;
 typedef struct lqcd_gauge lqcd_gauge;
 typedef struct lqcd_field lqcd_field;
 typedef struct lqcd_engine lqcd_engine;
+typedef struct lqcd_dslash_batch lqcd_dslash_batch;
 
 LQCD_API const char* lqcd_status_string(int status);
 /* Message of the last failing call on this host thread ("" if none). */
@@ -143,6 +144,18 @@ LQCD_API void lqcd_field_destroy(lqcd_field* f);
  * (with the gauge's compression) is used. Asynchronous on the context stream. */
 LQCD_API int lqcd_dslash_eo(const lqcd_gauge* g, const lqcd_field* in, lqcd_field* out, int out_parity,
                    int dagger);
+/* A reusable batch of n independent applications out_i = D_{p,1-p} in_i (as
+ * lqcd_dslash_eo), each with its own gauge field and lattice size, all fields of
+ * one precision and one context, executed in a single kernel launch by
+ * lqcd_dslash_batch_apply. Small lattices leave most of the GPU idle in a launch of
+ * their own; batching fills it. The gauges and fields are borrowed and must
+ * outlive the batch. Creation uploads the batch description (synchronous); apply
+ * is asynchronous on the context stream and allocates nothing. */
+LQCD_API int lqcd_dslash_batch_create(int n, const lqcd_gauge* const* g,
+                                      const lqcd_field* const* in, lqcd_field* const* out,
+                                      int out_parity, int dagger, lqcd_dslash_batch** batch);
+LQCD_API int lqcd_dslash_batch_apply(lqcd_dslash_batch* batch);
+LQCD_API void lqcd_dslash_batch_destroy(lqcd_dslash_batch* batch);
 /* out_e = in_e - kappa^2 D_eo D_oe in_e (or Mhat^dag = g5 Mhat g5 when dagger).
  * in and out hold the even parity (EVEN or FULL); uses an odd temporary of the context. */
 LQCD_API int lqcd_apply_Mhat(const lqcd_gauge* g, double kappa, const lqcd_field* in, lqcd_field* out,

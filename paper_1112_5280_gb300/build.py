@@ -80,13 +80,17 @@ if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True, ptxas_verbose="--ptxas" in sys.argv))
 
 
-def source_hash() -> str:
-    """Hash of the library sources (ties profile counters to the code they were taken on)."""
+# Files that define the Dslash kernel and its launch (a change to any of them
+# invalidates profile counters taken on the old code).
+DSLASH_KERNEL_FILES = ("field.cuh", "dslash.cuh", "batch.cuh", "kernels.cuh", "kernels_inst.cuh",
+                       "kernels_f32.cu", "kernels_f16.cu", "kernels_f64.cu", "launch.h", "layout.cu")
+
+
+def source_hash(files=DSLASH_KERNEL_FILES) -> str:
+    """Hash of kernel sources (ties profile counters to the code they were taken on)."""
     import hashlib
     h = hashlib.sha256()
-    for p in sorted(_deps()):
-        if p.endswith("build.py"):
-            continue
-        h.update(os.path.basename(p).encode())
-        h.update(open(p, "rb").read())
+    for name in sorted(files):
+        h.update(name.encode())
+        h.update(open(os.path.join(CSRC, name), "rb").read())
     return h.hexdigest()[:16]

@@ -15,7 +15,10 @@
 
 namespace lqcd {
 
-constexpr int TILE = 128;         // sites per tile = threads per CTA of batched kernels
+#ifndef LQCD_TILE
+#define LQCD_TILE 64
+#endif
+constexpr int TILE = LQCD_TILE;   // sites per tile (one tile per CTA pass of a batched kernel)
 constexpr int MAX_SLOTS = 1024;   // slots in one launch
 
 // Slot state machine of the Krylov engine.
@@ -118,7 +121,8 @@ __device__ __forceinline__ bool slot_runs(const Work& w) {
   return *((volatile int*)&w.sc->state) == w.run_if;
 }
 
-// Block-wide FP64 sum in a fixed order (TILE threads). Result valid in thread 0.
+// Block-wide FP64 sum in a fixed order (NT threads). Result valid in thread 0.
+template <int NT>
 __device__ __forceinline__ double block_sum(double v, double* sh) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -128,7 +132,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   double s = 0;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int i = 0; i < TILE / 32; ++i) s += sh[i];
+    for (int i = 0; i < NT / 32; ++i) s += sh[i];
   }
   __syncthreads();
   return s;
@@ -302,17 +306,18 @@ __device__ __noinline__ static void run_fin_bicg(const Work& w, const double* v)
 // Called by all threads of the CTA after its tile: records the partial sums, and
 // the slot's last tile sums all partials of the slot (in tile order) and runs
 // the finisher. Partials are strided by 3 (up to three sums per reduction).
+template <int NT>
 __device__ __forceinline__ void tile_finish(const Work& w, int tile_in_slot, double v0, double v1,
                                             double v2, double* partials) {
-  __shared__ double sh[TILE / 32];
+  __shared__ double sh[NT / 32];
   __shared__ int am_last;
   if (!w.red && w.fin == FIN_NONE) return;
   const int ns = (w.red >= 2) ? 3 : 1;
   double s[3];
-  s[0] = block_sum(v0, sh);
+  s[0] = block_sum<NT>(v0, sh);
   if (ns == 3) {
-    s[1] = block_sum(v1, sh);
-    s[2] = block_sum(v2, sh);
+    s[1] = block_sum<NT>(v1, sh);
+    s[2] = block_sum<NT>(v2, sh);
   }
   if (threadIdx.x == 0) {
     double* dst = partials + 3 * (size_t)(w.tile0 + tile_in_slot);
@@ -325,12 +330,12 @@ __device__ __forceinline__ void tile_finish(const Work& w, int tile_in_slot, dou
   if (am_last) {
     __threadfence();
     double acc[3] = {0, 0, 0};
-    for (int i = threadIdx.x; i < w.ntiles; i += TILE) {
+    for (int i = threadIdx.x; i < w.ntiles; i += NT) {
       const double* src = partials + 3 * (size_t)(w.tile0 + i);
       for (int k = 0; k < ns; ++k) acc[k] += __ldcg(src + k);
     }
     double tot[3] = {0, 0, 0};
-    for (int k = 0; k < ns; ++k) tot[k] = block_sum(acc[k], sh);
+    for (int k = 0; k < ns; ++k) tot[k] = block_sum<NT>(acc[k], sh);
     if (threadIdx.x == 0) {
       w.sc->counter = 0;
       run_fin(w, tot);

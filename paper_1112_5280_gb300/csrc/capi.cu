@@ -229,6 +229,8 @@ long long lqcd_ctx_launch_count(const lqcd_ctx* c) { return c ? c->launches : 0;
 
 void lqcd_set_grid_multiplier(int family, int mult) { set_grid_multiplier(family, mult); }
 
+
+
 // ------------------------------------------------------------------ gauge
 
 static int gauge_upload_impl(lqcd_ctx* c, const int dims[4], const double* U, bool dev, int prec,
@@ -529,6 +531,110 @@ int lqcd_dslash_eo(const lqcd_gauge* g, const lqcd_field* in, lqcd_field* out, i
   LQCD_TRY(ctx_set_device(g->ctx));
   return dslash_lin(g, in->prec, in->half[1 - out_parity], out->half[out_parity], nullptr, 1.0, 0.0,
                     out_parity, dagger != 0);
+}
+
+}  // extern "C"
+
+struct lqcd_dslash_batch {
+  lqcd_ctx* ctx = nullptr;
+  int prec = 0, nr = 18, dagger = 0, n = 0;
+  Launch L{};
+  Work* d_works = nullptr;
+  int* d_prefix = nullptr;
+};
+
+extern "C" {
+
+int lqcd_dslash_batch_create(int n, const lqcd_gauge* const* g, const lqcd_field* const* in,
+                             lqcd_field* const* out, int out_parity, int dagger,
+                             lqcd_dslash_batch** batch) {
+  clear_error();
+  if (!batch || !g || !in || !out || n < 1 || n > MAX_SLOTS)
+    return set_error(LQCD_EINVAL, "bad batch arguments (n = %d)", n);
+  *batch = nullptr;
+  if (out_parity != 0 && out_parity != 1) return set_error(LQCD_EINVAL, "parity %d", out_parity);
+  lqcd_ctx* c = g[0] ? g[0]->ctx : nullptr;
+  if (!c) return set_error(LQCD_EINVAL, "NULL gauge");
+  const int prec = in[0] ? in[0]->prec : -1;
+  int nr = -1;
+  std::vector<Work> w(n);
+  std::vector<int> prefix(n + 1, 0);
+  bool same_vh = true;
+  LQCD_TRY(ctx_set_device(c));
+  for (int i = 0; i < n; ++i) {
+    LQCD_TRY(check_pair(g[i], in[i], out[i]));
+    if (g[i]->ctx != c || in[i]->prec != prec) return set_error(LQCD_EINVAL, "batch mixes contexts or precisions");
+    if (!in[i]->half[1 - out_parity] || !out[i]->half[out_parity])
+      return set_error(LQCD_EINVAL, "entry %d: fields do not hold the needed parities", i);
+    const void* base;
+    int nri;
+    LQCD_TRY(gauge_links(g[i], prec, &base, &nri));
+    if (nr < 0) nr = nri;
+    if (nri != nr) return set_error(LQCD_EINVAL, "batch mixes 12- and 18-real links");
+    const int lp = link_prec_for(prec);
+    Work& x = w[i];
+    x = blank_work(g[i]->g);
+    x.out_par = out_parity;
+    x.in = in[i]->half[1 - out_parity];
+    x.out = out[i]->half[out_parity];
+    x.Uout = parity_links(base, lp, nr, g[i]->g.Vh, out_parity);
+    x.Uin = parity_links(base, lp, nr, g[i]->g.Vh, 1 - out_parity);
+    x.a = 1.0;
+    x.sc = c->scratch_sc;
+    x.tile0 = prefix[i];
+    prefix[i + 1] = prefix[i] + x.ntiles;
+    same_vh = same_vh && g[i]->g.Vh == g[0]->g.Vh;
+  }
+  lqcd_dslash_batch* b = new lqcd_dslash_batch();
+  b->ctx = c;
+  b->prec = prec;
+  b->nr = nr;
+  b->dagger = dagger != 0;
+  b->n = n;
+  cudaError_t e = cudaMalloc(&b->d_works, sizeof(Work) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_prefix, sizeof(int) * (n + 1));
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_works, w.data(), sizeof(Work) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_prefix, prefix.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (b->d_works) cudaFree(b->d_works);
+    if (b->d_prefix) cudaFree(b->d_prefix);
+    delete b;
+    return set_error(LQCD_ENOMEM, "dslash batch: %s", cudaGetErrorString(e));
+  }
+  memset(&b->L, 0, sizeof b->L);
+  b->L.works = b->d_works;
+  b->L.tile_prefix = b->d_prefix;
+  b->L.nslots = n;
+  b->L.ntiles = prefix[n];
+  b->L.interleave = (same_vh && n > 1) ? 1 : 0;
+  b->L.partials = nullptr;  // no reduction
+  if (n == 1) {
+    b->L.works = nullptr;
+    b->L.inline_work = w[0];
+  }
+  ctx_retain(c);
+  *batch = b;
+  return LQCD_OK;
+}
+
+int lqcd_dslash_batch_apply(lqcd_dslash_batch* b) {
+  clear_error();
+  if (!b) return set_error(LQCD_EINVAL, "batch is NULL");
+  LQCD_TRY(ctx_set_device(b->ctx));
+  LQCD_CK(launch_dslash(b->prec, b->nr, b->dagger != 0, EPI_LIN, b->L, 0, b->ctx->stream));
+  b->ctx->launches++;
+  return LQCD_OK;
+}
+
+void lqcd_dslash_batch_destroy(lqcd_dslash_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->ctx->device);
+  cudaStreamSynchronize(b->ctx->stream);
+  cudaFree(b->d_works);
+  cudaFree(b->d_prefix);
+  lqcd_ctx* c = b->ctx;
+  delete b;
+  ctx_release(c);
 }
 
 int lqcd_apply_Mhat(const lqcd_gauge* g, double kappa, const lqcd_field* in, lqcd_field* out,

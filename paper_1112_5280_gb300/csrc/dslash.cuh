@@ -54,12 +54,12 @@ __device__ __forceinline__ void neighbours(const Geom& g, int h, int par, int nf
 
 template <typename R>
 __device__ __forceinline__ Cx<R> sp(const R* v, int spin, int col) {
-  return {v[(spin * 3 + col) * 2], v[(spin * 3 + col) * 2 + 1]};
+  return {v[sidx(spin, col)], v[sidx(spin, col) + 1]};
 }
 template <typename R>
 __device__ __forceinline__ void acc_add(R* a, int spin, int col, Cx<R> w) {
-  a[(spin * 3 + col) * 2] += w.re;
-  a[(spin * 3 + col) * 2 + 1] += w.im;
+  a[sidx(spin, col)] += w.re;
+  a[sidx(spin, col) + 1] += w.im;
 }
 // i * w
 template <typename R>
@@ -137,26 +137,84 @@ __device__ __forceinline__ const char* link_dir(const void* base, int Vh, int mu
   return reinterpret_cast<const char*>(base) + (size_t)mu * NR * Vh * prec_bytes(LP);
 }
 
-template <int MU, int SP, int LP, int NR, bool DAG>
-__device__ __forceinline__ void hop_pair(const Geom& g, int h, const int nf[4], const int nb[4],
-                                         int t, const void* in, const void* Uout,
-                                         const void* Uin, typename SpinorIO<SP>::Real acc[24]) {
-  using R = typename SpinorIO<SP>::Real;
-  {  // forward: U_mu(x) psi(x + mu), projector (1 - g) for D, (1 + g) for D^dag
-    R psi[24], u[18];
-    SpinorIO<SP>::load(in, g.Vh, nf[MU], psi);
-    load_link<LP, NR>(link_dir<LP, NR>(Uout, g.Vh, MU), g.Vh, h, u);
-    const R eta = (MU == 3 && t == g.L[3] - 1) ? R(g.t_bc) : R(1);
-    hop<MU, DAG ? 1 : -1, false>(psi, u, eta, acc);
-  }
-  {  // backward: U_mu(x - mu)^dag psi(x - mu), projector (1 + g) for D, (1 - g) for D^dag
-    R psi[24], u[18];
-    SpinorIO<SP>::load(in, g.Vh, nb[MU], psi);
-    load_link<LP, NR>(link_dir<LP, NR>(Uin, g.Vh, MU), g.Vh, nb[MU], u);
-    const R eta = (MU == 3 && t == 0) ? R(g.t_bc) : R(1);
-    hop<MU, DAG ? -1 : 1, true>(psi, u, eta, acc);
-  }
+// Software-pipelined hop sequence. Hop K (0..7) is direction MU = K / 2,
+// forward for even K and backward for odd K. The raw words (spinor and link)
+// of hop K + D are loaded while hop K is computed, D = pipeline depth, so a
+// thread keeps up to D hops of loads in flight instead of one; at small
+// volumes, where every site already has a resident thread, this is what hides
+// the memory latency.
+#ifndef LQCD_DSLASH_DEPTH
+#define LQCD_DSLASH_DEPTH 3
+#endif
+constexpr int DSLASH_DEPTH = LQCD_DSLASH_DEPTH;
+
+template <int SP, int LP, int NR>
+struct HopBuf {
+  typename SpinorIO<SP>::Word s[SpinorIO<SP>::NW];
+  typename LinkIO<LP, NR>::Word u[LinkIO<LP, NR>::NW];
+};
+
+template <int K, int SP, int LP, int NR>
+__device__ __forceinline__ void issue_hop(const Geom& g, int h, const int nf[4], const int nb[4],
+                                          const void* in, const void* Uout, const void* Uin,
+                                          HopBuf<SP, LP, NR>& b) {
+  constexpr int MU = K / 2;
+  constexpr bool FWD = (K % 2) == 0;
+  const int n = FWD ? nf[MU] : nb[MU];
+  SpinorIO<SP>::load_raw(in, g.Vh, n, b.s);
+  LinkIO<LP, NR>::load_raw(link_dir<LP, NR>(FWD ? Uout : Uin, g.Vh, MU), g.Vh, FWD ? h : n, b.u);
 }
+
+template <int K, int SP, int LP, int NR, bool DAG>
+__device__ __forceinline__ void compute_hop(const Geom& g, int t, const HopBuf<SP, LP, NR>& b,
+                                            typename SpinorIO<SP>::Real acc[24]) {
+  using R = typename SpinorIO<SP>::Real;
+  constexpr int MU = K / 2;
+  constexpr bool FWD = (K % 2) == 0;
+  R psi[24], u[18];
+  SpinorIO<SP>::unpack(b.s, psi);
+  LinkIO<LP, NR>::unpack(b.u, u);
+  if (NR == 12) reconstruct_row2(u);
+  // forward: U_mu(x) psi(x + mu), projector (1 - g) for D, (1 + g) for D^dag
+  // backward: U_mu(x - mu)^dag psi(x - mu), projector (1 + g) for D, (1 - g) for D^dag
+  const R eta = (MU == 3 && t == (FWD ? g.L[3] - 1 : 0)) ? R(g.t_bc) : R(1);
+  constexpr int S = FWD ? (DAG ? 1 : -1) : (DAG ? -1 : 1);
+  hop<MU, S, !FWD>(psi, u, eta, acc);
+}
+
+template <int K, int D, int SP, int LP, int NR, bool DAG>
+struct HopPipe {
+  __device__ __forceinline__ static void run(const Geom& g, int h, int t, const int nf[4],
+                                             const int nb[4], const void* in, const void* Uout,
+                                             const void* Uin, HopBuf<SP, LP, NR> (&b)[D],
+                                             typename SpinorIO<SP>::Real acc[24]) {
+    compute_hop<K, SP, LP, NR, DAG>(g, t, b[K % D], acc);
+    if (K + D < 8) issue_hop<(K + D < 8 ? K + D : 0), SP, LP, NR>(g, h, nf, nb, in, Uout, Uin, b[K % D]);
+    HopPipe<K + 1, D, SP, LP, NR, DAG>::run(g, h, t, nf, nb, in, Uout, Uin, b, acc);
+  }
+};
+template <int D, int SP, int LP, int NR, bool DAG>
+struct HopPipe<8, D, SP, LP, NR, DAG> {
+  __device__ __forceinline__ static void run(const Geom&, int, int, const int*, const int*,
+                                             const void*, const void*, const void*,
+                                             HopBuf<SP, LP, NR> (&)[D],
+                                             typename SpinorIO<SP>::Real*) {}
+};
+
+template <int K, int D, int SP, int LP, int NR>
+struct HopPrologue {
+  __device__ __forceinline__ static void run(const Geom& g, int h, const int nf[4], const int nb[4],
+                                             const void* in, const void* Uout, const void* Uin,
+                                             HopBuf<SP, LP, NR> (&b)[D]) {
+    issue_hop<K, SP, LP, NR>(g, h, nf, nb, in, Uout, Uin, b[K]);
+    HopPrologue<K + 1, D, SP, LP, NR>::run(g, h, nf, nb, in, Uout, Uin, b);
+  }
+};
+template <int D, int SP, int LP, int NR>
+struct HopPrologue<D, D, SP, LP, NR> {
+  __device__ __forceinline__ static void run(const Geom&, int, const int*, const int*, const void*,
+                                             const void*, const void*, HopBuf<SP, LP, NR> (&)[D]) {}
+};
 
 // acc = (D_{p,1-p} in)(h) for output parity p. Uout: links of parity p, Uin: links of 1-p.
 template <int SP, int LP, int NR, bool DAG>
@@ -165,12 +223,11 @@ __device__ __forceinline__ void dslash_site(const Geom& g, int h, int out_par, c
                                             typename SpinorIO<SP>::Real acc[24]) {
   int nf[4], nb[4], t;
   neighbours(g, h, out_par, nf, nb, t);
+  HopBuf<SP, LP, NR> b[DSLASH_DEPTH];
+  HopPrologue<0, DSLASH_DEPTH, SP, LP, NR>::run(g, h, nf, nb, in, Uout, Uin, b);
 #pragma unroll
   for (int i = 0; i < 24; ++i) acc[i] = 0;
-  hop_pair<0, SP, LP, NR, DAG>(g, h, nf, nb, t, in, Uout, Uin, acc);
-  hop_pair<1, SP, LP, NR, DAG>(g, h, nf, nb, t, in, Uout, Uin, acc);
-  hop_pair<2, SP, LP, NR, DAG>(g, h, nf, nb, t, in, Uout, Uin, acc);
-  hop_pair<3, SP, LP, NR, DAG>(g, h, nf, nb, t, in, Uout, Uin, acc);
+  HopPipe<0, DSLASH_DEPTH, SP, LP, NR, DAG>::run(g, h, t, nf, nb, in, Uout, Uin, b, acc);
 }
 
 }  // namespace lqcd

@@ -28,6 +28,12 @@ enum Prec { P_F64 = 0, P_F32 = 1, P_F16 = 2, P_BF16 = 3 };
 
 __host__ __device__ inline int prec_bytes(int p) { return p == P_F64 ? 8 : (p == P_F32 ? 4 : 2); }
 
+// Device order of the 24 reals of a spinor: colour-major, so that the 8 reals
+// (4 spin x re/im) of one colour are contiguous words:
+//   real(spin, colour, re/im) = (colour * 4 + spin) * 2 + re/im
+// (the host layout is spin-major; the upload / download kernels permute).
+__host__ __device__ constexpr int sidx(int spin, int col) { return (col * 4 + spin) * 2; }
+
 template <typename T>
 struct Cx {
   T re, im;
@@ -113,6 +119,35 @@ template <>
 struct SpinorIO<P_F64> {
   using Real = double;
   static constexpr int CHUNKS = 12;
+  using Word = double2;
+  static constexpr int NW = 12;
+  __device__ static void load_raw(const void* base, int Vh, int h, Word w[NW]) {
+    const double2* p = reinterpret_cast<const double2*>(base) + h;
+#pragma unroll
+    for (int c = 0; c < NW; ++c) w[c] = ld_ro(p + (size_t)c * Vh);
+  }
+  __device__ static void unpack(const Word w[NW], double v[24]) {
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+      v[2 * c] = w[c].x;
+      v[2 * c + 1] = w[c].y;
+    }
+  }
+  // the 8 reals of colour a: words 4a .. 4a+3
+  __device__ static void load_colour(const void* base, int Vh, int h, int a, double v[8]) {
+    const double2* p = reinterpret_cast<const double2*>(base) + h + (size_t)(4 * a) * Vh;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const double2 d = ld_ro(p + (size_t)c * Vh);
+      v[2 * c] = d.x;
+      v[2 * c + 1] = d.y;
+    }
+  }
+  __device__ static void store_colour(void* base, int Vh, int h, int a, const double v[8]) {
+    double2* p = reinterpret_cast<double2*>(base) + h + (size_t)(4 * a) * Vh;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) p[(size_t)c * Vh] = make_double2(v[2 * c], v[2 * c + 1]);
+  }
   __device__ static void load(const void* base, int Vh, int h, double v[24]) {
     const double2* p = reinterpret_cast<const double2*>(base) + h;
 #pragma unroll
@@ -133,6 +168,34 @@ template <>
 struct SpinorIO<P_F32> {
   using Real = float;
   static constexpr int CHUNKS = 6;
+  using Word = float4;
+  static constexpr int NW = 6;
+  __device__ static void load_raw(const void* base, int Vh, int h, Word w[NW]) {
+    const float4* p = reinterpret_cast<const float4*>(base) + h;
+#pragma unroll
+    for (int c = 0; c < NW; ++c) w[c] = ld_ro(p + (size_t)c * Vh);
+  }
+  __device__ static void unpack(const Word w[NW], float v[24]) {
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+      v[4 * c] = w[c].x;
+      v[4 * c + 1] = w[c].y;
+      v[4 * c + 2] = w[c].z;
+      v[4 * c + 3] = w[c].w;
+    }
+  }
+  // the 8 reals of colour a: words 2a, 2a+1
+  __device__ static void load_colour(const void* base, int Vh, int h, int a, float v[8]) {
+    const float4* p = reinterpret_cast<const float4*>(base) + h + (size_t)(2 * a) * Vh;
+    const float4 d0 = ld_ro(p), d1 = ld_ro(p + Vh);
+    v[0] = d0.x; v[1] = d0.y; v[2] = d0.z; v[3] = d0.w;
+    v[4] = d1.x; v[5] = d1.y; v[6] = d1.z; v[7] = d1.w;
+  }
+  __device__ static void store_colour(void* base, int Vh, int h, int a, const float v[8]) {
+    float4* p = reinterpret_cast<float4*>(base) + h + (size_t)(2 * a) * Vh;
+    p[0] = make_float4(v[0], v[1], v[2], v[3]);
+    p[Vh] = make_float4(v[4], v[5], v[6], v[7]);
+  }
   __device__ static void load(const void* base, int Vh, int h, float v[24]) {
     const float4* p = reinterpret_cast<const float4*>(base) + h;
 #pragma unroll
@@ -156,8 +219,37 @@ template <bool BF>
 struct SpinorIO16 {
   using Real = float;
   static constexpr int CHUNKS = 3;
+  using Word = uint4;
+  static constexpr int NW = 3;
+  __device__ static void load_raw(const void* base, int Vh, int h, Word w[NW]) {
+    const uint4* p = reinterpret_cast<const uint4*>(base) + h;
+#pragma unroll
+    for (int c = 0; c < NW; ++c) w[c] = ld_ro(p + (size_t)c * Vh);
+  }
+  __device__ static void unpack(const Word w[NW], float v[24]) {
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+      const float2 a = unpack(w[c].x), b = unpack(w[c].y), e = unpack(w[c].z), f = unpack(w[c].w);
+      v[8 * c + 0] = a.x; v[8 * c + 1] = a.y; v[8 * c + 2] = b.x; v[8 * c + 3] = b.y;
+      v[8 * c + 4] = e.x; v[8 * c + 5] = e.y; v[8 * c + 6] = f.x; v[8 * c + 7] = f.y;
+    }
+  }
   __device__ static float2 unpack(unsigned w) { return BF ? unpack_b2(w) : unpack_h2(w); }
   __device__ static unsigned pack(float a, float b) { return BF ? pack_b2(a, b) : pack_h2(a, b); }
+  // the 8 reals of colour a: word a
+  __device__ static void load_colour(const void* base, int Vh, int h, int a, float v[8]) {
+    const uint4 d = ld_ro(reinterpret_cast<const uint4*>(base) + h + (size_t)a * Vh);
+    const float2 x = unpack(d.x), y = unpack(d.y), z = unpack(d.z), w = unpack(d.w);
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y; v[4] = z.x; v[5] = z.y; v[6] = w.x; v[7] = w.y;
+  }
+  __device__ static void store_colour(void* base, int Vh, int h, int a, const float v[8]) {
+    uint4 d;
+    d.x = pack(v[0], v[1]);
+    d.y = pack(v[2], v[3]);
+    d.z = pack(v[4], v[5]);
+    d.w = pack(v[6], v[7]);
+    reinterpret_cast<uint4*>(base)[h + (size_t)a * Vh] = d;
+  }
   __device__ static void load(const void* base, int Vh, int h, float v[24]) {
     const uint4* p = reinterpret_cast<const uint4*>(base) + h;
 #pragma unroll
@@ -193,75 +285,130 @@ struct SpinorIO<P_BF16> : SpinorIO16<true> {};
 template <int LP, int NR>
 struct LinkIO;
 
+// Raw words of one link (loaded once, bypassing L1) and their unpacking.
 template <int NR>
 struct LinkIO<P_F64, NR> {
   using Real = double;
-  __device__ static void load(const void* base_mu, int Vh, int h, double u[18]) {
+  using Word = double2;
+  static constexpr int NW = NR / 2;
+  __device__ static void load_raw(const void* base_mu, int Vh, int h, Word w[NW]) {
     const double2* p = reinterpret_cast<const double2*>(base_mu) + h;
 #pragma unroll
-    for (int c = 0; c < NR / 2; ++c) {
-      double2 d = ld_stream(p + (size_t)c * Vh);
-      u[2 * c] = d.x;
-      u[2 * c + 1] = d.y;
+    for (int c = 0; c < NW; ++c) w[c] = ld_stream(p + (size_t)c * Vh);
+  }
+  __device__ static void unpack(const Word w[NW], double u[18]) {
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+      u[2 * c] = w[c].x;
+      u[2 * c + 1] = w[c].y;
     }
+  }
+  __device__ static void load(const void* base_mu, int Vh, int h, double u[18]) {
+    Word w[NW];
+    load_raw(base_mu, Vh, h, w);
+    unpack(w, u);
   }
 };
 
 template <>
 struct LinkIO<P_F32, 18> {
   using Real = float;
-  __device__ static void load(const void* base_mu, int Vh, int h, float u[18]) {
+  using Word = float2;
+  static constexpr int NW = 9;
+  __device__ static void load_raw(const void* base_mu, int Vh, int h, Word w[NW]) {
     const float2* p = reinterpret_cast<const float2*>(base_mu) + h;
 #pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      float2 d = ld_stream(p + (size_t)c * Vh);
-      u[2 * c] = d.x;
-      u[2 * c + 1] = d.y;
+    for (int c = 0; c < NW; ++c) w[c] = ld_stream(p + (size_t)c * Vh);
+  }
+  __device__ static void unpack(const Word w[NW], float u[18]) {
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+      u[2 * c] = w[c].x;
+      u[2 * c + 1] = w[c].y;
     }
   }
+  __device__ static void load(const void* base_mu, int Vh, int h, float u[18]) {
+    Word w[NW];
+    load_raw(base_mu, Vh, h, w);
+    unpack(w, u);
+  }
 };
+
 template <>
 struct LinkIO<P_F32, 12> {
   using Real = float;
-  __device__ static void load(const void* base_mu, int Vh, int h, float u[18]) {
+  using Word = float4;
+  static constexpr int NW = 3;
+  __device__ static void load_raw(const void* base_mu, int Vh, int h, Word w[NW]) {
     const float4* p = reinterpret_cast<const float4*>(base_mu) + h;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      float4 d = ld_stream(p + (size_t)c * Vh);
-      u[4 * c] = d.x;
-      u[4 * c + 1] = d.y;
-      u[4 * c + 2] = d.z;
-      u[4 * c + 3] = d.w;
+    for (int c = 0; c < NW; ++c) w[c] = ld_stream(p + (size_t)c * Vh);
+  }
+  __device__ static void unpack(const Word w[NW], float u[18]) {
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+      u[4 * c] = w[c].x;
+      u[4 * c + 1] = w[c].y;
+      u[4 * c + 2] = w[c].z;
+      u[4 * c + 3] = w[c].w;
     }
   }
+  __device__ static void load(const void* base_mu, int Vh, int h, float u[18]) {
+    Word w[NW];
+    load_raw(base_mu, Vh, h, w);
+    unpack(w, u);
+  }
 };
+
 template <>
 struct LinkIO<P_F16, 18> {
   using Real = float;
-  __device__ static void load(const void* base_mu, int Vh, int h, float u[18]) {
+  using Word = unsigned;
+  static constexpr int NW = 9;
+  __device__ static void load_raw(const void* base_mu, int Vh, int h, Word w[NW]) {
     const unsigned* p = reinterpret_cast<const unsigned*>(base_mu) + h;
 #pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      float2 d = unpack_h2(ld_stream(p + (size_t)c * Vh));
+    for (int c = 0; c < NW; ++c) w[c] = ld_stream(p + (size_t)c * Vh);
+  }
+  __device__ static void unpack(const Word w[NW], float u[18]) {
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+      const float2 d = unpack_h2(w[c]);
       u[2 * c] = d.x;
       u[2 * c + 1] = d.y;
     }
   }
+  __device__ static void load(const void* base_mu, int Vh, int h, float u[18]) {
+    Word w[NW];
+    load_raw(base_mu, Vh, h, w);
+    unpack(w, u);
+  }
 };
+
 template <>
 struct LinkIO<P_F16, 12> {
   using Real = float;
-  __device__ static void load(const void* base_mu, int Vh, int h, float u[18]) {
+  using Word = uint2;
+  static constexpr int NW = 3;
+  __device__ static void load_raw(const void* base_mu, int Vh, int h, Word w[NW]) {
     const uint2* p = reinterpret_cast<const uint2*>(base_mu) + h;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      uint2 d = ld_stream(p + (size_t)c * Vh);
-      float2 a = unpack_h2(d.x), b = unpack_h2(d.y);
+    for (int c = 0; c < NW; ++c) w[c] = ld_stream(p + (size_t)c * Vh);
+  }
+  __device__ static void unpack(const Word w[NW], float u[18]) {
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+      const float2 a = unpack_h2(w[c].x), b = unpack_h2(w[c].y);
       u[4 * c] = a.x;
       u[4 * c + 1] = a.y;
       u[4 * c + 2] = b.x;
       u[4 * c + 3] = b.y;
     }
+  }
+  __device__ static void load(const void* base_mu, int Vh, int h, float u[18]) {
+    Word w[NW];
+    load_raw(base_mu, Vh, h, w);
+    unpack(w, u);
   }
 };
 

@@ -8,6 +8,14 @@ namespace lqcd {
 
 enum Epi { EPI_LIN = 0, EPI_CG = 1 };
 
+// Occupancy target (CTAs of TILE threads per SM) of the Dslash: 6 leaves 168
+// registers per thread, room for a 3-deep hop pipeline (measured best on
+// GB300 for batched and large lattices); a compile-time tunable.
+#ifndef LQCD_DSLASH_MIN_BLOCKS
+#define LQCD_DSLASH_MIN_BLOCKS 6
+#endif
+constexpr int DSLASH_MIN_BLOCKS = LQCD_DSLASH_MIN_BLOCKS;
+
 template <typename R>
 __device__ __forceinline__ double site_norm2(const R v[24]) {
   R s = 0;
@@ -44,7 +52,7 @@ __device__ __forceinline__ bool single_slot_idle(const Launch& L) {
 //                 r -= alpha (y1 + a * D in); x += alpha p      (EPI_CG, CG step)
 // with the Work's reduction (norm / dots) and scalar finisher per slot.
 template <int SP, int LP, int NR, bool DAG, int EPI>
-__global__ void __launch_bounds__(TILE) k_dslash(const Launch L) {
+__global__ void __launch_bounds__(TILE, DSLASH_MIN_BLOCKS) k_dslash(const Launch L) {
   using R = typename SpinorIO<SP>::Real;
   if (single_slot_idle(L)) return;
   for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
@@ -105,7 +113,7 @@ __global__ void __launch_bounds__(TILE) k_dslash(const Launch L) {
         SpinorIO<XSloppy<SP>::P>::store(w.z, w.g.Vh, h, x);
       }
     }
-    tile_finish(w, start / TILE, v0, v1, v2, L.partials);
+    tile_finish<TILE>(w, start / TILE, v0, v1, v2, L.partials);
   }
 }
 
@@ -261,7 +269,7 @@ __global__ void __launch_bounds__(TILE) k_blas(const Launch L) {
         v2 = site_norm2(r);
       }
     }
-    tile_finish(w, start / TILE, v0, v1, v2, L.partials);
+    tile_finish<TILE>(w, start / TILE, v0, v1, v2, L.partials);
   }
 }
 

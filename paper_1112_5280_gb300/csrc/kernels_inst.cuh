@@ -14,9 +14,9 @@ constexpr int LPX = (SPX == P_F64) ? P_F64 : (SPX == P_F32 ? P_F32 : P_F16);
 
 template <int NR, bool DAG, int EPI>
 cudaError_t go_dslash(const Launch& L, int grid, cudaStream_t s) {
-  auto fn = k_dslash<SPX, LPX, NR, DAG, EPI>;
   if (L.ntiles <= 0) return cudaSuccess;
-  if (grid <= 0) grid = grid_for((const void*)fn, L.ntiles, 0);
+  auto fn = k_dslash<SPX, LPX, NR, DAG, EPI>;
+  if (grid <= 0) grid = grid_for((const void*)fn, L.ntiles, 0, TILE);
   fn<<<grid, TILE, 0, s>>>(L);
   return cudaGetLastError();
 }
@@ -25,7 +25,7 @@ template <int OP, int P>
 cudaError_t go_blas(const Launch& L, int grid, cudaStream_t s) {
   auto fn = k_blas<P, OP>;
   if (L.ntiles <= 0) return cudaSuccess;
-  if (grid <= 0) grid = grid_for((const void*)fn, L.ntiles, 1);
+  if (grid <= 0) grid = grid_for((const void*)fn, L.ntiles, 1, TILE);
   fn<<<grid, TILE, 0, s>>>(L);
   return cudaGetLastError();
 }

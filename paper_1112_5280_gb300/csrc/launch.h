@@ -30,7 +30,8 @@ LQCD_DECL(bf16)
 // Number of SMs of the current device and the persistent-grid multiplier.
 int device_sm_count();
 void set_grid_multiplier(int kernel_family, int mult);  // 0 = occupancy limit
-int grid_for(const void* kernel_fn, int ntiles, int family);
+int grid_for(const void* kernel_fn, int ntiles, int family, int block);
+
 
 // layout kernels (layout.cu)
 cudaError_t gauge_from_aos(const double* d_aos, const Geom& g, int prec, int nr, void* d_out,

@@ -53,6 +53,12 @@ __device__ __forceinline__ size_t spinor_off(int p, int Vh, int h, int k) {
   return (size_t)(k / W) * Vh * W + (size_t)h * W + (k % W);
 }
 
+// host real k = (spin * 3 + colour) * 2 + re/im  ->  device position (colour-major)
+__device__ __forceinline__ int dev_real(int k) {
+  const int ri = k & 1, sc = k >> 1, spin = sc / 3, col = sc % 3;
+  return sidx(spin, col) + ri;
+}
+
 __device__ __forceinline__ void full_coords(const Geom& g, long long s, int& par, int& h) {
   int x = (int)(s % g.L[0]);
   long long r = s / g.L[0];
@@ -139,7 +145,7 @@ __global__ void k_spinor_from_aos(const double* __restrict__ aos, Geom g, void* 
   void* dst = par ? od : ev;
   if (!dst) return;
   const double* src = aos + s * 24;
-  for (int k = 0; k < 24; ++k) st_real<P>(dst, spinor_off(P, g.Vh, h, k), src[k]);
+  for (int k = 0; k < 24; ++k) st_real<P>(dst, spinor_off(P, g.Vh, h, dev_real(k)), src[k]);
 }
 
 template <int P>
@@ -151,7 +157,7 @@ __global__ void k_spinor_to_aos(const void* ev, const void* od, Geom g, double* 
   const void* src = par ? od : ev;
   if (!src) return;
   double* dst = aos + s * 24;
-  for (int k = 0; k < 24; ++k) dst[k] = ld_real<P>(src, spinor_off(P, g.Vh, h, k));
+  for (int k = 0; k < 24; ++k) dst[k] = ld_real<P>(src, spinor_off(P, g.Vh, h, dev_real(k)));
 }
 
 template <int PI, int PO>
@@ -270,7 +276,7 @@ void set_grid_multiplier(int family, int mult) {
   if (family >= 0 && family < 4) g_mult[family] = mult;
 }
 
-int grid_for(const void* fn, int ntiles, int family) {
+int grid_for(const void* fn, int ntiles, int family, int block) {
   const int nsm = device_sm_count();
   int occ;
   {
@@ -278,7 +284,7 @@ int grid_for(const void* fn, int ntiles, int family) {
     auto it = g_occ.find(fn);
     if (it == g_occ.end()) {
       int o = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, TILE, 0) != cudaSuccess || o < 1) o = 1;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, block, 0) != cudaSuccess || o < 1) o = 1;
       g_occ[fn] = o;
       occ = o;
     } else {

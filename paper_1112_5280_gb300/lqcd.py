@@ -95,6 +95,10 @@ def load(build_if_missing: bool = True):
     _sig(lib, "lqcd_dslash_eo", i, [_VP, _VP, _VP, i, i])
     _sig(lib, "lqcd_apply_Mhat", i, [_VP, d, _VP, _VP, i])
     _sig(lib, "lqcd_apply_M", i, [_VP, d, _VP, _VP, i])
+    _sig(lib, "lqcd_dslash_batch_create", i, [i, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), i, i,
+                                              C.POINTER(_VP)])
+    _sig(lib, "lqcd_dslash_batch_apply", i, [_VP])
+    _sig(lib, "lqcd_dslash_batch_destroy", None, [_VP])
     if hasattr(lib, "lqcd_apply_Mhat_noalloc"):
         _sig(lib, "lqcd_apply_Mhat_noalloc", i, [_VP, d, _VP, _VP, i])
     if hasattr(lib, "lqcd_solve"):
@@ -290,6 +294,36 @@ class Field:
 
 def dslash_eo(gauge: Gauge, fin: Field, fout: Field, out_parity: int, dagger=False):
     _check(gauge._lib.lqcd_dslash_eo(gauge.h, fin.h, fout.h, int(out_parity), int(bool(dagger))))
+
+
+class DslashBatch:
+    """n independent even-odd Dslash applications in one launch (lqcd_dslash_batch)."""
+
+    def __init__(self, gauges, fins, fouts, out_parity, dagger=False):
+        n = len(gauges)
+        if not (len(fins) == len(fouts) == n):
+            raise ValueError("gauges, fins and fouts must have the same length")
+        self._lib = gauges[0]._lib
+        self._keep = (list(gauges), list(fins), list(fouts))
+        h = _VP()
+        _check(self._lib.lqcd_dslash_batch_create(
+            n, (_VP * n)(*[g.h for g in gauges]), (_VP * n)(*[f.h for f in fins]),
+            (_VP * n)(*[f.h for f in fouts]), int(out_parity), int(bool(dagger)), C.byref(h)))
+        self.h = h
+
+    def apply(self):
+        _check(self._lib.lqcd_dslash_batch_apply(self.h))
+
+    def close(self):
+        if self.h:
+            self._lib.lqcd_dslash_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def apply_Mhat(gauge: Gauge, kappa: float, fin: Field, fout: Field, dagger=False):
