@@ -350,6 +350,7 @@ def run_ours(args, world, rank, local):
     clocks = sampler.summary(t0, t1)
     steps64 = max(3, args.steps // 8)
     ms64, _, _ = timed("f64", steps64, args.warmup)
+    msdf, _, _ = timed("df64", steps64, args.warmup)
     single = {}
     if not args.no_variants:
         for prec, nb in (("f32", 4), ("f64", 8)):
@@ -398,6 +399,8 @@ def run_ours(args, world, rank, local):
             "dslash_f32_gflops": flops_site * Vh * apps / (ms32 * 1e-3) / 1e9,
             "dslash_f32_effective_GBps_conventional_1440B": 1440 * Vh * apps / (ms32 * 1e-3) / 1e9,
             "dslash_f64_GBps": gbs64, "dslash_f64_us_per_application": ms64 * 1e3 / apps64,
+            "dslash_df64_GBps": b64 * apps64 / (msdf * 1e-3) / 1e9,
+            "dslash_df64_us_per_application": msdf * 1e3 / apps64,
             "dslash_f64_gflops": flops_site * Vh * apps64 / (ms64 * 1e-3) / 1e9,
             "one_application_per_launch": single,
         },
@@ -431,10 +434,12 @@ def run_solve_section(ctx, lqcd, inputs, world):
     out = {"workload": "32^3x64 kappa=0.155 eps=0.8, Gaussian source, tol 1e-10 (full-M FP64 residual)"}
     variants = [
         ("cg_mixed_f16_12", dict(sloppy_prec="f16", sloppy_compress=12), 6),
+        ("cg_mixed_f16_12_truef64", dict(sloppy_prec="f16", sloppy_compress=12, true_prec="f64"), 3),
         ("cg_mixed_bf16_12", dict(sloppy_prec="bf16", sloppy_compress=12), 3),
         ("cg_mixed_f32_12", dict(sloppy_prec="f32", sloppy_compress=12), 3),
         ("bicgstab_mixed_f32_12", dict(sloppy_prec="f32", sloppy_compress=12, solver=lqcd.BICGSTAB), 6),
         ("cg_fp64", dict(sloppy_prec="f64"), 3),
+        ("cg_df64", dict(sloppy_prec="df64"), 3),
         ("bicgstab_fp64", dict(sloppy_prec="f64", solver=lqcd.BICGSTAB), 2),
     ]
     for name, kw, reps in variants:

@@ -58,6 +58,10 @@ extern "C" {
 #define LQCD_F32 1
 #define LQCD_F16 2
 #define LQCD_BF16 3
+/* FP64-class: each real stored as an (hi, lo) pair of floats (8 bytes) and computed in
+ * double-float arithmetic (48-bit significand) on the FP32 pipes, which on GB300 run far
+ * faster than its FP64 pipe. Links of LQCD_DF64 fields are stored the same way. */
+#define LQCD_DF64 4
 
 /* field subsets */
 #define LQCD_EVEN 0
@@ -190,12 +194,16 @@ LQCD_API int lqcd_apply_Mhat_noalloc(const lqcd_gauge* g, double kappa, const lq
 
 typedef struct lqcd_solve_opts {
   int solver;           /* LQCD_CG or LQCD_BICGSTAB */
-  int sloppy_prec;      /* LQCD_F64: plain FP64 solve; LQCD_F32 / F16 / BF16: mixed precision */
+  int sloppy_prec;      /* LQCD_F64: plain FP64 solve; LQCD_DF64: double-float solve;
+                           LQCD_F32 / F16 / BF16: mixed precision */
   int sloppy_compress;  /* 18 or 12 reals per link of the sloppy operator */
   int maxiter;          /* iteration limit (default 50000) */
   double delta;         /* reliable-update threshold on |r| (<= 0: 0.1 mixed, none for FP64) */
   int chunk;            /* iterations per CUDA-graph replay / host poll (default 32) */
   int use_graph;        /* 1: capture iteration chunks as CUDA graphs (default 1) */
+  int true_prec;        /* FP64-class true residual, solution and outer correction: LQCD_F64
+                           (native) or LQCD_DF64 (double-float); -1 (default): LQCD_F64 for an
+                           FP64 solve, LQCD_DF64 otherwise */
 } lqcd_solve_opts;
 
 typedef struct lqcd_solve_info {

@@ -58,22 +58,29 @@ int lqcd::bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kapp
   if (src->prec != LQCD_F64 || src->subset != LQCD_FULL || x->subset != LQCD_FULL)
     return set_error(LQCD_EINVAL, "source must be FULL FP64 and x FULL");
   const int sp = o->sloppy_prec;
-  if (sp != LQCD_F64 && sp != LQCD_F32)
-    return set_error(LQCD_EINVAL, "BiCGStab runs with FP64 or FP32 inner precision");
+  if (sp != LQCD_F64 && sp != LQCD_F32 && sp != LQCD_DF64)
+    return set_error(LQCD_EINVAL, "BiCGStab runs with FP64, DF64 or FP32 inner precision");
+  // FP64-class vectors and operator of the outer defect correction
+  const int tp = (o->true_prec == -1) ? (sp == LQCD_F64 ? P_F64 : P_DF64) : o->true_prec;
+  if (tp != P_F64 && tp != P_DF64) return set_error(LQCD_EINVAL, "true_prec");
   if (!(tol > 0)) return set_error(LQCD_EINVAL, "tol must be > 0");
   lqcd_ctx* c = g->ctx;
   LQCD_CK(cudaSetDevice(c->device));
   cudaStream_t st = c->stream;
   const Geom gm = g->g;
   const int Vh = gm.Vh;
-  const int nr = (sp == LQCD_F64) ? 18 : o->sloppy_compress;
+  const int nr = (sp == LQCD_F64 || sp == LQCD_DF64) ? 18 : o->sloppy_compress;
   if (sp != LQCD_F64) {
     int rc = lqcd_gauge_add_copy(const_cast<lqcd_gauge*>(g), sp, nr);
     if (rc != LQCD_OK) return rc;
   }
+  if (tp != P_F64) {
+    int rc = lqcd_gauge_add_copy(const_cast<lqcd_gauge*>(g), tp, 18);
+    if (rc != LQCD_OK) return rc;
+  }
   const void* US = g->copy[link_prec_for(sp)][nr == 12];
-  const void* U64 = g->copy[P_F64][0];
-  const size_t h64 = a256(half_spinor_bytes(P_F64, Vh)), hs = a256(half_spinor_bytes(sp, Vh));
+  const void* U64 = g->copy[tp][0];
+  const size_t h64 = a256(half_spinor_bytes(tp, Vh)), hs = a256(half_spinor_bytes(sp, Vh));
   BicgBufs b;
   const size_t total = 6 * h64 + 8 * hs;
   cudaError_t err = cudaMalloc(&b.block, total);
@@ -99,11 +106,11 @@ int lqcd::bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kapp
   };
   auto dsl = [&](int prec, const Work& w, bool dag) {
     c->launches++;
-    return launch_dslash(prec, prec == P_F64 ? 18 : nr, dag, EPI_LIN, single_launch(w, c->partials), 0, st);
+    return launch_dslash(prec, prec == tp ? 18 : nr, dag, EPI_LIN, single_launch(w, c->partials), 0, st);
   };
   auto blas = [&](int prec, int op, const Work& w) {
     c->launches++;
-    return launch_blas(prec, op, single_launch(w, c->partials), 0, st);
+    return launch_blas(prec, op, single_launch(w, c->partials), 0, st, tp);
   };
   auto read_sc = [&](Scalars* h) -> int {
     LQCD_CK(cudaMemcpyAsync(h, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
@@ -114,8 +121,8 @@ int lqcd::bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kapp
   int status = LQCD_OK, iters = 0, outer = 0;
   double bnorm2 = 0;
   if (rc == LQCD_OK) {
-    err = cudaMemcpyAsync(b.be, src->half[0], half_spinor_bytes(P_F64, Vh), cudaMemcpyDeviceToDevice, st);
-    if (err == cudaSuccess) err = cudaMemcpyAsync(b.bo, src->half[1], half_spinor_bytes(P_F64, Vh), cudaMemcpyDeviceToDevice, st);
+    err = spinor_convert(src->half[0], P_F64, b.be, tp, Vh, 1.0, st);
+    if (err == cudaSuccess) err = spinor_convert(src->half[1], P_F64, b.bo, tp, Vh, 1.0, st);
     if (err == cudaSuccess) err = cudaMemsetAsync(b.x64, 0, h64, st);
     if (err == cudaSuccess) err = cudaMemsetAsync(sc, 0, sizeof(Scalars), st);
     // |b|^2
@@ -123,15 +130,15 @@ int lqcd::bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kapp
     w.red = 1;
     w.fin = FIN_STORE0;
     w.in = b.be;
-    if (err == cudaSuccess) err = blas(P_F64, B_NORM, w);
+    if (err == cudaSuccess) err = blas(tp, B_NORM, w);
     w.fin = FIN_STORE1;
     w.in = b.bo;
-    if (err == cudaSuccess) err = blas(P_F64, B_NORM, w);
+    if (err == cudaSuccess) err = blas(tp, B_NORM, w);
     // bhat = b_e + kappa D_eo b_o
     Work d = base();
-    links(d, U64, P_F64, 18, 0);
+    links(d, U64, tp, 18, 0);
     d.in = b.bo; d.out = b.bhat; d.y1 = b.be; d.c1 = 1.0; d.a = kappa;
-    if (err == cudaSuccess) err = dsl(P_F64, d, false);
+    if (err == cudaSuccess) err = dsl(tp, d, false);
     if (err == cudaSuccess) rc = read_sc(hs_);
     else rc = set_error(LQCD_ECUDA, "BiCGStab setup: %s", cudaGetErrorString(err));
     bnorm2 = hs_->res[0] + hs_->res[1];
@@ -141,14 +148,14 @@ int lqcd::bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kapp
   while (rc == LQCD_OK && status == LQCD_OK) {
     // FP64 true residual u = bhat - Mhat x
     Work d1 = base();
-    links(d1, U64, P_F64, 18, 1);
+    links(d1, U64, tp, 18, 1);
     d1.in = b.x64; d1.out = b.t64; d1.a = 1.0;
     Work d2 = base();
-    links(d2, U64, P_F64, 18, 0);
+    links(d2, U64, tp, 18, 0);
     d2.in = b.t64; d2.out = b.u64; d2.y1 = b.bhat; d2.c1 = 1.0; d2.y2 = b.x64; d2.c2 = -1.0;
     d2.a = kappa * kappa; d2.red = 1; d2.fin = FIN_STORE0;
-    err = dsl(P_F64, d1, false);
-    if (err == cudaSuccess) err = dsl(P_F64, d2, false);
+    err = dsl(tp, d1, false);
+    if (err == cudaSuccess) err = dsl(tp, d2, false);
     if (err != cudaSuccess) { rc = set_error(LQCD_ECUDA, "residual: %s", cudaGetErrorString(err)); break; }
     if ((rc = read_sc(hs_)) != LQCD_OK) break;
     const double u2 = hs_->res[0];
@@ -169,6 +176,7 @@ int lqcd::bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kapp
     // inner target: the remaining defect, limited by the sloppy precision
     double rel = 0.5 * std::sqrt(target2) / sigma;
     if (sp == LQCD_F32) rel = std::max(rel, 1e-5);
+    if (sp == LQCD_DF64 && tp == P_F64) rel = std::max(rel, 1e-12);
     if (err == cudaSuccess) {
       k_bicg_init<<<1, 1, 0, st>>>(sc, rel * rel, o->maxiter - iters);
       err = cudaGetLastError();
@@ -230,21 +238,21 @@ int lqcd::bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kapp
   if (rc == LQCD_OK) {
     // x_o = b_o + kappa D_oe x_e, full FP64 residual, copy out
     Work a = base();
-    links(a, U64, P_F64, 18, 1);
+    links(a, U64, tp, 18, 1);
     a.in = b.x64; a.out = b.t64; a.y1 = b.bo; a.c1 = 1.0; a.a = kappa;
     Work re = base();
-    links(re, U64, P_F64, 18, 0);
+    links(re, U64, tp, 18, 0);
     re.in = b.t64; re.out = b.u64; re.y1 = b.be; re.c1 = 1.0; re.y2 = b.x64; re.c2 = -1.0;
     re.a = kappa; re.red = 1; re.fin = FIN_STORE0;
     Work ro = base();
-    links(ro, U64, P_F64, 18, 1);
+    links(ro, U64, tp, 18, 1);
     ro.in = b.x64; ro.out = b.bhat; ro.y1 = b.bo; ro.c1 = 1.0; ro.y2 = b.t64; ro.c2 = -1.0;
     ro.a = kappa; ro.red = 1; ro.fin = FIN_STORE1;
-    err = dsl(P_F64, a, false);
-    if (err == cudaSuccess) err = dsl(P_F64, re, false);
-    if (err == cudaSuccess) err = dsl(P_F64, ro, false);
-    if (err == cudaSuccess) err = spinor_convert(b.x64, P_F64, x->half[0], x->prec, Vh, 1.0, st);
-    if (err == cudaSuccess) err = spinor_convert(b.t64, P_F64, x->half[1], x->prec, Vh, 1.0, st);
+    err = dsl(tp, a, false);
+    if (err == cudaSuccess) err = dsl(tp, re, false);
+    if (err == cudaSuccess) err = dsl(tp, ro, false);
+    if (err == cudaSuccess) err = spinor_convert(b.x64, tp, x->half[0], x->prec, Vh, 1.0, st);
+    if (err == cudaSuccess) err = spinor_convert(b.t64, tp, x->half[1], x->prec, Vh, 1.0, st);
     if (err != cudaSuccess) rc = set_error(LQCD_ECUDA, "reconstruction: %s", cudaGetErrorString(err));
     else if ((rc = read_sc(hs_)) == LQCD_OK)
       true_res = bnorm2 > 0 ? std::sqrt((hs_->res[0] + hs_->res[1]) / bnorm2) : 0.0;

@@ -75,13 +75,12 @@ int ctx_staging(lqcd_ctx* c, size_t bytes) {
   return LQCD_OK;
 }
 
-static int link_index(int lp) { return lp; }
-
 int gauge_links(const lqcd_gauge* gc, int field_prec, const void** base, int* nr) {
   lqcd_gauge* g = const_cast<lqcd_gauge*>(gc);
   const int lp = link_prec_for(field_prec);
+  if (lp < 0 || lp >= NPREC) return set_error(LQCD_EINVAL, "link precision %d", lp);
   const int n = g->compress;
-  void*& slot = g->copy[link_index(lp)][n == 12];
+  void*& slot = g->copy[lp][n == 12];
   if (!slot) {
     size_t b = gauge_copy_bytes(lp, n, g->g.Vh);
     LQCD_CK(cudaMalloc(&slot, b));
@@ -238,7 +237,7 @@ static int gauge_upload_impl(lqcd_ctx* c, const int dims[4], const double* U, bo
   clear_error();
   if (!c || !U || !out) return set_error(LQCD_EINVAL, "NULL argument");
   *out = nullptr;
-  if (prec < LQCD_F64 || prec > LQCD_BF16) return set_error(LQCD_EINVAL, "precision %d", prec);
+  if (prec < LQCD_F64 || prec > LQCD_DF64) return set_error(LQCD_EINVAL, "precision %d", prec);
   if (compress != 18 && compress != 12) return set_error(LQCD_EINVAL, "compress must be 18 or 12");
   Geom g;
   LQCD_TRY(make_geom(dims, t_bc, g));
@@ -295,10 +294,11 @@ int lqcd_gauge_upload_dev(lqcd_ctx* c, const int dims[4], const double* U, int p
 int lqcd_gauge_add_copy(lqcd_gauge* g, int prec, int compress) {
   clear_error();
   if (!g) return set_error(LQCD_EINVAL, "gauge is NULL");
-  if (prec < LQCD_F64 || prec > LQCD_BF16) return set_error(LQCD_EINVAL, "precision %d", prec);
+  if (prec < LQCD_F64 || prec > LQCD_DF64) return set_error(LQCD_EINVAL, "precision %d", prec);
   if (compress != 18 && compress != 12) return set_error(LQCD_EINVAL, "compress must be 18 or 12");
   LQCD_TRY(ctx_set_device(g->ctx));
   const int lp = link_prec_for(prec);
+  if (lp < 0 || lp >= NPREC) return set_error(LQCD_EINVAL, "link precision %d", lp);
   void*& slot = g->copy[lp][compress == 12];
   if (slot) return LQCD_OK;
   const size_t b = gauge_copy_bytes(lp, compress, g->g.Vh);
@@ -332,7 +332,7 @@ int lqcd_field_create(lqcd_ctx* c, const int dims[4], int prec, int subset, lqcd
   clear_error();
   if (!c || !out) return set_error(LQCD_EINVAL, "NULL argument");
   *out = nullptr;
-  if (prec < LQCD_F64 || prec > LQCD_BF16) return set_error(LQCD_EINVAL, "precision %d", prec);
+  if (prec < LQCD_F64 || prec > LQCD_DF64) return set_error(LQCD_EINVAL, "precision %d", prec);
   if (subset < LQCD_EVEN || subset > LQCD_FULL) return set_error(LQCD_EINVAL, "subset %d", subset);
   Geom g;
   LQCD_TRY(make_geom(dims, -1, g));

@@ -66,14 +66,16 @@ template <typename R>
 __device__ __forceinline__ Cx<R> mul_i(Cx<R> w) {
   return {-w.im, w.re};
 }
-template <typename R>
-__device__ __forceinline__ Cx<R> scale(Cx<R> w, R s) {
-  return {s * w.re, s * w.im};
+// S * w for a compile-time sign S = +-1
+template <int S, typename R>
+__device__ __forceinline__ Cx<R> sgn(Cx<R> w) {
+  if (S > 0) return w;
+  return {-w.re, -w.im};
 }
 
-// One hop: acc += eta * (1 + S g_MU) (U or U^dag) psi.
+// One hop: acc += eta * (1 + S g_MU) (U or U^dag) psi, eta = +-1.
 template <int MU, int S, bool ADJ, typename R>
-__device__ __forceinline__ void hop(const R psi[24], const R u[18], R eta, R acc[24]) {
+__device__ __forceinline__ void hop(const R psi[24], const R u[18], int eta, R acc[24]) {
   Cx<R> h0[3], h1[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -91,9 +93,9 @@ __device__ __forceinline__ void hop(const R psi[24], const R u[18], R eta, R acc
       h0[c] = {p0.re + S * p2.re, p0.im + S * p2.im};
       h1[c] = {p1.re + S * p3.re, p1.im + S * p3.im};
     }
-    if (MU == 3) {
-      h0[c] = scale(h0[c], eta);
-      h1[c] = scale(h1[c], eta);
+    if (MU == 3 && eta < 0) {
+      h0[c] = sgn<-1>(h0[c]);
+      h1[c] = sgn<-1>(h1[c]);
     }
   }
   Cx<R> w0[3], w1[3];
@@ -116,17 +118,17 @@ __device__ __forceinline__ void hop(const R psi[24], const R u[18], R eta, R acc
     acc_add(acc, 0, a, w0[a]);
     acc_add(acc, 1, a, w1[a]);
     if (MU == 0) {  // lower = S A^dag h, A^dag = [[0,i],[i,0]]
-      acc_add(acc, 2, a, scale(mul_i(w1[a]), R(S)));
-      acc_add(acc, 3, a, scale(mul_i(w0[a]), R(S)));
+      acc_add(acc, 2, a, sgn<S>(mul_i(w1[a])));
+      acc_add(acc, 3, a, sgn<S>(mul_i(w0[a])));
     } else if (MU == 1) {  // A^dag = [[0,1],[-1,0]]
-      acc_add(acc, 2, a, scale(w1[a], R(S)));
-      acc_add(acc, 3, a, scale(w0[a], R(-S)));
+      acc_add(acc, 2, a, sgn<S>(w1[a]));
+      acc_add(acc, 3, a, sgn<-S>(w0[a]));
     } else if (MU == 2) {  // A^dag = diag(i, -i)
-      acc_add(acc, 2, a, scale(mul_i(w0[a]), R(S)));
-      acc_add(acc, 3, a, scale(mul_i(w1[a]), R(-S)));
+      acc_add(acc, 2, a, sgn<S>(mul_i(w0[a])));
+      acc_add(acc, 3, a, sgn<-S>(mul_i(w1[a])));
     } else {
-      acc_add(acc, 2, a, scale(w0[a], R(S)));
-      acc_add(acc, 3, a, scale(w1[a], R(S)));
+      acc_add(acc, 2, a, sgn<S>(w0[a]));
+      acc_add(acc, 3, a, sgn<S>(w1[a]));
     }
   }
 }
@@ -143,10 +145,15 @@ __device__ __forceinline__ const char* link_dir(const void* base, int Vh, int mu
 // thread keeps up to D hops of loads in flight instead of one; at small
 // volumes, where every site already has a resident thread, this is what hides
 // the memory latency.
+// Depth per spinor precision: 3 (measured best on GB300) except double-float,
+// whose wide words leave registers for one hop in flight only.
 #ifndef LQCD_DSLASH_DEPTH
 #define LQCD_DSLASH_DEPTH 3
 #endif
-constexpr int DSLASH_DEPTH = LQCD_DSLASH_DEPTH;
+template <int SP>
+struct DslashDepth {
+  static constexpr int value = (SP == P_DF64) ? 1 : LQCD_DSLASH_DEPTH;
+};
 
 template <int SP, int LP, int NR>
 struct HopBuf {
@@ -177,7 +184,7 @@ __device__ __forceinline__ void compute_hop(const Geom& g, int t, const HopBuf<S
   if (NR == 12) reconstruct_row2(u);
   // forward: U_mu(x) psi(x + mu), projector (1 - g) for D, (1 + g) for D^dag
   // backward: U_mu(x - mu)^dag psi(x - mu), projector (1 + g) for D, (1 - g) for D^dag
-  const R eta = (MU == 3 && t == (FWD ? g.L[3] - 1 : 0)) ? R(g.t_bc) : R(1);
+  const int eta = (MU == 3 && t == (FWD ? g.L[3] - 1 : 0)) ? g.t_bc : 1;
   constexpr int S = FWD ? (DAG ? 1 : -1) : (DAG ? -1 : 1);
   hop<MU, S, !FWD>(psi, u, eta, acc);
 }
@@ -223,11 +230,12 @@ __device__ __forceinline__ void dslash_site(const Geom& g, int h, int out_par, c
                                             typename SpinorIO<SP>::Real acc[24]) {
   int nf[4], nb[4], t;
   neighbours(g, h, out_par, nf, nb, t);
-  HopBuf<SP, LP, NR> b[DSLASH_DEPTH];
-  HopPrologue<0, DSLASH_DEPTH, SP, LP, NR>::run(g, h, nf, nb, in, Uout, Uin, b);
+  constexpr int D = DslashDepth<SP>::value;
+  HopBuf<SP, LP, NR> b[D];
+  HopPrologue<0, D, SP, LP, NR>::run(g, h, nf, nb, in, Uout, Uin, b);
 #pragma unroll
   for (int i = 0; i < 24; ++i) acc[i] = 0;
-  HopPipe<0, DSLASH_DEPTH, SP, LP, NR, DAG>::run(g, h, t, nf, nb, in, Uout, Uin, b, acc);
+  HopPipe<0, D, SP, LP, NR, DAG>::run(g, h, t, nf, nb, in, Uout, Uin, b, acc);
 }
 
 }  // namespace lqcd

@@ -88,6 +88,7 @@ struct lqcd_engine {
   lqcd_ctx* ctx = nullptr;
   lqcd_solve_opts opts{};
   int sp = P_F32, xp = P_F32, nr = 12;
+  int tp = P_F64;  // FP64-class vectors and operator of the true residual: P_F64 or P_DF64
   double delta2 = 0.01;
   int ru_every = 8;
   size_t budget = 0;
@@ -117,7 +118,7 @@ namespace {
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 size_t slot_bytes(const lqcd_engine* e, int Vh) {
-  return 6 * align256(half_spinor_bytes(P_F64, Vh)) + 4 * align256(half_spinor_bytes(e->sp, Vh)) +
+  return 6 * align256(half_spinor_bytes(e->tp, Vh)) + 4 * align256(half_spinor_bytes(e->sp, Vh)) +
          align256(half_spinor_bytes(e->xp, Vh));
 }
 
@@ -128,12 +129,12 @@ void carve(SlotBuf& b, const lqcd_engine* e, int Vh) {
     p += align256(half_spinor_bytes(prec, Vh));
     return r;
   };
-  b.be = take(P_F64);
-  b.bo = take(P_F64);
-  b.bhat = take(P_F64);
-  b.x64 = take(P_F64);
-  b.u64 = take(P_F64);
-  b.t64 = take(P_F64);
+  b.be = take(e->tp);
+  b.bo = take(e->tp);
+  b.bhat = take(e->tp);
+  b.x64 = take(e->tp);
+  b.u64 = take(e->tp);
+  b.t64 = take(e->tp);
   b.r = take(e->sp);
   b.p = take(e->sp);
   b.q = take(e->sp);
@@ -158,7 +159,8 @@ void step_works(const lqcd_engine* e, const Request& q, Work out[NSTEP]) {
   const double kk = q.kappa * q.kappa;
   const void* US = sloppy_links(e, q.gauge);
   const int lpS = link_prec_for(e->sp);
-  const void* U64 = q.gauge->copy[P_F64][0];
+  const void* U64 = q.gauge->copy[e->tp][0];
+  const int tp = e->tp;
   auto links = [&](Work& w, const void* U, int lp, int nr, int out_par) {
     w.out_par = out_par;
     w.Uout = parity_links(U, lp, nr, Vh, out_par);
@@ -187,17 +189,17 @@ void step_works(const lqcd_engine* e, const Request& q, Work out[NSTEP]) {
   Work& f = out[RU_FOLD];
   f.in = b.xs; f.out = b.x64; f.run_if = S_UPDATE;
   Work& d1 = out[RU_D1];
-  links(d1, U64, P_F64, 18, 1);
+  links(d1, U64, tp, 18, 1);
   d1.in = b.x64; d1.out = b.t64; d1.a = 1.0; d1.run_if = S_UPDATE;
   Work& rs = out[RU_RES];
-  links(rs, U64, P_F64, 18, 0);
+  links(rs, U64, tp, 18, 0);
   rs.in = b.t64; rs.out = b.u64; rs.y1 = b.bhat; rs.c1 = 1.0; rs.y2 = b.x64; rs.c2 = -1.0;
   rs.a = kk; rs.red = 1; rs.fin = FIN_TRUERES; rs.run_if = S_UPDATE;
   Work& d2 = out[RU_D2];
-  links(d2, U64, P_F64, 18, 1);
+  links(d2, U64, tp, 18, 1);
   d2.in = b.u64; d2.out = b.t64; d2.a = 1.0; d2.run_if = S_UPDATE;
   Work& rh = out[RU_RHO];
-  links(rh, U64, P_F64, 18, 0);
+  links(rh, U64, tp, 18, 0);
   rh.in = b.t64; rh.out = b.u64; rh.y1 = b.u64; rh.c1 = 1.0; rh.a = -kk;
   rh.red = 1; rh.fin = FIN_RHO; rh.run_if = S_UPDATE;
   Work& cv = out[RU_CONV];
@@ -232,11 +234,11 @@ cudaError_t issue(lqcd_engine* e, int s, const Launch& L) {
   const StepKind k = kind_of(s);
   e->ctx->launches++;
   if (k.dslash) {
-    if (k.f64) return launch_dslash(P_F64, 18, k.dag, k.epi_or_op, L, 0, e->ctx->stream);
+    if (k.f64) return launch_dslash(e->tp, 18, k.dag, k.epi_or_op, L, 0, e->ctx->stream);
     return launch_dslash(e->sp, e->nr, k.dag, k.epi_or_op, L, 0, e->ctx->stream);
   }
   const int prec = (k.epi_or_op == B_RU_FOLD) ? e->xp : e->sp;
-  return launch_blas(prec, k.epi_or_op, L, 0, e->ctx->stream);
+  return launch_blas(prec, k.epi_or_op, L, 0, e->ctx->stream, e->tp);
 }
 
 Launch batch_launch(const lqcd_engine* e, int s) {
@@ -375,20 +377,21 @@ int alloc_block(lqcd_engine* e, size_t bytes, void** out) {
 // single-slot launches of the finishing steps (after DONE / FAILED)
 int finalize_launch(lqcd_engine* e, Request& q) {
   const Geom& g = q.g;
-  const void* U64 = q.gauge->copy[P_F64][0];
+  const int tp = e->tp;
+  const void* U64 = q.gauge->copy[tp][0];
   const SlotBuf& b = q.buf;
   cudaStream_t st = e->ctx->stream;
   auto lin = [&](int out_par, const void* in, void* out, const void* y1, double c1, const void* y2,
                  double c2, double a, int fin) -> int {
     Work w = slot_work(e, q);
     w.out_par = out_par;
-    w.Uout = parity_links(U64, P_F64, 18, g.Vh, out_par);
-    w.Uin = parity_links(U64, P_F64, 18, g.Vh, 1 - out_par);
+    w.Uout = parity_links(U64, tp, 18, g.Vh, out_par);
+    w.Uin = parity_links(U64, tp, 18, g.Vh, 1 - out_par);
     w.in = in; w.out = out; w.y1 = y1; w.c1 = c1; w.y2 = y2; w.c2 = c2; w.a = a;
     w.red = fin != FIN_NONE ? 1 : 0; w.fin = fin; w.run_if = -1;
     Launch L = single_launch(w, e->d_partials);
     e->ctx->launches++;
-    LQCD_CK(launch_dslash(P_F64, 18, false, EPI_LIN, L, 0, st));
+    LQCD_CK(launch_dslash(tp, 18, false, EPI_LIN, L, 0, st));
     return LQCD_OK;
   };
   int rc;
@@ -415,6 +418,7 @@ void lqcd_solve_opts_default(lqcd_solve_opts* o) {
   o->delta = 0.0;
   o->chunk = 32;
   o->use_graph = 1;
+  o->true_prec = -1;
 }
 
 int lqcd_engine_create(lqcd_ctx* c, const lqcd_solve_opts* opts, size_t budget, int max_slots,
@@ -427,7 +431,9 @@ int lqcd_engine_create(lqcd_ctx* c, const lqcd_solve_opts* opts, size_t budget, 
   lqcd_solve_opts_default(&o);
   if (opts) o = *opts;
   if (o.solver != LQCD_CG) return set_error(LQCD_EINVAL, "the batched engine runs CG");
-  if (o.sloppy_prec < LQCD_F64 || o.sloppy_prec > LQCD_BF16) return set_error(LQCD_EINVAL, "sloppy precision");
+  if (o.sloppy_prec < LQCD_F64 || o.sloppy_prec > LQCD_DF64) return set_error(LQCD_EINVAL, "sloppy precision");
+  if (o.true_prec != -1 && o.true_prec != LQCD_F64 && o.true_prec != LQCD_DF64)
+    return set_error(LQCD_EINVAL, "true_prec must be LQCD_F64, LQCD_DF64 or -1");
   if (o.sloppy_compress != 12 && o.sloppy_compress != 18) return set_error(LQCD_EINVAL, "sloppy compress");
   if (o.maxiter < 1) o.maxiter = 50000;
   if (o.chunk < 1) o.chunk = 32;
@@ -436,10 +442,12 @@ int lqcd_engine_create(lqcd_ctx* c, const lqcd_solve_opts* opts, size_t budget, 
   e->ctx = c;
   ctx_retain(c);
   e->opts = o;
+  const bool fp64_class = (o.sloppy_prec == LQCD_F64 || o.sloppy_prec == LQCD_DF64);
   e->sp = o.sloppy_prec;
-  e->xp = (o.sloppy_prec == LQCD_F64) ? P_F64 : P_F32;
-  e->nr = (o.sloppy_prec == LQCD_F64) ? 18 : o.sloppy_compress;
-  const double delta = o.delta > 0 ? o.delta : (o.sloppy_prec == LQCD_F64 ? 0.0 : 0.1);
+  e->xp = fp64_class ? o.sloppy_prec : P_F32;
+  e->nr = fp64_class ? 18 : o.sloppy_compress;
+  e->tp = (o.true_prec == -1) ? (o.sloppy_prec == LQCD_F64 ? P_F64 : P_DF64) : o.true_prec;
+  const double delta = o.delta > 0 ? o.delta : (fp64_class ? 0.0 : 0.1);
   e->delta2 = delta * delta;
   e->ru_every = std::min(8, o.chunk);
   e->budget = budget;
@@ -498,9 +506,13 @@ int lqcd_engine_submit(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field
   if (e->free_slots.empty()) return set_error(LQCD_EBUSY, "no free slot");
   if (e->budget && e->bytes_in_use + need > e->budget)
     return set_error(LQCD_EBUSY, "budget: %zu in use + %zu > %zu", e->bytes_in_use, need, e->budget);
-  // sloppy link copy
+  // sloppy and true-residual link copies
   if (e->sp != P_F64) {
     int rc = lqcd_gauge_add_copy(const_cast<lqcd_gauge*>(gauge), e->sp, e->nr);
+    if (rc != LQCD_OK) return rc;
+  }
+  if (e->tp != P_F64) {
+    int rc = lqcd_gauge_add_copy(const_cast<lqcd_gauge*>(gauge), e->tp, 18);
     if (rc != LQCD_OK) return rc;
   }
   Request q;
@@ -522,11 +534,11 @@ int lqcd_engine_submit(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field
   Request& R = e->reqs[q.id];
   rc = assign_tiles(e, R);
   cudaStream_t st = c->stream;
-  const size_t hb = half_spinor_bytes(P_F64, q.g.Vh);
+  const size_t hb = half_spinor_bytes(e->tp, q.g.Vh);
   Scalars* sc = e->d_sc + R.slot;
   if (rc == LQCD_OK) {
-    cudaError_t err = cudaMemcpyAsync(R.buf.be, src->half[0], hb, cudaMemcpyDeviceToDevice, st);
-    if (err == cudaSuccess) err = cudaMemcpyAsync(R.buf.bo, src->half[1], hb, cudaMemcpyDeviceToDevice, st);
+    cudaError_t err = spinor_convert(src->half[0], P_F64, R.buf.be, e->tp, q.g.Vh, 1.0, st);
+    if (err == cudaSuccess) err = spinor_convert(src->half[1], P_F64, R.buf.bo, e->tp, q.g.Vh, 1.0, st);
     if (err == cudaSuccess) err = cudaMemsetAsync(R.buf.x64, 0, hb, st);
     if (err == cudaSuccess) err = cudaMemsetAsync(R.buf.xs, 0, half_spinor_bytes(e->xp, q.g.Vh), st);
     if (err == cudaSuccess) err = cudaMemsetAsync(sc, 0, sizeof(Scalars), st);
@@ -538,26 +550,26 @@ int lqcd_engine_submit(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field
     w.red = 1;
     w.in = R.buf.be;
     w.fin = FIN_STORE0;
-    cudaError_t err = launch_blas(P_F64, B_NORM, single_launch(w, e->d_partials), 0, st);
+    cudaError_t err = launch_blas(e->tp, B_NORM, single_launch(w, e->d_partials), 0, st);
     w.in = R.buf.bo;
     w.fin = FIN_STORE1;
-    if (err == cudaSuccess) err = launch_blas(P_F64, B_NORM, single_launch(w, e->d_partials), 0, st);
+    if (err == cudaSuccess) err = launch_blas(e->tp, B_NORM, single_launch(w, e->d_partials), 0, st);
     if (err == cudaSuccess) {
       k_slot_init<<<1, 1, 0, st>>>(sc, tol * tol, 24.0 * q.g.Vh, e->opts.maxiter, e->delta2);
       err = cudaGetLastError();
     }
     if (err == cudaSuccess) {
       Work d = slot_work(e, R);
-      const void* U64 = gauge->copy[P_F64][0];
+      const void* U64 = gauge->copy[e->tp][0];
       d.out_par = 0;
-      d.Uout = parity_links(U64, P_F64, 18, q.g.Vh, 0);
-      d.Uin = parity_links(U64, P_F64, 18, q.g.Vh, 1);
+      d.Uout = parity_links(U64, e->tp, 18, q.g.Vh, 0);
+      d.Uin = parity_links(U64, e->tp, 18, q.g.Vh, 1);
       d.in = R.buf.bo;
       d.out = R.buf.bhat;
       d.y1 = R.buf.be;
       d.c1 = 1.0;
       d.a = kappa;
-      err = launch_dslash(P_F64, 18, false, EPI_LIN, single_launch(d, e->d_partials), 0, st);
+      err = launch_dslash(e->tp, 18, false, EPI_LIN, single_launch(d, e->d_partials), 0, st);
     }
     if (err == cudaSuccess) {
       // first true residual and restart (state UPDATE, restart_p = 1)
@@ -667,8 +679,8 @@ int lqcd_engine_result(lqcd_engine* e, long long id, lqcd_field* x, lqcd_solve_i
   if (x) {
     if (x->subset != LQCD_FULL || memcmp(x->g.L, q.g.L, sizeof q.g.L))
       return set_error(LQCD_EINVAL, "x must be a FULL field of the request's lattice");
-    LQCD_CK(spinor_convert(q.buf.x64, P_F64, x->half[0], x->prec, q.g.Vh, 1.0, e->ctx->stream));
-    LQCD_CK(spinor_convert(q.buf.t64, P_F64, x->half[1], x->prec, q.g.Vh, 1.0, e->ctx->stream));
+    LQCD_CK(spinor_convert(q.buf.x64, e->tp, x->half[0], x->prec, q.g.Vh, 1.0, e->ctx->stream));
+    LQCD_CK(spinor_convert(q.buf.t64, e->tp, x->half[1], x->prec, q.g.Vh, 1.0, e->ctx->stream));
   }
   if (info) *info = q.info;
   const int rc = q.info.status;

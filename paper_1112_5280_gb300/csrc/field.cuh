@@ -24,9 +24,63 @@
 
 namespace lqcd {
 
-enum Prec { P_F64 = 0, P_F32 = 1, P_F16 = 2, P_BF16 = 3 };
+// Storage precisions. P_DF64 stores each real as an (hi, lo) pair of floats
+// (8 bytes, like FP64) and computes in double-float arithmetic (below).
+enum Prec { P_F64 = 0, P_F32 = 1, P_F16 = 2, P_BF16 = 3, P_DF64 = 4 };
+constexpr int NPREC = 5;  // number of storage precisions (size of per-precision tables)
 
-__host__ __device__ inline int prec_bytes(int p) { return p == P_F64 ? 8 : (p == P_F32 ? 4 : 2); }
+__host__ __device__ inline int prec_bytes(int p) {
+  return (p == P_F64 || p == P_DF64) ? 8 : (p == P_F32 ? 4 : 2);
+}
+
+// ------------------------------------------------------------------ double-float
+// A real as the unevaluated sum hi + lo of two floats, |lo| <= ulp(hi) / 2, giving
+// a 48-bit significand on the FP32 pipes (GB300's FP64 pipe is a small fraction
+// of its FP32 rate). Addition uses Knuth's error-free two-sum of the high parts
+// plus the low parts; multiplication the FMA error-free product (Dekker's
+// product with the exact residual a*b - round(a*b) from one fused multiply-add).
+// The _rn intrinsics keep the compiler from contracting or reassociating the
+// error-free steps.
+struct df64 {
+  float hi, lo;
+  df64() = default;
+  __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
+  __device__ df64(int v) : hi((float)v), lo(0.0f) {}
+  __device__ df64(float v) : hi(v), lo(0.0f) {}
+  __device__ df64(double v) {
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(v - (double)hi);
+  }
+  __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ df64 df_renorm(float s, float e) {  // s + e -> (hi, lo)
+  const float h = __fadd_rn(s, e);
+  return df64(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float v = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return df_renorm(s, e);
+}
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return df_renorm(p, e);
+}
+__device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = a + b; }
+__device__ __forceinline__ df64& operator-=(df64& a, df64 b) { return a = a - b; }
+__device__ __forceinline__ df64& operator*=(df64& a, df64 b) { return a = a * b; }
+// small integer factors (the +-1 of spin projections) without a full product
+__device__ __forceinline__ df64 operator*(int s, df64 a) {
+  return s == 1 ? a : (s == -1 ? -a : df64(s) * a);
+}
+__device__ __forceinline__ bool isfinite_df(df64 a) { return isfinite(a.hi); }
 
 // Device order of the 24 reals of a spinor: colour-major, so that the 8 reals
 // (4 spin x re/im) of one colour are contiguous words:
@@ -215,6 +269,37 @@ struct SpinorIO<P_F32> {
   }
 };
 
+template <>
+struct SpinorIO<P_DF64> {
+  using Real = df64;
+  static constexpr int CHUNKS = 12;
+  using Word = float4;
+  static constexpr int NW = 12;
+  __device__ static void load_raw(const void* base, int Vh, int h, Word w[NW]) {
+    const float4* p = reinterpret_cast<const float4*>(base) + h;
+#pragma unroll
+    for (int c = 0; c < NW; ++c) w[c] = ld_ro(p + (size_t)c * Vh);
+  }
+  __device__ static void unpack(const Word w[NW], df64 v[24]) {
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+      v[2 * c] = df64(w[c].x, w[c].y);
+      v[2 * c + 1] = df64(w[c].z, w[c].w);
+    }
+  }
+  __device__ static void load(const void* base, int Vh, int h, df64 v[24]) {
+    Word w[NW];
+    load_raw(base, Vh, h, w);
+    unpack(w, v);
+  }
+  __device__ static void store(void* base, int Vh, int h, const df64 v[24]) {
+    float4* p = reinterpret_cast<float4*>(base) + h;
+#pragma unroll
+    for (int c = 0; c < NW; ++c)
+      p[(size_t)c * Vh] = make_float4(v[2 * c].hi, v[2 * c].lo, v[2 * c + 1].hi, v[2 * c + 1].lo);
+  }
+};
+
 template <bool BF>
 struct SpinorIO16 {
   using Real = float;
@@ -304,6 +389,30 @@ struct LinkIO<P_F64, NR> {
     }
   }
   __device__ static void load(const void* base_mu, int Vh, int h, double u[18]) {
+    Word w[NW];
+    load_raw(base_mu, Vh, h, w);
+    unpack(w, u);
+  }
+};
+
+template <int NR>
+struct LinkIO<P_DF64, NR> {
+  using Real = df64;
+  using Word = float4;
+  static constexpr int NW = NR / 2;
+  __device__ static void load_raw(const void* base_mu, int Vh, int h, Word w[NW]) {
+    const float4* p = reinterpret_cast<const float4*>(base_mu) + h;
+#pragma unroll
+    for (int c = 0; c < NW; ++c) w[c] = ld_stream(p + (size_t)c * Vh);
+  }
+  __device__ static void unpack(const Word w[NW], df64 u[18]) {
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+      u[2 * c] = df64(w[c].x, w[c].y);
+      u[2 * c + 1] = df64(w[c].z, w[c].w);
+    }
+  }
+  __device__ static void load(const void* base_mu, int Vh, int h, df64 u[18]) {
     Word w[NW];
     load_raw(base_mu, Vh, h, w);
     unpack(w, u);

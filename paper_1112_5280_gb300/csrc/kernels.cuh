@@ -14,7 +14,11 @@ enum Epi { EPI_LIN = 0, EPI_CG = 1 };
 #ifndef LQCD_DSLASH_MIN_BLOCKS
 #define LQCD_DSLASH_MIN_BLOCKS 6
 #endif
-constexpr int DSLASH_MIN_BLOCKS = LQCD_DSLASH_MIN_BLOCKS;
+// Double-float needs the full 255 registers per thread (4 CTAs of 64 threads).
+template <int SP>
+struct DslashMinBlocks {
+  static constexpr int value = (SP == P_DF64) ? 4 : LQCD_DSLASH_MIN_BLOCKS;
+};
 
 template <typename R>
 __device__ __forceinline__ double site_norm2(const R v[24]) {
@@ -37,11 +41,25 @@ __device__ __forceinline__ void site_dot(const R a[24], const R b[24], double& r
   im = (double)si;
 }
 
-// Storage of the sloppy solution accumulator: FP64 for an FP64 solve, else FP32.
+// Storage of the sloppy solution accumulator: that of an FP64-class solve, else FP32.
 template <int SP>
 struct XSloppy {
-  static constexpr int P = (SP == P_F64) ? P_F64 : P_F32;
+  static constexpr int P = (SP == P_F64 || SP == P_DF64) ? SP : P_F32;
 };
+
+// Conversions between the arithmetic types (double-float -> float rounds hi + lo).
+template <typename To>
+__device__ __forceinline__ To cvt(float x) { return To(x); }
+template <typename To>
+__device__ __forceinline__ To cvt(double x) { return To(x); }
+template <typename To>
+__device__ __forceinline__ To cvt(df64 x) { return To(x); }
+template <>
+__device__ __forceinline__ float cvt<float>(df64 x) { return __fadd_rn(x.hi, x.lo); }
+template <>
+__device__ __forceinline__ double cvt<double>(df64 x) { return (double)x; }
+template <>
+__device__ __forceinline__ df64 cvt<df64>(df64 x) { return x; }
 
 // Whole-CTA exit for a single-slot launch whose slot does not run.
 __device__ __forceinline__ bool single_slot_idle(const Launch& L) {
@@ -52,7 +70,7 @@ __device__ __forceinline__ bool single_slot_idle(const Launch& L) {
 //                 r -= alpha (y1 + a * D in); x += alpha p      (EPI_CG, CG step)
 // with the Work's reduction (norm / dots) and scalar finisher per slot.
 template <int SP, int LP, int NR, bool DAG, int EPI>
-__global__ void __launch_bounds__(TILE, DSLASH_MIN_BLOCKS) k_dslash(const Launch L) {
+__global__ void __launch_bounds__(TILE, DslashMinBlocks<SP>::value) k_dslash(const Launch L) {
   using R = typename SpinorIO<SP>::Real;
   if (single_slot_idle(L)) return;
   for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
@@ -132,21 +150,6 @@ enum Blas {
   B_FOLD64,       // x64(out) += a * xs(in) (SP) ; xs = 0
 };
 
-template <int P>
-__device__ __forceinline__ void load_d(const void* base, int Vh, int h, double v[24]) {
-  typename SpinorIO<P>::Real t[24];
-  SpinorIO<P>::load(base, Vh, h, t);
-#pragma unroll
-  for (int i = 0; i < 24; ++i) v[i] = (double)t[i];
-}
-template <int P>
-__device__ __forceinline__ void store_d(void* base, int Vh, int h, const double v[24]) {
-  typename SpinorIO<P>::Real t[24];
-#pragma unroll
-  for (int i = 0; i < 24; ++i) t[i] = (typename SpinorIO<P>::Real)v[i];
-  SpinorIO<P>::store(base, Vh, h, t);
-}
-
 // out = x + c * y (complex c)
 template <typename R>
 __device__ __forceinline__ void caxpy(R* out, const R* x, R cr, R ci, const R* y) {
@@ -158,9 +161,12 @@ __device__ __forceinline__ void caxpy(R* out, const R* x, R cr, R ci, const R* y
   }
 }
 
-template <int SP, int OP>
+// SP: precision of the sloppy / operated vectors; TP: precision of the
+// FP64-class vectors (true residual, solution accumulator) in the mixed ops.
+template <int SP, int OP, int TP = P_F64>
 __global__ void __launch_bounds__(TILE) k_blas(const Launch L) {
   using R = typename SpinorIO<SP>::Real;
+  using TR = typename SpinorIO<TP>::Real;
   if (single_slot_idle(L)) return;
   for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
     int slot, start;
@@ -179,26 +185,28 @@ __global__ void __launch_bounds__(TILE) k_blas(const Launch L) {
 #pragma unroll
         for (int i = 0; i < 24; ++i) p[i] = r[i] + beta * p[i];
         SpinorIO<SP>::store(w.out, Vh, h, p);
-      } else if (OP == B_RU_FOLD || OP == B_FOLD64) {
-        const double sg = (OP == B_RU_FOLD) ? w.sc->sigma : w.a;
-        double x[24], xs[24];
-        load_d<P_F64>(w.out, Vh, h, x);
-        load_d<SP>(w.in, Vh, h, xs);
+      } else if (OP == B_RU_FOLD || OP == B_FOLD64) {  // x (TP) += sigma * xs (SP); xs = 0
+        const TR sg = TR((OP == B_RU_FOLD) ? w.sc->sigma : w.a);
+        TR x[24];
+        R xs[24];
+        SpinorIO<TP>::load(w.out, Vh, h, x);
+        SpinorIO<SP>::load(w.in, Vh, h, xs);
 #pragma unroll
         for (int i = 0; i < 24; ++i) {
-          x[i] += sg * xs[i];
-          xs[i] = 0.0;
+          x[i] += sg * cvt<TR>(xs[i]);
+          xs[i] = R(0);
         }
-        store_d<P_F64>(w.out, Vh, h, x);
-        store_d<SP>(const_cast<void*>(w.in), Vh, h, xs);
-      } else if (OP == B_RU_CONVERT) {
-        const double inv = w.sc->res[5], pc = w.sc->res[4];
+        SpinorIO<TP>::store(w.out, Vh, h, x);
+        SpinorIO<SP>::store(const_cast<void*>(w.in), Vh, h, xs);
+      } else if (OP == B_RU_CONVERT) {  // r (SP) = rho (TP) / sigma; p = restart ? r : r + c p
+        const TR inv = TR(w.sc->res[5]);
+        const double pc = w.sc->res[4];
         const int restart = w.sc->restart_p;
-        double rho[24];
-        load_d<P_F64>(w.in, Vh, h, rho);
+        TR rho[24];
+        SpinorIO<TP>::load(w.in, Vh, h, rho);
         R r[24];
 #pragma unroll
-        for (int i = 0; i < 24; ++i) r[i] = (R)(rho[i] * inv);
+        for (int i = 0; i < 24; ++i) r[i] = cvt<R>(rho[i] * inv);
         SpinorIO<SP>::store(w.out, Vh, h, r);
         R p[24];
         if (restart) {
@@ -214,21 +222,23 @@ __global__ void __launch_bounds__(TILE) k_blas(const Launch L) {
         R v[24];
         SpinorIO<SP>::load(w.in, Vh, h, v);
         v0 = site_norm2(v);
-      } else if (OP == B_AXPBY) {
-        double v[24];
-        load_d<P_F64>(w.in, Vh, h, v);
-        const double a = w.a;
+      } else if (OP == B_AXPBY) {  // out (SP) = a * in (TP) [+ c1 * y1 (SP)]
+        TR v[24];
+        SpinorIO<TP>::load(w.in, Vh, h, v);
+        const TR a = TR(w.a);
+        R o[24];
         if (w.y1) {
-          double y[24];
-          load_d<SP>(w.y1, Vh, h, y);
+          R y[24];
+          SpinorIO<SP>::load(w.y1, Vh, h, y);
+          const TR c1 = TR(w.c1);
 #pragma unroll
-          for (int i = 0; i < 24; ++i) v[i] = a * v[i] + w.c1 * y[i];
+          for (int i = 0; i < 24; ++i) o[i] = cvt<R>(a * v[i] + c1 * cvt<TR>(y[i]));
         } else {
 #pragma unroll
-          for (int i = 0; i < 24; ++i) v[i] = a * v[i];
+          for (int i = 0; i < 24; ++i) o[i] = cvt<R>(a * v[i]);
         }
-        store_d<SP>(w.out, Vh, h, v);
-        if (w.red == 1) v0 = site_norm2(v);
+        SpinorIO<SP>::store(w.out, Vh, h, o);
+        if (w.red == 1) v0 = site_norm2(o);
       } else if (OP == B_ZERO) {
         R v[24];
 #pragma unroll

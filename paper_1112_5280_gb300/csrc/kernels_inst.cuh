@@ -10,7 +10,7 @@ namespace lqcd {
 
 namespace {
 constexpr int SPX = LQCD_SP;
-constexpr int LPX = (SPX == P_F64) ? P_F64 : (SPX == P_F32 ? P_F32 : P_F16);
+constexpr int LPX = (SPX == P_F64 || SPX == P_DF64 || SPX == P_F32) ? SPX : P_F16;
 
 template <int NR, bool DAG, int EPI>
 cudaError_t go_dslash(const Launch& L, int grid, cudaStream_t s) {
@@ -21,9 +21,9 @@ cudaError_t go_dslash(const Launch& L, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int OP, int P>
+template <int OP, int P, int TP = P_F64>
 cudaError_t go_blas(const Launch& L, int grid, cudaStream_t s) {
-  auto fn = k_blas<P, OP>;
+  auto fn = k_blas<P, OP, TP>;
   if (L.ntiles <= 0) return cudaSuccess;
   if (grid <= 0) grid = grid_for((const void*)fn, L.ntiles, 1, TILE);
   fn<<<grid, TILE, 0, s>>>(L);
@@ -45,19 +45,27 @@ cudaError_t LQCD_CAT(launch_dslash_, LQCD_SFX)(int nr, bool dag, int epi, const 
   return cudaErrorInvalidValue;
 }
 
-cudaError_t LQCD_CAT(launch_blas_, LQCD_SFX)(int op, const Launch& L, int grid, cudaStream_t s) {
+cudaError_t LQCD_CAT(launch_blas_, LQCD_SFX)(int op, int tp, const Launch& L, int grid,
+                                              cudaStream_t s) {
+  const bool df = (tp == P_DF64);
   switch (op) {
     case B_CG_P: return go_blas<B_CG_P, SPX>(L, grid, s);
-    case B_RU_CONVERT: return go_blas<B_RU_CONVERT, SPX>(L, grid, s);
     case B_NORM: return go_blas<B_NORM, SPX>(L, grid, s);
-    case B_AXPBY: return go_blas<B_AXPBY, SPX>(L, grid, s);
     case B_ZERO: return go_blas<B_ZERO, SPX>(L, grid, s);
     case B_BICG_P: return go_blas<B_BICG_P, SPX>(L, grid, s);
     case B_BICG_S: return go_blas<B_BICG_S, SPX>(L, grid, s);
     case B_BICG_X: return go_blas<B_BICG_X, SPX>(L, grid, s);
-    case B_FOLD64: return go_blas<B_FOLD64, SPX>(L, grid, s);
+    case B_RU_CONVERT:
+      return df ? go_blas<B_RU_CONVERT, SPX, P_DF64>(L, grid, s) : go_blas<B_RU_CONVERT, SPX, P_F64>(L, grid, s);
+    case B_AXPBY:
+      return df ? go_blas<B_AXPBY, SPX, P_DF64>(L, grid, s) : go_blas<B_AXPBY, SPX, P_F64>(L, grid, s);
+    case B_FOLD64:
     case B_RU_FOLD:
-      if (SPX == P_F64 || SPX == P_F32) return go_blas<B_RU_FOLD, SPX>(L, grid, s);
+      if (SPX == P_F64 || SPX == P_F32 || SPX == P_DF64) {
+        if (op == B_FOLD64)
+          return df ? go_blas<B_FOLD64, SPX, P_DF64>(L, grid, s) : go_blas<B_FOLD64, SPX, P_F64>(L, grid, s);
+        return df ? go_blas<B_RU_FOLD, SPX, P_DF64>(L, grid, s) : go_blas<B_RU_FOLD, SPX, P_F64>(L, grid, s);
+      }
       return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }

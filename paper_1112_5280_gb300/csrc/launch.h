@@ -9,22 +9,24 @@
 namespace lqcd {
 
 // Link storage precision paired with a spinor precision.
-inline int link_prec_for(int sp) { return sp == P_F64 ? P_F64 : (sp == P_F32 ? P_F32 : P_F16); }
+inline int link_prec_for(int sp) { return (sp == P_F64 || sp == P_F32 || sp == P_DF64) ? sp : P_F16; }
 
 // grid <= 0: persistent grid from the occupancy of the kernel (tuned multiplier).
 cudaError_t launch_dslash(int sp, int nr, bool dag, int epi, const Launch& L, int grid,
                           cudaStream_t s);
-cudaError_t launch_blas(int sp, int op, const Launch& L, int grid, cudaStream_t s);
+// tp: precision of the FP64-class operand of the mixed ops (P_F64 or P_DF64)
+cudaError_t launch_blas(int sp, int op, const Launch& L, int grid, cudaStream_t s, int tp = P_F64);
 
 // per precision
 #define LQCD_DECL(SFX)                                                                     \
   cudaError_t launch_dslash_##SFX(int nr, bool dag, int epi, const Launch& L, int grid,   \
                                   cudaStream_t s);                                         \
-  cudaError_t launch_blas_##SFX(int op, const Launch& L, int grid, cudaStream_t s);
+  cudaError_t launch_blas_##SFX(int op, int tp, const Launch& L, int grid, cudaStream_t s);
 LQCD_DECL(f64)
 LQCD_DECL(f32)
 LQCD_DECL(f16)
 LQCD_DECL(bf16)
+LQCD_DECL(df64)
 #undef LQCD_DECL
 
 // Number of SMs of the current device and the persistent-grid multiplier.

@@ -25,8 +25,19 @@ __device__ __forceinline__ void st_real<P_BF16>(void* b, size_t i, double v) {
   ((__nv_bfloat16*)b)[i] = __double2bfloat16(v);
 }
 
+template <>
+__device__ __forceinline__ void st_real<P_DF64>(void* b, size_t i, double v) {
+  const float hi = __double2float_rn(v);
+  ((float*)b)[2 * i] = hi;
+  ((float*)b)[2 * i + 1] = __double2float_rn(v - (double)hi);
+}
+
 template <int P>
 __device__ __forceinline__ double ld_real(const void* base, size_t i);
+template <>
+__device__ __forceinline__ double ld_real<P_DF64>(const void* b, size_t i) {
+  return (double)((const float*)b)[2 * i] + (double)((const float*)b)[2 * i + 1];
+}
 template <>
 __device__ __forceinline__ double ld_real<P_F64>(const void* b, size_t i) { return ((const double*)b)[i]; }
 template <>
@@ -39,7 +50,9 @@ __device__ __forceinline__ double ld_real<P_BF16>(const void* b, size_t i) {
 }
 
 // reals per storage word
-__host__ __device__ inline int link_word(int p, int nr) { return p == P_F64 ? 2 : (nr == 18 ? 2 : 4); }
+__host__ __device__ inline int link_word(int p, int nr) {
+  return (p == P_F64 || p == P_DF64) ? 2 : (nr == 18 ? 2 : 4);
+}
 __host__ __device__ inline int spinor_word(int p) { return 16 / prec_bytes(p); }
 
 // offset (in reals) of real k of link (parity, mu, h)
@@ -120,6 +133,8 @@ cudaError_t gauge_from_aos(const double* d_aos, const Geom& g, int prec, int nr,
                                      : go_gauge_from_aos<P_F32, 18>(d_aos, g, d_out, s);
   if (prec == P_F16) return nr == 12 ? go_gauge_from_aos<P_F16, 12>(d_aos, g, d_out, s)
                                      : go_gauge_from_aos<P_F16, 18>(d_aos, g, d_out, s);
+  if (prec == P_DF64) return nr == 12 ? go_gauge_from_aos<P_DF64, 12>(d_aos, g, d_out, s)
+                                      : go_gauge_from_aos<P_DF64, 18>(d_aos, g, d_out, s);
   return cudaErrorInvalidValue;
 }
 
@@ -131,6 +146,8 @@ cudaError_t gauge_convert(const void* d64, const Geom& g, int prec, int nr, void
                                      : go_gauge_convert<P_F32, 18>(d64, g, d_out, s);
   if (prec == P_F16) return nr == 12 ? go_gauge_convert<P_F16, 12>(d64, g, d_out, s)
                                      : go_gauge_convert<P_F16, 18>(d64, g, d_out, s);
+  if (prec == P_DF64) return nr == 12 ? go_gauge_convert<P_DF64, 12>(d64, g, d_out, s)
+                                      : go_gauge_convert<P_DF64, 18>(d64, g, d_out, s);
   return cudaErrorInvalidValue;
 }
 
@@ -188,6 +205,7 @@ cudaError_t spinor_from_aos(const double* d_aos, const Geom& g, int prec, void* 
     case P_F32: return go_from_aos<P_F32>(d_aos, g, d_even, d_odd, s);
     case P_F16: return go_from_aos<P_F16>(d_aos, g, d_even, d_odd, s);
     case P_BF16: return go_from_aos<P_BF16>(d_aos, g, d_even, d_odd, s);
+    case P_DF64: return go_from_aos<P_DF64>(d_aos, g, d_even, d_odd, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -199,6 +217,7 @@ cudaError_t spinor_to_aos(const void* d_even, const void* d_odd, const Geom& g, 
     case P_F32: return go_to_aos<P_F32>(d_even, d_odd, g, d_aos, s);
     case P_F16: return go_to_aos<P_F16>(d_even, d_odd, g, d_aos, s);
     case P_BF16: return go_to_aos<P_BF16>(d_even, d_odd, g, d_aos, s);
+    case P_DF64: return go_to_aos<P_DF64>(d_even, d_odd, g, d_aos, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -213,6 +232,7 @@ static cudaError_t go_convert_in(const void* in, void* out, int pout, int Vh, do
     case P_F32: k_spinor_convert<PI, P_F32><<<nb, 256, 0, s>>>(in, out, Vh, sc); break;
     case P_F16: k_spinor_convert<PI, P_F16><<<nb, 256, 0, s>>>(in, out, Vh, sc); break;
     case P_BF16: k_spinor_convert<PI, P_BF16><<<nb, 256, 0, s>>>(in, out, Vh, sc); break;
+    case P_DF64: k_spinor_convert<PI, P_DF64><<<nb, 256, 0, s>>>(in, out, Vh, sc); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -225,6 +245,7 @@ cudaError_t spinor_convert(const void* in, int pin, void* out, int pout, int Vh,
     case P_F32: return go_convert_in<P_F32>(in, out, pout, Vh, scale, s);
     case P_F16: return go_convert_in<P_F16>(in, out, pout, Vh, scale, s);
     case P_BF16: return go_convert_in<P_BF16>(in, out, pout, Vh, scale, s);
+    case P_DF64: return go_convert_in<P_DF64>(in, out, pout, Vh, scale, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -238,16 +259,18 @@ cudaError_t launch_dslash(int sp, int nr, bool dag, int epi, const Launch& L, in
     case P_F32: return launch_dslash_f32(nr, dag, epi, L, grid, s);
     case P_F16: return launch_dslash_f16(nr, dag, epi, L, grid, s);
     case P_BF16: return launch_dslash_bf16(nr, dag, epi, L, grid, s);
+    case P_DF64: return launch_dslash_df64(nr, dag, epi, L, grid, s);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_blas(int sp, int op, const Launch& L, int grid, cudaStream_t s) {
+cudaError_t launch_blas(int sp, int op, const Launch& L, int grid, cudaStream_t s, int tp) {
   switch (sp) {
-    case P_F64: return launch_blas_f64(op, L, grid, s);
-    case P_F32: return launch_blas_f32(op, L, grid, s);
-    case P_F16: return launch_blas_f16(op, L, grid, s);
-    case P_BF16: return launch_blas_bf16(op, L, grid, s);
+    case P_F64: return launch_blas_f64(op, tp, L, grid, s);
+    case P_F32: return launch_blas_f32(op, tp, L, grid, s);
+    case P_F16: return launch_blas_f16(op, tp, L, grid, s);
+    case P_BF16: return launch_blas_bf16(op, tp, L, grid, s);
+    case P_DF64: return launch_blas_df64(op, tp, L, grid, s);
   }
   return cudaErrorInvalidValue;
 }

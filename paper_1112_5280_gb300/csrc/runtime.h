@@ -34,7 +34,7 @@ struct lqcd_gauge {
   lqcd::Geom g{};
   int prec = 0;
   int compress = 18;
-  void* copy[4][2] = {};  // [link precision][compress == 12]
+  void* copy[lqcd::NPREC][2] = {};  // [link precision][compress == 12]
   size_t bytes = 0;
 };
 
@@ -85,3 +85,7 @@ Launch single_launch(const Work& w, double* partials);
 Work blank_work(const Geom& g);
 
 }  // namespace lqcd
+
+static_assert(LQCD_DF64 == lqcd::P_DF64 && LQCD_BF16 == lqcd::P_BF16 && LQCD_F16 == lqcd::P_F16 &&
+                  LQCD_F32 == lqcd::P_F32 && LQCD_F64 == lqcd::P_F64 && lqcd::NPREC == LQCD_DF64 + 1,
+              "public precision codes index the per-precision tables");

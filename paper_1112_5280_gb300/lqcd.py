@@ -16,11 +16,11 @@ import numpy as np
 from . import build as _build
 
 OK, EINVAL, ENOMEM, ENOCONV, EBREAKDOWN, ENONFINITE, ETIMEOUT, ECUDA, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7, -8
-F64, F32, F16, BF16 = 0, 1, 2, 3
+F64, F32, F16, BF16, DF64 = 0, 1, 2, 3, 4
 EVEN, ODD, FULL = 0, 1, 2
 CG, BICGSTAB = 0, 1
 
-PRECISIONS = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
+PRECISIONS = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "df64": DF64}
 
 
 class LqcdError(RuntimeError):
@@ -32,7 +32,7 @@ class LqcdError(RuntimeError):
 class SolveOpts(C.Structure):
     _fields_ = [("solver", C.c_int), ("sloppy_prec", C.c_int), ("sloppy_compress", C.c_int),
                 ("maxiter", C.c_int), ("delta", C.c_double), ("chunk", C.c_int),
-                ("use_graph", C.c_int)]
+                ("use_graph", C.c_int), ("true_prec", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -349,7 +349,7 @@ def solve_opts(**kw) -> SolveOpts:
     o = SolveOpts()
     load().lqcd_solve_opts_default(C.byref(o))
     for k, v in kw.items():
-        if k in ("sloppy_prec",):
+        if k in ("sloppy_prec", "true_prec") and isinstance(v, str):
             v = _prec(v)
         setattr(o, k, v)
     return o

@@ -1,5 +1,8 @@
 """GPU parity of the even-odd Wilson Dslash, Mhat and M against the FP64 oracle.
 
+DF64 (double-float storage and arithmetic, 48-bit significand) is held to the
+FP64 bar.
+
 Paper Section 3: the even-odd preconditioned hopping term "dslash" is the hot
 kernel. Every precision / compression / dagger / parity combination is
 compared element by element with the oracle on the same seeded inputs.
@@ -15,7 +18,7 @@ from paper_1112_5280_gb300 import lqcd, synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-5, "f16": 4e-3, "bf16": 3e-2}
+TOL = {"f64": 1e-12, "df64": 1e-12, "f32": 1e-5, "f16": 4e-3, "bf16": 3e-2}
 
 
 @pytest.fixture(scope="module")
@@ -40,7 +43,7 @@ LATTICES = [(6, 6, 4, 10), (2, 2, 2, 2), (4, 4, 4, 4), (2, 4, 6, 4)]
 
 
 @pytest.mark.parametrize("dims", LATTICES)
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32", "f16", "bf16"])
 @pytest.mark.parametrize("compress", [18, 12])
 def test_dslash_eo_parity(ctx, dims, prec, compress):
     U = synth.random_links(dims, 0.5, seed=1001)
@@ -72,7 +75,7 @@ def test_dslash_boundary_conditions(ctx, t_bc):
     assert _rel_err(got, ref) < 1e-12
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32"])
 def test_apply_M_and_Mhat(ctx, prec):
     dims = (6, 4, 4, 6)
     kappa = 0.15
@@ -162,7 +165,7 @@ def test_invalid_arguments_fail_loudly(ctx):
         lqcd.dslash_eo(g, fe, fo, 0)  # input must hold the odd parity
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32", "f16"])
 def test_dslash_sampled_sites_16x32(ctx, prec):
     """Benchmark workload shape (16^3 x 32, eps = 0.5): sampled output sites vs the oracle."""
     dims = (16, 16, 16, 32)
@@ -198,7 +201,7 @@ def test_objects_outlive_context_handle():
     g.close()
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32", "f16"])
 @pytest.mark.parametrize("same_size", [False, True])
 def test_dslash_batch_matches_oracle(ctx, prec, same_size):
     """n independent applications in one launch (mixed lattice sizes, or equal sizes in the

@@ -45,6 +45,22 @@ def test_cg_fp64_small_workload(ctx):
     _solve_check(ctx, (4, 4, 4, 4), 0.3, 0.12, "f64", compress=18)
 
 
+def test_cg_df64(ctx):
+    """CG entirely in double-float (storage and arithmetic)."""
+    _solve_check(ctx, (6, 4, 4, 6), 0.5, 0.15, "df64", compress=18)
+
+
+@pytest.mark.parametrize("true_prec", ["f64", "df64"])
+def test_mixed_true_residual_precision(ctx, true_prec):
+    """The FP64-class outer correction in native FP64 or in double-float reaches the same bar."""
+    dims = (6, 4, 4, 6)
+    U = synth.random_links(dims, 0.5, seed=1001)
+    b = synth.gaussian_spinor(dims, seed=2002)
+    g = ctx.gauge(dims, U, prec="f64")
+    x, info = lqcd.solve(g, b, 0.15, 1e-10, lqcd.solve_opts(sloppy_prec="f16", true_prec=true_prec))
+    assert info["status"] == 0 and oracle.true_residual(dims, U, 0.15, b, x) <= 1e-10
+
+
 @pytest.mark.parametrize("prec,compress", [("f32", 18), ("f32", 12), ("f16", 12), ("bf16", 12),
                                            ("f16", 18)])
 def test_cg_mixed_precision(ctx, prec, compress):
@@ -52,7 +68,7 @@ def test_cg_mixed_precision(ctx, prec, compress):
     _solve_check(ctx, (6, 4, 4, 6), 0.5, 0.15, prec, compress)
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32"])
 def test_bicgstab(ctx, prec):
     _solve_check(ctx, (6, 4, 4, 6), 0.5, 0.15, prec, 12, solver=lqcd.BICGSTAB)
     _solve_check(ctx, (4, 4, 4, 4), 0.3, 0.12, prec, 18, solver=lqcd.BICGSTAB)
