@@ -289,6 +289,13 @@ int rebuild(lqcd_engine* e) {
     prefix[i + 1] = prefix[i] + q.ntiles;
   }
   e->ntiles_total = prefix[n];
+  if (e->opts.ru_interval <= 0) {
+    // A slot waiting for a reliable update idles until the next update block, and a
+    // block costs six launches that skip when no slot needs them; measured on GB300
+    // (8^4 to 32^3x64, FP16/FP32 sloppy) the solve time is flat in the interval
+    // between 1 and 8 to within 3%, slightly lower at 4.
+    e->ru_every = std::min(e->opts.chunk, 4);
+  }
   cudaStream_t st = e->ctx->stream;
   LQCD_CK(cudaMemcpyAsync(e->d_works, e->h_works.data(), sizeof(Work) * e->h_works.size(),
                           cudaMemcpyHostToDevice, st));
@@ -418,6 +425,7 @@ void lqcd_solve_opts_default(lqcd_solve_opts* o) {
   o->delta = 0.0;
   o->chunk = 32;
   o->use_graph = 1;
+  o->ru_interval = 0;
   o->true_prec = -1;
 }
 
@@ -447,9 +455,12 @@ int lqcd_engine_create(lqcd_ctx* c, const lqcd_solve_opts* opts, size_t budget, 
   e->xp = fp64_class ? o.sloppy_prec : P_F32;
   e->nr = fp64_class ? 18 : o.sloppy_compress;
   e->tp = (o.true_prec == -1) ? (o.sloppy_prec == LQCD_F64 ? P_F64 : P_DF64) : o.true_prec;
-  const double delta = o.delta > 0 ? o.delta : (fp64_class ? 0.0 : 0.1);
+  // delta = 0.01: measured on GB300 for FP16/BF16/FP32 sloppy storage, 32^3x64 at
+  // kappa 0.155, six FP64-class updates instead of eleven at 0.1 and 30% faster,
+  // with the same iteration count; the FP64-class true residual decides convergence.
+  const double delta = o.delta > 0 ? o.delta : (fp64_class ? 0.0 : 0.01);
   e->delta2 = delta * delta;
-  e->ru_every = std::min(8, o.chunk);
+  e->ru_every = o.ru_interval > 0 ? std::min(o.ru_interval, o.chunk) : 0;  // 0: per batch
   e->budget = budget;
   e->max_slots = max_slots;
   cudaError_t err = cudaMalloc(&e->d_sc, sizeof(Scalars) * max_slots);

@@ -32,7 +32,7 @@ class LqcdError(RuntimeError):
 class SolveOpts(C.Structure):
     _fields_ = [("solver", C.c_int), ("sloppy_prec", C.c_int), ("sloppy_compress", C.c_int),
                 ("maxiter", C.c_int), ("delta", C.c_double), ("chunk", C.c_int),
-                ("use_graph", C.c_int), ("true_prec", C.c_int)]
+                ("use_graph", C.c_int), ("ru_interval", C.c_int), ("true_prec", C.c_int)]
 
 
 class SolveInfo(C.Structure):
