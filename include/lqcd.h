@@ -269,6 +269,9 @@ LQCD_API void lqcd_engine_destroy(lqcd_engine* e);
 /* Caps the persistent grid of batched kernel family (0 Dslash, 1 BLAS) at
  * mult CTAs per SM (0: occupancy limit). */
 LQCD_API void lqcd_set_grid_multiplier(int family, int mult);
+/* Dslash kernel form for LQCD_DF64 fields: 0 = one thread per output site, 1 = three
+ * threads per site, one per output colour (default). Results agree to rounding. */
+LQCD_API int lqcd_set_dslash_form(int prec, int form);
 
 #ifdef __cplusplus
 }

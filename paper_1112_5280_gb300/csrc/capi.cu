@@ -228,6 +228,14 @@ long long lqcd_ctx_launch_count(const lqcd_ctx* c) { return c ? c->launches : 0;
 
 void lqcd_set_grid_multiplier(int family, int mult) { set_grid_multiplier(family, mult); }
 
+int lqcd_set_dslash_form(int prec, int form) {
+  clear_error();
+  if (prec != LQCD_DF64 || (form != 0 && form != 1))
+    return set_error(LQCD_EINVAL, "the Dslash form is selectable for LQCD_DF64 only (0 site, 1 colour split)");
+  set_dslash_colour_split(prec, form == 1);
+  return LQCD_OK;
+}
+
 
 
 // ------------------------------------------------------------------ gauge

@@ -275,6 +275,21 @@ struct SpinorIO<P_DF64> {
   static constexpr int CHUNKS = 12;
   using Word = float4;
   static constexpr int NW = 12;
+  // the 8 reals of colour a (colour-major order): words 4a .. 4a+3
+  __device__ static void load_colour(const void* base, int Vh, int h, int a, df64 v[8]) {
+    const float4* p = reinterpret_cast<const float4*>(base) + h + (size_t)(4 * a) * Vh;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float4 d = ld_ro(p + (size_t)c * Vh);
+      v[2 * c] = df64(d.x, d.y);
+      v[2 * c + 1] = df64(d.z, d.w);
+    }
+  }
+  __device__ static void store_colour(void* base, int Vh, int h, int a, const df64 v[8]) {
+    float4* p = reinterpret_cast<float4*>(base) + h + (size_t)(4 * a) * Vh;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) p[(size_t)c * Vh] = make_float4(v[2 * c].hi, v[2 * c].lo, v[2 * c + 1].hi, v[2 * c + 1].lo);
+  }
   __device__ static void load_raw(const void* base, int Vh, int h, Word w[NW]) {
     const float4* p = reinterpret_cast<const float4*>(base) + h;
 #pragma unroll

@@ -135,6 +135,102 @@ __global__ void __launch_bounds__(TILE, DslashMinBlocks<SP>::value) k_dslash(con
   }
 }
 
+// Colour-split batched Dslash for 18-real links: 3 * TILE threads per CTA, threads
+// [c * TILE, (c + 1) * TILE) compute colour c of the tile's TILE sites. Same epilogues,
+// reductions and finishers as k_dslash (colour-local pieces of each site).
+template <typename R>
+__device__ __forceinline__ double colour_norm2(const R v[8]) {
+  R s = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += v[i] * v[i];
+  return (double)s;
+}
+template <typename R>
+__device__ __forceinline__ void colour_dot(const R a[8], const R b[8], double& re, double& im) {
+  R sr = 0, si = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    sr += a[2 * i] * b[2 * i] + a[2 * i + 1] * b[2 * i + 1];
+    si += a[2 * i] * b[2 * i + 1] - a[2 * i + 1] * b[2 * i];
+  }
+  re = (double)sr;
+  im = (double)si;
+}
+
+#ifndef LQCD_DSLASH3_MIN_BLOCKS
+#define LQCD_DSLASH3_MIN_BLOCKS 4
+#endif
+template <int SP, int LP, bool DAG, int EPI>
+__global__ void __launch_bounds__(3 * TILE, LQCD_DSLASH3_MIN_BLOCKS) k_dslash3(const Launch L) {
+  using R = typename SpinorIO<SP>::Real;
+  if (single_slot_idle(L)) return;
+  const int col = threadIdx.x / TILE;
+  const int j = threadIdx.x - col * TILE;
+  for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
+    int slot, start;
+    tile_of(L, tile, slot, start);
+    const Work& w = work_of(L, slot);
+    if (!slot_runs(w)) continue;
+    const int h = start + j;
+    const int Vh = w.g.Vh;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+    if (h < Vh) {
+      R acc[8];
+      if (col == 0) dslash_site3<SP, LP, DAG, 0>(w.g, h, w.out_par, w.in, w.Uout, w.Uin, acc);
+      else if (col == 1) dslash_site3<SP, LP, DAG, 1>(w.g, h, w.out_par, w.in, w.Uout, w.Uin, acc);
+      else dslash_site3<SP, LP, DAG, 2>(w.g, h, w.out_par, w.in, w.Uout, w.Uin, acc);
+      const R a = (R)w.a;
+      if (EPI == EPI_LIN) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] *= a;
+        R y[8];
+        if (w.y1) {
+          SpinorIO<SP>::load_colour(w.y1, Vh, h, col, y);
+          const R c = (R)w.c1;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) acc[i] += c * y[i];
+        }
+        if (w.y2) {
+          R y2[8];
+          SpinorIO<SP>::load_colour(w.y2, Vh, h, col, y2);
+          const R c = (R)w.c2;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) acc[i] += c * y2[i];
+        }
+        SpinorIO<SP>::store_colour(w.out, Vh, h, col, acc);
+        if (w.red == 1) {
+          v0 = colour_norm2(acc);
+        } else if (w.red == 2) {
+          R z[8];
+          SpinorIO<SP>::load_colour(w.zin, Vh, h, col, z);
+          colour_dot(z, acc, v0, v1);
+        } else if (w.red == 3) {
+          colour_dot(acc, y, v0, v1);
+          v2 = colour_norm2(acc);
+        }
+      } else {
+        const R alpha = (R)w.sc->alpha;
+        R y[8], r[8];
+        SpinorIO<SP>::load_colour(w.y1, Vh, h, col, y);
+        SpinorIO<SP>::load_colour(w.out, Vh, h, col, r);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) r[i] -= alpha * (y[i] + a * acc[i]);
+        SpinorIO<SP>::store_colour(w.out, Vh, h, col, r);
+        v0 = colour_norm2(r);
+        using XR = typename SpinorIO<XSloppy<SP>::P>::Real;
+        R p[8];
+        XR x[8];
+        SpinorIO<SP>::load_colour(w.zin, Vh, h, col, p);
+        SpinorIO<XSloppy<SP>::P>::load_colour(w.z, Vh, h, col, x);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] += cvt<XR>(alpha) * cvt<XR>(p[i]);
+        SpinorIO<XSloppy<SP>::P>::store_colour(w.z, Vh, h, col, x);
+      }
+    }
+    tile_finish<3 * TILE>(w, start / TILE, v0, v1, v2, L.partials);
+  }
+}
+
 // ------------------------------------------------------------------ fused BLAS
 
 enum Blas {

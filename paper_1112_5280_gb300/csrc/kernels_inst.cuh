@@ -15,6 +15,15 @@ constexpr int LPX = (SPX == P_F64 || SPX == P_DF64 || SPX == P_F32) ? SPX : P_F1
 template <int NR, bool DAG, int EPI>
 cudaError_t go_dslash(const Launch& L, int grid, cudaStream_t s) {
   if (L.ntiles <= 0) return cudaSuccess;
+  if constexpr (SPX == P_DF64 && NR == 18) {
+    if (dslash_colour_split(SPX)) {
+      // double-float: the colour-split form (latency bound at one thread per site)
+      auto fn3 = k_dslash3<SPX, LPX, DAG, EPI>;
+      if (grid <= 0) grid = grid_for((const void*)fn3, L.ntiles, 0, 3 * TILE);
+      fn3<<<grid, 3 * TILE, 0, s>>>(L);
+      return cudaGetLastError();
+    }
+  }
   auto fn = k_dslash<SPX, LPX, NR, DAG, EPI>;
   if (grid <= 0) grid = grid_for((const void*)fn, L.ntiles, 0, TILE);
   fn<<<grid, TILE, 0, s>>>(L);

@@ -34,6 +34,11 @@ int device_sm_count();
 void set_grid_multiplier(int kernel_family, int mult);  // 0 = occupancy limit
 int grid_for(const void* kernel_fn, int ntiles, int family, int block);
 
+// Whether the Dslash of spinor precision prec uses the colour-split form (double-float
+// only; a runtime switch for measurement).
+bool dslash_colour_split(int prec);
+void set_dslash_colour_split(int prec, bool on);
+
 
 // layout kernels (layout.cu)
 cudaError_t gauge_from_aos(const double* d_aos, const Geom& g, int prec, int nr, void* d_out,

@@ -299,6 +299,15 @@ void set_grid_multiplier(int family, int mult) {
   if (family >= 0 && family < 4) g_mult[family] = mult;
 }
 
+namespace {
+bool g_split[NPREC] = {false, false, false, false, true};
+}  // namespace
+
+bool dslash_colour_split(int prec) { return prec >= 0 && prec < NPREC && g_split[prec]; }
+void set_dslash_colour_split(int prec, bool on) {
+  if (prec >= 0 && prec < NPREC) g_split[prec] = on;
+}
+
 int grid_for(const void* fn, int ntiles, int family, int block) {
   const int nsm = device_sm_count();
   int occ;

@@ -77,6 +77,7 @@ def load(build_if_missing: bool = True):
     _sig(lib, "lqcd_ctx_sync", i, [_VP])
     _sig(lib, "lqcd_ctx_launch_count", ll, [_VP])
     _sig(lib, "lqcd_set_grid_multiplier", None, [i, i])
+    _sig(lib, "lqcd_set_dslash_form", i, [i, i])
     _sig(lib, "lqcd_gauge_upload", i, [_VP, _IP, _VP, i, i, i, C.POINTER(_VP)])
     _sig(lib, "lqcd_gauge_upload_dev", i, [_VP, _IP, _VP, i, i, i, C.POINTER(_VP)])
     _sig(lib, "lqcd_gauge_add_copy", i, [_VP, i, i])
@@ -339,6 +340,11 @@ def apply_Mhat_noalloc(gauge: Gauge, kappa: float, fin: Field, fout: Field, dagg
 
 def apply_M(gauge: Gauge, kappa: float, fin: Field, fout: Field, dagger=False):
     _check(gauge._lib.lqcd_apply_M(gauge.h, float(kappa), fin.h, fout.h, int(bool(dagger))))
+
+
+def set_dslash_form(prec, form: int):
+    """Dslash kernel form for DF64 fields: 0 one thread per site, 1 three per site."""
+    _check(load().lqcd_set_dslash_form(_prec(prec), int(form)))
 
 
 def set_grid_multiplier(family: int, mult: int):

@@ -221,3 +221,23 @@ def test_dslash_batch_matches_oracle(ctx, prec, same_size):
     for f, (dims, ref) in zip(fouts, refs):
         assert _rel_err(f.download(), ref, _par(dims, 0)) < TOL[prec]
     b.close()
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_df64_both_forms(ctx, form):
+    """Both Dslash forms of double-float (one thread per site, three per site) meet the FP64 bar."""
+    dims = (6, 6, 4, 10)
+    U = synth.random_links(dims, 0.5, seed=77)
+    psi = synth.gaussian_spinor(dims, seed=78)
+    lqcd.set_dslash_form("df64", form)
+    try:
+        g = ctx.gauge(dims, U, prec="df64", compress=18)
+        fin = ctx.field(dims, "df64", lqcd.FULL, data=psi)
+        fout = ctx.field(dims, "df64", lqcd.FULL)
+        for p in (0, 1):
+            for dag in (False, True):
+                lqcd.dslash_eo(g, fin, fout, p, dagger=dag)
+                ref = oracle.hop_eo(dims, U, psi, p, dagger=dag)
+                assert _rel_err(fout.download(), ref, _par(dims, p)) < 1e-12
+    finally:
+        lqcd.set_dslash_form("df64", 1)
