@@ -495,7 +495,13 @@ def run_mrhs_section(ctx, lqcd, inputs, world):
     for s_, x_ in zip(srcs, xs):
         lqcd.solve_fields(g, s_, MRHS_KAPPA, 1e-10, x_, o)
     t_seq = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    corr = lqcd.meson_correlator(xs, list(range(10)))
+    t_corr = time.perf_counter() - t0
     res = {"workload": "24^3x48 kappa=0.15, 12 point sources at a seeded site, FP32 inner / FP64 outer",
+           "meson_correlator_ms": t_corr * 1e3,
+           "pion_correlator_t0_t1": [float(corr[1, 0].real), float(corr[1, 1].real)],
            "multi_ms": t_multi * 1e3, "sequential_ms": t_seq * 1e3,
            "solves_per_s": 12 / t_multi, "speedup_vs_sequential": t_seq / t_multi,
            "max_true_resid": max(i["true_resid"] for i in infos),

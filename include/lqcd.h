@@ -236,6 +236,24 @@ LQCD_API int lqcd_solve_multi(const lqcd_gauge* g, int n, const lqcd_field* cons
                      double tol, const lqcd_solve_opts* opts, lqcd_field* const* xs,
                      lqcd_solve_info* infos);
 
+/* ---------------------------------------------------------------- meson correlators */
+
+/* Dirac structures Gamma of lqcd_meson_correlator (chiral basis above) */
+#define LQCD_G_1 0    /* scalar */
+#define LQCD_G_5 1    /* pseudoscalar g5 */
+#define LQCD_G_X 2    /* vector g_x, g_y, g_z, g_t: 2..5 */
+#define LQCD_G_5X 6   /* axial g5 g_x, ..., g5 g_t: 6..9 */
+
+/* Meson two-point functions from a point-source propagator (paper Section 4, eq. 4.1):
+ *   C_Gamma(t) = sum over spatial x of  - Tr[ S^dag(x) g5 Gamma S(x) Gamma g5 ],
+ * trace over spin and colour, where S(x) is the 12 x 12 matrix whose column 3*beta+b
+ * is props[3*beta+b] (the solution for the point source of spin beta, colour b) at
+ * site x. props: 12 FULL FP64 fields of one lattice. gammas: ngamma (<= 16) codes.
+ * host_corr: ngamma x Lt complex values (re, im), t the absolute time coordinate.
+ * Synchronous; the per-slice sum is in a fixed order (deterministic). */
+LQCD_API int lqcd_meson_correlator(const lqcd_field* const* props, int ngamma, const int* gammas,
+                                   double* host_corr);
+
 /* ---------------------------------------------------------------- batched engine (A11, A12) */
 
 /* A Krylov engine that advances many independent solves (any lattice sizes,

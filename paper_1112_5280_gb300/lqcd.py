@@ -100,6 +100,7 @@ def load(build_if_missing: bool = True):
                                               C.POINTER(_VP)])
     _sig(lib, "lqcd_dslash_batch_apply", i, [_VP])
     _sig(lib, "lqcd_dslash_batch_destroy", None, [_VP])
+    _sig(lib, "lqcd_meson_correlator", i, [C.POINTER(_VP), i, C.POINTER(C.c_int), _VP])
     if hasattr(lib, "lqcd_apply_Mhat_noalloc"):
         _sig(lib, "lqcd_apply_Mhat_noalloc", i, [_VP, d, _VP, _VP, i])
     if hasattr(lib, "lqcd_solve"):
@@ -340,6 +341,23 @@ def apply_Mhat_noalloc(gauge: Gauge, kappa: float, fin: Field, fout: Field, dagg
 
 def apply_M(gauge: Gauge, kappa: float, fin: Field, fout: Field, dagger=False):
     _check(gauge._lib.lqcd_apply_M(gauge.h, float(kappa), fin.h, fout.h, int(bool(dagger))))
+
+
+GAMMA_CODES = {"1": 0, "g5": 1, "gx": 2, "gy": 3, "gz": 4, "gt": 5,
+               "g5gx": 6, "g5gy": 7, "g5gz": 8, "g5gt": 9}
+
+
+def meson_correlator(props, gammas):
+    """C_Gamma(t) for the 12 FULL FP64 propagator fields (source spin*3 + colour order).
+    gammas: codes or names; returns complex array [len(gammas), Lt]."""
+    if len(props) != 12:
+        raise ValueError("need the 12 point-source solutions")
+    codes = [GAMMA_CODES[g] if isinstance(g, str) else int(g) for g in gammas]
+    lt = props[0].dims[3]
+    out = np.zeros((len(codes), lt, 2), dtype=np.float64)
+    _check(props[0]._lib.lqcd_meson_correlator((_VP * 12)(*[p.h for p in props]), len(codes),
+                                               (C.c_int * len(codes))(*codes), out.ctypes.data))
+    return out[..., 0] + 1j * out[..., 1]
 
 
 def set_dslash_form(prec, form: int):
