@@ -41,14 +41,17 @@ def _index(dims, c):
     return c[0] + dims[0] * (c[1] + dims[1] * (c[2] + dims[2] * c[3]))
 
 
-def dense_wilson(dims, U, kappa, t_bc=-1):
-    """Dense M (12V x 12V); row index = 12*site + 3*spin + colour."""
+def dense_wilson(dims, U, kappa, t_bc=-1, mu=0.0):
+    """Dense M (12V x 12V); row index = 12*site + 3*spin + colour. mu != 0 adds the
+    twisted-mass term 2 i kappa mu g5 on the diagonal."""
     dims = tuple(int(d) for d in dims)
     V = int(np.prod(dims))
     U = np.asarray(U).reshape(V, 4, 3, 3)
-    g, _ = gammas()
+    g, g5 = gammas()
     one = np.eye(4, dtype=np.complex128)
     M = np.eye(12 * V, dtype=np.complex128)
+    if mu != 0.0:
+        M = M + np.kron(np.eye(V), np.kron(2j * kappa * mu * g5, np.eye(3)))
     for c in _coords(dims):
         s = _index(dims, c)
         for mu in range(4):
@@ -85,12 +88,14 @@ def momenta(dims, t_antiperiodic=True):
     return np.array(out)
 
 
-def free_eigenvalues(dims, kappa, t_antiperiodic=True):
-    """1 - 2 kappa sum cos p +- 2 i kappa sqrt(sum sin^2 p), each 6-fold (2 spin x 3 colour)."""
+def free_eigenvalues(dims, kappa, t_antiperiodic=True, mu=0.0):
+    """1 - 2 kappa sum cos p +- 2 i kappa sqrt(sum sin^2 p + mu^2), each 6-fold: with
+    K = sum g_mu sin p_mu + mu g5, K^2 = (sum sin^2 p + mu^2) 1 since g5 anticommutes
+    with every g_mu."""
     ev = []
     for p in momenta(dims, t_antiperiodic):
         a = 1 - 2 * kappa * np.sum(np.cos(p))
-        b = 2 * kappa * np.sqrt(np.sum(np.sin(p) ** 2))
+        b = 2 * kappa * np.sqrt(np.sum(np.sin(p) ** 2) + mu * mu)
         ev += [a + 1j * b] * 6 + [a - 1j * b] * 6
     return np.array(ev)
 

@@ -29,11 +29,11 @@ def _load():
         lib.oracle_hop_eo.argtypes = [ip, C.c_int, dp, dp, dp, C.c_int, C.c_int]
         lib.oracle_hop_sites.argtypes = [ip, C.c_int, dp, dp, C.POINTER(C.c_longlong),
                                          C.c_longlong, dp, C.c_int]
-        lib.oracle_apply_M.argtypes = [ip, C.c_int, dp, C.c_double, dp, dp, C.c_int]
-        lib.oracle_apply_Mhat.argtypes = [ip, C.c_int, dp, C.c_double, dp, dp, C.c_int]
-        lib.oracle_solve.argtypes = [ip, C.c_int, dp, C.c_double, dp, dp, C.c_double, C.c_int,
-                                     C.c_int, dp]
-        lib.oracle_true_residual.argtypes = [ip, C.c_int, dp, C.c_double, dp, dp]
+        lib.oracle_apply_M.argtypes = [ip, C.c_int, dp, C.c_double, C.c_double, dp, dp, C.c_int]
+        lib.oracle_apply_Mhat.argtypes = [ip, C.c_int, dp, C.c_double, C.c_double, dp, dp, C.c_int]
+        lib.oracle_solve.argtypes = [ip, C.c_int, dp, C.c_double, C.c_double, dp, dp, C.c_double,
+                                     C.c_int, C.c_int, dp]
+        lib.oracle_true_residual.argtypes = [ip, C.c_int, dp, C.c_double, C.c_double, dp, dp]
         lib.oracle_true_residual.restype = C.c_double
         lib.oracle_set_threads.argtypes = [C.c_int]
         lib.oracle_get_threads.restype = C.c_int
@@ -108,49 +108,49 @@ def hop_sites(dims, U, psi, sites, t_bc=-1, dagger=False):
     return out
 
 
-def apply_M(dims, U, kappa, psi, t_bc=-1, dagger=False):
+def apply_M(dims, U, kappa, psi, t_bc=-1, dagger=False, mu=0.0):
     V = _vol(dims)
     U = _c128(U, (V, 4, 3, 3))
     psi = _c128(psi, (V, 4, 3))
     out = np.empty_like(psi)
-    rc = _load().oracle_apply_M(_dims(dims), int(t_bc), _ptr(U), float(kappa), _ptr(psi),
-                                _ptr(out), int(dagger))
+    rc = _load().oracle_apply_M(_dims(dims), int(t_bc), _ptr(U), float(kappa), float(mu),
+                                _ptr(psi), _ptr(out), int(dagger))
     if rc:
         raise ValueError(f"oracle_apply_M failed: {rc}")
     return out
 
 
-def apply_Mhat(dims, U, kappa, psi, t_bc=-1, dagger=False):
+def apply_Mhat(dims, U, kappa, psi, t_bc=-1, dagger=False, mu=0.0):
     V = _vol(dims)
     U = _c128(U, (V, 4, 3, 3))
     psi = _c128(psi, (V, 4, 3))
     out = np.empty_like(psi)
-    rc = _load().oracle_apply_Mhat(_dims(dims), int(t_bc), _ptr(U), float(kappa), _ptr(psi),
-                                   _ptr(out), int(dagger))
+    rc = _load().oracle_apply_Mhat(_dims(dims), int(t_bc), _ptr(U), float(kappa), float(mu),
+                                   _ptr(psi), _ptr(out), int(dagger))
     if rc:
         raise ValueError(f"oracle_apply_Mhat failed: {rc}")
     return out
 
 
-def solve(dims, U, kappa, b, tol=1e-10, maxiter=10000, method=METHOD_CG_EO, t_bc=-1):
+def solve(dims, U, kappa, b, tol=1e-10, maxiter=10000, method=METHOD_CG_EO, t_bc=-1, mu=0.0):
     """Returns (x, status, iterations, true_relative_residual)."""
     V = _vol(dims)
     U = _c128(U, (V, 4, 3, 3))
     b = _c128(b, (V, 4, 3))
     x = np.zeros_like(b)
     info = np.zeros(2, dtype=np.float64)
-    rc = _load().oracle_solve(_dims(dims), int(t_bc), _ptr(U), float(kappa), _ptr(b), _ptr(x),
-                              float(tol), int(maxiter), int(method),
+    rc = _load().oracle_solve(_dims(dims), int(t_bc), _ptr(U), float(kappa), float(mu), _ptr(b),
+                              _ptr(x), float(tol), int(maxiter), int(method),
                               info.ctypes.data_as(C.POINTER(C.c_double)))
     if rc < 0:
         raise ValueError(f"oracle_solve failed: {rc}")
     return x, int(rc), int(info[0]), float(info[1])
 
 
-def true_residual(dims, U, kappa, b, x, t_bc=-1):
+def true_residual(dims, U, kappa, b, x, t_bc=-1, mu=0.0):
     V = _vol(dims)
     U = _c128(U, (V, 4, 3, 3))
     b = _c128(b, (V, 4, 3))
     x = _c128(x, (V, 4, 3))
     return float(_load().oracle_true_residual(_dims(dims), int(t_bc), _ptr(U), float(kappa),
-                                              _ptr(b), _ptr(x)))
+                                              float(mu), _ptr(b), _ptr(x)))

@@ -197,39 +197,71 @@ int oracle_hop_sites(const int dims[4], int t_bc, const double* U, const double*
   return ORACLE_OK;
 }
 
-int oracle_apply_M(const int dims[4], int t_bc, const double* U, double kappa, const double* psi,
-                   double* out, int dagger) {
+/* g5 = diag(1, 1, -1, -1) in the chiral basis: sign of spin component sp */
+static double g5_sign(int sp) { return sp < 2 ? 1.0 : -1.0; }
+
+/* out = c * (1 + i tau g5) psi at every site of parity `only` (all sites if only < 0) */
+static void twist(const geom* g, cplx c, double tau, const cplx* psi, cplx* out, int only) {
+#pragma omp parallel for schedule(static)
+  for (long long s = 0; s < g->V; ++s) {
+    long long cc[4];
+    coords(g, s, cc);
+    if (only >= 0 && parity_of(cc) != only) continue;
+    for (int sp = 0; sp < 4; ++sp)
+      for (int a = 0; a < 3; ++a) {
+        const long long i = s * 12 + sp * 3 + a;
+        out[i] = c * (1.0 + I * tau * g5_sign(sp)) * psi[i];
+      }
+  }
+}
+
+int oracle_apply_M(const int dims[4], int t_bc, const double* U, double kappa, double mu,
+                   const double* psi, double* out, int dagger) {
   geom g;
   if (make_geom(dims, &g) != ORACLE_OK) return ORACLE_BADARG;
   int rc = oracle_hop(dims, t_bc, U, psi, out, dagger);
   if (rc) return rc;
   cplx* o = (cplx*)out;
   const cplx* p = (const cplx*)psi;
+  /* M = 1 - kappa D + 2 i kappa mu g5 ;  M^dag = 1 - kappa D^dag - 2 i kappa mu g5 */
+  const double tm = (dagger ? -2.0 : 2.0) * kappa * mu;
 #pragma omp parallel for schedule(static)
-  for (long long i = 0; i < g.V * 12; ++i) o[i] = p[i] - kappa * o[i];
+  for (long long s = 0; s < g.V; ++s)
+    for (int sp = 0; sp < 4; ++sp)
+      for (int a = 0; a < 3; ++a) {
+        const long long i = s * 12 + sp * 3 + a;
+        o[i] = p[i] - kappa * o[i] + I * tm * g5_sign(sp) * p[i];
+      }
   return ORACLE_OK;
 }
 
-/* Mhat = 1 - kappa^2 D_eo D_oe on the even sites (Schur complement of M).
- * For dagger: Mhat^dag = 1 - kappa^2 (D^dag)_eo (D^dag)_oe. */
-int oracle_apply_Mhat(const int dims[4], int t_bc, const double* U, double kappa,
+/* Mhat = A - kappa^2 D_eo A^-1 D_oe on the even sites (Schur complement of M), with
+ * A = 1 + i a g5, a = 2 kappa mu, A^-1 = (1 - i a g5) / (1 + a^2).
+ * For dagger: Mhat^dag = A^dag - kappa^2 (D^dag)_eo (A^-1)^dag (D^dag)_oe. */
+int oracle_apply_Mhat(const int dims[4], int t_bc, const double* U, double kappa, double mu,
                       const double* psi, double* out, int dagger) {
   geom g;
   if (make_geom(dims, &g) != ORACLE_OK) return ORACLE_BADARG;
+  const double a = (dagger ? -2.0 : 2.0) * kappa * mu;
   cplx* tmp = (cplx*)malloc(sizeof(cplx) * 12 * g.V);
-  if (!tmp) return ORACLE_BADARG;
+  cplx* tmp2 = (cplx*)malloc(sizeof(cplx) * 12 * g.V);
+  cplx* apsi = (cplx*)malloc(sizeof(cplx) * 12 * g.V);
+  if (!tmp || !tmp2 || !apsi) return ORACLE_BADARG;
   hop_impl(dims, t_bc, (const cplx*)U, (const cplx*)psi, tmp, 1, dagger);
-  hop_impl(dims, t_bc, (const cplx*)U, tmp, (cplx*)out, 0, dagger);
+  twist(&g, 1.0 / (1.0 + a * a), -a, tmp, tmp2, 1);
+  hop_impl(dims, t_bc, (const cplx*)U, tmp2, (cplx*)out, 0, dagger);
+  twist(&g, 1.0, a, (const cplx*)psi, apsi, 0);
   free(tmp);
+  free(tmp2);
   cplx* o = (cplx*)out;
-  const cplx* p = (const cplx*)psi;
 #pragma omp parallel for schedule(static)
   for (long long s = 0; s < g.V; ++s) {
     long long c[4];
     coords(&g, s, c);
     for (int k = 0; k < 12; ++k)
-      o[s * 12 + k] = (parity_of(c) == 0) ? p[s * 12 + k] - kappa * kappa * o[s * 12 + k] : 0;
+      o[s * 12 + k] = (parity_of(c) == 0) ? apsi[s * 12 + k] - kappa * kappa * o[s * 12 + k] : 0;
   }
+  free(apsi);
   return ORACLE_OK;
 }
 
@@ -259,6 +291,7 @@ typedef struct {
   int t_bc;
   const double* U;
   double kappa;
+  double mu;
   int eo;
   long long n; /* complex entries per vector (full lattice) */
   cplx* tmp;
@@ -267,9 +300,9 @@ typedef struct {
 /* y = A v with A = M (eo = 0) or Mhat (eo = 1) */
 static void op_apply(const opctx* c, const cplx* v, cplx* y, int dagger) {
   if (c->eo)
-    oracle_apply_Mhat(c->dims, c->t_bc, c->U, c->kappa, (const double*)v, (double*)y, dagger);
+    oracle_apply_Mhat(c->dims, c->t_bc, c->U, c->kappa, c->mu, (const double*)v, (double*)y, dagger);
   else
-    oracle_apply_M(c->dims, c->t_bc, c->U, c->kappa, (const double*)v, (double*)y, dagger);
+    oracle_apply_M(c->dims, c->t_bc, c->U, c->kappa, c->mu, (const double*)v, (double*)y, dagger);
 }
 
 /* Hestenes-Stiefel CG on A^dag A x = A^dag rhs, x0 = 0; stop on ||rhs - A x|| <= abs_tol. */
@@ -364,13 +397,13 @@ static int bicgstab(const opctx* c, const cplx* rhs, cplx* x, double abs_tol, in
   return status;
 }
 
-double oracle_true_residual(const int dims[4], int t_bc, const double* U, double kappa,
+double oracle_true_residual(const int dims[4], int t_bc, const double* U, double kappa, double mu,
                             const double* b, const double* x) {
   geom g;
   if (make_geom(dims, &g) != ORACLE_OK) return -1.0;
   long long n = 12 * g.V;
   cplx* y = malloc(sizeof(cplx) * n);
-  oracle_apply_M(dims, t_bc, U, kappa, x, (double*)y, 0);
+  oracle_apply_M(dims, t_bc, U, kappa, mu, x, (double*)y, 0);
   const cplx* bb = (const cplx*)b;
   for (long long i = 0; i < n; ++i) y[i] = bb[i] - y[i];
   double res = sqrt(vnorm2(y, n)) / sqrt(vnorm2(bb, n));
@@ -378,8 +411,8 @@ double oracle_true_residual(const int dims[4], int t_bc, const double* U, double
   return res;
 }
 
-int oracle_solve(const int dims[4], int t_bc, const double* U, double kappa, const double* b,
-                 double* x, double tol, int maxiter, int method, double* info) {
+int oracle_solve(const int dims[4], int t_bc, const double* U, double kappa, double mu,
+                 const double* b, double* x, double tol, int maxiter, int method, double* info) {
   geom g;
   if (make_geom(dims, &g) != ORACLE_OK) return ORACLE_BADARG;
   if (method < 0 || method > 2) return ORACLE_BADARG;
@@ -389,18 +422,22 @@ int oracle_solve(const int dims[4], int t_bc, const double* U, double kappa, con
   cplx* xx = (cplx*)x;
   double bnorm = sqrt(vnorm2(bb, n));
   double abs_tol = tol * bnorm;
-  opctx c = {dims, t_bc, U, kappa, method != 0, n, NULL};
+  opctx c = {dims, t_bc, U, kappa, mu, method != 0, n, NULL};
   int iters = 0, status;
   if (method == 0) {
     status = cg_normal(&c, bb, xx, abs_tol, maxiter, &iters);
   } else {
-    /* Schur complement: bhat_e = b_e + kappa D_eo b_o; x_o = b_o + kappa D_oe x_e.
+    /* Schur complement with A = 1 + i a g5 (a = 2 kappa mu):
+     *   bhat_e = b_e + kappa D_eo A^-1 b_o ;  x_o = A^-1 (b_o + kappa D_oe x_e).
      * The residual of Mhat on the even sites equals the full residual there,
      * and the odd residual vanishes by construction, so the same abs_tol applies. */
+    const double a = 2.0 * kappa * mu;
     cplx* bhat = calloc(n, sizeof(cplx));
     cplx* xe = calloc(n, sizeof(cplx));
     cplx* tmp = calloc(n, sizeof(cplx));
-    oracle_hop_eo(dims, t_bc, U, b, (double*)tmp, 0, 0);
+    cplx* ainv_bo = calloc(n, sizeof(cplx));
+    twist(&g, 1.0 / (1.0 + a * a), -a, bb, ainv_bo, 1);
+    oracle_hop_eo(dims, t_bc, U, (const double*)ainv_bo, (double*)tmp, 0, 0);
     for (long long s = 0; s < g.V; ++s) {
       long long cc[4];
       coords(&g, s, cc);
@@ -416,13 +453,21 @@ int oracle_solve(const int dims[4], int t_bc, const double* U, double kappa, con
       long long cc[4];
       coords(&g, s, cc);
       for (int k = 0; k < 12; ++k)
-        xx[s * 12 + k] = parity_of(cc) == 0 ? xe[s * 12 + k] : bb[s * 12 + k] + kappa * tmp[s * 12 + k];
+        tmp[s * 12 + k] = parity_of(cc) == 1 ? bb[s * 12 + k] + kappa * tmp[s * 12 + k] : 0;
     }
+    twist(&g, 1.0 / (1.0 + a * a), -a, tmp, tmp, 1);
+    for (long long s = 0; s < g.V; ++s) {
+      long long cc[4];
+      coords(&g, s, cc);
+      for (int k = 0; k < 12; ++k)
+        xx[s * 12 + k] = parity_of(cc) == 0 ? xe[s * 12 + k] : tmp[s * 12 + k];
+    }
+    free(ainv_bo);
     free(bhat); free(xe); free(tmp);
   }
   if (info) {
     info[0] = iters;
-    info[1] = oracle_true_residual(dims, t_bc, U, kappa, b, x);
+    info[1] = oracle_true_residual(dims, t_bc, U, kappa, mu, b, x);
   }
   return status;
 }

@@ -51,27 +51,32 @@ int oracle_hop_eo(const int dims[4], int t_bc, const double* U, const double* ps
 int oracle_hop_sites(const int dims[4], int t_bc, const double* U, const double* psi,
                      const long long* sites, long long nsites, double* out, int dagger);
 
-/* out = M psi = psi - kappa D psi (full lattice); dagger gives M^dag. */
-int oracle_apply_M(const int dims[4], int t_bc, const double* U, double kappa,
+/* out = M psi = psi - kappa D psi + 2 i kappa mu g5 psi (full lattice): the Wilson
+ * operator for mu = 0, the N_f = 2 twisted-mass operator (paper Section 3, one flavour;
+ * the other has -mu) otherwise. dagger gives M^dag. */
+int oracle_apply_M(const int dims[4], int t_bc, const double* U, double kappa, double mu,
                    const double* psi, double* out, int dagger);
 
-/* out_e = psi_e - kappa^2 D_eo D_oe psi_e on even sites, 0 on odd sites. */
-int oracle_apply_Mhat(const int dims[4], int t_bc, const double* U, double kappa,
+/* Schur complement on the even sites, A = 1 + 2 i kappa mu g5 the site-diagonal part:
+ * out_e = A psi_e - kappa^2 D_eo A^-1 D_oe psi_e, 0 on odd sites (mu = 0: 1 - k^2 D_eo D_oe).
+ * dagger gives its adjoint. */
+int oracle_apply_Mhat(const int dims[4], int t_bc, const double* U, double kappa, double mu,
                       const double* psi, double* out, int dagger);
 
 /* Solve M x = b.
  *   method 0: CG on M^dag M (full lattice)
- *   method 1: even-odd: CG on Mhat^dag Mhat for x_e, then x_o = b_o + kappa D_oe x_e
+ *   method 1: even-odd: CG on Mhat^dag Mhat for x_e, then x_o = A^-1 (b_o + kappa D_oe x_e)
  *   method 2: even-odd: BiCGStab on Mhat, then the same reconstruction
+ * (bhat_e = b_e + kappa D_eo A^-1 b_o; A = 1 for mu = 0)
  * Stops when ||b - M x|| <= tol ||b|| (full, unpreconditioned M, FP64).
  * x is overwritten (start value 0). info[0] = iterations, info[1] = final
  * true relative residual. Returns ORACLE_OK, ORACLE_MAXITER or ORACLE_BREAKDOWN. */
-int oracle_solve(const int dims[4], int t_bc, const double* U, double kappa,
+int oracle_solve(const int dims[4], int t_bc, const double* U, double kappa, double mu,
                  const double* b, double* x, double tol, int maxiter, int method,
                  double* info);
 
 /* ||b - M x|| / ||b|| with the full operator. */
-double oracle_true_residual(const int dims[4], int t_bc, const double* U, double kappa,
+double oracle_true_residual(const int dims[4], int t_bc, const double* U, double kappa, double mu,
                             const double* b, const double* x);
 
 #ifdef __cplusplus

@@ -31,11 +31,19 @@ MUTANTS = {
                                "for (int dir = 0; dir < 2 - (mu == 2); ++dir)"),
     "gamma_lower_block_sign": ("GAMMA[k][2 + a][b] = I * sig[k][a][b];",
                                "GAMMA[k][2 + a][b] = -I * sig[k][a][b];"),
-    "kappa_sign_in_M": ("o[i] = p[i] - kappa * o[i];", "o[i] = p[i] + kappa * o[i];"),
-    "schur_sign": ("p[s * 12 + k] - kappa * kappa * o[s * 12 + k]",
-                   "p[s * 12 + k] + kappa * kappa * o[s * 12 + k]"),
-    "odd_reconstruction_sign": ("bb[s * 12 + k] + kappa * tmp[s * 12 + k];",
-                                "bb[s * 12 + k] - kappa * tmp[s * 12 + k];"),
+    "kappa_sign_in_M": ("o[i] = p[i] - kappa * o[i] +", "o[i] = p[i] + kappa * o[i] +"),
+    "schur_sign": ("apsi[s * 12 + k] - kappa * kappa * o[s * 12 + k]",
+                   "apsi[s * 12 + k] + kappa * kappa * o[s * 12 + k]"),
+    "bhat_sign": ("bhat[s * 12 + k] = parity_of(cc) == 0 ? bb[s * 12 + k] + kappa * tmp[s * 12 + k]",
+                  "bhat[s * 12 + k] = parity_of(cc) == 0 ? bb[s * 12 + k] - kappa * tmp[s * 12 + k]"),
+    "odd_reconstruction_sign": ("tmp[s * 12 + k] = parity_of(cc) == 1 ? bb[s * 12 + k] + kappa * tmp",
+                                "tmp[s * 12 + k] = parity_of(cc) == 1 ? bb[s * 12 + k] - kappa * tmp"),
+    "twisted_term_sign": ("+ I * tm * g5_sign(sp) * p[i]", "- I * tm * g5_sign(sp) * p[i]"),
+    "twisted_term_no_g5": ("+ I * tm * g5_sign(sp) * p[i]", "+ I * tm * p[i]"),
+    "schur_inverse_twist_sign": ("twist(&g, 1.0 / (1.0 + a * a), -a, tmp, tmp2, 1);",
+                                 "twist(&g, 1.0 / (1.0 + a * a), a, tmp, tmp2, 1);"),
+    "odd_reconstruction_missing_inverse": ("    twist(&g, 1.0 / (1.0 + a * a), -a, tmp, tmp, 1);",
+                                           "    twist(&g, 1.0, 0.0, tmp, tmp, 1);"),
     "t_neighbour_off_by_one": ("n[mu] = (c[mu] + 1) % g->L[mu];",
                                "n[mu] = (c[mu] + 1 + (mu == 3)) % g->L[mu];"),
 }
@@ -100,8 +108,42 @@ def _pin_checks():
         xd = np.linalg.solve(dense.dense_wilson(dims, U, 0.12), b.reshape(-1))
         return bool(st == 0 and np.linalg.norm(x.reshape(-1) - xd) < 1e-9 * np.linalg.norm(xd))
 
+    def tm_hermiticity():
+        dims = (4, 2, 2, 4)
+        U = synth.random_links(dims, 0.5, seed=10)
+        phi, psi = synth.gaussian_spinor(dims, 11), synth.gaussian_spinor(dims, 12)
+        g5 = lambda v: v * np.array([1, 1, -1, -1])[None, :, None]  # noqa: E731
+        lhs = np.vdot(phi, oracle.apply_M(dims, U, 0.13, psi, mu=0.3))
+        rhs = np.vdot(g5(oracle.apply_M(dims, U, 0.13, g5(phi), mu=-0.3)), psi)
+        return bool(abs(lhs - rhs) < 1e-12 * abs(lhs))
+
+    def tm_solve_vs_lapack():
+        dims = (2, 2, 2, 4)
+        U = synth.random_links(dims, 0.3, seed=13)
+        b = synth.gaussian_spinor(dims, 14)
+        ok = True
+        for method in (oracle.METHOD_CG_EO, oracle.METHOD_BICGSTAB_EO):
+            x, st, _, _ = oracle.solve(dims, U, 0.14, b, tol=1e-11, maxiter=500, method=method, mu=0.4)
+            xd = np.linalg.solve(dense.dense_wilson(dims, U, 0.14, mu=0.4), b.reshape(-1))
+            ok &= st == 0 and np.linalg.norm(x.reshape(-1) - xd) < 1e-9 * np.linalg.norm(xd)
+        return bool(ok)
+
+    def tm_brute_force():
+        dims = (2, 2, 2, 2)
+        U = synth.random_links(dims, 0.3, seed=15)
+        V = synth.volume(dims)
+        M = dense.dense_wilson(dims, U, 0.12, mu=0.25)
+        cols = []
+        for j in range(12 * V):
+            e = np.zeros(12 * V, dtype=np.complex128)
+            e[j] = 1
+            cols.append(oracle.apply_M(dims, U, 0.12, e.reshape(V, 4, 3), mu=0.25).reshape(-1))
+        return bool(np.abs(M - np.stack(cols, axis=1)).max() < 1e-14)
+
     checks.update(plane_wave=plane_wave, hermiticity=hermiticity, covariance=covariance,
-                  brute_force=brute_force, eo_solve_vs_lapack=eo_solve_vs_lapack)
+                  brute_force=brute_force, eo_solve_vs_lapack=eo_solve_vs_lapack,
+                  tm_hermiticity=tm_hermiticity, tm_solve_vs_lapack=tm_solve_vs_lapack,
+                  tm_brute_force=tm_brute_force)
     return checks
 
 

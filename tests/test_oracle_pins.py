@@ -259,3 +259,73 @@ def test_link_generator_is_su3_and_twelve_real_exact():
         assert np.abs(U @ np.conj(np.swapaxes(U, -1, -2)) - np.eye(3)).max() < 1e-14
         r2 = np.conj(np.cross(U[:, 0, :], U[:, 1, :]))
         assert np.abs(r2 - U[:, 2, :]).max() < 1e-15
+
+
+# ---------------------------------------------------------------- twisted mass (Section 3: N_f = 2)
+
+@pytest.mark.parametrize("mu", [0.05, 0.4])
+def test_tm_gamma5_hermiticity_flips_mu(mu):
+    """M(mu)^dag = g5 M(-mu) g5 for M = 1 - k D + 2 i k mu g5, and the dagger path is the adjoint."""
+    dims = (4, 4, 2, 4)
+    U = synth.random_links(dims, 0.5, seed=201)
+    phi = synth.gaussian_spinor(dims, seed=202)
+    psi = synth.gaussian_spinor(dims, seed=203)
+    kappa = 0.14
+    lhs = _vdot(phi, oracle.apply_M(dims, U, kappa, psi, mu=mu))
+    rhs = _vdot(_g5(oracle.apply_M(dims, U, kappa, _g5(phi), mu=-mu)), psi)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    rhs2 = _vdot(oracle.apply_M(dims, U, kappa, phi, mu=mu, dagger=True), psi)
+    assert abs(lhs - rhs2) < 1e-12 * abs(lhs)
+
+
+def test_tm_free_spectrum():
+    """At U = 1 the twisted operator has eigenvalues 1 - 2k sum cos p +- 2ik sqrt(sum sin^2 p + mu^2)."""
+    dims = (2, 2, 2, 4)
+    kappa, mu = 0.12, 0.3
+    V = synth.volume(dims)
+    U = synth.unit_links(dims)
+    M = np.zeros((12 * V, 12 * V), dtype=np.complex128)
+    for j in range(12 * V):
+        e = np.zeros(12 * V, dtype=np.complex128)
+        e[j] = 1
+        M[:, j] = oracle.apply_M(dims, U, kappa, e.reshape(V, 4, 3), mu=mu).reshape(-1)
+    ev = np.linalg.eigvals(M)
+    ref = dense.free_eigenvalues(dims, kappa, mu=mu)
+    key = lambda a: np.lexsort((np.round(a.imag, 9), np.round(a.real, 9)))  # noqa: E731
+    assert np.abs(ev[key(ev)] - ref[key(ref)]).max() < 1e-12
+
+
+def test_tm_dense_and_schur():
+    dims = (2, 2, 2, 4)
+    U = synth.random_links(dims, 0.5, seed=204)
+    kappa, mu = 0.15, 0.2
+    V = synth.volume(dims)
+    M = dense.dense_wilson(dims, U, kappa, mu=mu)
+    cols = []
+    for j in range(12 * V):
+        e = np.zeros(12 * V, dtype=np.complex128)
+        e[j] = 1
+        cols.append(oracle.apply_M(dims, U, kappa, e.reshape(V, 4, 3), mu=mu).reshape(-1))
+    assert np.abs(M - np.stack(cols, axis=1)).max() < 1e-15
+    par = synth.parity_of_sites(dims)
+    ev = np.repeat(par == 0, 12)
+    od = ~ev
+    schur = M[np.ix_(ev, ev)] - M[np.ix_(ev, od)] @ np.linalg.solve(M[np.ix_(od, od)], M[np.ix_(od, ev)])
+    psi = synth.gaussian_spinor(dims, seed=205) * (par == 0)[:, None, None]
+    out = oracle.apply_Mhat(dims, U, kappa, psi, mu=mu)
+    assert np.abs(out.reshape(-1)[ev] - schur @ psi.reshape(-1)[ev]).max() < 1e-13
+    outd = oracle.apply_Mhat(dims, U, kappa, psi, mu=mu, dagger=True)
+    assert np.abs(outd.reshape(-1)[ev] - schur.conj().T @ psi.reshape(-1)[ev]).max() < 1e-13
+
+
+@pytest.mark.parametrize("method", [oracle.METHOD_CG_FULL, oracle.METHOD_CG_EO,
+                                    oracle.METHOD_BICGSTAB_EO])
+def test_tm_solvers_vs_lapack(method):
+    dims = (4, 4, 2, 4)
+    U = synth.random_links(dims, 0.4, seed=206)
+    b = synth.gaussian_spinor(dims, seed=207)
+    kappa, mu = 0.15, 0.1
+    x, status, _, res = oracle.solve(dims, U, kappa, b, tol=1e-11, method=method, mu=mu)
+    assert status == 0 and res <= 1e-11
+    xd = np.linalg.solve(dense.dense_wilson(dims, U, kappa, mu=mu), b.reshape(-1)).reshape(x.shape)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
