@@ -167,6 +167,15 @@ LQCD_API int lqcd_apply_Mhat(const lqcd_gauge* g, double kappa, const lqcd_field
 /* out = M in (full, unpreconditioned); both fields FULL. */
 LQCD_API int lqcd_apply_M(const lqcd_gauge* g, double kappa, const lqcd_field* in, lqcd_field* out,
                  int dagger);
+/* Twisted-mass operators (paper Section 3): M = A - kappa D with the site-diagonal
+ * A = 1 + i a g5, a = 2 kappa mu, and its even-odd Schur complement
+ * Mhat = A - kappa^2 D_eo A^-1 D_oe, A^-1 = (1 - i a g5) / (1 + a^2). dagger gives the
+ * adjoint (M(mu)^dag = g5 M(-mu) g5). Arguments, layouts and errors as for lqcd_apply_M
+ * and lqcd_apply_Mhat; mu = 0 is exactly the Wilson operator. */
+LQCD_API int lqcd_apply_M_tm(const lqcd_gauge* g, double kappa, double mu, const lqcd_field* in,
+                             lqcd_field* out, int dagger);
+LQCD_API int lqcd_apply_Mhat_tm(const lqcd_gauge* g, double kappa, double mu, const lqcd_field* in,
+                                lqcd_field* out, int dagger);
 
 /* Mhat exactly as lqcd_apply_Mhat, for callers that cannot let the library
  * allocate device memory: applications whose device memory belongs to their
@@ -206,6 +215,10 @@ typedef struct lqcd_solve_opts {
   int true_prec;        /* FP64-class true residual, solution and outer correction: LQCD_F64
                            (native) or LQCD_DF64 (double-float); -1 (default): LQCD_F64 for an
                            FP64 solve, LQCD_DF64 otherwise */
+  int pad;
+  double mu;            /* twisted mass (paper Section 3: M = 1 - kappa D + 2 i kappa mu g5,
+                           one flavour of the N_f = 2 doublet; the other is -mu). 0 (default):
+                           the Wilson operator. Any finite value. */
 } lqcd_solve_opts;
 
 typedef struct lqcd_solve_info {
@@ -269,6 +282,11 @@ LQCD_API size_t lqcd_engine_request_bytes(const lqcd_engine* e, const int dims[4
  * after results are collected), LQCD_ENOMEM when the request can never fit. */
 LQCD_API int lqcd_engine_submit(lqcd_engine* e, const lqcd_gauge* g, const lqcd_field* src, double kappa,
                        double tol, long long* request_id);
+/* The same for the twisted-mass operator with this request's mu (lqcd_engine_submit
+ * takes mu from the engine's options); requests with different kappa and mu share
+ * the engine's launches. LQCD_EINVAL for a non-finite kappa or mu. */
+LQCD_API int lqcd_engine_submit_tm(lqcd_engine* e, const lqcd_gauge* g, const lqcd_field* src,
+                                   double kappa, double mu, double tol, long long* request_id);
 /* Runs one chunk of iterations for every active solve; *n_active: solves still running. */
 LQCD_API int lqcd_engine_step(lqcd_engine* e, int* n_active);
 /* Ids of solves finished since the last call (up to max). */

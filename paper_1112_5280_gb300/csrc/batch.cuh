@@ -77,6 +77,12 @@ struct Work {
   void* z;          // secondary output (CG: x_sloppy)
   const void* zin;  // secondary input (CG: p)
   double a, c1, c2; // out = a * D in + c1 * y1 + c2 * y2
+  // Twisted mass (site-diagonal T(s, tau) = s (1 + i tau g5)): when `twist` is set, the
+  // hopping term becomes T(tw_s, tw_t) (a D in) and the operand vector (y2 in the linear
+  // epilogue, y1 in the CG step) is multiplied by T(1, ty_t) before its coefficient.
+  int twist;
+  int pad2;
+  double tw_s, tw_t, ty_t;
   Scalars* sc;
   int tile0;        // first partial of this slot
   int ntiles;       // tiles of this slot = ceil(Vh / TILE)

@@ -7,6 +7,10 @@
 // x += |u| e. The scalar recurrences (rho, alpha, omega, beta) run on the
 // device in the slot's finishers; the host only polls the state between
 // chunks of iterations.
+//
+// Twisted mass (a = 2 kappa mu != 0): Mhat = A - kappa^2 D_eo A^-1 D_oe with
+// A = 1 + i a g5; A^-1 multiplies the odd-target Dslash in its epilogue and A the
+// operand vector of the even-target one (twist fields of Work).
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -64,6 +68,11 @@ int lqcd::bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kapp
   const int tp = (o->true_prec == -1) ? (sp == LQCD_F64 ? P_F64 : P_DF64) : o->true_prec;
   if (tp != P_F64 && tp != P_DF64) return set_error(LQCD_EINVAL, "true_prec");
   if (!(tol > 0)) return set_error(LQCD_EINVAL, "tol must be > 0");
+  if (!std::isfinite(o->mu) || !std::isfinite(kappa)) return set_error(LQCD_EINVAL, "kappa and mu must be finite");
+  const double ta = 2.0 * kappa * o->mu, ts = 1.0 / (1.0 + ta * ta);
+  // hopping term times A^-1 (odd targets) / operand y2 times A (even targets)
+  auto tw_inv = [&](Work& w) { if (ta != 0.0) set_twist(w, ts, -ta, 0.0); };
+  auto tw_a = [&](Work& w) { if (ta != 0.0) set_twist(w, 1.0, 0.0, ta); };
   lqcd_ctx* c = g->ctx;
   LQCD_CK(cudaSetDevice(c->device));
   cudaStream_t st = c->stream;
@@ -134,10 +143,16 @@ int lqcd::bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kapp
     w.fin = FIN_STORE1;
     w.in = b.bo;
     if (err == cudaSuccess) err = blas(tp, B_NORM, w);
-    // bhat = b_e + kappa D_eo b_o
+    // t = A^-1 b_o ; bhat = b_e + kappa D_eo t
+    if (ta != 0.0 && err == cudaSuccess) {
+      Work tw = base();
+      tw.in = b.bo; tw.out = b.t64;
+      tw_inv(tw);
+      err = blas(tp, B_TWIST, tw);
+    }
     Work d = base();
     links(d, U64, tp, 18, 0);
-    d.in = b.bo; d.out = b.bhat; d.y1 = b.be; d.c1 = 1.0; d.a = kappa;
+    d.in = ta != 0.0 ? b.t64 : b.bo; d.out = b.bhat; d.y1 = b.be; d.c1 = 1.0; d.a = kappa;
     if (err == cudaSuccess) err = dsl(tp, d, false);
     if (err == cudaSuccess) rc = read_sc(hs_);
     else rc = set_error(LQCD_ECUDA, "BiCGStab setup: %s", cudaGetErrorString(err));
@@ -150,10 +165,12 @@ int lqcd::bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kapp
     Work d1 = base();
     links(d1, U64, tp, 18, 1);
     d1.in = b.x64; d1.out = b.t64; d1.a = 1.0;
+    tw_inv(d1);
     Work d2 = base();
     links(d2, U64, tp, 18, 0);
     d2.in = b.t64; d2.out = b.u64; d2.y1 = b.bhat; d2.c1 = 1.0; d2.y2 = b.x64; d2.c2 = -1.0;
     d2.a = kappa * kappa; d2.red = 1; d2.fin = FIN_STORE0;
+    tw_a(d2);
     err = dsl(tp, d1, false);
     if (err == cudaSuccess) err = dsl(tp, d2, false);
     if (err != cudaSuccess) { rc = set_error(LQCD_ECUDA, "residual: %s", cudaGetErrorString(err)); break; }
@@ -189,10 +206,15 @@ int lqcd::bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kapp
     Work w2 = base();  // o = D_oe p
     links(w2, US, link_prec_for(sp), nr, 1);
     w2.in = b.p; w2.out = b.o; w2.a = 1.0; w2.run_if = S_RUNNING;
+    tw_inv(w2);
     Work w3 = base();  // v = p - k^2 D_eo o ; alpha = rho / <r0, v>
     links(w3, US, link_prec_for(sp), nr, 0);
     w3.in = b.o; w3.out = b.v; w3.y1 = b.p; w3.c1 = 1.0; w3.a = -kk; w3.zin = b.r0;
     w3.red = 2; w3.fin = FIN_BICG_ALPHA; w3.run_if = S_RUNNING;
+    if (ta != 0.0) {  // v = A p - k^2 D_eo o
+      w3.y1 = nullptr; w3.c1 = 0.0; w3.y2 = b.p; w3.c2 = 1.0;
+      tw_a(w3);
+    }
     Work w4 = base();  // s = r - alpha v
     w4.in = b.r; w4.out = b.s; w4.y1 = b.v; w4.run_if = S_RUNNING;
     Work w5 = w2;      // o = D_oe s
@@ -201,6 +223,10 @@ int lqcd::bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kapp
     links(w6, US, link_prec_for(sp), nr, 0);
     w6.in = b.o; w6.out = b.t; w6.y1 = b.s; w6.c1 = 1.0; w6.a = -kk;
     w6.red = 3; w6.fin = FIN_BICG_OMEGA; w6.run_if = S_RUNNING;
+    if (ta != 0.0) {  // t = A s - k^2 D_eo o; y1 = s stays (weight 0) for <t, s>
+      w6.c1 = 0.0; w6.y2 = b.s; w6.c2 = 1.0;
+      tw_a(w6);
+    }
     Work w7 = base();  // x += alpha p + omega s ; r = s - omega t ; rho_new, |r|^2
     w7.in = b.s; w7.y1 = b.t; w7.zin = b.p; w7.z = b.xs; w7.out = b.r; w7.y2 = b.r0;
     w7.red = 4; w7.fin = FIN_BICG_RES; w7.run_if = S_RUNNING;
@@ -236,19 +262,29 @@ int lqcd::bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kapp
   }
   double true_res = -1;
   if (rc == LQCD_OK) {
-    // x_o = b_o + kappa D_oe x_e, full FP64 residual, copy out
+    // x_o = A^-1 (b_o + kappa D_oe x_e), full FP64 residual, copy out
+    err = cudaSuccess;
+    if (ta != 0.0) {
+      Work tw = base();
+      tw.in = b.bo; tw.out = b.t64;
+      tw_inv(tw);
+      err = blas(tp, B_TWIST, tw);
+    }
     Work a = base();
     links(a, U64, tp, 18, 1);
-    a.in = b.x64; a.out = b.t64; a.y1 = b.bo; a.c1 = 1.0; a.a = kappa;
+    a.in = b.x64; a.out = b.t64; a.y1 = ta != 0.0 ? b.t64 : b.bo; a.c1 = 1.0; a.a = kappa;
+    tw_inv(a);
     Work re = base();
     links(re, U64, tp, 18, 0);
     re.in = b.t64; re.out = b.u64; re.y1 = b.be; re.c1 = 1.0; re.y2 = b.x64; re.c2 = -1.0;
     re.a = kappa; re.red = 1; re.fin = FIN_STORE0;
+    tw_a(re);
     Work ro = base();
     links(ro, U64, tp, 18, 1);
     ro.in = b.x64; ro.out = b.bhat; ro.y1 = b.bo; ro.c1 = 1.0; ro.y2 = b.t64; ro.c2 = -1.0;
     ro.a = kappa; ro.red = 1; ro.fin = FIN_STORE1;
-    err = dsl(tp, a, false);
+    tw_a(ro);
+    if (err == cudaSuccess) err = dsl(tp, a, false);
     if (err == cudaSuccess) err = dsl(tp, re, false);
     if (err == cudaSuccess) err = dsl(tp, ro, false);
     if (err == cudaSuccess) err = spinor_convert(b.x64, tp, x->half[0], x->prec, Vh, 1.0, st);

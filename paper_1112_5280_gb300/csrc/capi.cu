@@ -1,5 +1,6 @@
 // C ABI: contexts, gauge and spinor fields, and the Wilson-Dirac operators.
 #include <cstdio>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -99,6 +100,7 @@ Work blank_work(const Geom& g) {
   w.run_if = -1;
   w.fin = FIN_NONE;
   w.ntiles = (g.Vh + TILE - 1) / TILE;
+  w.tw_s = 1.0;
   return w;
 }
 
@@ -502,9 +504,10 @@ static int check_pair(const lqcd_gauge* g, const lqcd_field* a, const lqcd_field
   return LQCD_OK;
 }
 
-// out_p = a * D_{p,1-p} in + c1 * y1_p
-static int dslash_lin(const lqcd_gauge* gauge, int prec, const void* in, void* out, const void* y1,
-                      double a, double c1, int out_par, bool dag) {
+// out_p = T(ds, dt) (a * D_{p,1-p} in) + c1 * y1_p + c2 T(1, yt) y2_p, T(s, t) = s (1 + i t g5)
+static int dslash_tw(const lqcd_gauge* gauge, int prec, const void* in, void* out, const void* y1,
+                     const void* y2, double a, double c1, double c2, int out_par, bool dag,
+                     double ds, double dt, double yt) {
   lqcd_ctx* c = gauge->ctx;
   const void* base;
   int nr;
@@ -517,13 +520,22 @@ static int dslash_lin(const lqcd_gauge* gauge, int prec, const void* in, void* o
   w.Uout = parity_links(base, lp, nr, gauge->g.Vh, out_par);
   w.Uin = parity_links(base, lp, nr, gauge->g.Vh, 1 - out_par);
   w.y1 = y1;
+  w.y2 = y2;
   w.a = a;
   w.c1 = c1;
+  w.c2 = c2;
+  if (dt != 0.0 || ds != 1.0 || yt != 0.0) set_twist(w, ds, dt, yt);
   w.sc = c->scratch_sc;
   Launch L = single_launch(w, c->partials);
   LQCD_CK(launch_dslash(prec, nr, dag, EPI_LIN, L, 0, c->stream));
   c->launches++;
   return LQCD_OK;
+}
+
+// out_p = a * D_{p,1-p} in + c1 * y1_p
+static int dslash_lin(const lqcd_gauge* gauge, int prec, const void* in, void* out, const void* y1,
+                      double a, double c1, int out_par, bool dag) {
+  return dslash_tw(gauge, prec, in, out, y1, nullptr, a, c1, 0.0, out_par, dag, 1.0, 0.0, 0.0);
 }
 
 int lqcd_dslash_eo(const lqcd_gauge* g, const lqcd_field* in, lqcd_field* out, int out_parity,
@@ -647,29 +659,55 @@ void lqcd_dslash_batch_destroy(lqcd_dslash_batch* b) {
 
 int lqcd_apply_Mhat(const lqcd_gauge* g, double kappa, const lqcd_field* in, lqcd_field* out,
                     int dagger) {
+  return lqcd_apply_Mhat_tm(g, kappa, 0.0, in, out, dagger);
+}
+
+int lqcd_apply_M(const lqcd_gauge* g, double kappa, const lqcd_field* in, lqcd_field* out,
+                 int dagger) {
+  return lqcd_apply_M_tm(g, kappa, 0.0, in, out, dagger);
+}
+
+int lqcd_apply_Mhat_tm(const lqcd_gauge* g, double kappa, double mu, const lqcd_field* in,
+                       lqcd_field* out, int dagger) {
   clear_error();
+  if (!std::isfinite(kappa) || !std::isfinite(mu)) return set_error(LQCD_EINVAL, "kappa and mu must be finite");
   LQCD_TRY(check_pair(g, in, out));
   if (!in->half[0] || !out->half[0]) return set_error(LQCD_EINVAL, "fields must hold the even parity");
   if (in->half[0] == out->half[0]) return set_error(LQCD_EINVAL, "in and out must differ");
   lqcd_ctx* c = g->ctx;
   LQCD_TRY(ctx_set_device(c));
   LQCD_TRY(ctx_tmp(c, half_spinor_bytes(in->prec, g->g.Vh)));
-  LQCD_TRY(dslash_lin(g, in->prec, in->half[0], c->tmp, nullptr, 1.0, 0.0, 1, dagger != 0));
-  return dslash_lin(g, in->prec, c->tmp, out->half[0], in->half[0], -kappa * kappa, 1.0, 0,
-                    dagger != 0);
+  if (mu == 0.0) {
+    LQCD_TRY(dslash_lin(g, in->prec, in->half[0], c->tmp, nullptr, 1.0, 0.0, 1, dagger != 0));
+    return dslash_lin(g, in->prec, c->tmp, out->half[0], in->half[0], -kappa * kappa, 1.0, 0,
+                      dagger != 0);
+  }
+  // tmp = A^-1 D_oe in (A^-dag D^dag_oe), out = A in - k^2 D_eo tmp (A^dag, D^dag)
+  const double a = (dagger ? -2.0 : 2.0) * kappa * mu;
+  LQCD_TRY(dslash_tw(g, in->prec, in->half[0], c->tmp, nullptr, nullptr, 1.0, 0.0, 0.0, 1,
+                     dagger != 0, 1.0 / (1.0 + a * a), -a, 0.0));
+  return dslash_tw(g, in->prec, c->tmp, out->half[0], nullptr, in->half[0], -kappa * kappa, 0.0, 1.0,
+                   0, dagger != 0, 1.0, 0.0, a);
 }
 
-int lqcd_apply_M(const lqcd_gauge* g, double kappa, const lqcd_field* in, lqcd_field* out,
-                 int dagger) {
+int lqcd_apply_M_tm(const lqcd_gauge* g, double kappa, double mu, const lqcd_field* in,
+                    lqcd_field* out, int dagger) {
   clear_error();
+  if (!std::isfinite(kappa) || !std::isfinite(mu)) return set_error(LQCD_EINVAL, "kappa and mu must be finite");
   LQCD_TRY(check_pair(g, in, out));
   if (in->subset != LQCD_FULL || out->subset != LQCD_FULL)
     return set_error(LQCD_EINVAL, "apply_M needs FULL fields");
   if (in == out) return set_error(LQCD_EINVAL, "in and out must differ");
   LQCD_TRY(ctx_set_device(g->ctx));
-  for (int p = 0; p < 2; ++p)
-    LQCD_TRY(dslash_lin(g, in->prec, in->half[1 - p], out->half[p], in->half[p], -kappa, 1.0, p,
-                        dagger != 0));
+  const double a = (dagger ? -2.0 : 2.0) * kappa * mu;  // A (A^dag)
+  for (int p = 0; p < 2; ++p) {
+    if (mu == 0.0)
+      LQCD_TRY(dslash_lin(g, in->prec, in->half[1 - p], out->half[p], in->half[p], -kappa, 1.0, p,
+                          dagger != 0));
+    else
+      LQCD_TRY(dslash_tw(g, in->prec, in->half[1 - p], out->half[p], nullptr, in->half[p], -kappa,
+                         0.0, 1.0, p, dagger != 0, 1.0, 0.0, a));
+  }
   return LQCD_OK;
 }
 

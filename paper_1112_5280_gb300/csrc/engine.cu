@@ -16,11 +16,19 @@
 //    kappa D_oe x_e and the full ||b - M x|| is measured in FP64.
 // With FP64 sloppy storage and delta = 0 this is the plain FP64 CG.
 //
+// Twisted mass (Section 3, M = A - kappa D with the site-diagonal A = 1 + i a g5,
+// a = 2 kappa mu): the Schur operator becomes Mhat = A - kappa^2 D_eo A^-1 D_oe,
+// Mhat^dag = A^dag - kappa^2 D^dag_eo A^-dag D^dag_oe, bhat = b_e + kappa D_eo A^-1 b_o
+// and x_o = A^-1 (b_o + kappa D_oe x_e). A^-1 = (1 - i a g5) / (1 + a^2); every factor
+// of A is applied inside the Dslash epilogues (twist fields of Work), so a twisted
+// iteration has the launches and the HBM traffic of a Wilson one.
+//
 // Every slot runs its own scalar recurrences on the device (finishers in
 // batch.cuh); the host replays CUDA graphs of `chunk` iterations and polls
 // slot states between replays.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <vector>
@@ -71,7 +79,7 @@ struct Request {
   long long id = 0;
   const lqcd_gauge* gauge = nullptr;
   Geom g{};
-  double kappa = 0, tol = 0;
+  double kappa = 0, tol = 0, mu = 0;
   int slot = -1;
   SlotBuf buf;
   int tile0 = 0, ntiles = 0;
@@ -204,6 +212,20 @@ void step_works(const lqcd_engine* e, const Request& q, Work out[NSTEP]) {
   rh.red = 1; rh.fin = FIN_RHO; rh.run_if = S_UPDATE;
   Work& cv = out[RU_CONV];
   cv.in = b.u64; cv.out = b.r; cv.z = b.p; cv.fin = FIN_RESUME; cv.run_if = S_UPDATE;
+  const double a = 2.0 * q.kappa * q.mu;
+  if (a != 0.0) {
+    const double s = 1.0 / (1.0 + a * a);
+    set_twist(k1, s, -a, 0.0);  // t = A^-1 D_oe p
+    k2.y1 = nullptr; k2.c1 = 0.0; k2.y2 = b.p; k2.c2 = 1.0;
+    set_twist(k2, 1.0, 0.0, a);   // q = A p - k^2 D_eo t
+    set_twist(k3, s, a, 0.0);     // t = A^-dag D^dag_oe q
+    set_twist(k4, 1.0, 0.0, -a);  // r -= alpha (A^dag q - k^2 D^dag_eo t)
+    set_twist(d1, s, -a, 0.0);
+    set_twist(rs, 1.0, 0.0, a);   // u = bhat - A x + k^2 D_eo t
+    set_twist(d2, s, a, 0.0);
+    rh.y1 = nullptr; rh.c1 = 0.0; rh.y2 = b.u64; rh.c2 = 1.0;
+    set_twist(rh, 1.0, 0.0, -a);  // rho = A^dag u - k^2 D^dag_eo t
+  }
 }
 
 struct StepKind {
@@ -388,25 +410,39 @@ int finalize_launch(lqcd_engine* e, Request& q) {
   const void* U64 = q.gauge->copy[tp][0];
   const SlotBuf& b = q.buf;
   cudaStream_t st = e->ctx->stream;
+  const double ta = 2.0 * q.kappa * q.mu, ts = 1.0 / (1.0 + ta * ta);
+  // tw: 0 none, 1 the hopping term times A^-1, 2 the y2 operand times A
   auto lin = [&](int out_par, const void* in, void* out, const void* y1, double c1, const void* y2,
-                 double c2, double a, int fin) -> int {
+                 double c2, double a, int fin, int tw) -> int {
     Work w = slot_work(e, q);
     w.out_par = out_par;
     w.Uout = parity_links(U64, tp, 18, g.Vh, out_par);
     w.Uin = parity_links(U64, tp, 18, g.Vh, 1 - out_par);
     w.in = in; w.out = out; w.y1 = y1; w.c1 = c1; w.y2 = y2; w.c2 = c2; w.a = a;
     w.red = fin != FIN_NONE ? 1 : 0; w.fin = fin; w.run_if = -1;
+    if (ta != 0.0 && tw == 1) set_twist(w, ts, -ta, 0.0);
+    if (ta != 0.0 && tw == 2) set_twist(w, 1.0, 0.0, ta);
     Launch L = single_launch(w, e->d_partials);
     e->ctx->launches++;
     LQCD_CK(launch_dslash(tp, 18, false, EPI_LIN, L, 0, st));
     return LQCD_OK;
   };
   int rc;
-  // x_o = b_o + kappa D_oe x_e
-  if ((rc = lin(1, b.x64, b.t64, b.bo, 1.0, nullptr, 0.0, q.kappa, FIN_NONE))) return rc;
-  // r_e = b_e - x_e + kappa D_eo x_o ; r_o = b_o - x_o + kappa D_oe x_e  (full M, FP64)
-  if ((rc = lin(0, b.t64, b.u64, b.be, 1.0, b.x64, -1.0, q.kappa, FIN_STORE0))) return rc;
-  if ((rc = lin(1, b.x64, b.bhat, b.bo, 1.0, b.t64, -1.0, q.kappa, FIN_STORE1))) return rc;
+  const void* bo = b.bo;
+  if (ta != 0.0) {
+    // t = A^-1 b_o, then x_o = t + kappa A^-1 D_oe x_e
+    Work w = slot_work(e, q);
+    w.in = b.bo; w.out = b.t64; w.run_if = -1;
+    set_twist(w, ts, -ta, 0.0);
+    e->ctx->launches++;
+    LQCD_CK(launch_blas(tp, B_TWIST, single_launch(w, e->d_partials), 0, st));
+    bo = b.t64;
+  }
+  // x_o = A^-1 (b_o + kappa D_oe x_e)
+  if ((rc = lin(1, b.x64, b.t64, bo, 1.0, nullptr, 0.0, q.kappa, FIN_NONE, 1))) return rc;
+  // r_e = b_e - A x_e + kappa D_eo x_o ; r_o = b_o - A x_o + kappa D_oe x_e  (full M, FP64)
+  if ((rc = lin(0, b.t64, b.u64, b.be, 1.0, b.x64, -1.0, q.kappa, FIN_STORE0, 2))) return rc;
+  if ((rc = lin(1, b.x64, b.bhat, b.bo, 1.0, b.t64, -1.0, q.kappa, FIN_STORE1, 2))) return rc;
   return LQCD_OK;
 }
 
@@ -427,6 +463,7 @@ void lqcd_solve_opts_default(lqcd_solve_opts* o) {
   o->use_graph = 1;
   o->ru_interval = 0;
   o->true_prec = -1;
+  o->mu = 0.0;
 }
 
 int lqcd_engine_create(lqcd_ctx* c, const lqcd_solve_opts* opts, size_t budget, int max_slots,
@@ -503,8 +540,18 @@ size_t lqcd_engine_request_bytes(const lqcd_engine* e, const int dims[4]) {
 
 int lqcd_engine_submit(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field* src, double kappa,
                        double tol, long long* request_id) {
+  if (!e) {
+    clear_error();
+    return set_error(LQCD_EINVAL, "engine is NULL");
+  }
+  return lqcd_engine_submit_tm(e, gauge, src, kappa, e->opts.mu, tol, request_id);
+}
+
+int lqcd_engine_submit_tm(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field* src, double kappa,
+                          double mu, double tol, long long* request_id) {
   clear_error();
   if (!e || !gauge || !src || !request_id) return set_error(LQCD_EINVAL, "NULL argument");
+  if (!std::isfinite(mu) || !std::isfinite(kappa)) return set_error(LQCD_EINVAL, "kappa and mu must be finite");
   if (src->prec != LQCD_F64 || src->subset != LQCD_FULL)
     return set_error(LQCD_EINVAL, "source must be a FULL FP64 field");
   if (memcmp(src->g.L, gauge->g.L, sizeof src->g.L)) return set_error(LQCD_EINVAL, "lattice mismatch");
@@ -532,6 +579,7 @@ int lqcd_engine_submit(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field
   q.g = gauge->g;
   q.kappa = kappa;
   q.tol = tol;
+  q.mu = mu;
   q.ntiles = (q.g.Vh + TILE - 1) / TILE;
   q.t0 = std::chrono::steady_clock::now();
   int rc = alloc_block(e, need, &q.buf.block);
@@ -569,13 +617,24 @@ int lqcd_engine_submit(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field
       k_slot_init<<<1, 1, 0, st>>>(sc, tol * tol, 24.0 * q.g.Vh, e->opts.maxiter, e->delta2);
       err = cudaGetLastError();
     }
+    const double ta = 2.0 * kappa * mu;
+    if (err == cudaSuccess && ta != 0.0) {
+      // t = A^-1 b_o
+      Work w3 = slot_work(e, R);
+      w3.in = R.buf.bo;
+      w3.out = R.buf.t64;
+      set_twist(w3, 1.0 / (1.0 + ta * ta), -ta, 0.0);
+      err = launch_blas(e->tp, B_TWIST, single_launch(w3, e->d_partials), 0, st);
+      c->launches++;
+    }
     if (err == cudaSuccess) {
+      // bhat_e = b_e + kappa D_eo A^-1 b_o
       Work d = slot_work(e, R);
       const void* U64 = gauge->copy[e->tp][0];
       d.out_par = 0;
       d.Uout = parity_links(U64, e->tp, 18, q.g.Vh, 0);
       d.Uin = parity_links(U64, e->tp, 18, q.g.Vh, 1);
-      d.in = R.buf.bo;
+      d.in = ta != 0.0 ? R.buf.t64 : R.buf.bo;
       d.out = R.buf.bhat;
       d.y1 = R.buf.be;
       d.c1 = 1.0;
@@ -774,7 +833,8 @@ int lqcd_solve_multi(const lqcd_gauge* g, int n, const lqcd_field* const* srcs, 
   int rc = lqcd_engine_create(g->ctx, &o, 0, n, &e);
   if (rc != LQCD_OK) return rc;
   std::vector<long long> ids(n);
-  for (int i = 0; i < n && rc == LQCD_OK; ++i) rc = lqcd_engine_submit(e, g, srcs[i], kappa, tol, &ids[i]);
+  for (int i = 0; i < n && rc == LQCD_OK; ++i)
+    rc = lqcd_engine_submit_tm(e, g, srcs[i], kappa, o.mu, tol, &ids[i]);
   if (rc == LQCD_OK) rc = run_engine(e, n, ids.data(), xs, infos);
   lqcd_engine_destroy(e);
   if (infos && rc != LQCD_ECUDA && rc != LQCD_EINVAL) {

@@ -61,6 +61,32 @@ __device__ __forceinline__ double cvt<double>(df64 x) { return (double)x; }
 template <>
 __device__ __forceinline__ df64 cvt<df64>(df64 x) { return x; }
 
+// v <- s (1 + i t g5) v for the complex components of a site (colour-major order:
+// component c has spin c % 4; g5 = +1 on spins 0, 1 and -1 on spins 2, 3).
+template <typename R>
+__device__ __forceinline__ void twist24(R v[24], double sd, double td) {
+  const R s = R(sd), t = R(td);
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    const R re = v[2 * c], im = v[2 * c + 1];
+    const R tt = (c % 4) < 2 ? t : -t;
+    v[2 * c] = s * (re - tt * im);
+    v[2 * c + 1] = s * (im + tt * re);
+  }
+}
+// the same for the 4 spins of one colour (v[2 spin], v[2 spin + 1])
+template <typename R>
+__device__ __forceinline__ void twist8(R v[8], double sd, double td) {
+  const R s = R(sd), t = R(td);
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp) {
+    const R re = v[2 * sp], im = v[2 * sp + 1];
+    const R tt = sp < 2 ? t : -t;
+    v[2 * sp] = s * (re - tt * im);
+    v[2 * sp + 1] = s * (im + tt * re);
+  }
+}
+
 // Whole-CTA exit for a single-slot launch whose slot does not run.
 __device__ __forceinline__ bool single_slot_idle(const Launch& L) {
   return L.nslots == 1 && !slot_runs(work_of(L, 0));
@@ -87,6 +113,7 @@ __global__ void __launch_bounds__(TILE, DslashMinBlocks<SP>::value) k_dslash(con
       if (EPI == EPI_LIN) {
 #pragma unroll
         for (int i = 0; i < 24; ++i) acc[i] *= a;
+        if (w.twist) twist24(acc, w.tw_s, w.tw_t);
         R y[24];
         if (w.y1) {
           SpinorIO<SP>::load(w.y1, w.g.Vh, h, y);
@@ -97,6 +124,7 @@ __global__ void __launch_bounds__(TILE, DslashMinBlocks<SP>::value) k_dslash(con
         if (w.y2) {
           R y2[24];
           SpinorIO<SP>::load(w.y2, w.g.Vh, h, y2);
+          if (w.twist) twist24(y2, 1.0, w.ty_t);
           const R c = (R)w.c2;
 #pragma unroll
           for (int i = 0; i < 24; ++i) acc[i] += c * y2[i];
@@ -117,6 +145,10 @@ __global__ void __launch_bounds__(TILE, DslashMinBlocks<SP>::value) k_dslash(con
         R y[24], r[24];
         SpinorIO<SP>::load(w.y1, w.g.Vh, h, y);
         SpinorIO<SP>::load(w.out, w.g.Vh, h, r);
+        if (w.twist) {
+          twist24(acc, w.tw_s, w.tw_t);
+          twist24(y, 1.0, w.ty_t);
+        }
 #pragma unroll
         for (int i = 0; i < 24; ++i) r[i] -= alpha * (y[i] + a * acc[i]);
         SpinorIO<SP>::store(w.out, w.g.Vh, h, r);
@@ -183,6 +215,7 @@ __global__ void __launch_bounds__(3 * TILE, LQCD_DSLASH3_MIN_BLOCKS) k_dslash3(c
       if (EPI == EPI_LIN) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) acc[i] *= a;
+        if (w.twist) twist8(acc, w.tw_s, w.tw_t);
         R y[8];
         if (w.y1) {
           SpinorIO<SP>::load_colour(w.y1, Vh, h, col, y);
@@ -193,6 +226,7 @@ __global__ void __launch_bounds__(3 * TILE, LQCD_DSLASH3_MIN_BLOCKS) k_dslash3(c
         if (w.y2) {
           R y2[8];
           SpinorIO<SP>::load_colour(w.y2, Vh, h, col, y2);
+          if (w.twist) twist8(y2, 1.0, w.ty_t);
           const R c = (R)w.c2;
 #pragma unroll
           for (int i = 0; i < 8; ++i) acc[i] += c * y2[i];
@@ -213,6 +247,10 @@ __global__ void __launch_bounds__(3 * TILE, LQCD_DSLASH3_MIN_BLOCKS) k_dslash3(c
         R y[8], r[8];
         SpinorIO<SP>::load_colour(w.y1, Vh, h, col, y);
         SpinorIO<SP>::load_colour(w.out, Vh, h, col, r);
+        if (w.twist) {
+          twist8(acc, w.tw_s, w.tw_t);
+          twist8(y, 1.0, w.ty_t);
+        }
 #pragma unroll
         for (int i = 0; i < 8; ++i) r[i] -= alpha * (y[i] + a * acc[i]);
         SpinorIO<SP>::store_colour(w.out, Vh, h, col, r);
@@ -244,6 +282,7 @@ enum Blas {
   B_BICG_S,       // s(out) = r(in) - alpha v(y1)
   B_BICG_X,       // x(z) += alpha p(zin) + omega s(in) ; r(out) = s - omega t(y1) ; <r0(y2), r>, |r|^2
   B_FOLD64,       // x64(out) += a * xs(in) (SP) ; xs = 0
+  B_TWIST,        // out = tw_s (1 + i tw_t g5) in
 };
 
 // out = x + c * y (complex c)
@@ -335,6 +374,11 @@ __global__ void __launch_bounds__(TILE) k_blas(const Launch L) {
         }
         SpinorIO<SP>::store(w.out, Vh, h, o);
         if (w.red == 1) v0 = site_norm2(o);
+      } else if (OP == B_TWIST) {
+        R v[24];
+        SpinorIO<SP>::load(w.in, Vh, h, v);
+        twist24(v, w.tw_s, w.tw_t);
+        SpinorIO<SP>::store(w.out, Vh, h, v);
       } else if (OP == B_ZERO) {
         R v[24];
 #pragma unroll

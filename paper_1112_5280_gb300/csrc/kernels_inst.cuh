@@ -61,6 +61,7 @@ cudaError_t LQCD_CAT(launch_blas_, LQCD_SFX)(int op, int tp, const Launch& L, in
     case B_CG_P: return go_blas<B_CG_P, SPX>(L, grid, s);
     case B_NORM: return go_blas<B_NORM, SPX>(L, grid, s);
     case B_ZERO: return go_blas<B_ZERO, SPX>(L, grid, s);
+    case B_TWIST: return go_blas<B_TWIST, SPX>(L, grid, s);
     case B_BICG_P: return go_blas<B_BICG_P, SPX>(L, grid, s);
     case B_BICG_S: return go_blas<B_BICG_S, SPX>(L, grid, s);
     case B_BICG_X: return go_blas<B_BICG_X, SPX>(L, grid, s);

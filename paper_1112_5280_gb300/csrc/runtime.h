@@ -83,6 +83,14 @@ int bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kappa, dou
 // a single-slot launch description
 Launch single_launch(const Work& w, double* partials);
 Work blank_work(const Geom& g);
+// Twisted-mass factors of a Work: the hopping term times ds (1 + i dt g5), the operand
+// vector (y2 of the linear epilogue, y1 of the CG step) times (1 + i yt g5).
+inline void set_twist(Work& w, double ds, double dt, double yt) {
+  w.twist = 1;
+  w.tw_s = ds;
+  w.tw_t = dt;
+  w.ty_t = yt;
+}
 
 }  // namespace lqcd
 

@@ -32,7 +32,8 @@ class LqcdError(RuntimeError):
 class SolveOpts(C.Structure):
     _fields_ = [("solver", C.c_int), ("sloppy_prec", C.c_int), ("sloppy_compress", C.c_int),
                 ("maxiter", C.c_int), ("delta", C.c_double), ("chunk", C.c_int),
-                ("use_graph", C.c_int), ("ru_interval", C.c_int), ("true_prec", C.c_int)]
+                ("use_graph", C.c_int), ("ru_interval", C.c_int), ("true_prec", C.c_int),
+                ("pad", C.c_int), ("mu", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -96,6 +97,8 @@ def load(build_if_missing: bool = True):
     _sig(lib, "lqcd_dslash_eo", i, [_VP, _VP, _VP, i, i])
     _sig(lib, "lqcd_apply_Mhat", i, [_VP, d, _VP, _VP, i])
     _sig(lib, "lqcd_apply_M", i, [_VP, d, _VP, _VP, i])
+    _sig(lib, "lqcd_apply_Mhat_tm", i, [_VP, d, d, _VP, _VP, i])
+    _sig(lib, "lqcd_apply_M_tm", i, [_VP, d, d, _VP, _VP, i])
     _sig(lib, "lqcd_dslash_batch_create", i, [i, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), i, i,
                                               C.POINTER(_VP)])
     _sig(lib, "lqcd_dslash_batch_apply", i, [_VP])
@@ -113,6 +116,7 @@ def load(build_if_missing: bool = True):
         _sig(lib, "lqcd_engine_create", i, [_VP, C.POINTER(SolveOpts), sz, i, C.POINTER(_VP)])
         _sig(lib, "lqcd_engine_request_bytes", sz, [_VP, _IP])
         _sig(lib, "lqcd_engine_submit", i, [_VP, _VP, _VP, d, d, C.POINTER(ll)])
+        _sig(lib, "lqcd_engine_submit_tm", i, [_VP, _VP, _VP, d, d, d, C.POINTER(ll)])
         _sig(lib, "lqcd_engine_step", i, [_VP, _IP])
         _sig(lib, "lqcd_engine_completed", i, [_VP, C.POINTER(ll), i, _IP])
         _sig(lib, "lqcd_engine_result", i, [_VP, ll, _VP, C.POINTER(SolveInfo)])
@@ -328,8 +332,13 @@ class DslashBatch:
             pass
 
 
-def apply_Mhat(gauge: Gauge, kappa: float, fin: Field, fout: Field, dagger=False):
-    _check(gauge._lib.lqcd_apply_Mhat(gauge.h, float(kappa), fin.h, fout.h, int(bool(dagger))))
+def apply_Mhat(gauge: Gauge, kappa: float, fin: Field, fout: Field, dagger=False, mu=0.0):
+    """Even-odd Schur operator; mu != 0 gives the twisted-mass one, A - k^2 D_eo A^-1 D_oe."""
+    if mu == 0.0:
+        _check(gauge._lib.lqcd_apply_Mhat(gauge.h, float(kappa), fin.h, fout.h, int(bool(dagger))))
+    else:
+        _check(gauge._lib.lqcd_apply_Mhat_tm(gauge.h, float(kappa), float(mu), fin.h, fout.h,
+                                             int(bool(dagger))))
 
 
 def apply_Mhat_noalloc(gauge: Gauge, kappa: float, fin: Field, fout: Field, dagger=False):
@@ -339,8 +348,13 @@ def apply_Mhat_noalloc(gauge: Gauge, kappa: float, fin: Field, fout: Field, dagg
                                               int(bool(dagger))))
 
 
-def apply_M(gauge: Gauge, kappa: float, fin: Field, fout: Field, dagger=False):
-    _check(gauge._lib.lqcd_apply_M(gauge.h, float(kappa), fin.h, fout.h, int(bool(dagger))))
+def apply_M(gauge: Gauge, kappa: float, fin: Field, fout: Field, dagger=False, mu=0.0):
+    """Full operator 1 - kappa D (+ 2 i kappa mu g5 for the twisted mass)."""
+    if mu == 0.0:
+        _check(gauge._lib.lqcd_apply_M(gauge.h, float(kappa), fin.h, fout.h, int(bool(dagger))))
+    else:
+        _check(gauge._lib.lqcd_apply_M_tm(gauge.h, float(kappa), float(mu), fin.h, fout.h,
+                                          int(bool(dagger))))
 
 
 GAMMA_CODES = {"1": 0, "g5": 1, "gx": 2, "gy": 3, "gz": 4, "gt": 5,
@@ -372,7 +386,10 @@ def set_grid_multiplier(family: int, mult: int):
 def solve_opts(**kw) -> SolveOpts:
     o = SolveOpts()
     load().lqcd_solve_opts_default(C.byref(o))
+    names = {f[0] for f in SolveOpts._fields_}
     for k, v in kw.items():
+        if k not in names or k == "pad":
+            raise TypeError(f"unknown solve option {k!r}")
         if k in ("sloppy_prec", "true_prec") and isinstance(v, str):
             v = _prec(v)
         setattr(o, k, v)
@@ -430,11 +447,16 @@ class Engine:
     def request_bytes(self, dims) -> int:
         return int(self._lib.lqcd_engine_request_bytes(self.h, _dims(dims)))
 
-    def submit(self, gauge: Gauge, src: Field, kappa, tol):
-        """Returns a request id, or None when the engine is busy (retry later)."""
+    def submit(self, gauge: Gauge, src: Field, kappa, tol, mu=None):
+        """Returns a request id, or None when the engine is busy (retry later). mu: the
+        request's twisted mass (None: the engine's option)."""
         rid = C.c_longlong()
-        rc = self._lib.lqcd_engine_submit(self.h, gauge.h, src.h, float(kappa), float(tol),
-                                          C.byref(rid))
+        if mu is None:
+            rc = self._lib.lqcd_engine_submit(self.h, gauge.h, src.h, float(kappa), float(tol),
+                                              C.byref(rid))
+        else:
+            rc = self._lib.lqcd_engine_submit_tm(self.h, gauge.h, src.h, float(kappa), float(mu),
+                                                 float(tol), C.byref(rid))
         if rc == EBUSY:
             return None
         _check(rc)
