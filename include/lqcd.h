@@ -107,7 +107,8 @@ LQCD_API long long lqcd_ctx_launch_count(const lqcd_ctx* ctx);
  * always kept (true residuals); `prec` / `compress` (18 or 12 reals, row 2
  * rebuilt from rows 0-1 as conj(row0 x row1), the RECONSTRUCT TWELVE of
  * Section 3) choose the default copy used for fields of that precision.
- * prec LQCD_F16 and LQCD_BF16 both store FP16 links. t_bc: +1 or -1.
+ * prec LQCD_F16 and LQCD_BF16 both store FP16 links; LQCD_DF64 links always keep
+ * 18 reals (compress is ignored for them). t_bc: +1 or -1.
  * The 12-real form assumes det U = 1 (true for the seeded generator). */
 LQCD_API int lqcd_gauge_upload(lqcd_ctx* ctx, const int dims[4], const double* host_U, int prec,
                       int compress, int t_bc, lqcd_gauge** out);
@@ -308,6 +309,35 @@ LQCD_API void lqcd_set_grid_multiplier(int family, int mult);
 /* Dslash kernel form for LQCD_DF64 fields: 0 = one thread per output site, 1 = three
  * threads per site, one per output colour (default). Results agree to rounding. */
 LQCD_API int lqcd_set_dslash_form(int prec, int form);
+
+/* Launch autotuner: the persistent batched Dslash takes its grid shape and kernel form
+ * from measurement on this device. lqcd_autotune_dslash times one batched Dslash launch
+ * over n slots (slot i on gauge g[i], which may repeat; fields of precision prec, zero
+ * valued scratch allocated and freed by the call) for every distinct persistent grid,
+ * 1 .. occupancy-limit CTAs per SM, of every compiled kernel form, and records the
+ * fastest. The default (occupancy limit, default form) is kept unless another choice is
+ * more than 2% faster. The record applies to every later Dslash launch (lqcd_dslash_eo,
+ * batches, operators, solves, engines) of the same precision and link reals whose tile
+ * count (64 output sites a tile) has the same floor(log2). Synchronous; not to be run
+ * while another thread launches on the same device. The table is process-wide. */
+typedef struct lqcd_tune_result {
+  int prec;         /* spinor precision of the key */
+  int nr;           /* link reals of the key (12 or 18) */
+  int ntiles;       /* tiles of the tuned launch */
+  int ctas_per_sm;  /* chosen persistent grid, CTAs per SM (0: occupancy limit) */
+  int form;         /* chosen kernel form: 0 one thread per site, 1 colour split (DF64) */
+  int candidates;   /* configurations timed */
+  double us_best;   /* per launch, chosen configuration */
+  double us_default;/* per launch, untuned default */
+} lqcd_tune_result;
+LQCD_API int lqcd_autotune_dslash(int n, const lqcd_gauge* const* g, int prec, lqcd_tune_result* out);
+/* Copies up to max table entries into out; *n = entries in the table. */
+LQCD_API int lqcd_tune_entries(lqcd_tune_result* out, int max, int* n);
+LQCD_API void lqcd_tune_clear(void);
+/* Text file of the table, tagged with the device name and SM count; loading a file
+ * made on another device model, or a malformed file, gives LQCD_EINVAL and loads nothing. */
+LQCD_API int lqcd_tune_save(const char* path);
+LQCD_API int lqcd_tune_load(const char* path);
 
 #ifdef __cplusplus
 }

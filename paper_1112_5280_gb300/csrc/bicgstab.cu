@@ -115,7 +115,8 @@ int lqcd::bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kapp
   };
   auto dsl = [&](int prec, const Work& w, bool dag) {
     c->launches++;
-    return launch_dslash(prec, prec == tp ? 18 : nr, dag, EPI_LIN, single_launch(w, c->partials), 0, st);
+    return launch_dslash(prec, prec == tp ? 18 : nr, dag, w.twist ? EPI_LIN_TW : EPI_LIN,
+                         single_launch(w, c->partials), 0, st);
   };
   auto blas = [&](int prec, int op, const Work& w) {
     c->launches++;

@@ -80,7 +80,7 @@ int gauge_links(const lqcd_gauge* gc, int field_prec, const void** base, int* nr
   lqcd_gauge* g = const_cast<lqcd_gauge*>(gc);
   const int lp = link_prec_for(field_prec);
   if (lp < 0 || lp >= NPREC) return set_error(LQCD_EINVAL, "link precision %d", lp);
-  const int n = g->compress;
+  const int n = (lp == P_DF64) ? 18 : g->compress;  // double-float links keep 18 reals
   void*& slot = g->copy[lp][n == 12];
   if (!slot) {
     size_t b = gauge_copy_bytes(lp, n, g->g.Vh);
@@ -309,6 +309,7 @@ int lqcd_gauge_add_copy(lqcd_gauge* g, int prec, int compress) {
   LQCD_TRY(ctx_set_device(g->ctx));
   const int lp = link_prec_for(prec);
   if (lp < 0 || lp >= NPREC) return set_error(LQCD_EINVAL, "link precision %d", lp);
+  if (lp == P_DF64) compress = 18;  // double-float links keep 18 reals
   void*& slot = g->copy[lp][compress == 12];
   if (slot) return LQCD_OK;
   const size_t b = gauge_copy_bytes(lp, compress, g->g.Vh);
@@ -527,7 +528,7 @@ static int dslash_tw(const lqcd_gauge* gauge, int prec, const void* in, void* ou
   if (dt != 0.0 || ds != 1.0 || yt != 0.0) set_twist(w, ds, dt, yt);
   w.sc = c->scratch_sc;
   Launch L = single_launch(w, c->partials);
-  LQCD_CK(launch_dslash(prec, nr, dag, EPI_LIN, L, 0, c->stream));
+  LQCD_CK(launch_dslash(prec, nr, dag, w.twist ? EPI_LIN_TW : EPI_LIN, L, 0, c->stream));
   c->launches++;
   return LQCD_OK;
 }

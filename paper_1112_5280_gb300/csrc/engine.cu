@@ -117,6 +117,7 @@ struct lqcd_engine {
   bool dirty = true;
   int ntiles_total = 0;
   int interleave = 0;
+  bool any_twist = false;  // some active request has mu != 0
   cudaGraphExec_t exec = nullptr;
   std::vector<Work> h_works;
 };
@@ -252,12 +253,15 @@ StepKind kind_of(int s) {
   return {false, false, false, 0};
 }
 
-cudaError_t issue(lqcd_engine* e, int s, const Launch& L) {
+// tw: some slot of the launch is twisted (its Dslash steps take the twisted epilogues;
+// untwisted slots carry the identity twist there and give the same bits)
+cudaError_t issue(lqcd_engine* e, int s, const Launch& L, bool tw) {
   const StepKind k = kind_of(s);
   e->ctx->launches++;
   if (k.dslash) {
-    if (k.f64) return launch_dslash(e->tp, 18, k.dag, k.epi_or_op, L, 0, e->ctx->stream);
-    return launch_dslash(e->sp, e->nr, k.dag, k.epi_or_op, L, 0, e->ctx->stream);
+    const int epi = k.epi_or_op + (tw ? EPI_LIN_TW - EPI_LIN : 0);
+    if (k.f64) return launch_dslash(e->tp, 18, k.dag, epi, L, 0, e->ctx->stream);
+    return launch_dslash(e->sp, e->nr, k.dag, epi, L, 0, e->ctx->stream);
   }
   const int prec = (k.epi_or_op == B_RU_FOLD) ? e->xp : e->sp;
   return launch_blas(prec, k.epi_or_op, L, 0, e->ctx->stream, e->tp);
@@ -278,12 +282,12 @@ Launch batch_launch(const lqcd_engine* e, int s) {
 cudaError_t issue_iteration_block(lqcd_engine* e, int iters) {
   for (int it = 0; it < iters; ++it) {
     for (int s : {K1, K2, K3, K4, K6}) {
-      cudaError_t err = issue(e, s, batch_launch(e, s));
+      cudaError_t err = issue(e, s, batch_launch(e, s), e->any_twist);
       if (err != cudaSuccess) return err;
     }
     if ((it + 1) % e->ru_every == 0 || it + 1 == iters) {
       for (int s : {RU_FOLD, RU_D1, RU_RES, RU_D2, RU_RHO, RU_CONV}) {
-        cudaError_t err = issue(e, s, batch_launch(e, s));
+        cudaError_t err = issue(e, s, batch_launch(e, s), e->any_twist);
         if (err != cudaSuccess) return err;
       }
     }
@@ -299,7 +303,11 @@ int rebuild(lqcd_engine* e) {
   // consecutive tiles then share links, which stream from HBM once per site block
   const lqcd_gauge* g0 = e->reqs[e->active[0]].gauge;
   bool same = true;
-  for (long long id : e->active) same = same && e->reqs[id].gauge == g0;
+  e->any_twist = false;
+  for (long long id : e->active) {
+    same = same && e->reqs[id].gauge == g0;
+    e->any_twist = e->any_twist || e->reqs[id].mu != 0.0;
+  }
   e->interleave = (same && n > 1) ? 1 : 0;
   std::vector<int> prefix(n + 1, 0);
   e->h_works.assign((size_t)NSTEP * e->max_slots, Work{});
@@ -424,7 +432,7 @@ int finalize_launch(lqcd_engine* e, Request& q) {
     if (ta != 0.0 && tw == 2) set_twist(w, 1.0, 0.0, ta);
     Launch L = single_launch(w, e->d_partials);
     e->ctx->launches++;
-    LQCD_CK(launch_dslash(tp, 18, false, EPI_LIN, L, 0, st));
+    LQCD_CK(launch_dslash(tp, 18, false, w.twist ? EPI_LIN_TW : EPI_LIN, L, 0, st));
     return LQCD_OK;
   };
   int rc;
@@ -647,7 +655,7 @@ int lqcd_engine_submit_tm(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_fi
       step_works(e, R, w2);
       for (int s : {RU_FOLD, RU_D1, RU_RES, RU_D2, RU_RHO, RU_CONV}) {
         if (err != cudaSuccess) break;
-        err = issue(e, s, single_launch(w2[s], e->d_partials));
+        err = issue(e, s, single_launch(w2[s], e->d_partials), mu != 0.0);
       }
     }
     c->launches += 4;

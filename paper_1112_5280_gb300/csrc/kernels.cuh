@@ -6,7 +6,15 @@
 
 namespace lqcd {
 
-enum Epi { EPI_LIN = 0, EPI_CG = 1 };
+// EPI_*_TW: the same epilogues with the twisted-mass factors of the Work (site-diagonal
+// s (1 + i t g5) on the hopping term and on the operand vector); separate instantiations
+// keep the Wilson kernels free of the twist code.
+enum Epi { EPI_LIN = 0, EPI_CG = 1, EPI_LIN_TW = 2, EPI_CG_TW = 3 };
+template <int EPI>
+struct EpiTraits {
+  static constexpr bool lin = (EPI == EPI_LIN || EPI == EPI_LIN_TW);
+  static constexpr bool tw = (EPI == EPI_LIN_TW || EPI == EPI_CG_TW);
+};
 
 // Occupancy target (CTAs of TILE threads per SM) of the Dslash: 6 leaves 168
 // registers per thread, room for a 3-deep hop pipeline (measured best on
@@ -94,6 +102,7 @@ __device__ __forceinline__ bool single_slot_idle(const Launch& L) {
 
 // Batched Dslash: out = a * D_{p,1-p} in + c1 * y1 + c2 * y2      (EPI_LIN)
 //                 r -= alpha (y1 + a * D in); x += alpha p      (EPI_CG, CG step)
+// (twisted: out = T(a D in) + c1 y1 + c2 T_y y2 and r -= alpha (T_y y1 + T(a D in)))
 // with the Work's reduction (norm / dots) and scalar finisher per slot.
 template <int SP, int LP, int NR, bool DAG, int EPI>
 __global__ void __launch_bounds__(TILE, DslashMinBlocks<SP>::value) k_dslash(const Launch L) {
@@ -110,10 +119,10 @@ __global__ void __launch_bounds__(TILE, DslashMinBlocks<SP>::value) k_dslash(con
       R acc[24];
       dslash_site<SP, LP, NR, DAG>(w.g, h, w.out_par, w.in, w.Uout, w.Uin, acc);
       const R a = (R)w.a;
-      if (EPI == EPI_LIN) {
+      if constexpr (EpiTraits<EPI>::lin) {
 #pragma unroll
         for (int i = 0; i < 24; ++i) acc[i] *= a;
-        if (w.twist) twist24(acc, w.tw_s, w.tw_t);
+        if constexpr (EpiTraits<EPI>::tw) twist24(acc, w.tw_s, w.tw_t);
         R y[24];
         if (w.y1) {
           SpinorIO<SP>::load(w.y1, w.g.Vh, h, y);
@@ -124,7 +133,7 @@ __global__ void __launch_bounds__(TILE, DslashMinBlocks<SP>::value) k_dslash(con
         if (w.y2) {
           R y2[24];
           SpinorIO<SP>::load(w.y2, w.g.Vh, h, y2);
-          if (w.twist) twist24(y2, 1.0, w.ty_t);
+          if constexpr (EpiTraits<EPI>::tw) twist24(y2, 1.0, w.ty_t);
           const R c = (R)w.c2;
 #pragma unroll
           for (int i = 0; i < 24; ++i) acc[i] += c * y2[i];
@@ -145,7 +154,7 @@ __global__ void __launch_bounds__(TILE, DslashMinBlocks<SP>::value) k_dslash(con
         R y[24], r[24];
         SpinorIO<SP>::load(w.y1, w.g.Vh, h, y);
         SpinorIO<SP>::load(w.out, w.g.Vh, h, r);
-        if (w.twist) {
+        if constexpr (EpiTraits<EPI>::tw) {
           twist24(acc, w.tw_s, w.tw_t);
           twist24(y, 1.0, w.ty_t);
         }
@@ -212,10 +221,10 @@ __global__ void __launch_bounds__(3 * TILE, LQCD_DSLASH3_MIN_BLOCKS) k_dslash3(c
       else if (col == 1) dslash_site3<SP, LP, DAG, 1>(w.g, h, w.out_par, w.in, w.Uout, w.Uin, acc);
       else dslash_site3<SP, LP, DAG, 2>(w.g, h, w.out_par, w.in, w.Uout, w.Uin, acc);
       const R a = (R)w.a;
-      if (EPI == EPI_LIN) {
+      if constexpr (EpiTraits<EPI>::lin) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) acc[i] *= a;
-        if (w.twist) twist8(acc, w.tw_s, w.tw_t);
+        if constexpr (EpiTraits<EPI>::tw) twist8(acc, w.tw_s, w.tw_t);
         R y[8];
         if (w.y1) {
           SpinorIO<SP>::load_colour(w.y1, Vh, h, col, y);
@@ -226,7 +235,7 @@ __global__ void __launch_bounds__(3 * TILE, LQCD_DSLASH3_MIN_BLOCKS) k_dslash3(c
         if (w.y2) {
           R y2[8];
           SpinorIO<SP>::load_colour(w.y2, Vh, h, col, y2);
-          if (w.twist) twist8(y2, 1.0, w.ty_t);
+          if constexpr (EpiTraits<EPI>::tw) twist8(y2, 1.0, w.ty_t);
           const R c = (R)w.c2;
 #pragma unroll
           for (int i = 0; i < 8; ++i) acc[i] += c * y2[i];
@@ -247,7 +256,7 @@ __global__ void __launch_bounds__(3 * TILE, LQCD_DSLASH3_MIN_BLOCKS) k_dslash3(c
         R y[8], r[8];
         SpinorIO<SP>::load_colour(w.y1, Vh, h, col, y);
         SpinorIO<SP>::load_colour(w.out, Vh, h, col, r);
-        if (w.twist) {
+        if constexpr (EpiTraits<EPI>::tw) {
           twist8(acc, w.tw_s, w.tw_t);
           twist8(y, 1.0, w.ty_t);
         }

@@ -1,5 +1,10 @@
 // Instantiates the batched kernels for one spinor precision LQCD_SP with
 // launch-function suffix LQCD_SFX. Included by kernels_<prec>.cu.
+//
+// LQCD_TW_UNIT: this translation unit holds only the twisted-mass Dslash epilogues
+// (launch_dslash_tw_<sfx>); LQCD_TW_EXTERN: the dispatcher of this unit forwards the
+// twisted epilogues to such a unit. Double-float uses the pair, so that its two
+// heaviest kernel sets compile in parallel.
 #include "kernels.cuh"
 #include "launch.h"
 
@@ -13,21 +18,44 @@ constexpr int SPX = LQCD_SP;
 constexpr int LPX = (SPX == P_F64 || SPX == P_DF64 || SPX == P_F32) ? SPX : P_F16;
 
 template <int NR, bool DAG, int EPI>
-cudaError_t go_dslash(const Launch& L, int grid, cudaStream_t s) {
+cudaError_t go_dslash(const Launch& L, int grid, cudaStream_t s, int form) {
   if (L.ntiles <= 0) return cudaSuccess;
+  int cps = 0;
+  if (form < 0 || grid <= 0) {
+    const TuneChoice t = tune_choice(SPX, NR, L.ntiles);
+    if (form < 0) form = t.form;
+    cps = t.ctas_per_sm;
+  }
+  // twisted double-float runs the colour-split form alone (the one-thread-per-site form
+  // is slower there and its twisted instantiations dominate the build)
+  constexpr bool split_only = (SPX == P_DF64 && EpiTraits<EPI>::tw);
   if constexpr (SPX == P_DF64 && NR == 18) {
-    if (dslash_colour_split(SPX)) {
+    if (form == 1 || split_only) {
       // double-float: the colour-split form (latency bound at one thread per site)
       auto fn3 = k_dslash3<SPX, LPX, DAG, EPI>;
-      if (grid <= 0) grid = grid_for((const void*)fn3, L.ntiles, 0, 3 * TILE);
+      if (grid <= 0) grid = grid_for((const void*)fn3, L.ntiles, 0, 3 * TILE, cps);
       fn3<<<grid, 3 * TILE, 0, s>>>(L);
       return cudaGetLastError();
     }
   }
-  auto fn = k_dslash<SPX, LPX, NR, DAG, EPI>;
-  if (grid <= 0) grid = grid_for((const void*)fn, L.ntiles, 0, TILE);
-  fn<<<grid, TILE, 0, s>>>(L);
-  return cudaGetLastError();
+  if constexpr (!split_only) {
+    auto fn = k_dslash<SPX, LPX, NR, DAG, EPI>;
+    if (grid <= 0) grid = grid_for((const void*)fn, L.ntiles, 0, TILE, cps);
+    fn<<<grid, TILE, 0, s>>>(L);
+    return cudaGetLastError();
+  } else {
+    return cudaErrorInvalidValue;
+  }
+}
+
+template <int NR>
+cudaError_t dispatch_tw(bool dag, int epi, const Launch& L, int grid, cudaStream_t s, int form) {
+  switch (epi) {
+    case EPI_LIN_TW: return dag ? go_dslash<NR, true, EPI_LIN_TW>(L, grid, s, form)
+                                : go_dslash<NR, false, EPI_LIN_TW>(L, grid, s, form);
+    case EPI_CG_TW: if (dag) return go_dslash<NR, true, EPI_CG_TW>(L, grid, s, form); break;
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <int OP, int P, int TP = P_F64>
@@ -40,18 +68,86 @@ cudaError_t go_blas(const Launch& L, int grid, cudaStream_t s) {
 }
 }  // namespace
 
-cudaError_t LQCD_CAT(launch_dslash_, LQCD_SFX)(int nr, bool dag, int epi, const Launch& L,
-                                                int grid, cudaStream_t s) {
-  if (nr == 18) {
-    if (epi == EPI_LIN) return dag ? go_dslash<18, true, EPI_LIN>(L, grid, s)
-                                   : go_dslash<18, false, EPI_LIN>(L, grid, s);
-    if (dag) return go_dslash<18, true, EPI_CG>(L, grid, s);
-  } else if (nr == 12) {
-    if (epi == EPI_LIN) return dag ? go_dslash<12, true, EPI_LIN>(L, grid, s)
-                                   : go_dslash<12, false, EPI_LIN>(L, grid, s);
-    if (dag) return go_dslash<12, true, EPI_CG>(L, grid, s);
+#ifdef LQCD_TW_UNIT
+
+// double-float links always have 18 reals
+cudaError_t LQCD_CAT(launch_dslash_tw_, LQCD_SFX)(int nr, bool dag, int epi, const Launch& L,
+                                                   int grid, cudaStream_t s, int form) {
+  if (nr != 18) return cudaErrorInvalidValue;
+  return dispatch_tw<18>(dag, epi, L, grid, s, form);
+}
+
+#else
+
+#ifdef LQCD_TW_EXTERN
+cudaError_t LQCD_CAT(launch_dslash_tw_, LQCD_SFX)(int nr, bool dag, int epi, const Launch& L,
+                                                   int grid, cudaStream_t s, int form);
+#endif
+
+namespace {
+template <int NR>
+cudaError_t dispatch_nr(bool dag, int epi, const Launch& L, int grid, cudaStream_t s, int form) {
+  switch (epi) {
+    case EPI_LIN: return dag ? go_dslash<NR, true, EPI_LIN>(L, grid, s, form)
+                             : go_dslash<NR, false, EPI_LIN>(L, grid, s, form);
+    case EPI_CG: if (dag) return go_dslash<NR, true, EPI_CG>(L, grid, s, form); break;
+    case EPI_LIN_TW:
+    case EPI_CG_TW:
+#ifdef LQCD_TW_EXTERN
+      return LQCD_CAT(launch_dslash_tw_, LQCD_SFX)(NR, dag, epi, L, grid, s, form);
+#else
+      return dispatch_tw<NR>(dag, epi, L, grid, s, form);
+#endif
   }
   return cudaErrorInvalidValue;
+}
+
+// 12-real links for every precision but double-float (whose links always have 18)
+template <int P>
+cudaError_t dispatch_12(bool dag, int epi, const Launch& L, int grid, cudaStream_t s, int form) {
+  if constexpr (P == P_DF64) {
+    return cudaErrorInvalidValue;
+  } else {
+    return dispatch_nr<12>(dag, epi, L, grid, s, form);
+  }
+}
+}  // namespace
+
+cudaError_t LQCD_CAT(launch_dslash_, LQCD_SFX)(int nr, bool dag, int epi, const Launch& L,
+                                                int grid, cudaStream_t s, int form) {
+  // a twisted single-slot work needs the twisted epilogue (a batched launch's works live
+  // on the device; their callers pick the epilogue from the slots they hold)
+  if (!L.works && L.inline_work.twist && epi != EPI_LIN_TW && epi != EPI_CG_TW) return cudaErrorInvalidValue;
+  if (nr == 18) return dispatch_nr<18>(dag, epi, L, grid, s, form);
+  if (nr == 12) return dispatch_12<SPX>(dag, epi, L, grid, s, form);
+  return cudaErrorInvalidValue;
+}
+
+namespace {
+// a template, so that the colour-split kernel is instantiated for double-float only
+template <int P>
+int colour_split_occupancy(int nr) {
+  if constexpr (P == P_DF64) {
+    if (nr == 18) return kernel_occupancy((const void*)k_dslash3<P, LPX, false, EPI_LIN>, 3 * TILE);
+  }
+  return 0;
+}
+template <int P>
+int site_occupancy_12() {
+  if constexpr (P == P_DF64) {
+    return 0;
+  } else {
+    return kernel_occupancy((const void*)k_dslash<P, LPX, 12, false, EPI_LIN>, TILE);
+  }
+}
+}  // namespace
+
+int LQCD_CAT(dslash_occupancy_, LQCD_SFX)(int nr, int form) {
+  if (form == 1) return colour_split_occupancy<SPX>(nr);
+  if (form != 0) return 0;
+  if (nr == 18) return kernel_occupancy((const void*)k_dslash<SPX, LPX, 18, false, EPI_LIN>, TILE);
+  if (nr == 12) return site_occupancy_12<SPX>();
+  return 0;
 }
 
 cudaError_t LQCD_CAT(launch_blas_, LQCD_SFX)(int op, int tp, const Launch& L, int grid,
@@ -80,5 +176,7 @@ cudaError_t LQCD_CAT(launch_blas_, LQCD_SFX)(int op, int tp, const Launch& L, in
     default: return cudaErrorInvalidValue;
   }
 }
+
+#endif  // LQCD_TW_UNIT
 
 }  // namespace lqcd

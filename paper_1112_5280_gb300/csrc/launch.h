@@ -11,16 +11,18 @@ namespace lqcd {
 // Link storage precision paired with a spinor precision.
 inline int link_prec_for(int sp) { return (sp == P_F64 || sp == P_F32 || sp == P_DF64) ? sp : P_F16; }
 
-// grid <= 0: persistent grid from the occupancy of the kernel (tuned multiplier).
+// grid <= 0: persistent grid of the autotuned CTAs per SM (else the occupancy limit);
+// form < 0: the autotuned Dslash form (else the default), 0 site, 1 colour split.
 cudaError_t launch_dslash(int sp, int nr, bool dag, int epi, const Launch& L, int grid,
-                          cudaStream_t s);
+                          cudaStream_t s, int form = -1);
 // tp: precision of the FP64-class operand of the mixed ops (P_F64 or P_DF64)
 cudaError_t launch_blas(int sp, int op, const Launch& L, int grid, cudaStream_t s, int tp = P_F64);
 
 // per precision
 #define LQCD_DECL(SFX)                                                                     \
   cudaError_t launch_dslash_##SFX(int nr, bool dag, int epi, const Launch& L, int grid,   \
-                                  cudaStream_t s);                                         \
+                                  cudaStream_t s, int form);                               \
+  int dslash_occupancy_##SFX(int nr, int form);                                            \
   cudaError_t launch_blas_##SFX(int op, int tp, const Launch& L, int grid, cudaStream_t s);
 LQCD_DECL(f64)
 LQCD_DECL(f32)
@@ -32,7 +34,19 @@ LQCD_DECL(df64)
 // Number of SMs of the current device and the persistent-grid multiplier.
 int device_sm_count();
 void set_grid_multiplier(int kernel_family, int mult);  // 0 = occupancy limit
-int grid_for(const void* kernel_fn, int ntiles, int family, int block);
+// ctas_per_sm > 0 caps the grid below the occupancy limit (autotuned choice)
+int grid_for(const void* kernel_fn, int ntiles, int family, int block, int ctas_per_sm = 0);
+int kernel_occupancy(const void* kernel_fn, int block);
+// resident CTAs per SM of the Dslash of this precision, link reals and form (0 if no such form)
+int dslash_occupancy(int sp, int nr, int form);
+
+// Autotuner table (tune.cu): the launch choice for Dslash launches of this precision and
+// link reals whose tile count has the same floor(log2) as a tuned launch.
+struct TuneChoice {
+  int ctas_per_sm;  // 0: occupancy limit
+  int form;         // 0 site, 1 colour split
+};
+TuneChoice tune_choice(int sp, int nr, int ntiles);
 
 // Whether the Dslash of spinor precision prec uses the colour-split form (double-float
 // only; a runtime switch for measurement).

@@ -253,15 +253,26 @@ cudaError_t spinor_convert(const void* in, int pin, void* out, int pout, int Vh,
 // ------------------------------------------------------------------ dispatch
 
 cudaError_t launch_dslash(int sp, int nr, bool dag, int epi, const Launch& L, int grid,
-                          cudaStream_t s) {
+                          cudaStream_t s, int form) {
   switch (sp) {
-    case P_F64: return launch_dslash_f64(nr, dag, epi, L, grid, s);
-    case P_F32: return launch_dslash_f32(nr, dag, epi, L, grid, s);
-    case P_F16: return launch_dslash_f16(nr, dag, epi, L, grid, s);
-    case P_BF16: return launch_dslash_bf16(nr, dag, epi, L, grid, s);
-    case P_DF64: return launch_dslash_df64(nr, dag, epi, L, grid, s);
+    case P_F64: return launch_dslash_f64(nr, dag, epi, L, grid, s, form);
+    case P_F32: return launch_dslash_f32(nr, dag, epi, L, grid, s, form);
+    case P_F16: return launch_dslash_f16(nr, dag, epi, L, grid, s, form);
+    case P_BF16: return launch_dslash_bf16(nr, dag, epi, L, grid, s, form);
+    case P_DF64: return launch_dslash_df64(nr, dag, epi, L, grid, s, form);
   }
   return cudaErrorInvalidValue;
+}
+
+int dslash_occupancy(int sp, int nr, int form) {
+  switch (sp) {
+    case P_F64: return dslash_occupancy_f64(nr, form);
+    case P_F32: return dslash_occupancy_f32(nr, form);
+    case P_F16: return dslash_occupancy_f16(nr, form);
+    case P_BF16: return dslash_occupancy_bf16(nr, form);
+    case P_DF64: return dslash_occupancy_df64(nr, form);
+  }
+  return 0;
 }
 
 cudaError_t launch_blas(int sp, int op, const Launch& L, int grid, cudaStream_t s, int tp) {
@@ -308,23 +319,26 @@ void set_dslash_colour_split(int prec, bool on) {
   if (prec >= 0 && prec < NPREC) g_split[prec] = on;
 }
 
-int grid_for(const void* fn, int ntiles, int family, int block) {
-  const int nsm = device_sm_count();
-  int occ;
-  {
-    std::lock_guard<std::mutex> lk(g_occ_mu);
-    auto it = g_occ.find(fn);
-    if (it == g_occ.end()) {
-      int o = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, block, 0) != cudaSuccess || o < 1) o = 1;
-      g_occ[fn] = o;
-      occ = o;
-    } else {
-      occ = it->second;
-    }
+int kernel_occupancy(const void* fn, int block) {
+  device_sm_count();  // resets the cache when the device changed
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  auto it = g_occ.find(fn);
+  if (it != g_occ.end()) return it->second;
+  int o = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, block, 0) != cudaSuccess || o < 1) {
+    cudaGetLastError();
+    o = 1;
   }
+  g_occ[fn] = o;
+  return o;
+}
+
+int grid_for(const void* fn, int ntiles, int family, int block, int ctas_per_sm) {
+  const int nsm = device_sm_count();
+  int occ = kernel_occupancy(fn, block);
   int m = (family >= 0 && family < 4) ? g_mult[family] : 0;
   if (m > 0 && m < occ) occ = m;
+  if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
   long long grid = (long long)nsm * occ;
   if (grid > ntiles) grid = ntiles;
   return (int)(grid < 1 ? 1 : grid);

@@ -46,6 +46,15 @@ class SolveInfo(C.Structure):
                 "ms": self.ms}
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("prec", C.c_int), ("nr", C.c_int), ("ntiles", C.c_int), ("ctas_per_sm", C.c_int),
+                ("form", C.c_int), ("candidates", C.c_int), ("us_best", C.c_double),
+                ("us_default", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 _VP = C.c_void_p
 _IP = C.POINTER(C.c_int)
@@ -104,6 +113,11 @@ def load(build_if_missing: bool = True):
     _sig(lib, "lqcd_dslash_batch_apply", i, [_VP])
     _sig(lib, "lqcd_dslash_batch_destroy", None, [_VP])
     _sig(lib, "lqcd_meson_correlator", i, [C.POINTER(_VP), i, C.POINTER(C.c_int), _VP])
+    _sig(lib, "lqcd_autotune_dslash", i, [i, C.POINTER(_VP), i, C.POINTER(TuneResult)])
+    _sig(lib, "lqcd_tune_entries", i, [C.POINTER(TuneResult), i, _IP])
+    _sig(lib, "lqcd_tune_clear", None, [])
+    _sig(lib, "lqcd_tune_save", i, [C.c_char_p])
+    _sig(lib, "lqcd_tune_load", i, [C.c_char_p])
     if hasattr(lib, "lqcd_apply_Mhat_noalloc"):
         _sig(lib, "lqcd_apply_Mhat_noalloc", i, [_VP, d, _VP, _VP, i])
     if hasattr(lib, "lqcd_solve"):
@@ -355,6 +369,39 @@ def apply_M(gauge: Gauge, kappa: float, fin: Field, fout: Field, dagger=False, m
     else:
         _check(gauge._lib.lqcd_apply_M_tm(gauge.h, float(kappa), float(mu), fin.h, fout.h,
                                           int(bool(dagger))))
+
+
+def autotune_dslash(gauges, prec) -> dict:
+    """Times the batched Dslash over one slot per gauge (gauges may repeat) for every
+    persistent grid and kernel form; later launches with the same key use the fastest."""
+    gauges = list(gauges)
+    if not gauges:
+        raise ValueError("need at least one gauge")
+    arr = (_VP * len(gauges))(*[g.h for g in gauges])
+    r = TuneResult()
+    _check(gauges[0]._lib.lqcd_autotune_dslash(len(gauges), arr, _prec(prec), C.byref(r)))
+    return r.as_dict()
+
+
+def tune_entries() -> list:
+    lib = load()
+    n = C.c_int()
+    _check(lib.lqcd_tune_entries(None, 0, C.byref(n)))
+    buf = (TuneResult * max(1, n.value))()
+    _check(lib.lqcd_tune_entries(buf, n.value, C.byref(n)))
+    return [buf[k].as_dict() for k in range(n.value)]
+
+
+def tune_clear() -> None:
+    load().lqcd_tune_clear()
+
+
+def tune_save(path) -> None:
+    _check(load().lqcd_tune_save(os.fsencode(path)))
+
+
+def tune_load(path) -> None:
+    _check(load().lqcd_tune_load(os.fsencode(path)))
 
 
 GAMMA_CODES = {"1": 0, "g5": 1, "gx": 2, "gy": 3, "gz": 4, "gt": 5,

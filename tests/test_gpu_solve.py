@@ -221,3 +221,18 @@ def test_near_critical_16x32_mixed_f16(ctx):
     x, info = lqcd.solve(g, b, 0.155, 1e-10, lqcd.solve_opts(sloppy_prec="f16", sloppy_compress=12))
     assert info["status"] == 0, info
     assert oracle.true_residual(dims, U, 0.155, b, x) <= 1e-10
+
+
+def test_full_size_solves_32x64(ctx):
+    """The bench's solve workload at full size (32^3x64, kappa 0.155, eps 0.8, seeds 1001 /
+    2002): mixed FP16-12 CG, Wilson and twisted mass (mu 0.01), each meets 1e-10 on the full
+    operator as measured by the oracle on the returned solution."""
+    dims, kappa, mu = (32, 32, 32, 64), 0.155, 0.01
+    U = synth.random_links(dims, 0.8, seed=synth.SEED_LINKS)
+    b = synth.gaussian_spinor(dims, seed=synth.SEED_SOURCE)
+    g = ctx.gauge(dims, U, prec="f64")
+    for m in (0.0, mu):
+        x, info = lqcd.solve(g, b, kappa, 1e-10, lqcd.solve_opts(sloppy_prec="f16", mu=m))
+        assert info["status"] == 0, (m, info)
+        assert oracle.true_residual(dims, U, kappa, b, x, mu=m) <= 1e-10, m
+    g.close()
