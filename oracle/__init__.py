@@ -9,6 +9,9 @@ Contents
     CG on the normal equations, even-odd CG and BiCGStab.
   * dense.py: brute-force dense matrices for tiny lattices (pure Python loops),
     the free-field closed forms and the FFT solve of the free field.
+  * contract.py: the meson correlator of eq. 4.1.
+  * gauge.py: bindings to heatbath.c, the SU(3) heatbath (Cabibbo-Marinari with
+    Creutz's SU(2) draw, Philox4x64-10 random numbers) and the plaquette.
 """
 from .wilson import (  # noqa: F401
     apply_M,

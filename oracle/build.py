@@ -12,12 +12,13 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so")
-SOURCES = [os.path.join(HERE, "wilson_oracle.c")]
+SOURCES = [os.path.join(HERE, "wilson_oracle.c"), os.path.join(HERE, "heatbath.c")]
+HEADERS = [os.path.join(HERE, "wilson_oracle.h"), os.path.join(HERE, "heatbath.h")]
 
 
 def build(force: bool = False) -> str:
     os.makedirs(BUILD_DIR, exist_ok=True)
-    newest_src = max(os.path.getmtime(p) for p in SOURCES + [os.path.join(HERE, "wilson_oracle.h")])
+    newest_src = max(os.path.getmtime(p) for p in SOURCES + HEADERS)
     if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest_src:
         return LIB_PATH
     tmp = LIB_PATH + f".tmp{os.getpid()}"
