@@ -282,7 +282,12 @@ def cpu_baseline_oracle(budget_s=12.0):
 
 # ------------------------------------------------------------------ GPU arm
 
+TUNE = True  # autotune launch shapes before timing (off with --no-autotune)
+
+
 def run_ours(args, world, rank, local):
+    global TUNE
+    TUNE = not args.no_autotune
     inputs = generate_inputs(full=not args.dslash_only)
     sets = inputs["sets"]
     import torch
@@ -311,9 +316,14 @@ def run_ours(args, world, rank, local):
         for _ in range(APPS_PER_STEP // NSETS):
             batch.apply()
 
+    tuned = {}
+
     def timed(prec, steps, warmup, batched=True):
         """One step = 100 applications captured once as a CUDA graph, replayed `steps` times."""
         gs, fi, fo = make(prec)
+        if not args.no_autotune:  # launch shape of this precision and slot count, measured
+            tuned[f"{prec}_x{NSETS if batched else 1}"] = lqcd.autotune_dslash(
+                gs if batched else gs[:1], prec)
         batch = lqcd.DslashBatch(gs, fi, fo, 0) if batched else None
         run = (lambda: step_batched(batch)) if batched else (lambda: step_single(gs, fi, fo))
         run()  # eager pass: link copies and launch configuration exist before capture
@@ -387,6 +397,7 @@ def run_ours(args, world, rank, local):
                    "l2": f"inputs larger than L2: rotating {NSETS} independent field sets (~500 MB)",
                    "bytes_per_site": algorithmic_bytes_per_site(4, 18),
                    "timing": "each step captured once as a CUDA graph and replayed; CUDA events on the launch stream",
+                   "autotune": tuned or "off",
                    "parallelism": f"replicas x{world} (independent lattices per GPU)"},
         "roofline": {"bound": "hbm", "achieved": gbs_rank, "peak": peak, "unit": "GB/s",
                      "frac": gbs_rank / peak, "peak_kind": f"{peak_kind} copy bandwidth (burst)",
@@ -434,6 +445,9 @@ def run_solve_section(ctx, lqcd, inputs, world):
     x = ctx.field(SOLVE_DIMS, "f64", lqcd.FULL)
     out = {"workload": "32^3x64 kappa=0.155 eps=0.8, Gaussian source, tol 1e-10 (full-M FP64 residual); "
                        f"tm_*: twisted mass mu={SOLVE_MU}"}
+    if TUNE:
+        out["autotune"] = {f"{p_}_{c_}": lqcd.autotune_dslash([g], p_, c_)
+                           for p_, c_ in (("f16", 12), ("bf16", 12), ("f32", 12), ("f64", 18), ("df64", 18))}
     variants = [
         ("cg_mixed_f16_12", dict(sloppy_prec="f16", sloppy_compress=12), 6),
         ("cg_mixed_f16_12_truef64", dict(sloppy_prec="f16", sloppy_compress=12, true_prec="f64"), 3),
@@ -484,6 +498,10 @@ def run_mrhs_section(ctx, lqcd, inputs, world):
             for s_ in range(4) for c_ in range(3)]
     xs = [ctx.field(d, "f64", lqcd.FULL) for _ in srcs]
     o = lqcd.solve_opts(sloppy_prec="f32", sloppy_compress=12)
+    tuned = {}
+    if TUNE:  # the 12-slot sloppy launch and the FP64-class update launch
+        tuned = {"f32_12_x12": lqcd.autotune_dslash([g] * 12, "f32", 12),
+                 "df64_18_x12": lqcd.autotune_dslash([g] * 12, "df64", 18)}
     lqcd.solve_multi(g, srcs, MRHS_KAPPA, 1e-10, xs, o)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -504,7 +522,7 @@ def run_mrhs_section(ctx, lqcd, inputs, world):
            "solves_per_s": 12 / t_multi, "speedup_vs_sequential": t_seq / t_multi,
            "max_true_resid": max(i["true_resid"] for i in infos),
            "converged": all(i["status"] == 0 for i in infos),
-           "iters": [i["iters"] for i in infos]}
+           "iters": [i["iters"] for i in infos], "autotune": tuned or "off"}
     for o_ in [g] + srcs + xs:
         o_.close()
     return res
@@ -518,6 +536,10 @@ def run_mlat_section(ctx, lqcd, inputs, world):
     gs = [ctx.gauge(d, U, prec="f64") for d, _, U, _ in items]
     srcs = [ctx.field(d, "f64", lqcd.FULL, data=b) for d, _, _, b in items]
     xs = {d: ctx.field(d, "f64", lqcd.FULL) for d in MLAT_SIZES}
+    tuned = {}
+    if TUNE:  # all 64 slots in one launch: the sloppy and the FP64-class operator
+        tuned = {"f32_12_x64": lqcd.autotune_dslash(gs, "f32", 12),
+                 "df64_18_x64": lqcd.autotune_dslash(gs, "df64", 18)}
 
     def batched():
         eng = lqcd.Engine(ctx, o, max_slots=MLAT_N)
@@ -543,7 +565,7 @@ def run_mlat_section(ctx, lqcd, inputs, world):
            "total_sites": sites, "batched_ms": t_b * 1e3, "sequential_ms": t_s * 1e3,
            "solves_per_s": MLAT_N / t_b, "speedup_vs_sequential": t_s / t_b,
            "max_true_resid": max(i["true_resid"] for i in infos),
-           "converged": all(i["status"] == 0 for i in infos)}
+           "converged": all(i["status"] == 0 for i in infos), "autotune": tuned or "off"}
     for o_ in gs + srcs + list(xs.values()):
         o_.close()
     return res
@@ -621,6 +643,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (no autotuner)")
     ap.add_argument("--no-variants", action="store_true", help="skip the one-application-per-launch timings")
     ap.add_argument("--dslash-only", action="store_true", help="skip the solver, multi-RHS, multi-lattice and serving sections")
     args = ap.parse_args()

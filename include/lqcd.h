@@ -117,6 +117,8 @@ LQCD_API int lqcd_gauge_upload_dev(lqcd_ctx* ctx, const int dims[4], const doubl
                           int compress, int t_bc, lqcd_gauge** out);
 /* Adds a resident copy in another precision / compression (from the FP64 copy). */
 LQCD_API int lqcd_gauge_add_copy(lqcd_gauge* g, int prec, int compress);
+/* Copies the FP64 master copy back to the host layout above (V x 4 x 3 x 3 complex). */
+LQCD_API int lqcd_gauge_download(const lqcd_gauge* g, double* host_U);
 /* Device bytes held by the gauge field (all copies). */
 LQCD_API size_t lqcd_gauge_bytes(const lqcd_gauge* g);
 LQCD_API void lqcd_gauge_destroy(lqcd_gauge* g);
@@ -250,6 +252,25 @@ LQCD_API int lqcd_solve_multi(const lqcd_gauge* g, int n, const lqcd_field* cons
                      double tol, const lqcd_solve_opts* opts, lqcd_field* const* xs,
                      lqcd_solve_info* infos);
 
+/* ---------------------------------------------------------------- pure gauge */
+
+/* SU(3) heatbath of the Wilson plaquette action S = beta sum_P (1 - Re Tr U_P / 3)
+ * (paper Section 3: the pure-gauge side needs an SU(3) heatbath, citing Creutz), in
+ * place on the gauge field's FP64 master copy; every other copy of g is refreshed
+ * afterwards. nsweeps sweeps, numbered sweep0, sweep0 + 1, ...; a sweep updates the
+ * links class by class (mu = 0..3, parity even then odd), each link by Cabibbo-Marinari
+ * over the SU(2) subgroups (0,1), (1,2), (0,2) with Creutz's SU(2) draw. Random numbers
+ * are Philox4x64-10 with key (seed, 0) and counter (4 s + mu, sweep, subgroup, attempt),
+ * s the lexicographic site index, so the result depends only on the links, beta, seed
+ * and sweep numbers. reunit != 0: reunitarise every link after each sweep. A draw that
+ * is not accepted within 1000 attempts leaves its subgroup unchanged; *fails (may be
+ * NULL) counts them. beta must be finite and >= 0. Synchronous. */
+LQCD_API int lqcd_heatbath(lqcd_gauge* g, double beta, int nsweeps, unsigned long long seed,
+                           unsigned long long sweep0, int reunit, long long* fails);
+/* Average plaquette sum_{x, mu<nu} Re Tr U_munu(x) / (18 V) of the FP64 master copy,
+ * summed in a fixed order (deterministic). Synchronous. */
+LQCD_API int lqcd_plaquette(const lqcd_gauge* g, double* plaq);
+
 /* ---------------------------------------------------------------- meson correlators */
 
 /* Dirac structures Gamma of lqcd_meson_correlator (chiral basis above) */
@@ -330,7 +351,8 @@ typedef struct lqcd_tune_result {
   double us_best;   /* per launch, chosen configuration */
   double us_default;/* per launch, untuned default */
 } lqcd_tune_result;
-LQCD_API int lqcd_autotune_dslash(int n, const lqcd_gauge* const* g, int prec, lqcd_tune_result* out);
+LQCD_API int lqcd_autotune_dslash(int n, const lqcd_gauge* const* g, int prec, int compress,
+                                  lqcd_tune_result* out);
 /* Copies up to max table entries into out; *n = entries in the table. */
 LQCD_API int lqcd_tune_entries(lqcd_tune_result* out, int max, int* n);
 LQCD_API void lqcd_tune_clear(void);

@@ -124,12 +124,6 @@ static int ctx_set_device(lqcd_ctx* c) {
   return LQCD_OK;
 }
 
-#define LQCD_TRY(x)              \
-  do {                           \
-    int rc_ = (x);               \
-    if (rc_ != LQCD_OK) return rc_; \
-  } while (0)
-
 extern "C" {
 
 const char* lqcd_status_string(int s) {

@@ -1,0 +1,447 @@
+// Pure-gauge SU(3) heatbath and plaquette (paper Section 3: the pure-gauge side needs an
+// SU(3) heatbath, citing Creutz) on the FP64 master copy of a gauge field.
+//
+// Wilson action S = beta sum_P (1 - Re Tr U_P / 3). A sweep updates the links class by
+// class, mu = 0..3 and parity even, odd: the links U_mu(x) of one class share no staple,
+// so one thread per link updates a class in one launch. Each link is updated by
+// Cabibbo-Marinari over the SU(2) subgroups on index pairs (0,1), (1,2), (0,2): with
+// V = U W (W the staple sum) and the subgroup block X of V, Re Tr(a X) = a.c for
+// a = a0 + i a.sigma, k = |c|, v = c / k; b is drawn with density
+// exp(beta k b0 / 3) on the 3-sphere by Creutz's method (b0 = 1 + ln(y) / alpha with y
+// uniform in (exp(-2 alpha), 1], accepted with probability sqrt(1 - b0^2), uniform
+// direction), a = b v, and U <- R U, R the embedding of a. Every sweep ends with a
+// reunitarisation (Gram-Schmidt of rows 0, 1; row 2 = conj(row0 x row1)) when asked.
+//
+// Random numbers: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11), key (seed, 0),
+// counter (4 s + mu, sweep, subgroup, attempt) with s = x + Lx (y + Ly (z + Lz t)),
+// u = ((r >> 11) + 1) 2^-53; four uniforms per attempt (b0, acceptance, cos theta,
+// phi). So a sweep's result depends on (seed, sweep) and the links only, not on the
+// launch shape. At most 1000 attempts per draw: a subgroup that never accepts is left
+// unchanged and counted (the count is returned).
+#include <cmath>
+#include <cstring>
+
+#include "kernels.cuh"
+#include "runtime.h"
+
+namespace lqcd {
+namespace {
+
+constexpr int HB_THREADS = 128;
+constexpr int HB_MAX_ATTEMPTS = 1000;
+
+struct C2 {
+  double re, im;
+};
+__device__ __forceinline__ C2 cmul(C2 a, C2 b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ C2 cmulc(C2 a, C2 b) {  // a * conj(b)
+  return {a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im};
+}
+__device__ __forceinline__ C2 cadd(C2 a, C2 b) { return {a.re + b.re, a.im + b.im}; }
+
+struct M3 {
+  C2 e[9];
+};
+
+// ---------------------------------------------------------------- Philox4x64-10
+
+__device__ __forceinline__ void philox4x64(uint64_t c[4], uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    const uint64_t hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+    const uint64_t hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+    const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+__device__ __forceinline__ double unit_open0(uint64_t r) { return ((double)(r >> 11) + 1.0) * 0x1.0p-53; }
+
+// ---------------------------------------------------------------- geometry and links
+
+struct Site {
+  int c[4];
+};
+
+__device__ __forceinline__ Site site_of(const Geom& g, int par, int h) {
+  Site s;
+  const int xh = h % g.Lxh;
+  int r = h / g.Lxh;
+  s.c[1] = r % g.L[1];
+  r /= g.L[1];
+  s.c[2] = r % g.L[2];
+  s.c[3] = r / g.L[2];
+  s.c[0] = 2 * xh + ((par + s.c[1] + s.c[2] + s.c[3]) & 1);
+  return s;
+}
+__device__ __forceinline__ Site shifted(const Geom& g, Site s, int mu, int d) {
+  int v = s.c[mu] + d;
+  v = v < 0 ? v + g.L[mu] : (v >= g.L[mu] ? v - g.L[mu] : v);
+  s.c[mu] = v;
+  return s;
+}
+// double2 index of word 0 of link (site, mu) in the FP64 18-real layout
+__device__ __forceinline__ size_t link_base(const Geom& g, const Site& s, int mu) {
+  const int par = (s.c[0] + s.c[1] + s.c[2] + s.c[3]) & 1;
+  const int h = (s.c[0] >> 1) + g.Lxh * (s.c[1] + g.L[1] * (s.c[2] + g.L[2] * s.c[3]));
+  return (size_t)(par * 4 + mu) * 9 * g.Vh + h;
+}
+__device__ __forceinline__ M3 load_link(const double2* U, const Geom& g, const Site& s, int mu) {
+  const size_t b = link_base(g, s, mu);
+  M3 m;
+#pragma unroll
+  for (int w = 0; w < 9; ++w) {
+    const double2 d = U[b + (size_t)w * g.Vh];
+    m.e[w] = {d.x, d.y};
+  }
+  return m;
+}
+__device__ __forceinline__ void store_link(double2* U, const Geom& g, const Site& s, int mu, const M3& m) {
+  const size_t b = link_base(g, s, mu);
+#pragma unroll
+  for (int w = 0; w < 9; ++w) U[b + (size_t)w * g.Vh] = make_double2(m.e[w].re, m.e[w].im);
+}
+
+__device__ __forceinline__ M3 mul_nn(const M3& a, const M3& b) {
+  M3 c;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      C2 s = cmul(a.e[i * 3], b.e[j]);
+      s = cadd(s, cmul(a.e[i * 3 + 1], b.e[3 + j]));
+      s = cadd(s, cmul(a.e[i * 3 + 2], b.e[6 + j]));
+      c.e[i * 3 + j] = s;
+    }
+  return c;
+}
+__device__ __forceinline__ M3 mul_nd(const M3& a, const M3& b) {  // a b^dag
+  M3 c;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      C2 s = cmulc(a.e[i * 3], b.e[j * 3]);
+      s = cadd(s, cmulc(a.e[i * 3 + 1], b.e[j * 3 + 1]));
+      s = cadd(s, cmulc(a.e[i * 3 + 2], b.e[j * 3 + 2]));
+      c.e[i * 3 + j] = s;
+    }
+  return c;
+}
+__device__ __forceinline__ M3 mul_dn(const M3& a, const M3& b) {  // a^dag b
+  M3 c;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      C2 s = cmulc(b.e[j], a.e[i]);
+      s = cadd(s, cmulc(b.e[3 + j], a.e[3 + i]));
+      s = cadd(s, cmulc(b.e[6 + j], a.e[6 + i]));
+      c.e[i * 3 + j] = s;
+    }
+  return c;
+}
+
+// W_mu(x) = sum_{nu != mu} U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag + U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu)
+template <int mu>
+__device__ __forceinline__ M3 staple(const double2* U, const Geom& g, const Site& x) {
+  M3 W;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) W.e[i] = {0.0, 0.0};
+  const Site xp = shifted(g, x, mu, 1);
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == mu) continue;
+    const Site xn = shifted(g, x, nu, 1), xm = shifted(g, x, nu, -1), xpm = shifted(g, xp, nu, -1);
+    const M3 up = mul_nd(mul_nd(load_link(U, g, xp, nu), load_link(U, g, xn, mu)), load_link(U, g, x, nu));
+    const M3 lo = mul_dn(mul_nn(load_link(U, g, xm, mu), load_link(U, g, xpm, nu)), load_link(U, g, xm, nu));
+#pragma unroll
+    for (int i = 0; i < 9; ++i) W.e[i] = cadd(W.e[i], cadd(up.e[i], lo.e[i]));
+  }
+  return W;
+}
+
+// Creutz's SU(2) draw; false after HB_MAX_ATTEMPTS
+__device__ __noinline__ bool su2_draw(double alpha, uint64_t seed, uint64_t c0, uint64_t c1, uint64_t c2, double b[4]) {
+  for (int attempt = 0; attempt < HB_MAX_ATTEMPTS; ++attempt) {
+    uint64_t r[4] = {c0, c1, c2, (uint64_t)attempt};
+    philox4x64(r, seed, 0);
+    const double u0 = unit_open0(r[0]), u1 = unit_open0(r[1]), u2 = unit_open0(r[2]), u3 = unit_open0(r[3]);
+    const double b0 = alpha < 1e-12 ? 1.0 - 2.0 * u0 : 1.0 + log1p(-u0 * (-expm1(-2.0 * alpha))) / alpha;
+    const double s2 = 1.0 - b0 * b0;
+    if (u1 * u1 <= s2) {
+      const double rr = sqrt(fmax(s2, 0.0));
+      const double ct = 2.0 * u2 - 1.0;
+      const double st = sqrt(fmax(1.0 - ct * ct, 0.0));
+      double sp, cp;
+      sincospi(2.0 * u3, &sp, &cp);
+      b[0] = b0;
+      b[1] = rr * st * cp;
+      b[2] = rr * st * sp;
+      b[3] = rr * ct;
+      return true;
+    }
+  }
+  return false;
+}
+
+template <int mu>
+__global__ void __launch_bounds__(HB_THREADS) k_heatbath(double2* U, Geom g, int par, double beta,
+                                                         uint64_t seed, uint64_t sweep,
+                                                         unsigned long long* fails) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= g.Vh) return;
+  const Site x = site_of(g, par, h);
+  const M3 W = staple<mu>(U, g, x);
+  M3 u = load_link(U, g, x, mu);
+  M3 V = mul_nn(u, W);
+  const uint64_t s = (uint64_t)x.c[0] + (uint64_t)g.L[0] * ((uint64_t)x.c[1] + (uint64_t)g.L[1] *
+                     ((uint64_t)x.c[2] + (uint64_t)g.L[2] * (uint64_t)x.c[3]));
+  const uint64_t link_id = 4 * s + (uint64_t)mu;
+  int nfail = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int i = k == 1 ? 1 : 0, j = k == 0 ? 1 : 2;  // (0,1), (1,2), (0,2)
+    const C2 x00 = V.e[i * 3 + i], x01 = V.e[i * 3 + j], x10 = V.e[j * 3 + i], x11 = V.e[j * 3 + j];
+    const double c0 = x00.re + x11.re, c1 = -(x01.im + x10.im), c2 = x10.re - x01.re, c3 = -(x00.im - x11.im);
+    const double kk = sqrt(c0 * c0 + c1 * c1 + c2 * c2 + c3 * c3);
+    double v[4] = {1.0, 0.0, 0.0, 0.0};
+    if (kk > 0.0) {
+      v[0] = c0 / kk;
+      v[1] = c1 / kk;
+      v[2] = c2 / kk;
+      v[3] = c3 / kk;
+    }
+    double b[4];
+    if (!su2_draw(beta * kk / 3.0, seed, link_id, sweep, (uint64_t)k, b)) {
+      ++nfail;
+      continue;
+    }
+    // a = b v with mat(q) = [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]]
+    const C2 B[4] = {{b[0], b[3]}, {b[2], b[1]}, {-b[2], b[1]}, {b[0], -b[3]}};
+    const C2 Vm[4] = {{v[0], v[3]}, {v[2], v[1]}, {-v[2], v[1]}, {v[0], -v[3]}};
+    C2 A[4];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) A[r * 2 + q] = cadd(cmul(B[r * 2], Vm[q]), cmul(B[r * 2 + 1], Vm[2 + q]));
+    // U <- R U and V <- R V (rows i, j)
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+      const C2 ui = u.e[i * 3 + col], uj = u.e[j * 3 + col];
+      u.e[i * 3 + col] = cadd(cmul(A[0], ui), cmul(A[1], uj));
+      u.e[j * 3 + col] = cadd(cmul(A[2], ui), cmul(A[3], uj));
+      const C2 vi = V.e[i * 3 + col], vj = V.e[j * 3 + col];
+      V.e[i * 3 + col] = cadd(cmul(A[0], vi), cmul(A[1], vj));
+      V.e[j * 3 + col] = cadd(cmul(A[2], vi), cmul(A[3], vj));
+    }
+  }
+  store_link(U, g, x, mu, u);
+  if (nfail) atomicAdd(fails, (unsigned long long)nfail);
+}
+
+__global__ void k_reunitarise(double2* U, Geom g) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // (par, mu, h)
+  if (i >= 8LL * g.Vh) return;
+  const int h = (int)(i % g.Vh);
+  const size_t base = (size_t)(i / g.Vh) * 9 * g.Vh + h;
+  C2 r[9];
+#pragma unroll
+  for (int w = 0; w < 9; ++w) {
+    const double2 d = U[base + (size_t)w * g.Vh];
+    r[w] = {d.x, d.y};
+  }
+  double n0 = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) n0 += r[c].re * r[c].re + r[c].im * r[c].im;
+  n0 = 1.0 / sqrt(n0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) r[c] = {r[c].re * n0, r[c].im * n0};
+  C2 p = {0.0, 0.0};  // <row0, row1>
+#pragma unroll
+  for (int c = 0; c < 3; ++c) p = cadd(p, cmulc(r[3 + c], r[c]));
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const C2 t = cmul(p, r[c]);
+    r[3 + c] = {r[3 + c].re - t.re, r[3 + c].im - t.im};
+  }
+  double n1 = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) n1 += r[3 + c].re * r[3 + c].re + r[3 + c].im * r[3 + c].im;
+  n1 = 1.0 / sqrt(n1);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) r[3 + c] = {r[3 + c].re * n1, r[3 + c].im * n1};
+  // row 2 = conj(row0 x row1)
+  auto cr = [&](int a, int b, int c, int d) {
+    const C2 x = cmul(r[a], r[b]), y = cmul(r[c], r[d]);
+    return C2{x.re - y.re, -(x.im - y.im)};
+  };
+  r[6] = cr(1, 5, 2, 4);
+  r[7] = cr(2, 3, 0, 5);
+  r[8] = cr(0, 4, 1, 3);
+#pragma unroll
+  for (int w = 0; w < 9; ++w) U[base + (size_t)w * g.Vh] = make_double2(r[w].re, r[w].im);
+}
+
+// per-CTA partial of sum_{x, mu<nu} Re Tr U_munu(x) over the sites of both parities
+constexpr int PLAQ_THREADS = 256;
+__global__ void __launch_bounds__(PLAQ_THREADS) k_plaquette(const double2* U, Geom g, double* partials) {
+  __shared__ double red[PLAQ_THREADS];
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // (par, h)
+  double acc = 0.0;
+  if (i < 2LL * g.Vh) {
+    const Site x = site_of(g, (int)(i / g.Vh), (int)(i % g.Vh));
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+      for (int nu = mu + 1; nu < 4; ++nu) {
+        const M3 a = mul_nn(load_link(U, g, x, mu), load_link(U, g, shifted(g, x, mu, 1), nu));
+        const M3 b = mul_nn(load_link(U, g, x, nu), load_link(U, g, shifted(g, x, nu, 1), mu));
+        double tr = 0.0;
+#pragma unroll
+        for (int w = 0; w < 9; ++w) tr += a.e[w].re * b.e[w].re + a.e[w].im * b.e[w].im;  // Re Tr a b^dag
+        acc += tr;
+      }
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = PLAQ_THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+// out = sum of n partials in a fixed order (one CTA, strided then tree)
+__global__ void k_sum_ordered(const double* partials, int n, double* out) {
+  __shared__ double red[PLAQ_THREADS];
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < n; k += PLAQ_THREADS) acc += partials[k];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = PLAQ_THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+// FP64 18-real layout -> host AoS U[s][mu][row][col] (re, im)
+__global__ void k_gauge_to_aos(const double2* U, Geom g, double2* aos) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // (par, h)
+  if (i >= 2LL * g.Vh) return;
+  const Site x = site_of(g, (int)(i / g.Vh), (int)(i % g.Vh));
+  const size_t s = (size_t)x.c[0] + (size_t)g.L[0] * (x.c[1] + (size_t)g.L[1] * (x.c[2] + (size_t)g.L[2] * x.c[3]));
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const size_t b = link_base(g, x, mu);
+#pragma unroll
+    for (int w = 0; w < 9; ++w) aos[(s * 4 + mu) * 9 + w] = U[b + (size_t)w * g.Vh];
+  }
+}
+
+// derived link copies follow the master after an update
+int refresh_copies(lqcd_gauge* g) {
+  for (int p = 0; p < NPREC; ++p)
+    for (int c = 0; c < 2; ++c) {
+      if (p == P_F64 && c == 0) continue;
+      if (!g->copy[p][c]) continue;
+      LQCD_CK(gauge_convert(g->copy[P_F64][0], g->g, p, c ? 12 : 18, g->copy[p][c], g->ctx->stream));
+    }
+  return LQCD_OK;
+}
+
+}  // namespace
+}  // namespace lqcd
+
+using namespace lqcd;
+
+extern "C" {
+
+int lqcd_heatbath(lqcd_gauge* g, double beta, int nsweeps, unsigned long long seed,
+                  unsigned long long sweep0, int reunit, long long* fails_out) {
+  clear_error();
+  if (!g) return set_error(LQCD_EINVAL, "gauge is NULL");
+  if (!(beta >= 0.0) || !std::isfinite(beta)) return set_error(LQCD_EINVAL, "beta must be finite and >= 0");
+  if (nsweeps < 0) return set_error(LQCD_EINVAL, "nsweeps %d", nsweeps);
+  lqcd_ctx* c = g->ctx;
+  LQCD_CK(cudaSetDevice(c->device));
+  cudaStream_t st = c->stream;
+  LQCD_TRY(ctx_partials(c, 1));
+  unsigned long long* d_fails = reinterpret_cast<unsigned long long*>(c->partials);
+  LQCD_CK(cudaMemsetAsync(d_fails, 0, sizeof(unsigned long long), st));
+  double2* U = static_cast<double2*>(g->copy[P_F64][0]);
+  const unsigned grid = (unsigned)((g->g.Vh + HB_THREADS - 1) / HB_THREADS);
+  const unsigned rgrid = (unsigned)((8LL * g->g.Vh + 255) / 256);
+  for (int sw = 0; sw < nsweeps; ++sw) {
+    const uint64_t sweep = (uint64_t)(sweep0 + (unsigned long long)sw);
+    for (int mu = 0; mu < 4; ++mu)
+      for (int par = 0; par < 2; ++par) {
+        switch (mu) {
+          case 0: k_heatbath<0><<<grid, HB_THREADS, 0, st>>>(U, g->g, par, beta, seed, sweep, d_fails); break;
+          case 1: k_heatbath<1><<<grid, HB_THREADS, 0, st>>>(U, g->g, par, beta, seed, sweep, d_fails); break;
+          case 2: k_heatbath<2><<<grid, HB_THREADS, 0, st>>>(U, g->g, par, beta, seed, sweep, d_fails); break;
+          default: k_heatbath<3><<<grid, HB_THREADS, 0, st>>>(U, g->g, par, beta, seed, sweep, d_fails); break;
+        }
+        c->launches++;
+      }
+    if (reunit) {
+      k_reunitarise<<<rgrid, 256, 0, st>>>(U, g->g);
+      c->launches++;
+    }
+    LQCD_CK(cudaGetLastError());
+  }
+  LQCD_TRY(refresh_copies(g));
+  unsigned long long fails = 0;
+  LQCD_CK(cudaMemcpyAsync(&fails, d_fails, sizeof fails, cudaMemcpyDeviceToHost, st));
+  LQCD_CK(cudaStreamSynchronize(st));
+  if (fails_out) *fails_out = (long long)fails;
+  return LQCD_OK;
+}
+
+int lqcd_plaquette(const lqcd_gauge* g, double* plaq) {
+  clear_error();
+  if (!g || !plaq) return set_error(LQCD_EINVAL, "NULL argument");
+  lqcd_ctx* c = g->ctx;
+  LQCD_CK(cudaSetDevice(c->device));
+  cudaStream_t st = c->stream;
+  const int nb = (int)((2LL * g->g.Vh + PLAQ_THREADS - 1) / PLAQ_THREADS);
+  LQCD_TRY(ctx_partials(c, (size_t)nb + 1));
+  k_plaquette<<<nb, PLAQ_THREADS, 0, st>>>(static_cast<const double2*>(g->copy[P_F64][0]), g->g, c->partials);
+  k_sum_ordered<<<1, PLAQ_THREADS, 0, st>>>(c->partials, nb, c->partials + nb);
+  c->launches += 2;
+  LQCD_CK(cudaGetLastError());
+  double sum = 0.0;
+  LQCD_CK(cudaMemcpyAsync(&sum, c->partials + nb, sizeof sum, cudaMemcpyDeviceToHost, st));
+  LQCD_CK(cudaStreamSynchronize(st));
+  *plaq = sum / (18.0 * 2.0 * (double)g->g.Vh);
+  return LQCD_OK;
+}
+
+int lqcd_gauge_download(const lqcd_gauge* g, double* host_U) {
+  clear_error();
+  if (!g || !host_U) return set_error(LQCD_EINVAL, "NULL argument");
+  lqcd_ctx* c = g->ctx;
+  LQCD_CK(cudaSetDevice(c->device));
+  const size_t bytes = (size_t)2 * g->g.Vh * 4 * 18 * sizeof(double);
+  LQCD_TRY(ctx_staging(c, bytes));
+  const unsigned grid = (unsigned)((2LL * g->g.Vh + 255) / 256);
+  k_gauge_to_aos<<<grid, 256, 0, c->stream>>>(static_cast<const double2*>(g->copy[P_F64][0]), g->g,
+                                              reinterpret_cast<double2*>(c->staging));
+  c->launches++;
+  LQCD_CK(cudaGetLastError());
+  LQCD_CK(cudaMemcpyAsync(host_U, c->staging, bytes, cudaMemcpyDeviceToHost, c->stream));
+  LQCD_CK(cudaStreamSynchronize(c->stream));
+  return LQCD_OK;
+}
+
+}  // extern "C"

@@ -61,6 +61,12 @@ void clear_error();
       return ::lqcd::set_error(LQCD_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
+#define LQCD_TRY(x)                 \
+  do {                              \
+    int rc_ = (x);                  \
+    if (rc_ != LQCD_OK) return rc_; \
+  } while (0)
+
 int make_geom(const int dims[4], int t_bc, Geom& g);
 size_t half_spinor_bytes(int prec, int Vh);
 size_t gauge_copy_bytes(int prec, int nr, int Vh);

@@ -75,10 +75,11 @@ static void fill_result(lqcd_tune_result* r, int prec, int nr, const Entry& e) {
 
 extern "C" {
 
-int lqcd_autotune_dslash(int n, const lqcd_gauge* const* g, int prec, lqcd_tune_result* out) {
+int lqcd_autotune_dslash(int n, const lqcd_gauge* const* g, int prec, int compress, lqcd_tune_result* out) {
   clear_error();
   if (n < 1 || n > MAX_SLOTS || !g || !g[0]) return set_error(LQCD_EINVAL, "bad gauge list (n = %d)", n);
   if (prec < LQCD_F64 || prec > LQCD_DF64) return set_error(LQCD_EINVAL, "precision %d", prec);
+  if (compress != 0 && compress != 12 && compress != 18) return set_error(LQCD_EINVAL, "compress %d", compress);
   lqcd_ctx* c = g[0]->ctx;
   LQCD_CK(cudaSetDevice(c->device));
   cudaStream_t st = c->stream;
@@ -91,7 +92,15 @@ int lqcd_autotune_dslash(int n, const lqcd_gauge* const* g, int prec, lqcd_tune_
     if (!g[i] || g[i]->ctx != c) return set_error(LQCD_EINVAL, "gauge %d: NULL or another context", i);
     const void* base;
     int nri;
-    int rc = gauge_links(g[i], prec, &base, &nri);
+    int rc;
+    if (compress == 0) {
+      rc = gauge_links(g[i], prec, &base, &nri);
+    } else {
+      const int lp = link_prec_for(prec);
+      nri = (lp == P_DF64) ? 18 : compress;
+      rc = lqcd_gauge_add_copy(const_cast<lqcd_gauge*>(g[i]), prec, nri);
+      base = g[i]->copy[lp][nri == 12];
+    }
     if (rc != LQCD_OK) return rc;
     if (nr < 0) nr = nri;
     if (nri != nr) return set_error(LQCD_EINVAL, "gauge list mixes 12- and 18-real links");

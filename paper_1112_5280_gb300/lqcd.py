@@ -113,7 +113,10 @@ def load(build_if_missing: bool = True):
     _sig(lib, "lqcd_dslash_batch_apply", i, [_VP])
     _sig(lib, "lqcd_dslash_batch_destroy", None, [_VP])
     _sig(lib, "lqcd_meson_correlator", i, [C.POINTER(_VP), i, C.POINTER(C.c_int), _VP])
-    _sig(lib, "lqcd_autotune_dslash", i, [i, C.POINTER(_VP), i, C.POINTER(TuneResult)])
+    _sig(lib, "lqcd_gauge_download", i, [_VP, _VP])
+    _sig(lib, "lqcd_heatbath", i, [_VP, d, i, C.c_ulonglong, C.c_ulonglong, i, C.POINTER(ll)])
+    _sig(lib, "lqcd_plaquette", i, [_VP, C.POINTER(d)])
+    _sig(lib, "lqcd_autotune_dslash", i, [i, C.POINTER(_VP), i, i, C.POINTER(TuneResult)])
     _sig(lib, "lqcd_tune_entries", i, [C.POINTER(TuneResult), i, _IP])
     _sig(lib, "lqcd_tune_clear", None, [])
     _sig(lib, "lqcd_tune_save", i, [C.c_char_p])
@@ -243,6 +246,29 @@ class Gauge:
     def nbytes(self) -> int:
         return int(self._lib.lqcd_gauge_bytes(self.h))
 
+    def download(self, out=None):
+        """FP64 master copy in the host layout [V, 4, 3, 3] complex128."""
+        V = int(np.prod(self.dims))
+        if out is None:
+            out = np.empty((V, 4, 3, 3), dtype=np.complex128)
+        if out.shape != (V, 4, 3, 3) or out.dtype != np.complex128 or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous [V,4,3,3] complex128 array")
+        _check(self._lib.lqcd_gauge_download(self.h, out.ctypes.data))
+        return out
+
+    def heatbath(self, beta, nsweeps=1, seed=0, sweep0=0, reunit=True) -> int:
+        """SU(3) heatbath sweeps in place (Cabibbo-Marinari with Creutz's SU(2) draw);
+        returns the number of subgroup draws that hit the attempt limit."""
+        fails = C.c_longlong()
+        _check(self._lib.lqcd_heatbath(self.h, float(beta), int(nsweeps), int(seed), int(sweep0),
+                                       int(bool(reunit)), C.byref(fails)))
+        return fails.value
+
+    def plaquette(self) -> float:
+        p = C.c_double()
+        _check(self._lib.lqcd_plaquette(self.h, C.byref(p)))
+        return p.value
+
     def close(self):
         if self.h:
             self._lib.lqcd_gauge_destroy(self.h)
@@ -371,15 +397,17 @@ def apply_M(gauge: Gauge, kappa: float, fin: Field, fout: Field, dagger=False, m
                                           int(bool(dagger))))
 
 
-def autotune_dslash(gauges, prec) -> dict:
+def autotune_dslash(gauges, prec, compress=0) -> dict:
     """Times the batched Dslash over one slot per gauge (gauges may repeat) for every
-    persistent grid and kernel form; later launches with the same key use the fastest."""
+    persistent grid and kernel form; later launches with the same key use the fastest.
+    compress: 12 or 18 link reals (0: each gauge's default copy)."""
     gauges = list(gauges)
     if not gauges:
         raise ValueError("need at least one gauge")
     arr = (_VP * len(gauges))(*[g.h for g in gauges])
     r = TuneResult()
-    _check(gauges[0]._lib.lqcd_autotune_dslash(len(gauges), arr, _prec(prec), C.byref(r)))
+    _check(gauges[0]._lib.lqcd_autotune_dslash(len(gauges), arr, _prec(prec), int(compress),
+                                               C.byref(r)))
     return r.as_dict()
 
 
