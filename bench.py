@@ -72,6 +72,9 @@ MRHS_KAPPA = 0.15
 MLAT_SIZES = ((8, 8, 8, 8), (12, 12, 12, 24), (16, 16, 16, 32))  # 64 uneven lattices
 MLAT_N = 64
 SERVE_POOL = 2                   # resident gauge fields / sources per serving lattice size
+HB_DIMS, HB_BETA = (32, 32, 32, 64), 6.0  # pure-gauge SU(3) heatbath
+HB_FLOPS_PER_LINK = 3500         # FP64 flops of one link update (staple 2484, U W 198, 3 subgroups ~810)
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12  # SMs x max clock x FP64 FMA/clk/SM x 2 (1.26)
 
 
 def generate_inputs(full: bool):
@@ -422,6 +425,7 @@ def run_ours(args, world, rank, local):
         line["multi_rhs"] = run_mrhs_section(ctx, lqcd, inputs, world)
         line["multi_lattice"] = run_mlat_section(ctx, lqcd, inputs, world)
         line["serve"] = run_serve_section(ctx, lqcd, inputs, world, rank)
+        line["heatbath"] = run_heatbath_section(ctx, lqcd, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle()
     if rank == 0:
@@ -568,6 +572,34 @@ def run_mlat_section(ctx, lqcd, inputs, world):
            "converged": all(i["status"] == 0 for i in infos), "autotune": tuned or "off"}
     for o_ in gs + srcs + list(xs.values()):
         o_.close()
+    return res
+
+
+def run_heatbath_section(ctx, lqcd, world):
+    """SU(3) heatbath sweeps at 32^3x64, beta 6.0, from a cold start (unit links): link
+    updates/s, FP64 ALU roofline, plaquette."""
+    import torch
+    from paper_1112_5280_gb300 import synth
+    g = ctx.gauge(HB_DIMS, synth.unit_links(HB_DIMS), prec="f64")
+    g.heatbath(HB_BETA, nsweeps=3, seed=synth.SEED_LINKS)  # warm-up sweeps (part of thermalisation)
+    n = 10
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    fails = g.heatbath(HB_BETA, nsweeps=n, seed=synth.SEED_LINKS, sweep0=3)
+    dt = max_over_ranks(time.perf_counter() - t0, world)
+    links = 4 * synth.volume(HB_DIMS)
+    rate = links * n / dt
+    achieved = rate * HB_FLOPS_PER_LINK / 1e12
+    res = {"workload": f"{'x'.join(map(str, HB_DIMS))} Wilson gauge action beta={HB_BETA}, cold start, "
+                       "Cabibbo-Marinari + Creutz, reunitarised every sweep",
+           "sweeps": n, "ms_per_sweep": dt / n * 1e3, "link_updates_per_s": rate * world,
+           "plaquette_after": g.plaquette(), "attempt_limit_hits": fails,
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": achieved / FP64_PEAK_TFLOPS,
+                        "peak_kind": "derived FP64: 152 SMs x 2.07 GHz x 2 FMA/clk/SM x 2 flop",
+                        "flops_per_link_update": HB_FLOPS_PER_LINK}}
+    g.close()
     return res
 
 
