@@ -10,6 +10,8 @@ Contents
   * dense.py: brute-force dense matrices for tiny lattices (pure Python loops),
     the free-field closed forms and the FFT solve of the free field.
   * contract.py: the meson correlator of eq. 4.1.
+  * hmc.py: HMC for N_f = 2 (twisted-mass) Wilson fermions with even-odd
+    preconditioning: actions, gauge and fermion forces, leapfrog and 2MN integrators.
   * gauge.py: bindings to heatbath.c, the SU(3) heatbath (Cabibbo-Marinari with
     Creutz's SU(2) draw, Philox4x64-10 random numbers) and the plaquette.
 """

@@ -109,6 +109,18 @@ def gaussian_spinor(dims, seed: int = SEED_SOURCE) -> np.ndarray:
     return _gaussian_complex(rng, (volume(dims), 4, 3))
 
 
+def gaussian_momenta(dims, seed: int) -> np.ndarray:
+    """HMC momenta P[V, 4, 3, 3]: P = i H, H traceless Hermitian with density
+    ~ exp(-Tr(H^2) / 2) (a GUE sample with its trace removed), so that
+    ~ exp(-sum |P_ij|^2 / 2)."""
+    rng = np.random.default_rng(seed)
+    V = volume(dims)
+    a = _gaussian_complex(rng, (V, 4, 3, 3))
+    h = 0.5 * (a + np.conj(np.swapaxes(a, -1, -2)))
+    h = h - (np.trace(h, axis1=-2, axis2=-1) / 3)[..., None, None] * np.eye(3)
+    return 1j * h
+
+
 def gauge_transform_field(dims, seed: int) -> np.ndarray:
     """Random SU(3) matrix g(x) per site, for gauge-covariance checks."""
     rng = np.random.default_rng(seed)
