@@ -75,6 +75,7 @@ extern "C" {
 typedef struct lqcd_ctx lqcd_ctx;
 typedef struct lqcd_gauge lqcd_gauge;
 typedef struct lqcd_field lqcd_field;
+typedef struct lqcd_mom lqcd_mom;
 typedef struct lqcd_engine lqcd_engine;
 typedef struct lqcd_dslash_batch lqcd_dslash_batch;
 
@@ -271,6 +272,76 @@ LQCD_API int lqcd_heatbath(lqcd_gauge* g, double beta, int nsweeps, unsigned lon
  * summed in a fixed order (deterministic). Synchronous. */
 LQCD_API int lqcd_plaquette(const lqcd_gauge* g, double* plaq);
 
+/* ---------------------------------------------------------------- HMC */
+
+/* Hybrid Monte Carlo for N_f = 2 (twisted-mass) Wilson fermions with even-odd
+ * preconditioning (paper Section 3: HMC with even-odd preconditioning, the 2MN integrator
+ * and multiple integration timescales). Conventions:
+ *   S = beta sum_P (1 - Re Tr U_P / 3) + phi^dag (Mhat^dag Mhat)^-1 phi (even sites),
+ *   Mhat as lqcd_apply_Mhat_tm; momenta P traceless anti-Hermitian per link, kinetic energy
+ *   -sum Tr(P^2) / 2; dU/dt = P U, dP/dt = -G with G the su(3) gradient of S
+ *   (dS/de = -sum Tr(H G) for U -> exp(e H) U).
+ * A momentum field (lqcd_mom) holds one traceless anti-Hermitian 3x3 per link in FP64; its
+ * host layout is that of the links, V x 4 x 3 x 3 complex. */
+LQCD_API int lqcd_mom_create(lqcd_ctx* ctx, const int dims[4], lqcd_mom** out);  /* zeroed */
+LQCD_API int lqcd_mom_upload(lqcd_mom* m, const double* host);
+LQCD_API int lqcd_mom_download(const lqcd_mom* m, double* host);
+LQCD_API int lqcd_mom_zero(lqcd_mom* m);
+/* -sum Tr(P^2) / 2, summed in a fixed order. Synchronous. */
+LQCD_API int lqcd_mom_kinetic(const lqcd_mom* m, double* energy);
+LQCD_API void lqcd_mom_destroy(lqcd_mom* m);
+/* m += coeff G_g, G_g = (beta/3) TA(U W) (W the staple sum, TA the traceless
+ * anti-Hermitian part). Asynchronous. */
+LQCD_API int lqcd_gauge_force(const lqcd_gauge* g, double beta, double coeff, lqcd_mom* m);
+/* m += coeff G_f for the solution x = (Mhat^dag Mhat)^-1 phi (FULL FP64 field, even half
+ * used): with Y = Mhat x, Phi = x_e + A^-1 D_oe x_e, Psi = Y + A^-dag (D^dag)_oe Y,
+ * G_f = -2 kappa^2 eta TA(U [((1 - g_mu) Phi(x+mu))^T conj(Psi(x)) + Psi(x+mu)^T
+ * conj((1 + g_mu) Phi(x))]) (spin summed; eta the t-boundary sign). *s_f (may be NULL)
+ * receives S_f = |Y|^2 = phi^dag x. Synchronous. */
+LQCD_API int lqcd_fermion_force(const lqcd_gauge* g, double kappa, double mu, const lqcd_field* x,
+                                double coeff, lqcd_mom* m, double* s_f);
+/* U_mu(x) <- exp(eps P_mu(x)) U_mu(x) on the FP64 master (Taylor series of order 16 after
+ * scaling |eps P| below 1/2, then squaring); derived link copies are rebuilt. */
+LQCD_API int lqcd_gauge_update(lqcd_gauge* g, const lqcd_mom* m, double eps);
+/* Solves (Mhat^dag Mhat) x_e = src_e by the CG engine (mixed precision with reliable
+ * updates as lqcd_solve; opts->mu the twisted mass; CG only) to
+ * |src_e - Mhat^dag Mhat x_e| <= tol |src_e| in FP64-class arithmetic. src, x: FULL FP64
+ * fields; the odd half of src is ignored and that of x is zeroed. */
+LQCD_API int lqcd_solve_normal(const lqcd_gauge* g, const lqcd_field* src, double kappa, double tol,
+                               const lqcd_solve_opts* opts, lqcd_field* x, lqcd_solve_info* info);
+
+#define LQCD_LEAPFROG 0
+#define LQCD_2MN 1   /* second-order minimum norm (Omelyan, Mryglod, Folk), lambda 0.1931833275 */
+
+typedef struct lqcd_hmc_params {
+  double beta, kappa, mu;  /* gauge coupling, hopping parameter, twisted mass */
+  double tau;              /* trajectory length */
+  int nsteps;              /* outer (fermion force) steps */
+  int ngauge;              /* inner (gauge force) steps per outer step, >= 1 */
+  int scheme;              /* LQCD_LEAPFROG or LQCD_2MN, on both levels */
+  int pad;
+  double tol;              /* residual of the force solves (normal equations) */
+  double accept_u;         /* uniform in (0, 1] for the Metropolis test; <= 0: no test, links kept */
+} lqcd_hmc_params;
+
+typedef struct lqcd_hmc_info {
+  double dH, H0, H1;                 /* H1 - H0 */
+  double kinetic0, kinetic1, gauge0, gauge1, fermion0, fermion1;
+  double plaquette;                  /* of the links left in g */
+  int accepted, force_evals, solver_iters, pad;
+  double ms;
+} lqcd_hmc_info;
+
+LQCD_API void lqcd_hmc_params_default(lqcd_hmc_params* p);
+/* One molecular-dynamics trajectory from (g, m) with pseudofermion phi (FULL FP64, even half
+ * used; S_f at the start = phi^dag (Mhat^dag Mhat)^-1 phi). Updates g and m in place. The
+ * gauge force runs ngauge inner steps per outer step; kicks at the same links are merged,
+ * so a trajectory takes nsteps + 1 fermion solves (leapfrog) or 2 nsteps + 1 (2MN). With
+ * accept_u > 0 the links are restored when accept_u > exp(-dH). opts: the solver (CG;
+ * sloppy precision, reliable updates); opts->mu is replaced by p->mu. Synchronous. */
+LQCD_API int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m,
+                                 const lqcd_field* phi, const lqcd_solve_opts* opts, lqcd_hmc_info* info);
+
 /* ---------------------------------------------------------------- meson correlators */
 
 /* Dirac structures Gamma of lqcd_meson_correlator (chiral basis above) */
@@ -309,6 +380,11 @@ LQCD_API int lqcd_engine_submit(lqcd_engine* e, const lqcd_gauge* g, const lqcd_
  * the engine's launches. LQCD_EINVAL for a non-finite kappa or mu. */
 LQCD_API int lqcd_engine_submit_tm(lqcd_engine* e, const lqcd_gauge* g, const lqcd_field* src,
                                    double kappa, double mu, double tol, long long* request_id);
+/* Admits a solve of the even-odd normal equations (Mhat^dag Mhat) x_e = src_e (the HMC
+ * force solve): src FULL FP64 with its odd half ignored; converged when
+ * |src_e - Mhat^dag Mhat x_e| <= tol |src_e| (FP64-class); the result's odd half is zero. */
+LQCD_API int lqcd_engine_submit_normal(lqcd_engine* e, const lqcd_gauge* g, const lqcd_field* src,
+                                       double kappa, double mu, double tol, long long* request_id);
 /* Runs one chunk of iterations for every active solve; *n_active: solves still running. */
 LQCD_API int lqcd_engine_step(lqcd_engine* e, int* n_active);
 /* Ids of solves finished since the last call (up to max). */

@@ -54,7 +54,8 @@ struct Scalars {
   double nreal;     // 24 * Vh, for the RMS normalisation of sloppy vectors
   double res[6];    // generic reduction results / coefficients
   double cres[8];   // complex scalars (BiCGStab): re, im pairs
-  int state, status, iter, maxiter, last, n_updates, restart_p, pad;
+  int state, status, iter, maxiter, last, n_updates, restart_p;
+  int normal;       // 1: solve Mhat^dag Mhat x = phi; converged on |phi - Mhat^dag Mhat x|
   unsigned counter;
   unsigned pad2[3];
 };
@@ -194,6 +195,8 @@ __device__ __noinline__ static void run_fin(const Work& w, const double* v) {
       if (!isfinite(sum)) {
         s->state = S_FAILED;
         s->status = ST_NONFINITE;
+      } else if (s->normal) {
+        // normal equations: u = -Mhat x; the decision falls on rho = phi + Mhat^dag u
       } else if (sum <= s->target2) {
         s->state = S_DONE;
         s->status = ST_OK;
@@ -204,6 +207,18 @@ __device__ __noinline__ static void run_fin(const Work& w, const double* v) {
       break;
     case FIN_RHO: {  // rho = Mhat^dag u: new sloppy unit, p coefficient, stop estimate
       s->rho2 = sum;
+      if (s->normal && isfinite(sum)) {  // rho = phi - Mhat^dag Mhat x is the residual itself
+        if (sum <= s->target2) {
+          s->state = S_DONE;
+          s->status = ST_OK;
+          break;
+        }
+        if (s->last) {
+          s->state = S_FAILED;
+          s->status = ST_MAXITER;
+          break;
+        }
+      }
       if (!isfinite(sum) || !(sum > 0.0)) {
         s->state = S_FAILED;
         s->status = isfinite(sum) ? ST_BREAKDOWN : ST_NONFINITE;
@@ -219,7 +234,8 @@ __device__ __noinline__ static void run_fin(const Work& w, const double* v) {
       }
       s->res[4] = pc;
       s->res[5] = 1.0 / sig_new;
-      const double c2 = s->true_r2 / sum;  // |u|^2 / |Mhat^dag u|^2 at this x
+      // |u|^2 / |Mhat^dag u|^2 at this x (normal equations: the sloppy r is rho itself)
+      const double c2 = s->normal ? 1.0 : s->true_r2 / sum;
       s->sigma = sig_new;
       s->rr = sum / (sig_new * sig_new);
       s->rr_max = s->rr;

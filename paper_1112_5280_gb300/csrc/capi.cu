@@ -499,8 +499,10 @@ static int check_pair(const lqcd_gauge* g, const lqcd_field* a, const lqcd_field
   return LQCD_OK;
 }
 
+}  // extern "C"
+
 // out_p = T(ds, dt) (a * D_{p,1-p} in) + c1 * y1_p + c2 T(1, yt) y2_p, T(s, t) = s (1 + i t g5)
-static int dslash_tw(const lqcd_gauge* gauge, int prec, const void* in, void* out, const void* y1,
+int lqcd::dslash_tw(const lqcd_gauge* gauge, int prec, const void* in, void* out, const void* y1,
                      const void* y2, double a, double c1, double c2, int out_par, bool dag,
                      double ds, double dt, double yt) {
   lqcd_ctx* c = gauge->ctx;
@@ -526,6 +528,8 @@ static int dslash_tw(const lqcd_gauge* gauge, int prec, const void* in, void* ou
   c->launches++;
   return LQCD_OK;
 }
+
+extern "C" {
 
 // out_p = a * D_{p,1-p} in + c1 * y1_p
 static int dslash_lin(const lqcd_gauge* gauge, int prec, const void* in, void* out, const void* y1,

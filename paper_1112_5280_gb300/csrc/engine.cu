@@ -40,8 +40,9 @@ namespace lqcd {
 
 enum Step { K1 = 0, K2, K3, K4, K6, RU_FOLD, RU_D1, RU_RES, RU_D2, RU_RHO, RU_CONV, NSTEP };
 
-__global__ void k_slot_init(Scalars* s, double tol2, double nreal, int maxiter, double delta2) {
-  s->res[3] = s->res[0] + s->res[1];  // |b|^2 of the full source
+__global__ void k_slot_init(Scalars* s, double tol2, double nreal, int maxiter, double delta2, int normal) {
+  s->res[3] = s->res[0] + s->res[1];  // |b|^2 of the full source (normal equations: |phi_e|^2)
+  s->normal = normal;
   s->target2 = tol2 * s->res[3];
   s->sigma = 1.0;
   s->nreal = nreal;
@@ -80,6 +81,7 @@ struct Request {
   const lqcd_gauge* gauge = nullptr;
   Geom g{};
   double kappa = 0, tol = 0, mu = 0;
+  bool normal = false;  // Mhat^dag Mhat x_e = src_e instead of M x = src
   int slot = -1;
   SlotBuf buf;
   int tile0 = 0, ntiles = 0;
@@ -213,6 +215,10 @@ void step_works(const lqcd_engine* e, const Request& q, Work out[NSTEP]) {
   rh.red = 1; rh.fin = FIN_RHO; rh.run_if = S_UPDATE;
   Work& cv = out[RU_CONV];
   cv.in = b.u64; cv.out = b.r; cv.z = b.p; cv.fin = FIN_RESUME; cv.run_if = S_UPDATE;
+  if (q.normal) {  // rho = phi - Mhat^dag Mhat x = phi + Mhat^dag u with u = -Mhat x (bhat = 0)
+    rh.y2 = b.be;
+    rh.c2 = 1.0;
+  }
   const double a = 2.0 * q.kappa * q.mu;
   if (a != 0.0) {
     const double s = 1.0 / (1.0 + a * a);
@@ -224,8 +230,8 @@ void step_works(const lqcd_engine* e, const Request& q, Work out[NSTEP]) {
     set_twist(d1, s, -a, 0.0);
     set_twist(rs, 1.0, 0.0, a);   // u = bhat - A x + k^2 D_eo t
     set_twist(d2, s, a, 0.0);
-    rh.y1 = nullptr; rh.c1 = 0.0; rh.y2 = b.u64; rh.c2 = 1.0;
-    set_twist(rh, 1.0, 0.0, -a);  // rho = A^dag u - k^2 D^dag_eo t
+    rh.y1 = q.normal ? b.be : nullptr; rh.c1 = q.normal ? 1.0 : 0.0; rh.y2 = b.u64; rh.c2 = 1.0;
+    set_twist(rh, 1.0, 0.0, -a);  // rho = A^dag u - k^2 D^dag_eo t (+ phi)
   }
 }
 
@@ -413,6 +419,10 @@ int alloc_block(lqcd_engine* e, size_t bytes, void** out) {
 
 // single-slot launches of the finishing steps (after DONE / FAILED)
 int finalize_launch(lqcd_engine* e, Request& q) {
+  if (q.normal) {  // x_e is the answer; no odd half
+    LQCD_CK(cudaMemsetAsync(q.buf.t64, 0, half_spinor_bytes(e->tp, q.g.Vh), e->ctx->stream));
+    return LQCD_OK;
+  }
   const Geom& g = q.g;
   const int tp = e->tp;
   const void* U64 = q.gauge->copy[tp][0];
@@ -555,8 +565,21 @@ int lqcd_engine_submit(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field
   return lqcd_engine_submit_tm(e, gauge, src, kappa, e->opts.mu, tol, request_id);
 }
 
+static int submit_impl(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field* src, double kappa,
+                       double mu, double tol, bool normal, long long* request_id);
+
 int lqcd_engine_submit_tm(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field* src, double kappa,
                           double mu, double tol, long long* request_id) {
+  return submit_impl(e, gauge, src, kappa, mu, tol, false, request_id);
+}
+
+int lqcd_engine_submit_normal(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field* src, double kappa,
+                              double mu, double tol, long long* request_id) {
+  return submit_impl(e, gauge, src, kappa, mu, tol, true, request_id);
+}
+
+static int submit_impl(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field* src, double kappa,
+                       double mu, double tol, bool normal, long long* request_id) {
   clear_error();
   if (!e || !gauge || !src || !request_id) return set_error(LQCD_EINVAL, "NULL argument");
   if (!std::isfinite(mu) || !std::isfinite(kappa)) return set_error(LQCD_EINVAL, "kappa and mu must be finite");
@@ -588,6 +611,7 @@ int lqcd_engine_submit_tm(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_fi
   q.kappa = kappa;
   q.tol = tol;
   q.mu = mu;
+  q.normal = normal;
   q.ntiles = (q.g.Vh + TILE - 1) / TILE;
   q.t0 = std::chrono::steady_clock::now();
   int rc = alloc_block(e, need, &q.buf.block);
@@ -605,7 +629,10 @@ int lqcd_engine_submit_tm(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_fi
   Scalars* sc = e->d_sc + R.slot;
   if (rc == LQCD_OK) {
     cudaError_t err = spinor_convert(src->half[0], P_F64, R.buf.be, e->tp, q.g.Vh, 1.0, st);
-    if (err == cudaSuccess) err = spinor_convert(src->half[1], P_F64, R.buf.bo, e->tp, q.g.Vh, 1.0, st);
+    if (err == cudaSuccess) {
+      if (normal) err = cudaMemsetAsync(R.buf.bo, 0, hb, st);  // only phi_e counts
+      else err = spinor_convert(src->half[1], P_F64, R.buf.bo, e->tp, q.g.Vh, 1.0, st);
+    }
     if (err == cudaSuccess) err = cudaMemsetAsync(R.buf.x64, 0, hb, st);
     if (err == cudaSuccess) err = cudaMemsetAsync(R.buf.xs, 0, half_spinor_bytes(e->xp, q.g.Vh), st);
     if (err == cudaSuccess) err = cudaMemsetAsync(sc, 0, sizeof(Scalars), st);
@@ -622,11 +649,15 @@ int lqcd_engine_submit_tm(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_fi
     w.fin = FIN_STORE1;
     if (err == cudaSuccess) err = launch_blas(e->tp, B_NORM, single_launch(w, e->d_partials), 0, st);
     if (err == cudaSuccess) {
-      k_slot_init<<<1, 1, 0, st>>>(sc, tol * tol, 24.0 * q.g.Vh, e->opts.maxiter, e->delta2);
+      k_slot_init<<<1, 1, 0, st>>>(sc, tol * tol, 24.0 * q.g.Vh, e->opts.maxiter, e->delta2, normal ? 1 : 0);
       err = cudaGetLastError();
     }
     const double ta = 2.0 * kappa * mu;
-    if (err == cudaSuccess && ta != 0.0) {
+    if (err == cudaSuccess && normal) {
+      // normal equations: bhat = 0, so the update computes u = -Mhat x and rho = phi + Mhat^dag u
+      err = cudaMemsetAsync(R.buf.bhat, 0, hb, st);
+    }
+    if (err == cudaSuccess && ta != 0.0 && !normal) {
       // t = A^-1 b_o
       Work w3 = slot_work(e, R);
       w3.in = R.buf.bo;
@@ -635,7 +666,7 @@ int lqcd_engine_submit_tm(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_fi
       err = launch_blas(e->tp, B_TWIST, single_launch(w3, e->d_partials), 0, st);
       c->launches++;
     }
-    if (err == cudaSuccess) {
+    if (err == cudaSuccess && !normal) {
       // bhat_e = b_e + kappa D_eo A^-1 b_o
       Work d = slot_work(e, R);
       const void* U64 = gauge->copy[e->tp][0];
@@ -717,7 +748,8 @@ int lqcd_engine_step(lqcd_engine* e, int* n_active) {
         q.info.status = status_of(s.status);
         q.info.iters = s.iter;
         q.info.reliable_updates = s.n_updates;
-        q.info.true_resid = s.res[3] > 0 ? sqrt((s.res[0] + s.res[1]) / s.res[3]) : 0.0;
+        const double r2 = q.normal ? s.rho2 : s.res[0] + s.res[1];
+        q.info.true_resid = s.res[3] > 0 ? sqrt(r2 / s.res[3]) : 0.0;
         q.info.ms = std::chrono::duration<double, std::milli>(now - q.t0).count();
         if (q.info.status == LQCD_OK && !(q.info.true_resid <= q.tol)) {
           // the Schur residual met the tolerance but the full one did not

@@ -1,0 +1,633 @@
+// Hybrid Monte Carlo for N_f = 2 (twisted-mass) Wilson fermions with even-odd
+// preconditioning (paper Section 3: an HMC with even-odd preconditioning, the 2MN
+// integrator and multiple integration timescales for N_f = 2 twisted-mass Wilson
+// fermions).
+//
+//   S = S_g + S_f, S_g = beta sum_P (1 - Re Tr U_P / 3), S_f = phi^dag (Mhat^dag Mhat)^-1 phi
+//   on the even sites, Mhat = A - kappa^2 D_eo A^-1 D_oe, A = 1 + i a g5, a = 2 kappa mu.
+//   Momenta P traceless anti-Hermitian; H = -sum Tr(P^2) / 2 + S; dU/dt = P U, dP/dt = -G.
+//   G is the su(3) gradient: dS/de = -sum Tr(H G) for U -> exp(e H) U, so a term
+//   c Re Tr(U B) gives G = -c TA(U B), TA(M) = (M - M^dag)/2 - Tr(M - M^dag)/6.
+//     gauge:   G_g = (beta/3) TA(U W), W the staple sum;
+//     fermion: X = (Mhat^dag Mhat)^-1 phi, Y = Mhat X, Phi = X_e + A^-1 D_oe X_e,
+//              Psi = Y_e + A^-dag (D^dag)_oe Y_e, and
+//              G_f = -2 kappa^2 eta TA(U [ ((1 - g_mu) Phi(x+mu))^T conj(Psi(x))
+//                                          + Psi(x+mu)^T conj((1 + g_mu) Phi(x)) ]),
+//              spin summed, colour indices left as a 3 x 3 matrix, eta the t-boundary sign.
+//   S_f = |Y|^2 comes free with each force.
+// Integrators: leapfrog and the second-order minimum-norm scheme of Omelyan, Mryglod and
+// Folk (lambda = 0.1931833275037836), the gauge force on a nested inner level. Kicks at
+// the same links are merged (one solve where two fermion kicks meet).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "gauge_field.cuh"
+#include "kernels.cuh"
+#include "runtime.h"
+
+namespace lqcd {
+namespace {
+
+using namespace gf;
+
+constexpr int HMC_THREADS = 128;
+
+__device__ __forceinline__ C2 times_i(C2 a) { return {-a.im, a.re}; }
+__device__ __forceinline__ C2 times_mi(C2 a) { return {a.im, -a.re}; }
+__device__ __forceinline__ C2 neg(C2 a) { return {-a.re, -a.im}; }
+__device__ __forceinline__ C2 csub(C2 a, C2 b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ C2 cscale(C2 a, double s) { return {a.re * s, a.im * s}; }
+
+// gamma_mu v on one colour's four spin components (chiral basis: g_k = [[0, -i s_k],
+// [i s_k, 0]] for mu = 0, 1, 2, g_t = [[0, 1], [1, 0]])
+template <int MU>
+__device__ __forceinline__ void gamma_mul(const C2 v[4], C2 o[4]) {
+  if (MU == 0) {
+    o[0] = times_mi(v[3]); o[1] = times_mi(v[2]); o[2] = times_i(v[1]); o[3] = times_i(v[0]);
+  } else if (MU == 1) {
+    o[0] = neg(v[3]); o[1] = v[2]; o[2] = v[1]; o[3] = neg(v[0]);
+  } else if (MU == 2) {
+    o[0] = times_mi(v[2]); o[1] = times_i(v[3]); o[2] = times_i(v[0]); o[3] = times_mi(v[1]);
+  } else {
+    o[0] = v[2]; o[1] = v[3]; o[2] = v[0]; o[3] = v[1];
+  }
+}
+
+__device__ __forceinline__ int eo_index(const Geom& g, const Site& s) {
+  return (s.c[0] >> 1) + g.Lxh * (s.c[1] + g.L[1] * (s.c[2] + g.L[2] * s.c[3]));
+}
+
+// psi[spin][colour] of an FP64 half field (colour-major device layout)
+__device__ __forceinline__ void load_spinor(const void* half, int Vh, int h, C2 psi[4][3]) {
+  double v[24];
+  SpinorIO<P_F64>::load(half, Vh, h, v);
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) psi[s][c] = {v[sidx(s, c)], v[sidx(s, c) + 1]};
+}
+
+__device__ __forceinline__ M3 traceless_ah(const M3& m, double scale) {
+  M3 a;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const C2 x = m.e[i * 3 + j], y = m.e[j * 3 + i];
+      a.e[i * 3 + j] = {0.5 * (x.re - y.re) * scale, 0.5 * (x.im + y.im) * scale};
+    }
+  const double tr = (a.e[0].im + a.e[4].im + a.e[8].im) / 3.0;
+  a.e[0].im -= tr;
+  a.e[4].im -= tr;
+  a.e[8].im -= tr;
+  return a;
+}
+
+__device__ __forceinline__ void add_mom(double2* P, const Geom& g, const Site& x, int mu, const M3& f) {
+  const size_t b = link_base(g, x, mu);
+#pragma unroll
+  for (int w = 0; w < 9; ++w) {
+    double2 d = P[b + (size_t)w * g.Vh];
+    d.x += f.e[w].re;
+    d.y += f.e[w].im;
+    P[b + (size_t)w * g.Vh] = d;
+  }
+}
+
+// P_mu(x) += coeff (beta / 3) TA(U W)
+template <int MU>
+__global__ void __launch_bounds__(HMC_THREADS) k_gauge_force(const double2* U, Geom g, double c, double2* P) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2LL * g.Vh) return;
+  const Site x = site_of(g, (int)(i / g.Vh), (int)(i % g.Vh));
+  const M3 W = staple<MU>(U, g, x);
+  add_mom(P, g, x, MU, traceless_ah(mul_nn(load_link(U, g, x, MU), W), c));
+}
+
+// P_mu(x) += c eta TA(U B), B = ((1 - g_mu) Phi(x+mu))^T conj(Psi(x)) + Psi(x+mu)^T conj((1 + g_mu) Phi(x))
+template <int MU>
+__global__ void __launch_bounds__(HMC_THREADS) k_fermion_force(const double2* U, Geom g, const void* phi_e,
+                                                              const void* phi_o, const void* psi_e,
+                                                              const void* psi_o, double c, double2* P) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2LL * g.Vh) return;
+  const int par = (int)(i / g.Vh), h = (int)(i % g.Vh);
+  const Site x = site_of(g, par, h);
+  const Site xp = shifted(g, x, MU, 1);
+  const int hp = eo_index(g, xp);
+  const void* phi_x = par ? phi_o : phi_e;
+  const void* psi_x = par ? psi_o : psi_e;
+  const void* phi_n = par ? phi_e : phi_o;
+  const void* psi_n = par ? psi_e : psi_o;
+  C2 B[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) B[k] = {0.0, 0.0};
+  {
+    C2 f[4][3], s[4][3];
+    load_spinor(phi_n, g.Vh, hp, f);  // Phi(x + mu)
+    load_spinor(psi_x, g.Vh, h, s);   // Psi(x)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      C2 v[4], gv[4];
+#pragma unroll
+      for (int sp = 0; sp < 4; ++sp) v[sp] = f[sp][b];
+      gamma_mul<MU>(v, gv);
+#pragma unroll
+      for (int sp = 0; sp < 4; ++sp) v[sp] = csub(v[sp], gv[sp]);  // (1 - g_mu) Phi(x+mu), colour b
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) B[b * 3 + a] = cadd(B[b * 3 + a], cmulc(v[sp], s[sp][a]));
+    }
+  }
+  {
+    C2 f[4][3], s[4][3];
+    load_spinor(phi_x, g.Vh, h, f);   // Phi(x)
+    load_spinor(psi_n, g.Vh, hp, s);  // Psi(x + mu)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      C2 v[4], gv[4];
+#pragma unroll
+      for (int sp = 0; sp < 4; ++sp) v[sp] = f[sp][b];
+      gamma_mul<MU>(v, gv);
+#pragma unroll
+      for (int sp = 0; sp < 4; ++sp) v[sp] = cadd(v[sp], gv[sp]);  // (1 + g_mu) Phi(x), colour b
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) B[a * 3 + b] = cadd(B[a * 3 + b], cmulc(s[sp][a], v[sp]));
+    }
+  }
+  const double eta = (MU == 3 && x.c[3] == g.L[3] - 1) ? (double)g.t_bc : 1.0;
+  M3 Bm;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Bm.e[k] = B[k];
+  add_mom(P, g, x, MU, traceless_ah(mul_nn(load_link(U, g, x, MU), Bm), c * eta));
+}
+
+// U <- exp(eps P) U: Taylor series to order 16 after scaling |eps P| below 1/2, then squaring
+__global__ void k_expm_update(double2* U, Geom g, const double2* P, double eps) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // (par, mu, h)
+  if (i >= 8LL * g.Vh) return;
+  const int h = (int)(i % g.Vh);
+  const size_t base = (size_t)(i / g.Vh) * 9 * g.Vh + h;
+  M3 A, u;
+#pragma unroll
+  for (int w = 0; w < 9; ++w) {
+    const double2 p = P[base + (size_t)w * g.Vh], l = U[base + (size_t)w * g.Vh];
+    A.e[w] = {p.x * eps, p.y * eps};
+    u.e[w] = {l.x, l.y};
+  }
+  double nrm = 0.0;  // infinity norm
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    double row = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) row += hypot(A.e[r * 3 + k].re, A.e[r * 3 + k].im);
+    nrm = fmax(nrm, row);
+  }
+  int sq = 0;
+  while (nrm > 0.5 && sq < 60) {
+    nrm *= 0.5;
+    ++sq;
+  }
+  const double sc = ldexp(1.0, -sq);
+#pragma unroll
+  for (int w = 0; w < 9; ++w) A.e[w] = cscale(A.e[w], sc);
+  M3 E;  // Horner: E = 1 + A (1 + A/2 (1 + ... (1 + A/16)))
+#pragma unroll
+  for (int w = 0; w < 9; ++w) E.e[w] = {(w % 4 == 0) ? 1.0 : 0.0, 0.0};
+  for (int k = 16; k >= 1; --k) {
+    M3 T = mul_nn(A, E);
+#pragma unroll
+    for (int w = 0; w < 9; ++w) E.e[w] = cadd({(w % 4 == 0) ? 1.0 : 0.0, 0.0}, cscale(T.e[w], 1.0 / k));
+  }
+  for (int k = 0; k < sq; ++k) E = mul_nn(E, E);
+  const M3 un = mul_nn(E, u);
+#pragma unroll
+  for (int w = 0; w < 9; ++w) U[base + (size_t)w * g.Vh] = make_double2(un.e[w].re, un.e[w].im);
+}
+
+constexpr int RED_THREADS = 256;
+// per-CTA partial of sum |P_ij|^2 / 2
+__global__ void __launch_bounds__(RED_THREADS) k_kinetic(const double2* P, long long n, double* partials) {
+  __shared__ double red[RED_THREADS];
+  double acc = 0.0;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double2 d = P[i];
+    acc = 0.5 * (d.x * d.x + d.y * d.y);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_partials(const double* partials, int n, double* out) {
+  __shared__ double red[RED_THREADS];
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < n; k += RED_THREADS) acc += partials[k];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+int check_mom(const lqcd_gauge* g, const lqcd_mom* m) {
+  if (!g || !m) return set_error(LQCD_EINVAL, "NULL gauge or momentum field");
+  if (g->ctx != m->ctx || memcmp(g->g.L, m->g.L, sizeof g->g.L))
+    return set_error(LQCD_EINVAL, "gauge and momentum field differ in context or lattice");
+  return LQCD_OK;
+}
+
+int gauge_force_impl(const lqcd_gauge* g, double beta, double coeff, lqcd_mom* m) {
+  const double c = coeff * beta / 3.0;
+  const double2* U = static_cast<const double2*>(g->copy[P_F64][0]);
+  const unsigned nb = blocks(2LL * g->g.Vh, HMC_THREADS);
+  cudaStream_t st = g->ctx->stream;
+  k_gauge_force<0><<<nb, HMC_THREADS, 0, st>>>(U, g->g, c, m->d);
+  k_gauge_force<1><<<nb, HMC_THREADS, 0, st>>>(U, g->g, c, m->d);
+  k_gauge_force<2><<<nb, HMC_THREADS, 0, st>>>(U, g->g, c, m->d);
+  k_gauge_force<3><<<nb, HMC_THREADS, 0, st>>>(U, g->g, c, m->d);
+  g->ctx->launches += 4;
+  LQCD_CK(cudaGetLastError());
+  return LQCD_OK;
+}
+
+// |half|^2 of an FP64 half field, synchronous
+int half_norm2(lqcd_ctx* c, const void* half, const Geom& g, double* out) {
+  LQCD_TRY(ctx_partials(c, 3 * (size_t)((g.Vh + TILE - 1) / TILE)));
+  Work w = blank_work(g);
+  w.sc = c->scratch_sc;
+  w.in = half;
+  w.red = 1;
+  w.fin = FIN_STORE0;
+  LQCD_CK(launch_blas(P_F64, B_NORM, single_launch(w, c->partials), 0, c->stream));
+  c->launches++;
+  LQCD_CK(cudaMemcpyAsync(c->host_sc, c->scratch_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
+  LQCD_CK(cudaStreamSynchronize(c->stream));
+  *out = c->host_sc->res[0];
+  return LQCD_OK;
+}
+
+// From X (even half of x, FP64): Y = Mhat X, the odd halves of Phi and Psi, S_f = |Y|^2 and
+// P += coeff G_f. x and y are FULL FP64 fields (their odd halves are overwritten).
+int fermion_force_from_x(const lqcd_gauge* g, double kappa, double mu, lqcd_field* x, lqcd_field* y,
+                         double coeff, lqcd_mom* m, double* s_f) {
+  const double a = 2.0 * kappa * mu, s = 1.0 / (1.0 + a * a);
+  LQCD_TRY(lqcd_apply_Mhat_tm(g, kappa, mu, x, y, 0));
+  double yy = 0.0;
+  LQCD_TRY(half_norm2(g->ctx, y->half[0], g->g, &yy));
+  if (s_f) *s_f = yy;
+  // Phi_o = A^-1 D_oe X_e, Psi_o = A^-dag (D^dag)_oe Y_e
+  LQCD_TRY(dslash_tw(g, P_F64, x->half[0], x->half[1], nullptr, nullptr, 1.0, 0.0, 0.0, 1, false, s, -a, 0.0));
+  LQCD_TRY(dslash_tw(g, P_F64, y->half[0], y->half[1], nullptr, nullptr, 1.0, 0.0, 0.0, 1, true, s, a, 0.0));
+  const double c = -2.0 * kappa * kappa * coeff;
+  const double2* U = static_cast<const double2*>(g->copy[P_F64][0]);
+  const unsigned nb = blocks(2LL * g->g.Vh, HMC_THREADS);
+  cudaStream_t st = g->ctx->stream;
+  const void *pe = x->half[0], *po = x->half[1], *se = y->half[0], *so = y->half[1];
+  k_fermion_force<0><<<nb, HMC_THREADS, 0, st>>>(U, g->g, pe, po, se, so, c, m->d);
+  k_fermion_force<1><<<nb, HMC_THREADS, 0, st>>>(U, g->g, pe, po, se, so, c, m->d);
+  k_fermion_force<2><<<nb, HMC_THREADS, 0, st>>>(U, g->g, pe, po, se, so, c, m->d);
+  k_fermion_force<3><<<nb, HMC_THREADS, 0, st>>>(U, g->g, pe, po, se, so, c, m->d);
+  g->ctx->launches += 4;
+  LQCD_CK(cudaGetLastError());
+  return LQCD_OK;
+}
+
+int solve_normal_with(lqcd_engine* e, const lqcd_gauge* g, const lqcd_field* phi, double kappa, double mu,
+                      double tol, lqcd_field* x, lqcd_solve_info* info) {
+  long long id = 0;
+  LQCD_TRY(lqcd_engine_submit_normal(e, g, phi, kappa, mu, tol, &id));
+  int active = 1;
+  while (active > 0) LQCD_TRY(lqcd_engine_step(e, &active));
+  return lqcd_engine_result(e, id, x, info);
+}
+
+int update_links(lqcd_gauge* g, const lqcd_mom* m, double eps) {
+  k_expm_update<<<blocks(8LL * g->g.Vh, 128), 128, 0, g->ctx->stream>>>(static_cast<double2*>(g->copy[P_F64][0]),
+                                                                          g->g, m->d, eps);
+  g->ctx->launches++;
+  LQCD_CK(cudaGetLastError());
+  return refresh_gauge_copies(g);
+}
+
+int kinetic_impl(const lqcd_mom* m, double* out) {
+  lqcd_ctx* c = m->ctx;
+  const long long n = 72LL * m->g.Vh;  // complex entries: 2 parities x 4 mu x 9 x V/2
+  const int nb = (int)blocks(n, RED_THREADS);
+  LQCD_TRY(ctx_partials(c, (size_t)nb + 1));
+  k_kinetic<<<nb, RED_THREADS, 0, c->stream>>>(m->d, n, c->partials);
+  k_sum_partials<<<1, RED_THREADS, 0, c->stream>>>(c->partials, nb, c->partials + nb);
+  c->launches += 2;
+  LQCD_CK(cudaGetLastError());
+  LQCD_CK(cudaMemcpyAsync(out, c->partials + nb, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LQCD_CK(cudaStreamSynchronize(c->stream));
+  return LQCD_OK;
+}
+
+}  // namespace
+}  // namespace lqcd
+
+using namespace lqcd;
+
+extern "C" {
+
+int lqcd_mom_create(lqcd_ctx* c, const int dims[4], lqcd_mom** out) {
+  clear_error();
+  if (!c || !dims || !out) return set_error(LQCD_EINVAL, "NULL argument");
+  *out = nullptr;
+  Geom g;
+  LQCD_TRY(make_geom(dims, -1, g));
+  LQCD_CK(cudaSetDevice(c->device));
+  lqcd_mom* m = new lqcd_mom();
+  m->ctx = c;
+  m->g = g;
+  m->bytes = gauge_copy_bytes(P_F64, 18, g.Vh);
+  if (cudaMalloc(&m->d, m->bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete m;
+    return set_error(LQCD_ENOMEM, "momentum field (%zu bytes)", gauge_copy_bytes(P_F64, 18, g.Vh));
+  }
+  cudaError_t e = cudaMemsetAsync(m->d, 0, m->bytes, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    cudaFree(m->d);
+    delete m;
+    return set_error(LQCD_ECUDA, "momentum field: %s", cudaGetErrorString(e));
+  }
+  ctx_retain(c);
+  *out = m;
+  return LQCD_OK;
+}
+
+void lqcd_mom_destroy(lqcd_mom* m) {
+  if (!m) return;
+  cudaSetDevice(m->ctx->device);
+  cudaStreamSynchronize(m->ctx->stream);
+  cudaFree(m->d);
+  lqcd_ctx* c = m->ctx;
+  delete m;
+  ctx_release(c);
+}
+
+int lqcd_mom_upload(lqcd_mom* m, const double* host) {
+  clear_error();
+  if (!m || !host) return set_error(LQCD_EINVAL, "NULL argument");
+  lqcd_ctx* c = m->ctx;
+  LQCD_CK(cudaSetDevice(c->device));
+  LQCD_TRY(ctx_staging(c, m->bytes));
+  LQCD_CK(cudaMemcpyAsync(c->staging, host, m->bytes, cudaMemcpyHostToDevice, c->stream));
+  LQCD_CK(gauge_from_aos(c->staging, m->g, P_F64, 18, m->d, c->stream));
+  c->launches++;
+  LQCD_CK(cudaStreamSynchronize(c->stream));
+  return LQCD_OK;
+}
+
+int lqcd_mom_download(const lqcd_mom* m, double* host) {
+  clear_error();
+  if (!m || !host) return set_error(LQCD_EINVAL, "NULL argument");
+  lqcd_ctx* c = m->ctx;
+  LQCD_CK(cudaSetDevice(c->device));
+  LQCD_TRY(ctx_staging(c, m->bytes));
+  LQCD_CK(links_to_aos(m->d, m->g, reinterpret_cast<double2*>(c->staging), c->stream));
+  c->launches++;
+  LQCD_CK(cudaMemcpyAsync(host, c->staging, m->bytes, cudaMemcpyDeviceToHost, c->stream));
+  LQCD_CK(cudaStreamSynchronize(c->stream));
+  return LQCD_OK;
+}
+
+int lqcd_mom_zero(lqcd_mom* m) {
+  clear_error();
+  if (!m) return set_error(LQCD_EINVAL, "NULL argument");
+  LQCD_CK(cudaSetDevice(m->ctx->device));
+  LQCD_CK(cudaMemsetAsync(m->d, 0, m->bytes, m->ctx->stream));
+  return LQCD_OK;
+}
+
+int lqcd_mom_kinetic(const lqcd_mom* m, double* energy) {
+  clear_error();
+  if (!m || !energy) return set_error(LQCD_EINVAL, "NULL argument");
+  LQCD_CK(cudaSetDevice(m->ctx->device));
+  return kinetic_impl(m, energy);
+}
+
+int lqcd_gauge_force(const lqcd_gauge* g, double beta, double coeff, lqcd_mom* m) {
+  clear_error();
+  LQCD_TRY(check_mom(g, m));
+  if (!std::isfinite(beta) || !std::isfinite(coeff)) return set_error(LQCD_EINVAL, "beta and coeff must be finite");
+  LQCD_CK(cudaSetDevice(g->ctx->device));
+  return gauge_force_impl(g, beta, coeff, m);
+}
+
+int lqcd_fermion_force(const lqcd_gauge* g, double kappa, double mu, const lqcd_field* x, double coeff,
+                       lqcd_mom* m, double* s_f) {
+  clear_error();
+  LQCD_TRY(check_mom(g, m));
+  if (!x || x->prec != LQCD_F64 || x->subset != LQCD_FULL || memcmp(x->g.L, g->g.L, sizeof g->g.L))
+    return set_error(LQCD_EINVAL, "x must be a FULL FP64 field of the gauge's lattice");
+  if (!std::isfinite(kappa) || !std::isfinite(mu) || !std::isfinite(coeff))
+    return set_error(LQCD_EINVAL, "kappa, mu and coeff must be finite");
+  lqcd_ctx* c = g->ctx;
+  LQCD_CK(cudaSetDevice(c->device));
+  int dims[4] = {g->g.L[0], g->g.L[1], g->g.L[2], g->g.L[3]};
+  lqcd_field *xx = nullptr, *y = nullptr;
+  int rc = lqcd_field_create(c, dims, LQCD_F64, LQCD_FULL, &xx);
+  if (rc == LQCD_OK) rc = lqcd_field_create(c, dims, LQCD_F64, LQCD_FULL, &y);
+  if (rc == LQCD_OK) rc = lqcd_field_copy(xx, x, 1.0);
+  if (rc == LQCD_OK) rc = fermion_force_from_x(g, kappa, mu, xx, y, coeff, m, s_f);
+  lqcd_field_destroy(xx);
+  lqcd_field_destroy(y);
+  return rc;
+}
+
+int lqcd_gauge_update(lqcd_gauge* g, const lqcd_mom* m, double eps) {
+  clear_error();
+  LQCD_TRY(check_mom(g, m));
+  if (!std::isfinite(eps)) return set_error(LQCD_EINVAL, "eps must be finite");
+  LQCD_CK(cudaSetDevice(g->ctx->device));
+  return update_links(g, m, eps);
+}
+
+int lqcd_solve_normal(const lqcd_gauge* g, const lqcd_field* src, double kappa, double tol,
+                      const lqcd_solve_opts* opts, lqcd_field* x, lqcd_solve_info* info) {
+  clear_error();
+  if (!g || !src || !x) return set_error(LQCD_EINVAL, "NULL argument");
+  lqcd_solve_opts o;
+  lqcd_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.solver != LQCD_CG) return set_error(LQCD_EINVAL, "the normal equations are solved by CG");
+  lqcd_engine* e = nullptr;
+  LQCD_TRY(lqcd_engine_create(g->ctx, &o, 0, 1, &e));
+  const int rc = solve_normal_with(e, g, src, kappa, o.mu, tol, x, info);
+  lqcd_engine_destroy(e);
+  return rc;
+}
+
+void lqcd_hmc_params_default(lqcd_hmc_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof *p);
+  p->beta = 5.6;
+  p->kappa = 0.156;
+  p->mu = 0.0;
+  p->tau = 1.0;
+  p->nsteps = 10;
+  p->ngauge = 4;
+  p->scheme = LQCD_2MN;
+  p->tol = 1e-10;
+  p->accept_u = 0.0;
+}
+
+int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m, const lqcd_field* phi,
+                        const lqcd_solve_opts* opts, lqcd_hmc_info* info) {
+  clear_error();
+  const auto t0 = std::chrono::steady_clock::now();
+  if (info) memset(info, 0, sizeof *info);
+  LQCD_TRY(check_mom(g, m));
+  if (!p || !phi) return set_error(LQCD_EINVAL, "NULL argument");
+  if (phi->prec != LQCD_F64 || phi->subset != LQCD_FULL || memcmp(phi->g.L, g->g.L, sizeof g->g.L))
+    return set_error(LQCD_EINVAL, "phi must be a FULL FP64 field of the gauge's lattice (even half used)");
+  if (p->nsteps < 1 || p->ngauge < 1 || !(p->tau > 0) || !std::isfinite(p->tau) || !(p->tol > 0) ||
+      (p->scheme != LQCD_LEAPFROG && p->scheme != LQCD_2MN) || !std::isfinite(p->beta) ||
+      !std::isfinite(p->kappa) || !std::isfinite(p->mu))
+    return set_error(LQCD_EINVAL, "bad HMC parameters");
+  lqcd_ctx* c = g->ctx;
+  LQCD_CK(cudaSetDevice(c->device));
+  lqcd_solve_opts o;
+  lqcd_solve_opts_default(&o);
+  if (opts) o = *opts;
+  o.solver = LQCD_CG;
+  o.mu = p->mu;
+  int dims[4] = {g->g.L[0], g->g.L[1], g->g.L[2], g->g.L[3]};
+  lqcd_field *x = nullptr, *y = nullptr;
+  lqcd_engine* e = nullptr;
+  void* backup = nullptr;
+  const size_t ubytes = gauge_copy_bytes(P_F64, 18, g->g.Vh);
+  int rc = lqcd_field_create(c, dims, LQCD_F64, LQCD_FULL, &x);
+  if (rc == LQCD_OK) rc = lqcd_field_create(c, dims, LQCD_F64, LQCD_FULL, &y);
+  if (rc == LQCD_OK) rc = lqcd_engine_create(c, &o, 0, 1, &e);
+  if (rc == LQCD_OK && p->accept_u > 0.0) {
+    if (cudaMalloc(&backup, ubytes) != cudaSuccess) {
+      cudaGetLastError();
+      rc = set_error(LQCD_ENOMEM, "link backup");
+    } else if (cudaMemcpyAsync(backup, g->copy[P_F64][0], ubytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
+      rc = set_error(LQCD_ECUDA, "link backup copy");
+    }
+  }
+  // energies at the start
+  double kin0 = 0, kin1 = 0, plaq0 = 0, plaq1 = 0, sf0 = 0, sf1 = 0;
+  if (rc == LQCD_OK) rc = kinetic_impl(m, &kin0);
+  if (rc == LQCD_OK) rc = lqcd_plaquette(g, &plaq0);
+  // kicks at the current links are merged until the links move
+  double pend_f = 0.0, pend_g = 0.0;
+  int force_evals = 0, solves_iters = 0;
+  bool first_f = true;
+  auto flush = [&]() -> int {
+    if (pend_g != 0.0) LQCD_TRY(gauge_force_impl(g, p->beta, -pend_g, m));
+    if (pend_f != 0.0) {
+      lqcd_solve_info si{};
+      LQCD_TRY(solve_normal_with(e, g, phi, p->kappa, p->mu, p->tol, x, &si));
+      solves_iters += si.iters;
+      double s = 0.0;
+      LQCD_TRY(fermion_force_from_x(g, p->kappa, p->mu, x, y, -pend_f, m, &s));
+      if (first_f) sf0 = s;
+      first_f = false;
+      sf1 = s;
+      ++force_evals;
+    }
+    pend_f = pend_g = 0.0;
+    return LQCD_OK;
+  };
+  auto drift = [&](double h) -> int {
+    LQCD_TRY(flush());
+    return update_links(g, m, h);
+  };
+  const double lam = 0.1931833275037836;
+  auto inner = [&](double h) -> int {
+    const double eg = h / p->ngauge;
+    for (int k = 0; k < p->ngauge; ++k) {
+      if (p->scheme == LQCD_LEAPFROG) {
+        pend_g += 0.5 * eg;
+        LQCD_TRY(drift(eg));
+        pend_g += 0.5 * eg;
+      } else {
+        pend_g += lam * eg;
+        LQCD_TRY(drift(0.5 * eg));
+        pend_g += (1.0 - 2.0 * lam) * eg;
+        LQCD_TRY(drift(0.5 * eg));
+        pend_g += lam * eg;
+      }
+    }
+    return LQCD_OK;
+  };
+  const double eps = p->tau / p->nsteps;
+  for (int k = 0; k < p->nsteps && rc == LQCD_OK; ++k) {
+    if (p->scheme == LQCD_LEAPFROG) {
+      pend_f += 0.5 * eps;
+      rc = inner(eps);
+      pend_f += 0.5 * eps;
+    } else {
+      pend_f += lam * eps;
+      rc = inner(0.5 * eps);
+      if (rc == LQCD_OK) {
+        pend_f += (1.0 - 2.0 * lam) * eps;
+        rc = inner(0.5 * eps);
+      }
+      pend_f += lam * eps;
+    }
+  }
+  if (rc == LQCD_OK) rc = flush();
+  if (rc == LQCD_OK) rc = kinetic_impl(m, &kin1);
+  if (rc == LQCD_OK) rc = lqcd_plaquette(g, &plaq1);
+  const double V = 2.0 * g->g.Vh;
+  const double sg0 = p->beta * 6.0 * V * (1.0 - plaq0), sg1 = p->beta * 6.0 * V * (1.0 - plaq1);
+  const double h0 = kin0 + sg0 + sf0, h1 = kin1 + sg1 + sf1;
+  int accepted = 1;
+  if (rc == LQCD_OK && p->accept_u > 0.0) {
+    accepted = std::log(p->accept_u) <= -(h1 - h0) ? 1 : 0;
+    if (!accepted) {
+      if (cudaMemcpyAsync(g->copy[P_F64][0], backup, ubytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+        rc = set_error(LQCD_ECUDA, "link restore");
+      else
+        rc = refresh_gauge_copies(g);
+    }
+  }
+  if (backup) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(backup);
+  }
+  lqcd_engine_destroy(e);
+  lqcd_field_destroy(x);
+  lqcd_field_destroy(y);
+  if (info) {
+    info->dH = h1 - h0;
+    info->H0 = h0;
+    info->H1 = h1;
+    info->kinetic0 = kin0;
+    info->kinetic1 = kin1;
+    info->gauge0 = sg0;
+    info->gauge1 = sg1;
+    info->fermion0 = sf0;
+    info->fermion1 = sf1;
+    info->plaquette = accepted ? plaq1 : plaq0;
+    info->accepted = accepted;
+    info->force_evals = force_evals;
+    info->solver_iters = solves_iters;
+    info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return rc;
+}
+
+}  // extern "C"

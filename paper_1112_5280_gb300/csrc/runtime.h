@@ -38,6 +38,15 @@ struct lqcd_gauge {
   size_t bytes = 0;
 };
 
+// HMC momenta / forces: traceless anti-Hermitian 3x3 per link, FP64, in the link layout
+// [parity][mu][word][V/2] of double2 (word = row * 3 + column)
+struct lqcd_mom {
+  lqcd_ctx* ctx = nullptr;
+  lqcd::Geom g{};
+  double2* d = nullptr;
+  size_t bytes = 0;
+};
+
 struct lqcd_field {
   lqcd_ctx* ctx = nullptr;
   lqcd::Geom g{};
@@ -81,6 +90,17 @@ int gauge_links(const lqcd_gauge* g, int field_prec, const void** base, int* nr)
 inline const void* parity_links(const void* base, int lp, int nr, int Vh, int par) {
   return static_cast<const char*>(base) + (size_t)par * gauge_copy_bytes(lp, nr, Vh) / 2;
 }
+
+// out_p = T(ds, dt) (a D_{p,1-p} in) + c1 y1_p + c2 T(1, yt) y2_p on the context stream,
+// T(s, t) = s (1 + i t g5); half fields of precision prec (capi.cu)
+int dslash_tw(const lqcd_gauge* gauge, int prec, const void* in, void* out, const void* y1,
+              const void* y2, double a, double c1, double c2, int out_par, bool dag, double ds,
+              double dt, double yt);
+
+// pure gauge (heatbath.cu): derived link copies rebuilt from the FP64 master; FP64
+// link layout -> host AoS layout on the device
+int refresh_gauge_copies(lqcd_gauge* g);
+cudaError_t links_to_aos(const double2* U, const Geom& g, double2* aos, cudaStream_t s);
 
 // BiCGStab on Mhat (bicgstab.cu)
 int bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kappa, double tol,

@@ -46,6 +46,26 @@ class SolveInfo(C.Structure):
                 "ms": self.ms}
 
 
+class HmcParams(C.Structure):
+    _fields_ = [("beta", C.c_double), ("kappa", C.c_double), ("mu", C.c_double), ("tau", C.c_double),
+                ("nsteps", C.c_int), ("ngauge", C.c_int), ("scheme", C.c_int), ("pad", C.c_int),
+                ("tol", C.c_double), ("accept_u", C.c_double)]
+
+
+class HmcInfo(C.Structure):
+    _fields_ = [("dH", C.c_double), ("H0", C.c_double), ("H1", C.c_double), ("kinetic0", C.c_double),
+                ("kinetic1", C.c_double), ("gauge0", C.c_double), ("gauge1", C.c_double),
+                ("fermion0", C.c_double), ("fermion1", C.c_double), ("plaquette", C.c_double),
+                ("accepted", C.c_int), ("force_evals", C.c_int), ("solver_iters", C.c_int), ("pad", C.c_int),
+                ("ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+LEAPFROG, TWO_MN = 0, 1
+
+
 class TuneResult(C.Structure):
     _fields_ = [("prec", C.c_int), ("nr", C.c_int), ("ntiles", C.c_int), ("ctas_per_sm", C.c_int),
                 ("form", C.c_int), ("candidates", C.c_int), ("us_best", C.c_double),
@@ -114,6 +134,18 @@ def load(build_if_missing: bool = True):
     _sig(lib, "lqcd_dslash_batch_destroy", None, [_VP])
     _sig(lib, "lqcd_meson_correlator", i, [C.POINTER(_VP), i, C.POINTER(C.c_int), _VP])
     _sig(lib, "lqcd_gauge_download", i, [_VP, _VP])
+    _sig(lib, "lqcd_mom_create", i, [_VP, _IP, C.POINTER(_VP)])
+    _sig(lib, "lqcd_mom_upload", i, [_VP, _VP])
+    _sig(lib, "lqcd_mom_download", i, [_VP, _VP])
+    _sig(lib, "lqcd_mom_zero", i, [_VP])
+    _sig(lib, "lqcd_mom_kinetic", i, [_VP, C.POINTER(d)])
+    _sig(lib, "lqcd_mom_destroy", None, [_VP])
+    _sig(lib, "lqcd_gauge_force", i, [_VP, d, d, _VP])
+    _sig(lib, "lqcd_fermion_force", i, [_VP, d, d, _VP, d, _VP, C.POINTER(d)])
+    _sig(lib, "lqcd_gauge_update", i, [_VP, _VP, d])
+    _sig(lib, "lqcd_hmc_params_default", None, [C.POINTER(HmcParams)])
+    _sig(lib, "lqcd_hmc_trajectory", i, [_VP, C.POINTER(HmcParams), _VP, _VP, C.POINTER(SolveOpts),
+                                         C.POINTER(HmcInfo)])
     _sig(lib, "lqcd_heatbath", i, [_VP, d, i, C.c_ulonglong, C.c_ulonglong, i, C.POINTER(ll)])
     _sig(lib, "lqcd_plaquette", i, [_VP, C.POINTER(d)])
     _sig(lib, "lqcd_autotune_dslash", i, [i, C.POINTER(_VP), i, i, C.POINTER(TuneResult)])
@@ -134,6 +166,8 @@ def load(build_if_missing: bool = True):
         _sig(lib, "lqcd_engine_request_bytes", sz, [_VP, _IP])
         _sig(lib, "lqcd_engine_submit", i, [_VP, _VP, _VP, d, d, C.POINTER(ll)])
         _sig(lib, "lqcd_engine_submit_tm", i, [_VP, _VP, _VP, d, d, d, C.POINTER(ll)])
+        _sig(lib, "lqcd_engine_submit_normal", i, [_VP, _VP, _VP, d, d, d, C.POINTER(ll)])
+        _sig(lib, "lqcd_solve_normal", i, [_VP, _VP, d, d, C.POINTER(SolveOpts), _VP, C.POINTER(SolveInfo)])
         _sig(lib, "lqcd_engine_step", i, [_VP, _IP])
         _sig(lib, "lqcd_engine_completed", i, [_VP, C.POINTER(ll), i, _IP])
         _sig(lib, "lqcd_engine_result", i, [_VP, ll, _VP, C.POINTER(SolveInfo)])
@@ -213,6 +247,9 @@ class Context:
     def gauge(self, dims, U, prec="f64", compress=18, t_bc=-1):
         return Gauge(self, dims, U, prec, compress, t_bc)
 
+    def mom(self, dims, data=None):
+        return Mom(self, dims, data)
+
     def field(self, dims, prec="f64", subset=FULL, data=None):
         f = Field(self, dims, prec, subset)
         if data is not None:
@@ -272,6 +309,49 @@ class Gauge:
     def close(self):
         if self.h:
             self._lib.lqcd_gauge_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mom:
+    """HMC momentum / force field (lqcd_mom): traceless anti-Hermitian 3x3 per link, FP64."""
+
+    def __init__(self, ctx: Context, dims, data=None):
+        self.ctx, self.dims = ctx, tuple(int(d) for d in dims)
+        self._lib = ctx._lib
+        h = _VP()
+        _check(self._lib.lqcd_mom_create(ctx.h, _dims(dims), C.byref(h)))
+        self.h = h
+        if data is not None:
+            self.upload(data)
+
+    def upload(self, P):
+        V = int(np.prod(self.dims))
+        P = _host_array(P, (V, 4, 3, 3))
+        _check(self._lib.lqcd_mom_upload(self.h, P.ctypes.data))
+
+    def download(self):
+        V = int(np.prod(self.dims))
+        out = np.empty((V, 4, 3, 3), dtype=np.complex128)
+        _check(self._lib.lqcd_mom_download(self.h, out.ctypes.data))
+        return out
+
+    def zero(self):
+        _check(self._lib.lqcd_mom_zero(self.h))
+
+    def kinetic(self) -> float:
+        e = C.c_double()
+        _check(self._lib.lqcd_mom_kinetic(self.h, C.byref(e)))
+        return e.value
+
+    def close(self):
+        if self.h:
+            self._lib.lqcd_mom_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -395,6 +475,55 @@ def apply_M(gauge: Gauge, kappa: float, fin: Field, fout: Field, dagger=False, m
     else:
         _check(gauge._lib.lqcd_apply_M_tm(gauge.h, float(kappa), float(mu), fin.h, fout.h,
                                           int(bool(dagger))))
+
+
+def gauge_force(gauge: Gauge, beta, coeff, mom: Mom):
+    """mom += coeff (beta/3) TA(U W)."""
+    _check(gauge._lib.lqcd_gauge_force(gauge.h, float(beta), float(coeff), mom.h))
+
+
+def fermion_force(gauge: Gauge, kappa, mu, x: Field, coeff, mom: Mom) -> float:
+    """mom += coeff G_f for x = (Mhat^dag Mhat)^-1 phi; returns S_f = phi^dag x."""
+    sf = C.c_double()
+    _check(gauge._lib.lqcd_fermion_force(gauge.h, float(kappa), float(mu), x.h, float(coeff), mom.h,
+                                         C.byref(sf)))
+    return sf.value
+
+
+def gauge_update(gauge: Gauge, mom: Mom, eps):
+    """U <- exp(eps P) U."""
+    _check(gauge._lib.lqcd_gauge_update(gauge.h, mom.h, float(eps)))
+
+
+def solve_normal(gauge: Gauge, src: Field, kappa, tol, x: Field, opts: SolveOpts | None = None):
+    """(Mhat^dag Mhat) x_e = src_e by CG; returns the info dict."""
+    info = SolveInfo()
+    o = opts if opts is not None else solve_opts()
+    rc = gauge._lib.lqcd_solve_normal(gauge.h, src.h, float(kappa), float(tol), C.byref(o), x.h,
+                                      C.byref(info))
+    if rc not in (OK, ENOCONV, EBREAKDOWN, ENONFINITE):
+        _check(rc)
+    return info.as_dict()
+
+
+def hmc_params(**kw) -> HmcParams:
+    p = HmcParams()
+    load().lqcd_hmc_params_default(C.byref(p))
+    names = {f[0] for f in HmcParams._fields_}
+    for k, v in kw.items():
+        if k not in names or k == "pad":
+            raise TypeError(f"unknown HMC parameter {k!r}")
+        setattr(p, k, v)
+    return p
+
+
+def hmc_trajectory(gauge: Gauge, params: HmcParams, mom: Mom, phi: Field, opts: SolveOpts | None = None):
+    """One MD trajectory (and Metropolis test when params.accept_u > 0); returns the info dict."""
+    info = HmcInfo()
+    o = opts if opts is not None else solve_opts()
+    _check(gauge._lib.lqcd_hmc_trajectory(gauge.h, C.byref(params), mom.h, phi.h, C.byref(o),
+                                          C.byref(info)))
+    return info.as_dict()
 
 
 def autotune_dslash(gauges, prec, compress=0) -> dict:
@@ -522,11 +651,16 @@ class Engine:
     def request_bytes(self, dims) -> int:
         return int(self._lib.lqcd_engine_request_bytes(self.h, _dims(dims)))
 
-    def submit(self, gauge: Gauge, src: Field, kappa, tol, mu=None):
+    def submit(self, gauge: Gauge, src: Field, kappa, tol, mu=None, normal=False):
         """Returns a request id, or None when the engine is busy (retry later). mu: the
-        request's twisted mass (None: the engine's option)."""
+        request's twisted mass (None: the engine's option). normal: solve
+        (Mhat^dag Mhat) x_e = src_e instead of M x = src."""
         rid = C.c_longlong()
-        if mu is None:
+        if normal:
+            m = 0.0 if mu is None else float(mu)
+            rc = self._lib.lqcd_engine_submit_normal(self.h, gauge.h, src.h, float(kappa), m, float(tol),
+                                                     C.byref(rid))
+        elif mu is None:
             rc = self._lib.lqcd_engine_submit(self.h, gauge.h, src.h, float(kappa), float(tol),
                                               C.byref(rid))
         else:
