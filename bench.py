@@ -426,6 +426,7 @@ def run_ours(args, world, rank, local):
         line["multi_lattice"] = run_mlat_section(ctx, lqcd, inputs, world)
         line["serve"] = run_serve_section(ctx, lqcd, inputs, world, rank)
         line["heatbath"] = run_heatbath_section(ctx, lqcd, world)
+        line["hmc"] = run_hmc_section(ctx, lqcd, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle()
     if rank == 0:
@@ -603,6 +604,54 @@ def run_heatbath_section(ctx, lqcd, world):
     return res
 
 
+HMC_DIMS, HMC_BETA, HMC_KAPPA, HMC_MU = (16, 16, 16, 32), 5.6, 0.15, 0.01
+
+
+def run_hmc_section(ctx, lqcd, world):
+    """One N_f = 2 twisted-mass HMC trajectory (2MN, tau 1, 8 outer x 4 gauge steps, force
+    solves to 1e-10 with FP16-12 sloppy CG) at 16^3x32 on links thermalised by 20 heatbath
+    sweeps at beta 5.6."""
+    import torch
+    from paper_1112_5280_gb300 import synth
+    d = HMC_DIMS
+    g = ctx.gauge(d, synth.unit_links(d))
+    g.heatbath(HMC_BETA, nsweeps=20, seed=synth.SEED_LINKS)
+    ev = (synth.parity_of_sites(d) == 0)[:, None, None]
+    eta = ctx.field(d, "f64", lqcd.FULL)
+    phi = ctx.field(d, "f64", lqcd.FULL)
+
+    def refresh(k):
+        """Momentum and pseudofermion heatbath of trajectory k: phi = Mhat^dag eta at the current links."""
+        eta.upload(synth.gaussian_spinor(d, seed=synth.SEED_SOURCE + 10 + k) * ev)
+        lqcd.apply_Mhat(g, HMC_KAPPA, eta, phi, dagger=True, mu=HMC_MU)
+        m.upload(synth.gaussian_momenta(d, seed=synth.SEED_SOURCE + 20 + k))
+
+    m = ctx.mom(d)
+    p = lqcd.hmc_params(beta=HMC_BETA, kappa=HMC_KAPPA, mu=HMC_MU, tau=1.0, nsteps=8, ngauge=4,
+                        scheme=lqcd.TWO_MN, tol=1e-10)
+    opts = lqcd.solve_opts(sloppy_prec="f16", sloppy_compress=12)
+    warm = []
+    for k in range(2):  # towards the dynamical ensemble (accepted unconditionally)
+        refresh(k)
+        warm.append(lqcd.hmc_trajectory(g, p, m, phi, opts)["dH"])
+    refresh(2)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    info = lqcd.hmc_trajectory(g, p, m, phi, opts)
+    dt = max_over_ranks(time.perf_counter() - t0, world)
+    res = {"workload": f"{'x'.join(map(str, d))} N_f=2 twisted mass kappa={HMC_KAPPA} mu={HMC_MU}, "
+                       f"beta={HMC_BETA} (links: 20 heatbath sweeps, then 2 HMC trajectories), 2MN tau=1 8x4 steps, "
+                       "force solves 1e-10 (FP16-12 sloppy CG, double-float updates)",
+           "ms_per_trajectory": dt * 1e3, "trajectories_per_s": world / dt,
+           "dH": info["dH"], "dH_warmup": warm, "force_evals": info["force_evals"],
+           "solver_iters": info["solver_iters"],
+           "plaquette": info["plaquette"], "fermion_action_start": info["fermion0"]}
+    for o_ in (g, m, eta, phi):
+        o_.close()
+    return res
+
+
 def run_serve_section(ctx, lqcd, inputs, world, rank):
     """Poisson stream over {8^4, 16^3x32, 24^3x48, 32^3x64} (0.4/0.3/0.2/0.1), resident gauge
     fields, admission by HBM budget, continuous batching; closed-loop capacity, then open loop
@@ -678,12 +727,30 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (no autotuner)")
     ap.add_argument("--no-variants", action="store_true", help="skip the one-application-per-launch timings")
     ap.add_argument("--dslash-only", action="store_true", help="skip the solver, multi-RHS, multi-lattice and serving sections")
+    ap.add_argument("--section", choices=["heatbath", "hmc"],
+                    help="run one section alone and print its JSON (profiling); no contract line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.section:
+        return run_one_section(args, world, rank, local)
     return run_ours(args, world, rank, local)
+
+
+def run_one_section(args, world, rank, local):
+    import torch
+    from paper_1112_5280_gb300 import lqcd
+    dev = local if world > 1 else 0
+    torch.cuda.set_device(dev)
+    ctx = lqcd.Context(dev, torch.cuda.Stream(device=dev))
+    fn = {"heatbath": run_heatbath_section, "hmc": run_hmc_section}[args.section]
+    res = fn(ctx, lqcd, world)
+    if rank == 0:
+        print(json.dumps({"section": args.section, **res}))
+    ctx.close()
+    return 0
 
 
 if __name__ == "__main__":

@@ -23,6 +23,8 @@ constexpr int MAX_SLOTS = 1024;   // slots in one launch
 
 // Slot state machine of the Krylov engine.
 enum SlotState { S_RUNNING = 0, S_UPDATE = 1, S_DONE = 2, S_FAILED = 3, S_IDLE = 4 };
+// run_if of a step that a slot never takes (the other reliable-update path)
+constexpr int S_NEVER = 99;
 // Status codes written into Scalars::status (mirrors the public LQCD_* codes).
 enum SlotStatus { ST_OK = 0, ST_MAXITER = -3, ST_BREAKDOWN = -4, ST_NONFINITE = -5 };
 
@@ -36,6 +38,7 @@ enum Fin {
   FIN_TRUERES,   // reliable update: |bhat - Mhat x|^2 -> converged?
   FIN_RHO,       // reliable update: |Mhat^dag u|^2 -> new sloppy scale and p coefficient
   FIN_RESUME,    // reliable update done: back to RUNNING
+  FIN_RHO2,      // reliable update, sloppy rho = Mhat^dag (u / sigma_u): the same as FIN_RHO
   FIN_BICG_RHO,  // BiCGStab scalars (see solver.cu)
   FIN_BICG_ALPHA,
   FIN_BICG_OMEGA,
@@ -204,7 +207,31 @@ __device__ __noinline__ static void run_fin(const Work& w, const double* v) {
         s->state = S_FAILED;
         s->status = ST_MAXITER;
       }
+      // unit of the sloppy copy u / sigma_u taken by the sloppy-rho update path
+      s->res[2] = sum > 0.0 ? sqrt(s->nreal / sum) : 0.0;
       break;
+    case FIN_RHO2: {  // sum = |Mhat^dag (u / sigma_u)|^2 in the sloppy unit sigma_u
+      const double sig_u = s->res[2] > 0.0 ? 1.0 / s->res[2] : 0.0;
+      const double rho2 = sum * sig_u * sig_u;
+      s->rho2 = rho2;
+      if (!isfinite(sum) || !(sum > 0.0)) {
+        s->state = S_FAILED;
+        s->status = isfinite(sum) ? ST_BREAKDOWN : ST_NONFINITE;
+        break;
+      }
+      double pc = 0.0;
+      if (!s->restart_p) {  // beta of the replaced CG step (true units), p moved to the unit sig_u
+        const double beta = rho2 / (s->sigma * s->sigma * s->rr_prev);
+        pc = beta * s->sigma / sig_u;
+      }
+      s->res[4] = pc;
+      const double c2 = s->true_r2 / rho2;
+      s->sigma = sig_u;
+      s->rr = sum;
+      s->rr_max = sum;
+      s->stop_rr = 0.5 * s->target2 / (c2 * sig_u * sig_u);
+      break;
+    }
     case FIN_RHO: {  // rho = Mhat^dag u: new sloppy unit, p coefficient, stop estimate
       s->rho2 = sum;
       if (s->normal && isfinite(sum)) {  // rho = phi - Mhat^dag Mhat x is the residual itself

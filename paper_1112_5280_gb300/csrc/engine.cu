@@ -7,9 +7,10 @@
 //    BF16, arithmetic in FP32) in units of sigma (RMS 1 per real after each
 //    update), the sloppy solution xs in FP32;
 //  * an update folds sigma * xs into the FP64 solution x, recomputes the true
-//    residual u = bhat - Mhat x and rho = Mhat^dag u in FP64 with FP64 links,
-//    restarts r = rho / sigma_new and keeps the search direction p (rescaled,
-//    with the CG beta of the replaced step);
+//    residual u = bhat - Mhat x in FP64-class arithmetic with FP64-class links,
+//    then rho = Mhat^dag u (in the sloppy precision from u / |u|_rms for M x = b;
+//    in FP64-class arithmetic for the normal equations), restarts r = rho / sigma_new
+//    and keeps the search direction p (rescaled, with the CG beta of the replaced step);
 //  * an update is triggered when |r| drops below delta * max|r| since the last
 //    one, when the sloppy residual predicts convergence, or at maxiter. The
 //    solve ends when |bhat - Mhat x| <= tol |b| in FP64; then x_o = b_o +
@@ -38,7 +39,12 @@
 
 namespace lqcd {
 
-enum Step { K1 = 0, K2, K3, K4, K6, RU_FOLD, RU_D1, RU_RES, RU_D2, RU_RHO, RU_CONV, NSTEP };
+// RU_D2 / RU_RHO / RU_CONV: rho = Mhat^dag u in FP64-class arithmetic (normal-equation
+// solves, whose convergence is decided on rho); RU_QS / RU_D2S / RU_RHOS / RU_PS: rho in
+// the sloppy precision from the sloppy copy u / sigma_u (M x = b solves, whose convergence
+// is decided on u; rho only restarts the sloppy recurrence).
+enum Step { K1 = 0, K2, K3, K4, K6, RU_FOLD, RU_D1, RU_RES, RU_D2, RU_RHO, RU_CONV,
+            RU_QS, RU_D2S, RU_RHOS, RU_PS, NSTEP };
 
 __global__ void k_slot_init(Scalars* s, double tol2, double nreal, int maxiter, double delta2, int normal) {
   s->res[3] = s->res[0] + s->res[1];  // |b|^2 of the full source (normal equations: |phi_e|^2)
@@ -120,6 +126,7 @@ struct lqcd_engine {
   int ntiles_total = 0;
   int interleave = 0;
   bool any_twist = false;  // some active request has mu != 0
+  bool any_normal = false, any_plain = false;  // active normal-equation / M x = b requests
   cudaGraphExec_t exec = nullptr;
   std::vector<Work> h_works;
 };
@@ -215,6 +222,20 @@ void step_works(const lqcd_engine* e, const Request& q, Work out[NSTEP]) {
   rh.red = 1; rh.fin = FIN_RHO; rh.run_if = S_UPDATE;
   Work& cv = out[RU_CONV];
   cv.in = b.u64; cv.out = b.r; cv.z = b.p; cv.fin = FIN_RESUME; cv.run_if = S_UPDATE;
+  // sloppy rho path: q = u / sigma_u, t = D^dag_oe q, r = Mhat^dag q (+ norm), p = r + c p
+  Work& qs = out[RU_QS];
+  qs.in = b.u64; qs.out = b.q; qs.run_if = S_UPDATE;
+  Work& d2s = out[RU_D2S];
+  links(d2s, US, lpS, e->nr, 1);
+  d2s.in = b.q; d2s.out = b.t; d2s.a = 1.0; d2s.run_if = S_UPDATE;
+  Work& rhs = out[RU_RHOS];
+  links(rhs, US, lpS, e->nr, 0);
+  rhs.in = b.t; rhs.out = b.r; rhs.y1 = b.q; rhs.c1 = 1.0; rhs.a = -kk;
+  rhs.red = 1; rhs.fin = FIN_RHO2; rhs.run_if = S_UPDATE;
+  Work& ps = out[RU_PS];
+  ps.in = b.r; ps.z = b.p; ps.fin = FIN_RESUME; ps.run_if = S_UPDATE;
+  for (int st : {RU_D2, RU_RHO, RU_CONV}) out[st].run_if = q.normal ? S_UPDATE : S_NEVER;
+  for (int st : {RU_QS, RU_D2S, RU_RHOS, RU_PS}) out[st].run_if = q.normal ? S_NEVER : S_UPDATE;
   if (q.normal) {  // rho = phi - Mhat^dag Mhat x = phi + Mhat^dag u with u = -Mhat x (bhat = 0)
     rh.y2 = b.be;
     rh.c2 = 1.0;
@@ -232,6 +253,9 @@ void step_works(const lqcd_engine* e, const Request& q, Work out[NSTEP]) {
     set_twist(d2, s, a, 0.0);
     rh.y1 = q.normal ? b.be : nullptr; rh.c1 = q.normal ? 1.0 : 0.0; rh.y2 = b.u64; rh.c2 = 1.0;
     set_twist(rh, 1.0, 0.0, -a);  // rho = A^dag u - k^2 D^dag_eo t (+ phi)
+    set_twist(d2s, s, a, 0.0);
+    rhs.y1 = nullptr; rhs.c1 = 0.0; rhs.y2 = b.q; rhs.c2 = 1.0;
+    set_twist(rhs, 1.0, 0.0, -a);  // r = A^dag q - k^2 D^dag_eo t
   }
 }
 
@@ -255,6 +279,10 @@ StepKind kind_of(int s) {
     case RU_D2: return {true, true, true, EPI_LIN};
     case RU_RHO: return {true, true, true, EPI_LIN};
     case RU_CONV: return {false, false, false, B_RU_CONVERT};
+    case RU_QS: return {false, false, false, B_RU_SCALE};
+    case RU_D2S: return {true, false, true, EPI_LIN};
+    case RU_RHOS: return {true, false, true, EPI_LIN};
+    case RU_PS: return {false, false, false, B_RU_P};
   }
   return {false, false, false, 0};
 }
@@ -285,6 +313,14 @@ Launch batch_launch(const lqcd_engine* e, int s) {
   return L;
 }
 
+// the reliable-update steps for a launch holding normal-equation and / or M x = b slots
+std::vector<int> ru_steps(bool normal, bool plain) {
+  std::vector<int> v = {RU_FOLD, RU_D1, RU_RES};
+  if (normal) v.insert(v.end(), {RU_D2, RU_RHO, RU_CONV});
+  if (plain) v.insert(v.end(), {RU_QS, RU_D2S, RU_RHOS, RU_PS});
+  return v;
+}
+
 cudaError_t issue_iteration_block(lqcd_engine* e, int iters) {
   for (int it = 0; it < iters; ++it) {
     for (int s : {K1, K2, K3, K4, K6}) {
@@ -292,7 +328,7 @@ cudaError_t issue_iteration_block(lqcd_engine* e, int iters) {
       if (err != cudaSuccess) return err;
     }
     if ((it + 1) % e->ru_every == 0 || it + 1 == iters) {
-      for (int s : {RU_FOLD, RU_D1, RU_RES, RU_D2, RU_RHO, RU_CONV}) {
+      for (int s : ru_steps(e->any_normal, e->any_plain)) {
         cudaError_t err = issue(e, s, batch_launch(e, s), e->any_twist);
         if (err != cudaSuccess) return err;
       }
@@ -310,9 +346,12 @@ int rebuild(lqcd_engine* e) {
   const lqcd_gauge* g0 = e->reqs[e->active[0]].gauge;
   bool same = true;
   e->any_twist = false;
+  e->any_normal = e->any_plain = false;
   for (long long id : e->active) {
     same = same && e->reqs[id].gauge == g0;
     e->any_twist = e->any_twist || e->reqs[id].mu != 0.0;
+    if (e->reqs[id].normal) e->any_normal = true;
+    else e->any_plain = true;
   }
   e->interleave = (same && n > 1) ? 1 : 0;
   std::vector<int> prefix(n + 1, 0);
@@ -684,7 +723,7 @@ static int submit_impl(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field
       // first true residual and restart (state UPDATE, restart_p = 1)
       Work w2[NSTEP];
       step_works(e, R, w2);
-      for (int s : {RU_FOLD, RU_D1, RU_RES, RU_D2, RU_RHO, RU_CONV}) {
+      for (int s : ru_steps(normal, !normal)) {
         if (err != cudaSuccess) break;
         err = issue(e, s, single_launch(w2[s], e->d_partials), mu != 0.0);
       }
@@ -719,7 +758,8 @@ int lqcd_engine_step(lqcd_engine* e, int* n_active) {
     if (e->opts.use_graph) {
       LQCD_CK(cudaGraphLaunch(e->exec, st));
       c->launches += (long long)e->opts.chunk * 5 +
-                     ((e->opts.chunk + e->ru_every - 1) / e->ru_every) * 6;
+                     ((e->opts.chunk + e->ru_every - 1) / e->ru_every) *
+                         (long long)ru_steps(e->any_normal, e->any_plain).size();
     } else {
       cudaError_t err = issue_iteration_block(e, e->opts.chunk);
       if (err != cudaSuccess) return set_error(LQCD_ECUDA, "iteration: %s", cudaGetErrorString(err));

@@ -167,7 +167,8 @@ __global__ void __launch_bounds__(HMC_THREADS) k_fermion_force(const double2* U,
   add_mom(P, g, x, MU, traceless_ah(mul_nn(load_link(U, g, x, MU), Bm), c * eta));
 }
 
-// U <- exp(eps P) U: Taylor series to order 16 after scaling |eps P| below 1/2, then squaring
+// U <- exp(eps P) U: Taylor series after scaling |eps P| below 1/2 (order from the norm,
+// at most 16), then squaring
 __global__ void k_expm_update(double2* U, Geom g, const double2* P, double eps) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // (par, mu, h)
   if (i >= 8LL * g.Vh) return;
@@ -196,10 +197,16 @@ __global__ void k_expm_update(double2* U, Geom g, const double2* P, double eps) 
   const double sc = ldexp(1.0, -sq);
 #pragma unroll
   for (int w = 0; w < 9; ++w) A.e[w] = cscale(A.e[w], sc);
-  M3 E;  // Horner: E = 1 + A (1 + A/2 (1 + ... (1 + A/16)))
+  // Taylor order: the smallest n with nrm^(n+1) / (n+1)! below 2^-56 (n <= 16 as nrm <= 1/2)
+  int order = 1;
+  for (double term = nrm; order < 16; ++order) {
+    term *= nrm / (order + 1);
+    if (term < 0x1.0p-56) break;
+  }
+  M3 E;  // Horner: E = 1 + A (1 + A/2 (1 + ... (1 + A/n)))
 #pragma unroll
   for (int w = 0; w < 9; ++w) E.e[w] = {(w % 4 == 0) ? 1.0 : 0.0, 0.0};
-  for (int k = 16; k >= 1; --k) {
+  for (int k = order; k >= 1; --k) {
     M3 T = mul_nn(A, E);
 #pragma unroll
     for (int w = 0; w < 9; ++w) E.e[w] = cadd({(w % 4 == 0) ? 1.0 : 0.0, 0.0}, cscale(T.e[w], 1.0 / k));
@@ -316,12 +323,13 @@ int solve_normal_with(lqcd_engine* e, const lqcd_gauge* g, const lqcd_field* phi
   return lqcd_engine_result(e, id, x, info);
 }
 
-int update_links(lqcd_gauge* g, const lqcd_mom* m, double eps) {
+// refresh: rebuild the derived link copies now (else the caller does before they are read)
+int update_links(lqcd_gauge* g, const lqcd_mom* m, double eps, bool refresh) {
   k_expm_update<<<blocks(8LL * g->g.Vh, 128), 128, 0, g->ctx->stream>>>(static_cast<double2*>(g->copy[P_F64][0]),
                                                                           g->g, m->d, eps);
   g->ctx->launches++;
   LQCD_CK(cudaGetLastError());
-  return refresh_gauge_copies(g);
+  return refresh ? refresh_gauge_copies(g) : LQCD_OK;
 }
 
 int kinetic_impl(const lqcd_mom* m, double* out) {
@@ -458,7 +466,7 @@ int lqcd_gauge_update(lqcd_gauge* g, const lqcd_mom* m, double eps) {
   LQCD_TRY(check_mom(g, m));
   if (!std::isfinite(eps)) return set_error(LQCD_EINVAL, "eps must be finite");
   LQCD_CK(cudaSetDevice(g->ctx->device));
-  return update_links(g, m, eps);
+  return update_links(g, m, eps, true);
 }
 
 int lqcd_solve_normal(const lqcd_gauge* g, const lqcd_field* src, double kappa, double tol,
@@ -533,10 +541,12 @@ int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m, co
   // kicks at the current links are merged until the links move
   double pend_f = 0.0, pend_g = 0.0;
   int force_evals = 0, solves_iters = 0;
-  bool first_f = true;
+  bool first_f = true, copies_stale = false;  // derived link copies are rebuilt only for the solves
   auto flush = [&]() -> int {
     if (pend_g != 0.0) LQCD_TRY(gauge_force_impl(g, p->beta, -pend_g, m));
     if (pend_f != 0.0) {
+      if (copies_stale) LQCD_TRY(refresh_gauge_copies(g));
+      copies_stale = false;
       lqcd_solve_info si{};
       LQCD_TRY(solve_normal_with(e, g, phi, p->kappa, p->mu, p->tol, x, &si));
       solves_iters += si.iters;
@@ -552,7 +562,8 @@ int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m, co
   };
   auto drift = [&](double h) -> int {
     LQCD_TRY(flush());
-    return update_links(g, m, h);
+    copies_stale = true;
+    return update_links(g, m, h, false);
   };
   const double lam = 0.1931833275037836;
   auto inner = [&](double h) -> int {
@@ -589,6 +600,7 @@ int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m, co
     }
   }
   if (rc == LQCD_OK) rc = flush();
+  if (rc == LQCD_OK && copies_stale) rc = refresh_gauge_copies(g);
   if (rc == LQCD_OK) rc = kinetic_impl(m, &kin1);
   if (rc == LQCD_OK) rc = lqcd_plaquette(g, &plaq1);
   const double V = 2.0 * g->g.Vh;

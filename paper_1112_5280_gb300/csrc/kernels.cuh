@@ -292,6 +292,8 @@ enum Blas {
   B_BICG_X,       // x(z) += alpha p(zin) + omega s(in) ; r(out) = s - omega t(y1) ; <r0(y2), r>, |r|^2
   B_FOLD64,       // x64(out) += a * xs(in) (SP) ; xs = 0
   B_TWIST,        // out = tw_s (1 + i tw_t g5) in
+  B_RU_SCALE,     // out (SP) = in (TP) * res[2]
+  B_RU_P,         // p(z) = restart ? r(in) : r + res[4] p
 };
 
 // out = x + c * y (complex c)
@@ -360,6 +362,27 @@ __global__ void __launch_bounds__(TILE) k_blas(const Launch L) {
           SpinorIO<SP>::load(w.z, Vh, h, p);
 #pragma unroll
           for (int i = 0; i < 24; ++i) p[i] = r[i] + (R)pc * p[i];
+        }
+        SpinorIO<SP>::store(w.z, Vh, h, p);
+      } else if (OP == B_RU_SCALE) {  // sloppy copy of an FP64-class vector in the unit 1 / res[2]
+        const TR sc = TR(w.sc->res[2]);
+        TR u[24];
+        SpinorIO<TP>::load(w.in, Vh, h, u);
+        R q[24];
+#pragma unroll
+        for (int i = 0; i < 24; ++i) q[i] = cvt<R>(u[i] * sc);
+        SpinorIO<SP>::store(w.out, Vh, h, q);
+      } else if (OP == B_RU_P) {
+        R r[24], p[24];
+        SpinorIO<SP>::load(w.in, Vh, h, r);
+        if (w.sc->restart_p) {
+#pragma unroll
+          for (int i = 0; i < 24; ++i) p[i] = r[i];
+        } else {
+          const R pc = (R)w.sc->res[4];
+          SpinorIO<SP>::load(w.z, Vh, h, p);
+#pragma unroll
+          for (int i = 0; i < 24; ++i) p[i] = r[i] + pc * p[i];
         }
         SpinorIO<SP>::store(w.z, Vh, h, p);
       } else if (OP == B_NORM) {
