@@ -422,6 +422,7 @@ def run_ours(args, world, rank, local):
     }
     if not args.dslash_only:
         line["solve"] = run_solve_section(ctx, lqcd, inputs, world)
+        line["dslash32"] = run_dslash32_section(ctx, lqcd, world, U=inputs["solve"][0])
         line["multi_rhs"] = run_mrhs_section(ctx, lqcd, inputs, world)
         line["multi_lattice"] = run_mlat_section(ctx, lqcd, inputs, world)
         line["serve"] = run_serve_section(ctx, lqcd, inputs, world, rank)
@@ -607,6 +608,49 @@ def run_heatbath_section(ctx, lqcd, world):
 HMC_DIMS, HMC_BETA, HMC_KAPPA, HMC_MU = (16, 16, 16, 32), 5.6, 0.15, 0.01
 
 
+def run_dslash32_section(ctx, lqcd, world, U=None):
+    """The solvers' sloppy operator at 32^3x64: one even-odd Dslash application per launch
+    (FP16 and FP32 spinors, 12-real links), 200 launches replayed from a CUDA graph."""
+    import torch
+    from paper_1112_5280_gb300 import synth
+    d = SOLVE_DIMS
+    if U is None:
+        U = synth.random_links(d, SOLVE_EPS, seed=synth.SEED_LINKS)
+    Vh = synth.volume(d) // 2
+    psi = synth.gaussian_spinor(d, seed=synth.SEED_SOURCE)
+    out = {"workload": "32^3x64 even-odd Dslash, 12-real links, one application per launch"}
+    peak, _ = measured_peaks()
+    for prec, nb in (("f16", 2), ("f32", 4)):
+        g = ctx.gauge(d, U, prec=prec, compress=12)
+        fi = ctx.field(d, prec, lqcd.ODD, data=psi)
+        fo = ctx.field(d, prec, lqcd.EVEN)
+        lqcd.dslash_eo(g, fi, fo, 0)
+        ctx.sync()
+        st = ctx._stream  # the context's launch stream (a torch stream)
+        graph = torch.cuda.CUDAGraph()
+        n = 200
+        with torch.cuda.graph(graph, stream=st):
+            for _ in range(n):
+                lqcd.dslash_eo(g, fi, fo, 0)
+        for _ in range(3):
+            graph.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            e0.record(st)
+            graph.replay()
+            e1.record(st)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / n
+        gbs = algorithmic_bytes_per_site(nb, 12) * Vh / (us * 1e-6) / 1e9
+        out[prec] = {"us_per_application": us, "GBps": gbs, "frac_of_measured_hbm": gbs / peak,
+                     "bytes_per_site": algorithmic_bytes_per_site(nb, 12)}
+        del graph
+        for o_ in (g, fi, fo):
+            o_.close()
+    return out
+
+
 def run_hmc_section(ctx, lqcd, world):
     """One N_f = 2 twisted-mass HMC trajectory (2MN, tau 1, 8 outer x 4 gauge steps, force
     solves to 1e-10 with FP16-12 sloppy CG) at 16^3x32 on links thermalised by 20 heatbath
@@ -727,7 +771,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (no autotuner)")
     ap.add_argument("--no-variants", action="store_true", help="skip the one-application-per-launch timings")
     ap.add_argument("--dslash-only", action="store_true", help="skip the solver, multi-RHS, multi-lattice and serving sections")
-    ap.add_argument("--section", choices=["heatbath", "hmc"],
+    ap.add_argument("--section", choices=["heatbath", "hmc", "dslash32"],
                     help="run one section alone and print its JSON (profiling); no contract line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -745,7 +789,8 @@ def run_one_section(args, world, rank, local):
     dev = local if world > 1 else 0
     torch.cuda.set_device(dev)
     ctx = lqcd.Context(dev, torch.cuda.Stream(device=dev))
-    fn = {"heatbath": run_heatbath_section, "hmc": run_hmc_section}[args.section]
+    fn = {"heatbath": run_heatbath_section, "hmc": run_hmc_section,
+          "dslash32": run_dslash32_section}[args.section]
     res = fn(ctx, lqcd, world)
     if rank == 0:
         print(json.dumps({"section": args.section, **res}))

@@ -47,7 +47,9 @@ def up_to_date() -> bool:
 
 def _compile(src, extra):
     obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    cmd = [_nvcc()] + NVCC_FLAGS + extra + ["-c", src, "-o", obj]
+    # LQCD_NVCC_EXTRA: extra nvcc flags, e.g. -D values of the compile-time tunables
+    env_extra = os.environ.get("LQCD_NVCC_EXTRA", "").split()
+    cmd = [_nvcc()] + NVCC_FLAGS + extra + env_extra + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

@@ -8,10 +8,16 @@
 // B = Gamma g5, has one non-zero per row and column: A[al][pi(al)] = a_al,
 // B[rho(be)][be] = b_be. Then
 //   C(x) = - sum_{al, a, be, b} conj(S[al a][be b]) a_al b_be S[pi(al) a][rho(be) b],
-// a sum of 144 products per Gamma. A CTA stages the 12 solutions of its 32
-// sites in shared memory once and evaluates every requested Gamma from there;
-// each CTA covers sites of one time slice and writes one partial per Gamma,
-// summed per slice in a fixed order.
+// a sum of 144 products per Gamma. The requested Gammas fall into a few classes
+// of equal permutations (pi, rho) (three for the sixteen of the chiral basis: the
+// identity for 1 and g5, and two pairings for g_x, g_y / g_z, g_t and their g5
+// partners), so per class and site the "spin Gram" entries
+//   G[al][be] = sum_{a, b} conj(S[al a][be b]) S[pi(al) a][rho(be) b]
+// are formed once and each Gamma is C(x) = - sum a_al b_be G[al][be]. A CTA stages
+// the 12 solutions of its 32 sites in shared memory; four threads per site (one
+// per source spin be) form G[.][be] for every class. Each CTA covers sites of one
+// time slice and writes one partial per Gamma; a second kernel sums the partials
+// of each slice in a fixed order.
 #include <array>
 #include <complex>
 #include <cstring>
@@ -33,6 +39,9 @@ struct Monomial {  // one non-zero per row: M[r][col[r]] = (re[r], im[r])
 };
 struct GammaTab {
   Monomial A[MAXG], Bt[MAXG];  // A = g5 Gamma (by rows), B^T = (Gamma g5)^T (by columns of B)
+  int cls[MAXG];               // permutation class of each Gamma
+  int pi[MAXG][4], rho[MAXG][4];  // permutations of each class
+  int nclass;
 };
 
 __constant__ GammaTab c_gamma;
@@ -93,72 +102,102 @@ bool monomial_rows(const M4& m, Monomial& out) {
   return true;
 }
 
+constexpr int CTHREADS = 4 * CSITES;  // four threads (source spins) per site
+
 // S[j][src][comp]: comp = device real pair index (colour-major: (a * 4 + al))
-__global__ void __launch_bounds__(CSITES) k_meson(const double2* const* props, Geom g, int ngam,
-                                                  int tiles_per_slice, double* partials) {
+__global__ void __launch_bounds__(CTHREADS) k_meson(const double2* const* props, Geom g, int ngam,
+                                                    int tiles_per_slice, double* partials) {
   extern __shared__ double2 sm[];  // [CSITES][12 sources][12 components]
+  __shared__ double red[CTHREADS / 32][2 * MAXG];
   const int S3 = g.L[0] * g.L[1] * g.L[2];
   const int t = blockIdx.x / tiles_per_slice;
   const int k = blockIdx.x % tiles_per_slice;
-  const int j = threadIdx.x;
-  const int s3 = k * CSITES + j;
-  const bool active = s3 < S3;
-  double2* my = sm + (size_t)j * 144;
-  if (active) {
+  // staging: thread i loads components of site i % CSITES
+  for (int i = threadIdx.x; i < CSITES * 12; i += CTHREADS) {
+    const int j = i % CSITES, src = i / CSITES;
+    const int s3 = k * CSITES + j;
+    if (s3 >= S3) continue;
     const long long s = (long long)t * S3 + s3;
     const int x = (int)(s % g.L[0]);
     const long long r = s / g.L[0];
     const int y = (int)(r % g.L[1]), z = (int)((r / g.L[1]) % g.L[2]);
     const int par = (x + y + z + t) & 1;
     const int h = (int)(s >> 1);
-    for (int src = 0; src < 12; ++src) {
-      const double2* base = props[2 * src + par];
+    const double2* base = props[2 * src + par];
+    double2* my = sm + (size_t)j * 144 + src * 12;
 #pragma unroll
-      for (int c = 0; c < 12; ++c) my[src * 12 + c] = base[(size_t)c * g.Vh + h];
-    }
+    for (int c = 0; c < 12; ++c) my[c] = base[(size_t)c * g.Vh + h];
   }
-  for (int gi = 0; gi < ngam; ++gi) {
-    double cr = 0.0, ci = 0.0;
-    if (active) {
-      const Monomial& A = c_gamma.A[gi];
-      const Monomial& Bt = c_gamma.Bt[gi];
-      for (int be = 0; be < 4; ++be) {
-        const int rb = Bt.col[be];  // B[rb][be] != 0
-        const double br = Bt.re[be], bi = Bt.im[be];
+  __syncthreads();
+  const int j = threadIdx.x % CSITES, be = threadIdx.x / CSITES;
+  const bool active = k * CSITES + j < S3;
+  const double2* my = sm + (size_t)j * 144;
+  double acc[2 * MAXG];
+#pragma unroll
+  for (int q = 0; q < 2 * MAXG; ++q) acc[q] = 0.0;
+  if (active) {
+    for (int cl = 0; cl < c_gamma.nclass; ++cl) {
+      const int rb = c_gamma.rho[cl][be];
+      double gr[4], gi[4];
+#pragma unroll
+      for (int al = 0; al < 4; ++al) {
+        const int pa = c_gamma.pi[cl][al];
+        double sr = 0.0, si = 0.0;
+#pragma unroll
         for (int b = 0; b < 3; ++b) {
           const double2* c1 = my + (3 * be + b) * 12;
           const double2* c2 = my + (3 * rb + b) * 12;
-          double sr = 0.0, si = 0.0;
 #pragma unroll
-          for (int al = 0; al < 4; ++al) {
-            const int pa = A.col[al];
-            const double ar = A.re[al], ai = A.im[al];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              const double2 u = c1[a * 4 + al];  // S[al a][be b]
-              const double2 v = c2[a * 4 + pa];  // S[pi(al) a][rb b]
-              // conj(u) * (ar + i ai) * v
-              const double wr = ar * v.x - ai * v.y, wi = ar * v.y + ai * v.x;
-              sr += u.x * wr + u.y * wi;
-              si += u.x * wi - u.y * wr;
-            }
+          for (int a = 0; a < 3; ++a) {
+            const double2 u = c1[a * 4 + al];  // S[al a][be b]
+            const double2 v = c2[a * 4 + pa];  // S[pi(al) a][rho(be) b]
+            sr += u.x * v.x + u.y * v.y;       // conj(u) v
+            si += u.x * v.y - u.y * v.x;
           }
-          cr += br * sr - bi * si;
-          ci += br * si + bi * sr;
         }
+        gr[al] = sr;
+        gi[al] = si;
+      }
+      for (int gm = 0; gm < ngam; ++gm) {
+        if (c_gamma.cls[gm] != cl) continue;
+        const Monomial& A = c_gamma.A[gm];
+        const double br = c_gamma.Bt[gm].re[be], bi = c_gamma.Bt[gm].im[be];
+        double cr = 0.0, ci = 0.0;
+#pragma unroll
+        for (int al = 0; al < 4; ++al) {  // a_al G[al][be]
+          cr += A.re[al] * gr[al] - A.im[al] * gi[al];
+          ci += A.re[al] * gi[al] + A.im[al] * gr[al];
+        }
+        acc[2 * gm] += br * cr - bi * ci;  // times b_be
+        acc[2 * gm + 1] += br * ci + bi * cr;
       }
     }
-    // fixed-order warp sum
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      cr += __shfl_down_sync(0xffffffffu, cr, o);
-      ci += __shfl_down_sync(0xffffffffu, ci, o);
-    }
-    if (j == 0) {
-      partials[((size_t)blockIdx.x * ngam + gi) * 2] = -cr;
-      partials[((size_t)blockIdx.x * ngam + gi) * 2 + 1] = -ci;
-    }
   }
+  // fixed-order reduction: warp shuffles, then the warps in order
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int q = 0; q < 2 * ngam; ++q) {
+    double v = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wid][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * ngam) {
+    double v = 0.0;
+    for (int w = 0; w < CTHREADS / 32; ++w) v += red[w][threadIdx.x];
+    partials[(size_t)blockIdx.x * 2 * ngam + threadIdx.x] = -v;
+  }
+}
+
+// corr[gm][t] = sum over the tiles of slice t of the partials, in tile order
+__global__ void k_meson_slices(const double* partials, int ngam, int tiles_per_slice, int lt, double* corr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // (gm, t, re/im)
+  if (i >= 2 * ngam * lt) return;
+  const int q = i % (2 * ngam), t = i / (2 * ngam);
+  double v = 0.0;
+  for (int k = 0; k < tiles_per_slice; ++k) v += partials[((size_t)t * tiles_per_slice + k) * 2 * ngam + q];
+  const int gm = q / 2, ri = q % 2;
+  corr[((size_t)gm * lt + t) * 2 + ri] = v;
 }
 
 }  // namespace
@@ -191,6 +230,17 @@ extern "C" int lqcd_meson_correlator(const lqcd_field* const* props, int ngamma,
       for (int c = 0; c < 4; ++c) Bt[c][r] = B[r][c];
     if (!monomial_rows(A, tab.A[i]) || !monomial_rows(Bt, tab.Bt[i]))
       return set_error(LQCD_EINVAL, "gamma code %d is not monomial", gammas[i]);
+    // permutation class: pi from the rows of A, rho from the columns of B
+    int cl = 0;
+    for (; cl < tab.nclass; ++cl)
+      if (!memcmp(tab.pi[cl], tab.A[i].col, sizeof tab.pi[cl]) && !memcmp(tab.rho[cl], tab.Bt[i].col, sizeof tab.rho[cl]))
+        break;
+    if (cl == tab.nclass) {
+      memcpy(tab.pi[cl], tab.A[i].col, sizeof tab.pi[cl]);
+      memcpy(tab.rho[cl], tab.Bt[i].col, sizeof tab.rho[cl]);
+      ++tab.nclass;
+    }
+    tab.cls[i] = cl;
   }
   lqcd_ctx* c = f0->ctx;
   LQCD_CK(cudaSetDevice(c->device));
@@ -203,29 +253,22 @@ extern "C" int lqcd_meson_correlator(const lqcd_field* const* props, int ngamma,
   for (int i = 0; i < 12; ++i)
     for (int p = 0; p < 2; ++p) hp[2 * i + p] = static_cast<const double2*>(props[i]->half[p]);
   LQCD_CK(cudaMemcpyToSymbolAsync(c_gamma, &tab, sizeof tab, 0, cudaMemcpyHostToDevice, c->stream));
-  int rc = ctx_staging(c, npart * sizeof(double) + 24 * sizeof(void*) + 256);
+  const size_t ncorr = (size_t)2 * ngamma * g.L[3];
+  const size_t nd = ((npart + ncorr + 31) / 32) * 32;
+  int rc = ctx_staging(c, nd * sizeof(double) + 24 * sizeof(void*) + 256);
   if (rc != LQCD_OK) return rc;
   double* d_part = c->staging;
-  const double2** d_props = reinterpret_cast<const double2**>(d_part + ((npart + 31) / 32) * 32);
+  const double2** d_props = reinterpret_cast<const double2**>(d_part + nd);
   LQCD_CK(cudaMemcpyAsync(d_props, hp.data(), 24 * sizeof(void*), cudaMemcpyHostToDevice, c->stream));
   const size_t smem = (size_t)CSITES * 144 * sizeof(double2);
   LQCD_CK(cudaFuncSetAttribute(k_meson, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_meson<<<nblk, CSITES, smem, c->stream>>>(d_props, g, ngamma, tps, d_part);
+  double* d_corr = d_part + npart;  // ngamma x Lt complex, after the partials
+  k_meson<<<nblk, CTHREADS, smem, c->stream>>>(d_props, g, ngamma, tps, d_part);
+  const int nout = 2 * ngamma * g.L[3];
+  k_meson_slices<<<(nout + 127) / 128, 128, 0, c->stream>>>(d_part, ngamma, tps, g.L[3], d_corr);
   LQCD_CK(cudaGetLastError());
-  c->launches++;
-  std::vector<double> part(npart);
-  LQCD_CK(cudaMemcpyAsync(part.data(), d_part, npart * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  c->launches += 2;
+  LQCD_CK(cudaMemcpyAsync(host_corr, d_corr, (size_t)nout * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   LQCD_CK(cudaStreamSynchronize(c->stream));
-  for (int gi = 0; gi < ngamma; ++gi)
-    for (int t = 0; t < g.L[3]; ++t) {
-      double re = 0, im = 0;
-      for (int k = 0; k < tps; ++k) {
-        const size_t b = (size_t)(t * tps + k);
-        re += part[(b * ngamma + gi) * 2];
-        im += part[(b * ngamma + gi) * 2 + 1];
-      }
-      host_corr[((size_t)gi * g.L[3] + t) * 2] = re;
-      host_corr[((size_t)gi * g.L[3] + t) * 2 + 1] = im;
-    }
   return LQCD_OK;
 }

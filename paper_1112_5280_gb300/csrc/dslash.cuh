@@ -150,9 +150,13 @@ __device__ __forceinline__ const char* link_dir(const void* base, int Vh, int mu
 #ifndef LQCD_DSLASH_DEPTH
 #define LQCD_DSLASH_DEPTH 3
 #endif
+#ifndef LQCD_DSLASH_DEPTH_HALF
+#define LQCD_DSLASH_DEPTH_HALF LQCD_DSLASH_DEPTH
+#endif
 template <int SP>
 struct DslashDepth {
-  static constexpr int value = (SP == P_DF64) ? 1 : LQCD_DSLASH_DEPTH;
+  static constexpr int value =
+      (SP == P_DF64) ? 1 : ((SP == P_F16 || SP == P_BF16) ? LQCD_DSLASH_DEPTH_HALF : LQCD_DSLASH_DEPTH);
 };
 
 template <int SP, int LP, int NR>

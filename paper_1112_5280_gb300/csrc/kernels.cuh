@@ -22,10 +22,16 @@ struct EpiTraits {
 #ifndef LQCD_DSLASH_MIN_BLOCKS
 #define LQCD_DSLASH_MIN_BLOCKS 6
 #endif
+// FP16 / BF16 spinors: the same bytes in flight come from half the words, so the half
+// precisions may take a different occupancy target.
+#ifndef LQCD_DSLASH_MIN_BLOCKS_HALF
+#define LQCD_DSLASH_MIN_BLOCKS_HALF LQCD_DSLASH_MIN_BLOCKS
+#endif
 // Double-float needs the full 255 registers per thread (4 CTAs of 64 threads).
 template <int SP>
 struct DslashMinBlocks {
-  static constexpr int value = (SP == P_DF64) ? 4 : LQCD_DSLASH_MIN_BLOCKS;
+  static constexpr int value =
+      (SP == P_DF64) ? 4 : ((SP == P_F16 || SP == P_BF16) ? LQCD_DSLASH_MIN_BLOCKS_HALF : LQCD_DSLASH_MIN_BLOCKS);
 };
 
 template <typename R>
