@@ -479,7 +479,8 @@ def run_solve_section(ctx, lqcd, inputs, world):
             ms.append((time.perf_counter() - t0) * 1e3)
             infos.append(info)
         st = _lat_stats(ms)
-        st.update(iters=infos[-1]["iters"], reliable_updates=infos[-1]["reliable_updates"],
+        st.update(ms_each=[round(v, 2) for v in ms], iters=infos[-1]["iters"],
+                  reliable_updates=infos[-1]["reliable_updates"],
                   true_resid=max(i["true_resid"] for i in infos),
                   converged=all(i["status"] == 0 for i in infos))
         out[name] = st
@@ -771,7 +772,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (no autotuner)")
     ap.add_argument("--no-variants", action="store_true", help="skip the one-application-per-launch timings")
     ap.add_argument("--dslash-only", action="store_true", help="skip the solver, multi-RHS, multi-lattice and serving sections")
-    ap.add_argument("--section", choices=["heatbath", "hmc", "dslash32"],
+    ap.add_argument("--section", choices=["heatbath", "hmc", "dslash32", "solve"],
                     help="run one section alone and print its JSON (profiling); no contract line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -789,9 +790,15 @@ def run_one_section(args, world, rank, local):
     dev = local if world > 1 else 0
     torch.cuda.set_device(dev)
     ctx = lqcd.Context(dev, torch.cuda.Stream(device=dev))
-    fn = {"heatbath": run_heatbath_section, "hmc": run_hmc_section,
-          "dslash32": run_dslash32_section}[args.section]
-    res = fn(ctx, lqcd, world)
+    if args.section == "solve":
+        from paper_1112_5280_gb300 import synth
+        inputs = {"solve": (synth.random_links(SOLVE_DIMS, SOLVE_EPS, seed=synth.SEED_LINKS),
+                            synth.gaussian_spinor(SOLVE_DIMS, seed=synth.SEED_SOURCE))}
+        res = run_solve_section(ctx, lqcd, inputs, world)
+    else:
+        fn = {"heatbath": run_heatbath_section, "hmc": run_hmc_section,
+              "dslash32": run_dslash32_section}[args.section]
+        res = fn(ctx, lqcd, world)
     if rank == 0:
         print(json.dumps({"section": args.section, **res}))
     ctx.close()
