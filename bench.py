@@ -606,7 +606,7 @@ def run_heatbath_section(ctx, lqcd, world):
     return res
 
 
-HMC_DIMS, HMC_BETA, HMC_KAPPA, HMC_MU = (16, 16, 16, 32), 5.6, 0.15, 0.01
+HMC_DIMS, HMC_BETA, HMC_KAPPA, HMC_MU = (16, 16, 16, 32), 5.6, 0.14, 0.01
 
 
 def run_dslash32_section(ctx, lqcd, world, U=None):

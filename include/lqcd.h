@@ -334,7 +334,8 @@ typedef struct lqcd_hmc_info {
 
 LQCD_API void lqcd_hmc_params_default(lqcd_hmc_params* p);
 /* One molecular-dynamics trajectory from (g, m) with pseudofermion phi (FULL FP64, even half
- * used; S_f at the start = phi^dag (Mhat^dag Mhat)^-1 phi). Updates g and m in place. The
+ * used; S_f at the start = phi^dag (Mhat^dag Mhat)^-1 phi, evaluated from each force solve's X
+ * as 2 Re <phi, X> - |Mhat X|^2, whose error is quadratic in the solve's). Updates g and m in place. The
  * gauge force runs ngauge inner steps per outer step; kicks at the same links are merged,
  * so a trajectory takes nsteps + 1 fermion solves (leapfrog) or 2 nsteps + 1 (2MN). With
  * accept_u > 0 the links are restored when accept_u > exp(-dH). opts: the solver (CG;

@@ -272,15 +272,16 @@ int gauge_force_impl(const lqcd_gauge* g, double beta, double coeff, lqcd_mom* m
   return LQCD_OK;
 }
 
-// |half|^2 of an FP64 half field, synchronous
-int half_norm2(lqcd_ctx* c, const void* half, const Geom& g, double* out) {
+// |half|^2 (other == NULL) or Re <half, other> of FP64 half fields, synchronous
+int half_norm2(lqcd_ctx* c, const void* half, const Geom& g, double* out, const void* other = nullptr) {
   LQCD_TRY(ctx_partials(c, 3 * (size_t)((g.Vh + TILE - 1) / TILE)));
   Work w = blank_work(g);
   w.sc = c->scratch_sc;
   w.in = half;
+  w.y1 = other;
   w.red = 1;
   w.fin = FIN_STORE0;
-  LQCD_CK(launch_blas(P_F64, B_NORM, single_launch(w, c->partials), 0, c->stream));
+  LQCD_CK(launch_blas(P_F64, other ? B_RDOT : B_NORM, single_launch(w, c->partials), 0, c->stream));
   c->launches++;
   LQCD_CK(cudaMemcpyAsync(c->host_sc, c->scratch_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
   LQCD_CK(cudaStreamSynchronize(c->stream));
@@ -288,14 +289,21 @@ int half_norm2(lqcd_ctx* c, const void* half, const Geom& g, double* out) {
   return LQCD_OK;
 }
 
-// From X (even half of x, FP64): Y = Mhat X, the odd halves of Phi and Psi, S_f = |Y|^2 and
+// From X (even half of x, FP64): Y = Mhat X, the odd halves of Phi and Psi, S_f and
 // P += coeff G_f. x and y are FULL FP64 fields (their odd halves are overwritten).
+// S_f: with phi, the variational 2 Re <phi, X> - |Y|^2, whose error is quadratic in the
+// solve's (X = X* - e gives S* - |Mhat e|^2); without, |Y|^2 = phi^dag X (linear error).
 int fermion_force_from_x(const lqcd_gauge* g, double kappa, double mu, lqcd_field* x, lqcd_field* y,
-                         double coeff, lqcd_mom* m, double* s_f) {
+                         double coeff, lqcd_mom* m, double* s_f, const lqcd_field* phi = nullptr) {
   const double a = 2.0 * kappa * mu, s = 1.0 / (1.0 + a * a);
   LQCD_TRY(lqcd_apply_Mhat_tm(g, kappa, mu, x, y, 0));
   double yy = 0.0;
   LQCD_TRY(half_norm2(g->ctx, y->half[0], g->g, &yy));
+  if (phi) {
+    double px = 0.0;
+    LQCD_TRY(half_norm2(g->ctx, x->half[0], g->g, &px, phi->half[0]));
+    yy = 2.0 * px - yy;
+  }
   if (s_f) *s_f = yy;
   // Phi_o = A^-1 D_oe X_e, Psi_o = A^-dag (D^dag)_oe Y_e
   LQCD_TRY(dslash_tw(g, P_F64, x->half[0], x->half[1], nullptr, nullptr, 1.0, 0.0, 0.0, 1, false, s, -a, 0.0));
@@ -551,7 +559,7 @@ int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m, co
       LQCD_TRY(solve_normal_with(e, g, phi, p->kappa, p->mu, p->tol, x, &si));
       solves_iters += si.iters;
       double s = 0.0;
-      LQCD_TRY(fermion_force_from_x(g, p->kappa, p->mu, x, y, -pend_f, m, &s));
+      LQCD_TRY(fermion_force_from_x(g, p->kappa, p->mu, x, y, -pend_f, m, &s, phi));
       if (first_f) sf0 = s;
       first_f = false;
       sf1 = s;

@@ -300,6 +300,7 @@ enum Blas {
   B_TWIST,        // out = tw_s (1 + i tw_t g5) in
   B_RU_SCALE,     // out (SP) = in (TP) * res[2]
   B_RU_P,         // p(z) = restart ? r(in) : r + res[4] p
+  B_RDOT,         // Re <in, y1>
 };
 
 // out = x + c * y (complex c)
@@ -391,6 +392,14 @@ __global__ void __launch_bounds__(TILE) k_blas(const Launch L) {
           for (int i = 0; i < 24; ++i) p[i] = r[i] + pc * p[i];
         }
         SpinorIO<SP>::store(w.z, Vh, h, p);
+      } else if (OP == B_RDOT) {
+        R a[24], b[24];
+        SpinorIO<SP>::load(w.in, Vh, h, a);
+        SpinorIO<SP>::load(w.y1, Vh, h, b);
+        R acc = 0;
+#pragma unroll
+        for (int i = 0; i < 24; ++i) acc += a[i] * b[i];
+        v0 = (double)acc;
       } else if (OP == B_NORM) {
         R v[24];
         SpinorIO<SP>::load(w.in, Vh, h, v);

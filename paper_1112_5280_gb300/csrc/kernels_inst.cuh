@@ -159,6 +159,7 @@ cudaError_t LQCD_CAT(launch_blas_, LQCD_SFX)(int op, int tp, const Launch& L, in
     case B_ZERO: return go_blas<B_ZERO, SPX>(L, grid, s);
     case B_TWIST: return go_blas<B_TWIST, SPX>(L, grid, s);
     case B_RU_P: return go_blas<B_RU_P, SPX>(L, grid, s);
+    case B_RDOT: return go_blas<B_RDOT, SPX>(L, grid, s);
     case B_RU_SCALE:
       return df ? go_blas<B_RU_SCALE, SPX, P_DF64>(L, grid, s) : go_blas<B_RU_SCALE, SPX, P_F64>(L, grid, s);
     case B_BICG_P: return go_blas<B_BICG_P, SPX>(L, grid, s);
