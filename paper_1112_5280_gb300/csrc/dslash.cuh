@@ -15,6 +15,8 @@
 // two colour vectors by the link, and rebuilds the lower spin components.
 #pragma once
 
+#include <type_traits>
+
 #include "field.cuh"
 
 namespace lqcd {
@@ -276,48 +278,104 @@ __device__ __forceinline__ void link_row18(const void* base_mu, int Vh, int h, R
   }
 }
 
-// acc (spin s: acc[2 s], acc[2 s + 1]) += eta (1 + S g_MU) x (row) h for one colour
-template <int MU, int S, typename R>
-__device__ __forceinline__ void hop3(const R psi[24], const R r[6], int eta, R acc[8]) {
-  Cx<R> h0[3], h1[3];
+// Double-float form of hop3 below: projections and the row products summed with the
+// unnormalised double-float operations (df_add_u, df_mac_u); acc stays unnormalised
+// across the hops and is normalised once by dslash_site3.
+template <int MU, int S>
+__device__ __forceinline__ void hop3_df(const df64 psi[24], const df64 r[6], int eta, df64 acc[8]) {
+  Cx<df64> h0[3], h1[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const Cx<R> p0 = sp(psi, 0, c), p1 = sp(psi, 1, c), p2 = sp(psi, 2, c), p3 = sp(psi, 3, c);
+    const Cx<df64> p0 = sp(psi, 0, c), p1 = sp(psi, 1, c), p2 = sp(psi, 2, c), p3 = sp(psi, 3, c);
     if (MU == 0) {
-      h0[c] = {p0.re + S * p3.im, p0.im - S * p3.re};
-      h1[c] = {p1.re + S * p2.im, p1.im - S * p2.re};
+      h0[c] = {df_add_u(p0.re, S * p3.im), df_add_u(p0.im, S * -p3.re)};
+      h1[c] = {df_add_u(p1.re, S * p2.im), df_add_u(p1.im, S * -p2.re)};
     } else if (MU == 1) {
-      h0[c] = {p0.re - S * p3.re, p0.im - S * p3.im};
-      h1[c] = {p1.re + S * p2.re, p1.im + S * p2.im};
+      h0[c] = {df_add_u(p0.re, S * -p3.re), df_add_u(p0.im, S * -p3.im)};
+      h1[c] = {df_add_u(p1.re, S * p2.re), df_add_u(p1.im, S * p2.im)};
     } else if (MU == 2) {
-      h0[c] = {p0.re + S * p2.im, p0.im - S * p2.re};
-      h1[c] = {p1.re - S * p3.im, p1.im + S * p3.re};
+      h0[c] = {df_add_u(p0.re, S * p2.im), df_add_u(p0.im, S * -p2.re)};
+      h1[c] = {df_add_u(p1.re, S * -p3.im), df_add_u(p1.im, S * p3.re)};
     } else {
-      h0[c] = {p0.re + S * p2.re, p0.im + S * p2.im};
-      h1[c] = {p1.re + S * p3.re, p1.im + S * p3.im};
+      h0[c] = {df_add_u(p0.re, S * p2.re), df_add_u(p0.im, S * p2.im)};
+      h1[c] = {df_add_u(p1.re, S * p3.re), df_add_u(p1.im, S * p3.im)};
     }
   }
-  Cx<R> w0 = cmul(Cx<R>{r[0], r[1]}, h0[0]), w1 = cmul(Cx<R>{r[0], r[1]}, h1[0]);
+  // w = row . h: re = sum (r.re h.re - r.im h.im), im = sum (r.re h.im + r.im h.re)
+  Cx<df64> w0{df64(0.0f, 0.0f), df64(0.0f, 0.0f)}, w1 = w0;
 #pragma unroll
-  for (int b = 1; b < 3; ++b) {
-    const Cx<R> rb{r[2 * b], r[2 * b + 1]};
-    const Cx<R> m0 = cmul(rb, h0[b]), m1 = cmul(rb, h1[b]);
-    w0.re += m0.re; w0.im += m0.im;
-    w1.re += m1.re; w1.im += m1.im;
+  for (int b = 0; b < 3; ++b) {
+    const df64 rr = r[2 * b], ri = r[2 * b + 1];
+    df_mac_u(w0.re, rr, h0[b].re);
+    df_mac_u(w0.re, -ri, h0[b].im);
+    df_mac_u(w0.im, rr, h0[b].im);
+    df_mac_u(w0.im, ri, h0[b].re);
+    df_mac_u(w1.re, rr, h1[b].re);
+    df_mac_u(w1.re, -ri, h1[b].im);
+    df_mac_u(w1.im, rr, h1[b].im);
+    df_mac_u(w1.im, ri, h1[b].re);
   }
   if (MU == 3 && eta < 0) {
     w0 = sgn<-1>(w0);
     w1 = sgn<-1>(w1);
   }
-  acc[0] += w0.re; acc[1] += w0.im;
-  acc[2] += w1.re; acc[3] += w1.im;
-  Cx<R> l2, l3;
+  acc[0] = df_add_u(acc[0], w0.re); acc[1] = df_add_u(acc[1], w0.im);
+  acc[2] = df_add_u(acc[2], w1.re); acc[3] = df_add_u(acc[3], w1.im);
+  Cx<df64> l2, l3;
   if (MU == 0) { l2 = sgn<S>(mul_i(w1)); l3 = sgn<S>(mul_i(w0)); }
   else if (MU == 1) { l2 = sgn<S>(w1); l3 = sgn<-S>(w0); }
   else if (MU == 2) { l2 = sgn<S>(mul_i(w0)); l3 = sgn<-S>(mul_i(w1)); }
   else { l2 = sgn<S>(w0); l3 = sgn<S>(w1); }
-  acc[4] += l2.re; acc[5] += l2.im;
-  acc[6] += l3.re; acc[7] += l3.im;
+  acc[4] = df_add_u(acc[4], l2.re); acc[5] = df_add_u(acc[5], l2.im);
+  acc[6] = df_add_u(acc[6], l3.re); acc[7] = df_add_u(acc[7], l3.im);
+}
+
+// acc (spin s: acc[2 s], acc[2 s + 1]) += eta (1 + S g_MU) x (row) h for one colour
+template <int MU, int S, typename R>
+__device__ __forceinline__ void hop3(const R psi[24], const R r[6], int eta, R acc[8]) {
+  if constexpr (std::is_same<R, df64>::value) {
+    hop3_df<MU, S>(psi, r, eta, acc);
+  } else {
+    Cx<R> h0[3], h1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const Cx<R> p0 = sp(psi, 0, c), p1 = sp(psi, 1, c), p2 = sp(psi, 2, c), p3 = sp(psi, 3, c);
+      if (MU == 0) {
+        h0[c] = {p0.re + S * p3.im, p0.im - S * p3.re};
+        h1[c] = {p1.re + S * p2.im, p1.im - S * p2.re};
+      } else if (MU == 1) {
+        h0[c] = {p0.re - S * p3.re, p0.im - S * p3.im};
+        h1[c] = {p1.re + S * p2.re, p1.im + S * p2.im};
+      } else if (MU == 2) {
+        h0[c] = {p0.re + S * p2.im, p0.im - S * p2.re};
+        h1[c] = {p1.re - S * p3.im, p1.im + S * p3.re};
+      } else {
+        h0[c] = {p0.re + S * p2.re, p0.im + S * p2.im};
+        h1[c] = {p1.re + S * p3.re, p1.im + S * p3.im};
+      }
+    }
+    Cx<R> w0 = cmul(Cx<R>{r[0], r[1]}, h0[0]), w1 = cmul(Cx<R>{r[0], r[1]}, h1[0]);
+#pragma unroll
+    for (int b = 1; b < 3; ++b) {
+      const Cx<R> rb{r[2 * b], r[2 * b + 1]};
+      const Cx<R> m0 = cmul(rb, h0[b]), m1 = cmul(rb, h1[b]);
+      w0.re += m0.re; w0.im += m0.im;
+      w1.re += m1.re; w1.im += m1.im;
+    }
+    if (MU == 3 && eta < 0) {
+      w0 = sgn<-1>(w0);
+      w1 = sgn<-1>(w1);
+    }
+    acc[0] += w0.re; acc[1] += w0.im;
+    acc[2] += w1.re; acc[3] += w1.im;
+    Cx<R> l2, l3;
+    if (MU == 0) { l2 = sgn<S>(mul_i(w1)); l3 = sgn<S>(mul_i(w0)); }
+    else if (MU == 1) { l2 = sgn<S>(w1); l3 = sgn<-S>(w0); }
+    else if (MU == 2) { l2 = sgn<S>(mul_i(w0)); l3 = sgn<-S>(mul_i(w1)); }
+    else { l2 = sgn<S>(w0); l3 = sgn<S>(w1); }
+    acc[4] += l2.re; acc[5] += l2.im;
+    acc[6] += l3.re; acc[7] += l3.im;
+  }
 }
 
 template <int K, int SP, int LP, bool DAG, int COL>
@@ -352,6 +410,10 @@ __device__ __forceinline__ void dslash_site3(const Geom& g, int h, int out_par, 
   hop3_k<5, SP, LP, DAG, COL>(g, h, nf, nb, t, in, Uout, Uin, acc);
   hop3_k<6, SP, LP, DAG, COL>(g, h, nf, nb, t, in, Uout, Uin, acc);
   hop3_k<7, SP, LP, DAG, COL>(g, h, nf, nb, t, in, Uout, Uin, acc);
+  if constexpr (std::is_same<typename SpinorIO<SP>::Real, df64>::value) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = df_norm(acc[i]);
+  }
 }
 
 }  // namespace lqcd

@@ -82,6 +82,33 @@ __device__ __forceinline__ df64 operator*(int s, df64 a) {
 }
 __device__ __forceinline__ bool isfinite_df(df64 a) { return isfinite(a.hi); }
 
+// Double-float sums left unnormalised inside a site's hop sums: the pair (hi, lo) still
+// carries the exact sum of what went in, but |lo| may exceed ulp(hi) / 2 until df_norm.
+// An add is a two-sum of the high words plus the low words (8 operations instead of 11);
+// a multiply-accumulate feeds the exact product error into the low word (12 instead of
+// 7 + 11). The low word only collects rounding errors, so it stays far below hi.
+__device__ __forceinline__ df64 df_add_u(df64 a, df64 b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float v = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+  return df64(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ void df_mac_u(df64& acc, df64 a, df64 b) {  // acc += a b
+  const float p = __fmul_rn(a.hi, b.hi);
+  float pe = __fmaf_rn(a.hi, b.hi, -p);
+  pe = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, pe));
+  const float s = __fadd_rn(acc.hi, p);
+  const float v = __fsub_rn(s, acc.hi);
+  const float e = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, v)), __fsub_rn(p, v));
+  acc = df64(s, __fadd_rn(acc.lo, __fadd_rn(e, pe)));
+}
+// normalised form of an unnormalised pair (two-sum of hi and lo)
+__device__ __forceinline__ df64 df_norm(df64 a) {
+  const float s = __fadd_rn(a.hi, a.lo);
+  const float v = __fsub_rn(s, a.hi);
+  return df64(s, __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(a.lo, v)));
+}
+
 // Device order of the 24 reals of a spinor: colour-major, so that the 8 reals
 // (4 spin x re/im) of one colour are contiguous words:
 //   real(spin, colour, re/im) = (colour * 4 + spin) * 2 + re/im

@@ -181,14 +181,10 @@ __global__ void k_expm_update(double2* U, Geom g, const double2* P, double eps) 
     A.e[w] = {p.x * eps, p.y * eps};
     u.e[w] = {l.x, l.y};
   }
-  double nrm = 0.0;  // infinity norm
+  double nrm = 0.0;  // Frobenius norm (submultiplicative, so it bounds the Taylor tail)
 #pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    double row = 0.0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) row += hypot(A.e[r * 3 + k].re, A.e[r * 3 + k].im);
-    nrm = fmax(nrm, row);
-  }
+  for (int w = 0; w < 9; ++w) nrm += A.e[w].re * A.e[w].re + A.e[w].im * A.e[w].im;
+  nrm = sqrt(nrm);
   int sq = 0;
   while (nrm > 0.5 && sq < 60) {
     nrm *= 0.5;
