@@ -146,3 +146,39 @@ def test_bad_hmc_arguments(ctx):
             lqcd.hmc_trajectory(g, lqcd.hmc_params(**kw), m, f)
     with pytest.raises(lqcd.LqcdError):
         lqcd.hmc_trajectory(g, lqcd.hmc_params(), m, ctx.field(dims, "f32", lqcd.FULL))
+
+
+def test_engine_mixes_normal_and_plain_requests(ctx):
+    """Normal-equation and M x = b requests (Wilson and twisted) share one engine, each on its
+    own reliable-update path, and each result equals its solo solve bit for bit."""
+    opts = lqcd.solve_opts(sloppy_prec="f32")
+    eng = lqcd.Engine(ctx, opts, max_slots=8)
+    dims = (6, 4, 4, 6)
+    U = synth.random_links(dims, 0.5, seed=251)
+    g = ctx.gauge(dims, U)
+    ev = _even(dims)
+    cases = [(True, 0.0, 252), (False, 0.0, 253), (True, 0.1, 254), (False, 0.1, 255)]
+    items = []
+    for normal, mu, seed in cases:
+        b = synth.gaussian_spinor(dims, seed=seed)
+        if normal:
+            b = b * ev
+        src = ctx.field(dims, "f64", lqcd.FULL, data=b)
+        items.append((eng.submit(g, src, 0.14, 1e-11, mu=mu, normal=normal), normal, mu, b, src))
+    while eng.step() > 0:
+        pass
+    for rid, normal, mu, b, src in items:
+        x = ctx.field(dims, "f64", lqcd.FULL)
+        info = eng.result(rid, x)
+        assert info["status"] == 0, (normal, mu, info)
+        xm = x.download()
+        solo = ctx.field(dims, "f64", lqcd.FULL)
+        o = lqcd.solve_opts(sloppy_prec="f32", mu=mu)
+        if normal:
+            lqcd.solve_normal(g, src, 0.14, 1e-11, solo, o)
+            Xo, _ = ohmc.solve_normal(dims, U, 0.14, mu, b, tol=1e-14)
+            assert np.linalg.norm(xm - Xo) / np.linalg.norm(Xo) < 1e-7
+        else:
+            lqcd.solve_fields(g, src, 0.14, 1e-11, solo, o)
+        assert np.array_equal(solo.download(), xm), (normal, mu)
+    eng.close()
