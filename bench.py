@@ -619,10 +619,10 @@ def run_dslash32_section(ctx, lqcd, world, U=None):
         U = synth.random_links(d, SOLVE_EPS, seed=synth.SEED_LINKS)
     Vh = synth.volume(d) // 2
     psi = synth.gaussian_spinor(d, seed=synth.SEED_SOURCE)
-    out = {"workload": "32^3x64 even-odd Dslash, 12-real links, one application per launch"}
+    out = {"workload": "32^3x64 even-odd Dslash, 12- and 18-real links, one application per launch"}
     peak, _ = measured_peaks()
-    for prec, nb in (("f16", 2), ("f32", 4)):
-        g = ctx.gauge(d, U, prec=prec, compress=12)
+    for prec, nb, nr in (("f16", 2, 12), ("f32", 4, 12), ("f16", 2, 18), ("f32", 4, 18)):
+        g = ctx.gauge(d, U, prec=prec, compress=nr)
         fi = ctx.field(d, prec, lqcd.ODD, data=psi)
         fo = ctx.field(d, prec, lqcd.EVEN)
         lqcd.dslash_eo(g, fi, fo, 0)
@@ -643,9 +643,10 @@ def run_dslash32_section(ctx, lqcd, world, U=None):
             e1.record(st)
         torch.cuda.synchronize()
         us = e0.elapsed_time(e1) * 1e3 / n
-        gbs = algorithmic_bytes_per_site(nb, 12) * Vh / (us * 1e-6) / 1e9
-        out[prec] = {"us_per_application": us, "GBps": gbs, "frac_of_measured_hbm": gbs / peak,
-                     "bytes_per_site": algorithmic_bytes_per_site(nb, 12)}
+        gbs = algorithmic_bytes_per_site(nb, nr) * Vh / (us * 1e-6) / 1e9
+        out[prec if nr == 12 else f"{prec}_18"] = {
+            "us_per_application": us, "GBps": gbs, "frac_of_measured_hbm": gbs / peak,
+            "bytes_per_site": algorithmic_bytes_per_site(nb, nr)}
         del graph
         for o_ in (g, fi, fo):
             o_.close()

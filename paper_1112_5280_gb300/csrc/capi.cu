@@ -188,6 +188,7 @@ void ctx_release(lqcd_ctx* c) {
   if (c->refs.fetch_sub(1) != 1) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  ctx_drop_engine(c);
   if (c->partials) cudaFree(c->partials);
   if (c->scratch_sc) cudaFree(c->scratch_sc);
   if (c->host_sc) cudaFreeHost(c->host_sc);

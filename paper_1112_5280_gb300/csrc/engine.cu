@@ -102,6 +102,7 @@ using namespace lqcd;
 
 struct lqcd_engine {
   lqcd_ctx* ctx = nullptr;
+  bool holds_ctx = true;  // false for a context's cached engine
   lqcd_solve_opts opts{};
   int sp = P_F32, xp = P_F32, nr = 12;
   int tp = P_F64;  // FP64-class vectors and operator of the true residual: P_F64 or P_DF64
@@ -585,8 +586,9 @@ void lqcd_engine_destroy(lqcd_engine* e) {
   if (e->d_prefix) cudaFree(e->d_prefix);
   if (e->d_partials) cudaFree(e->d_partials);
   lqcd_ctx* c = e->ctx;
+  const bool release = e->holds_ctx;
   delete e;
-  ctx_release(c);
+  if (release) ctx_release(c);
 }
 
 size_t lqcd_engine_request_bytes(const lqcd_engine* e, const int dims[4]) {
@@ -866,6 +868,54 @@ int lqcd_engine_stats(const lqcd_engine* e, int* active, size_t* bytes) {
 
 // ------------------------------------------------------------------ one-shot solves
 
+}  // extern "C"
+
+namespace lqcd {
+
+static bool same_opts(const lqcd_solve_opts& a, const lqcd_solve_opts& b) {
+  return a.solver == b.solver && a.sloppy_prec == b.sloppy_prec && a.sloppy_compress == b.sloppy_compress &&
+         a.maxiter == b.maxiter && a.delta == b.delta && a.chunk == b.chunk && a.use_graph == b.use_graph &&
+         a.ru_interval == b.ru_interval && a.true_prec == b.true_prec;  // mu is per request
+}
+
+void ctx_drop_engine(lqcd_ctx* c) {
+  if (c->engine_cache) lqcd_engine_destroy(c->engine_cache);
+  c->engine_cache = nullptr;
+}
+
+int ctx_engine(lqcd_ctx* c, const lqcd_solve_opts& o, int n, lqcd_engine** out) {
+  lqcd_engine* e = c->engine_cache;
+  if (e && same_opts(c->engine_opts, o) && e->max_slots >= n && e->active.empty() && e->reqs.empty()) {
+    *out = e;
+    return LQCD_OK;
+  }
+  ctx_drop_engine(c);
+  int rc = lqcd_engine_create(c, &o, 0, std::max(n, 16), &e);
+  if (rc != LQCD_OK) return rc;
+  e->holds_ctx = false;  // the context owns this engine
+  ctx_release(c);        // undo the reference lqcd_engine_create took
+  c->engine_cache = e;
+  c->engine_opts = o;
+  *out = e;
+  return LQCD_OK;
+}
+
+void engine_trim_pool(lqcd_engine* e, size_t keep_bytes) {
+  if (e->bytes_pooled <= keep_bytes) return;
+  cudaStreamSynchronize(e->ctx->stream);
+  // free the smallest blocks first; the largest (most recent lattice) usually stays
+  while (e->bytes_pooled > keep_bytes && !e->pool.empty()) {
+    auto it = e->pool.begin();
+    cudaFree(it->second);
+    e->bytes_pooled -= it->first;
+    e->pool.erase(it);
+  }
+}
+
+}  // namespace lqcd
+
+extern "C" {
+
 static int run_engine(lqcd_engine* e, int n, const long long* ids, lqcd_field* const* xs,
                       lqcd_solve_info* infos) {
   int active = n;
@@ -910,13 +960,21 @@ int lqcd_solve_multi(const lqcd_gauge* g, int n, const lqcd_field* const* srcs, 
     return first_bad;
   }
   lqcd_engine* e = nullptr;
-  int rc = lqcd_engine_create(g->ctx, &o, 0, n, &e);
+  int rc = ctx_engine(g->ctx, o, n, &e);
   if (rc != LQCD_OK) return rc;
   std::vector<long long> ids(n);
-  for (int i = 0; i < n && rc == LQCD_OK; ++i)
+  int submitted = 0;
+  for (int i = 0; i < n && rc == LQCD_OK; ++i) {
     rc = lqcd_engine_submit_tm(e, g, srcs[i], kappa, o.mu, tol, &ids[i]);
+    if (rc == LQCD_OK) ++submitted;
+  }
   if (rc == LQCD_OK) rc = run_engine(e, n, ids.data(), xs, infos);
-  lqcd_engine_destroy(e);
+  if (rc != LQCD_OK && !(rc == LQCD_ENOCONV || rc == LQCD_EBREAKDOWN || rc == LQCD_ENONFINITE)) {
+    ctx_drop_engine(g->ctx);  // a failed submit or launch may leave requests behind
+  } else {
+    engine_trim_pool(e, (size_t)8 << 30);
+  }
+  (void)submitted;
   if (infos && rc != LQCD_ECUDA && rc != LQCD_EINVAL) {
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (n == 1) infos[0].ms = ms;

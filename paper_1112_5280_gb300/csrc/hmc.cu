@@ -482,9 +482,10 @@ int lqcd_solve_normal(const lqcd_gauge* g, const lqcd_field* src, double kappa, 
   if (opts) o = *opts;
   if (o.solver != LQCD_CG) return set_error(LQCD_EINVAL, "the normal equations are solved by CG");
   lqcd_engine* e = nullptr;
-  LQCD_TRY(lqcd_engine_create(g->ctx, &o, 0, 1, &e));
+  LQCD_TRY(ctx_engine(g->ctx, o, 1, &e));
   const int rc = solve_normal_with(e, g, src, kappa, o.mu, tol, x, info);
-  lqcd_engine_destroy(e);
+  if (rc != LQCD_OK && rc != LQCD_ENOCONV && rc != LQCD_EBREAKDOWN && rc != LQCD_ENONFINITE)
+    ctx_drop_engine(g->ctx);
   return rc;
 }
 
@@ -529,7 +530,7 @@ int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m, co
   const size_t ubytes = gauge_copy_bytes(P_F64, 18, g->g.Vh);
   int rc = lqcd_field_create(c, dims, LQCD_F64, LQCD_FULL, &x);
   if (rc == LQCD_OK) rc = lqcd_field_create(c, dims, LQCD_F64, LQCD_FULL, &y);
-  if (rc == LQCD_OK) rc = lqcd_engine_create(c, &o, 0, 1, &e);
+  if (rc == LQCD_OK) rc = ctx_engine(c, o, 1, &e);
   if (rc == LQCD_OK && p->accept_u > 0.0) {
     if (cudaMalloc(&backup, ubytes) != cudaSuccess) {
       cudaGetLastError();
@@ -624,7 +625,7 @@ int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m, co
     cudaStreamSynchronize(c->stream);
     cudaFree(backup);
   }
-  lqcd_engine_destroy(e);
+  if (rc != LQCD_OK && e) ctx_drop_engine(c);  // a failure may leave a request in the engine
   lqcd_field_destroy(x);
   lqcd_field_destroy(y);
   if (info) {

@@ -23,6 +23,10 @@ struct lqcd_ctx {
   double* staging = nullptr;          // host-layout FP64 staging on the device
   size_t staging_bytes = 0;
   long long launches = 0;
+  // engine reused by the one-shot solves (lqcd_solve*, the HMC driver) while their options
+  // match; it holds no reference to the context and is destroyed with it
+  struct lqcd_engine* engine_cache = nullptr;
+  lqcd_solve_opts engine_opts{};
   // The context handle and every gauge, field and engine made from it hold one
   // reference; lqcd_ctx_destroy drops the handle's and the context is freed
   // when the last object goes, so objects may outlive the handle.
@@ -101,6 +105,12 @@ int dslash_tw(const lqcd_gauge* gauge, int prec, const void* in, void* out, cons
 // link layout -> host AoS layout on the device
 int refresh_gauge_copies(lqcd_gauge* g);
 cudaError_t links_to_aos(const double2* U, const Geom& g, double2* aos, cudaStream_t s);
+
+// the context's cached engine for options o and at least n slots (engine.cu)
+int ctx_engine(lqcd_ctx* c, const lqcd_solve_opts& o, int n, lqcd_engine** out);
+void ctx_drop_engine(lqcd_ctx* c);
+// after a one-shot solve: free pooled slot blocks beyond keep_bytes
+void engine_trim_pool(lqcd_engine* e, size_t keep_bytes);
 
 // BiCGStab on Mhat (bicgstab.cu)
 int bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kappa, double tol,
