@@ -126,5 +126,98 @@ __device__ __forceinline__ M3 staple(const double2* U, const Geom& g, const Site
   return W;
 }
 
+// ---------------------------------------------------------------- double-float matrices
+// The FP64 pipes of this part run at 1/64 of the FP32 rate, so the SU(3) products of the
+// gauge kernels run in double-float (pairs of FP32, 48-bit significand) on the FP32 pipes,
+// reading the gauge field's double-float copy (float4 = (re.hi, re.lo, im.hi, im.lo) per
+// complex entry, the same word layout as the FP64 master). Products accumulate unnormalised
+// and each entry is normalised once.
+
+struct C2d {
+  df64 re, im;
+};
+struct M3d {
+  C2d e[9];
+};
+
+__device__ __forceinline__ M3d load_link_df(const float4* U, const Geom& g, const Site& s, int mu) {
+  const size_t b = link_base(g, s, mu);
+  M3d m;
+#pragma unroll
+  for (int w = 0; w < 9; ++w) {
+    const float4 d = U[b + (size_t)w * g.Vh];
+    m.e[w] = {df64(d.x, d.y), df64(d.z, d.w)};
+  }
+  return m;
+}
+__device__ __forceinline__ void store_link_df(float4* U, const Geom& g, const Site& s, int mu, const M3d& m) {
+  const size_t b = link_base(g, s, mu);
+#pragma unroll
+  for (int w = 0; w < 9; ++w) U[b + (size_t)w * g.Vh] = make_float4(m.e[w].re.hi, m.e[w].re.lo, m.e[w].im.hi, m.e[w].im.lo);
+}
+__device__ __forceinline__ M3d to_df(const M3& a) {
+  M3d m;
+#pragma unroll
+  for (int w = 0; w < 9; ++w) m.e[w] = {df64(a.e[w].re), df64(a.e[w].im)};
+  return m;
+}
+__device__ __forceinline__ M3 to_double(const M3d& a) {
+  M3 m;
+#pragma unroll
+  for (int w = 0; w < 9; ++w) m.e[w] = {(double)a.e[w].re, (double)a.e[w].im};
+  return m;
+}
+
+// c = a op(b) with op(b) = b (DAGB false) or b^dag; a^dag b when DAGA
+template <bool DAGA, bool DAGB>
+__device__ __forceinline__ M3d mul_d(const M3d& a, const M3d& b) {
+  M3d c;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      df64 re(0.0f, 0.0f), im(0.0f, 0.0f);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const C2d x = DAGA ? a.e[k * 3 + i] : a.e[i * 3 + k];
+        const C2d y = DAGB ? b.e[j * 3 + k] : b.e[k * 3 + j];
+        // x' y' with x' = conj(x) when DAGA, y' = conj(y) when DAGB
+        const df64 xi = DAGA ? -x.im : x.im, yi = DAGB ? -y.im : y.im;
+        df_mac_u(re, x.re, y.re);
+        df_mac_u(re, -xi, yi);
+        df_mac_u(im, x.re, yi);
+        df_mac_u(im, xi, y.re);
+      }
+      c.e[i * 3 + j] = {df_norm(re), df_norm(im)};
+    }
+  return c;
+}
+
+// the staple sum of staple<mu>, in double-float from the double-float copy Ud
+template <int mu>
+__device__ __forceinline__ M3d staple_df(const float4* Ud, const Geom& g, const Site& x) {
+  M3d W;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) W.e[i] = {df64(0.0f, 0.0f), df64(0.0f, 0.0f)};
+  const Site xp = shifted(g, x, mu, 1);
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == mu) continue;
+    const Site xn = shifted(g, x, nu, 1), xm = shifted(g, x, nu, -1), xpm = shifted(g, xp, nu, -1);
+    const M3d up = mul_d<false, true>(mul_d<false, true>(load_link_df(Ud, g, xp, nu), load_link_df(Ud, g, xn, mu)),
+                                      load_link_df(Ud, g, x, nu));
+    const M3d lo = mul_d<true, false>(mul_d<false, false>(load_link_df(Ud, g, xm, mu), load_link_df(Ud, g, xpm, nu)),
+                                      load_link_df(Ud, g, xm, nu));
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      W.e[i].re = df_add_u(W.e[i].re, df_add_u(up.e[i].re, lo.e[i].re));
+      W.e[i].im = df_add_u(W.e[i].im, df_add_u(up.e[i].im, lo.e[i].im));
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) W.e[i] = {df_norm(W.e[i].re), df_norm(W.e[i].im)};
+  return W;
+}
+
 }  // namespace gf
 }  // namespace lqcd

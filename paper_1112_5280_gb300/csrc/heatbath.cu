@@ -80,14 +80,15 @@ __device__ __noinline__ bool su2_draw(double alpha, uint64_t seed, uint64_t c0, 
   return false;
 }
 
+// the staple sum in double-float from the copy Ud; the updated link goes to U and Ud
 template <int mu>
-__global__ void __launch_bounds__(HB_THREADS) k_heatbath(double2* U, Geom g, int par, double beta,
+__global__ void __launch_bounds__(HB_THREADS) k_heatbath(double2* U, float4* Ud, Geom g, int par, double beta,
                                                          uint64_t seed, uint64_t sweep,
                                                          unsigned long long* fails) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= g.Vh) return;
   const Site x = site_of(g, par, h);
-  const M3 W = staple<mu>(U, g, x);
+  const M3 W = to_double(staple_df<mu>(Ud, g, x));
   M3 u = load_link(U, g, x, mu);
   M3 V = mul_nn(u, W);
   const uint64_t s = (uint64_t)x.c[0] + (uint64_t)g.L[0] * ((uint64_t)x.c[1] + (uint64_t)g.L[1] *
@@ -132,10 +133,11 @@ __global__ void __launch_bounds__(HB_THREADS) k_heatbath(double2* U, Geom g, int
     }
   }
   store_link(U, g, x, mu, u);
+  store_link_df(Ud, g, x, mu, to_df(u));
   if (nfail) atomicAdd(fails, (unsigned long long)nfail);
 }
 
-__global__ void k_reunitarise(double2* U, Geom g) {
+__global__ void k_reunitarise(double2* U, float4* Ud, Geom g) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // (par, mu, h)
   if (i >= 8LL * g.Vh) return;
   const int h = (int)(i % g.Vh);
@@ -175,7 +177,11 @@ __global__ void k_reunitarise(double2* U, Geom g) {
   r[7] = cr(2, 3, 0, 5);
   r[8] = cr(0, 4, 1, 3);
 #pragma unroll
-  for (int w = 0; w < 9; ++w) U[base + (size_t)w * g.Vh] = make_double2(r[w].re, r[w].im);
+  for (int w = 0; w < 9; ++w) {
+    U[base + (size_t)w * g.Vh] = make_double2(r[w].re, r[w].im);
+    const df64 re(r[w].re), im(r[w].im);
+    Ud[base + (size_t)w * g.Vh] = make_float4(re.hi, re.lo, im.hi, im.lo);
+  }
 }
 
 // per-CTA partial of sum_{x, mu<nu} Re Tr U_munu(x) over the sites of both parities
@@ -272,6 +278,12 @@ int lqcd_heatbath(lqcd_gauge* g, double beta, int nsweeps, unsigned long long se
   unsigned long long* d_fails = reinterpret_cast<unsigned long long*>(c->partials);
   LQCD_CK(cudaMemsetAsync(d_fails, 0, sizeof(unsigned long long), st));
   double2* U = static_cast<double2*>(g->copy[P_F64][0]);
+  // the double-float copy the staples read, rebuilt from the master at the start
+  const void* dfbase;
+  int dfnr;
+  LQCD_TRY(gauge_links(g, P_DF64, &dfbase, &dfnr));
+  float4* Ud = static_cast<float4*>(const_cast<void*>(dfbase));
+  LQCD_CK(gauge_convert(U, g->g, P_DF64, 18, Ud, st));
   const unsigned grid = (unsigned)((g->g.Vh + HB_THREADS - 1) / HB_THREADS);
   const unsigned rgrid = (unsigned)((8LL * g->g.Vh + 255) / 256);
   for (int sw = 0; sw < nsweeps; ++sw) {
@@ -279,15 +291,15 @@ int lqcd_heatbath(lqcd_gauge* g, double beta, int nsweeps, unsigned long long se
     for (int mu = 0; mu < 4; ++mu)
       for (int par = 0; par < 2; ++par) {
         switch (mu) {
-          case 0: k_heatbath<0><<<grid, HB_THREADS, 0, st>>>(U, g->g, par, beta, seed, sweep, d_fails); break;
-          case 1: k_heatbath<1><<<grid, HB_THREADS, 0, st>>>(U, g->g, par, beta, seed, sweep, d_fails); break;
-          case 2: k_heatbath<2><<<grid, HB_THREADS, 0, st>>>(U, g->g, par, beta, seed, sweep, d_fails); break;
-          default: k_heatbath<3><<<grid, HB_THREADS, 0, st>>>(U, g->g, par, beta, seed, sweep, d_fails); break;
+          case 0: k_heatbath<0><<<grid, HB_THREADS, 0, st>>>(U, Ud, g->g, par, beta, seed, sweep, d_fails); break;
+          case 1: k_heatbath<1><<<grid, HB_THREADS, 0, st>>>(U, Ud, g->g, par, beta, seed, sweep, d_fails); break;
+          case 2: k_heatbath<2><<<grid, HB_THREADS, 0, st>>>(U, Ud, g->g, par, beta, seed, sweep, d_fails); break;
+          default: k_heatbath<3><<<grid, HB_THREADS, 0, st>>>(U, Ud, g->g, par, beta, seed, sweep, d_fails); break;
         }
         c->launches++;
       }
     if (reunit) {
-      k_reunitarise<<<rgrid, 256, 0, st>>>(U, g->g);
+      k_reunitarise<<<rgrid, 256, 0, st>>>(U, Ud, g->g);
       c->launches++;
     }
     LQCD_CK(cudaGetLastError());

@@ -38,7 +38,6 @@ __device__ __forceinline__ C2 times_i(C2 a) { return {-a.im, a.re}; }
 __device__ __forceinline__ C2 times_mi(C2 a) { return {a.im, -a.re}; }
 __device__ __forceinline__ C2 neg(C2 a) { return {-a.re, -a.im}; }
 __device__ __forceinline__ C2 csub(C2 a, C2 b) { return {a.re - b.re, a.im - b.im}; }
-__device__ __forceinline__ C2 cscale(C2 a, double s) { return {a.re * s, a.im * s}; }
 
 // gamma_mu v on one colour's four spin components (chiral basis: g_k = [[0, -i s_k],
 // [i s_k, 0]] for mu = 0, 1, 2, g_t = [[0, 1], [1, 0]])
@@ -96,13 +95,14 @@ __device__ __forceinline__ void add_mom(double2* P, const Geom& g, const Site& x
   }
 }
 
-// P_mu(x) += coeff (beta / 3) TA(U W)
+// P_mu(x) += coeff (beta / 3) TA(U W); the staple sum in double-float from the copy Ud
 template <int MU>
-__global__ void __launch_bounds__(HMC_THREADS) k_gauge_force(const double2* U, Geom g, double c, double2* P) {
+__global__ void __launch_bounds__(HMC_THREADS) k_gauge_force(const double2* U, const float4* Ud, Geom g, double c,
+                                                            double2* P) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2LL * g.Vh) return;
   const Site x = site_of(g, (int)(i / g.Vh), (int)(i % g.Vh));
-  const M3 W = staple<MU>(U, g, x);
+  const M3 W = to_double(staple_df<MU>(Ud, g, x));
   add_mom(P, g, x, MU, traceless_ah(mul_nn(load_link(U, g, x, MU), W), c));
 }
 
@@ -167,23 +167,23 @@ __global__ void __launch_bounds__(HMC_THREADS) k_fermion_force(const double2* U,
   add_mom(P, g, x, MU, traceless_ah(mul_nn(load_link(U, g, x, MU), Bm), c * eta));
 }
 
-// U <- exp(eps P) U: Taylor series after scaling |eps P| below 1/2 (order from the norm,
-// at most 16), then squaring
-__global__ void k_expm_update(double2* U, Geom g, const double2* P, double eps) {
+// U <- exp(eps P) U in double-float: Taylor series after scaling |eps P| below 1/2 (order
+// from the norm, at most 16), then squaring; U read from the double-float copy Ud, the
+// product written to both the FP64 master U and Ud
+__global__ void k_expm_update(double2* U, float4* Ud, Geom g, const double2* P, double eps) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // (par, mu, h)
   if (i >= 8LL * g.Vh) return;
   const int h = (int)(i % g.Vh);
   const size_t base = (size_t)(i / g.Vh) * 9 * g.Vh + h;
-  M3 A, u;
+  double nrm = 0.0;  // Frobenius norm of eps P (submultiplicative, so it bounds the Taylor tail)
+  double2 p[9];
 #pragma unroll
   for (int w = 0; w < 9; ++w) {
-    const double2 p = P[base + (size_t)w * g.Vh], l = U[base + (size_t)w * g.Vh];
-    A.e[w] = {p.x * eps, p.y * eps};
-    u.e[w] = {l.x, l.y};
+    p[w] = P[base + (size_t)w * g.Vh];
+    p[w].x *= eps;
+    p[w].y *= eps;
+    nrm += p[w].x * p[w].x + p[w].y * p[w].y;
   }
-  double nrm = 0.0;  // Frobenius norm (submultiplicative, so it bounds the Taylor tail)
-#pragma unroll
-  for (int w = 0; w < 9; ++w) nrm += A.e[w].re * A.e[w].re + A.e[w].im * A.e[w].im;
   nrm = sqrt(nrm);
   int sq = 0;
   while (nrm > 0.5 && sq < 60) {
@@ -191,26 +191,42 @@ __global__ void k_expm_update(double2* U, Geom g, const double2* P, double eps) 
     ++sq;
   }
   const double sc = ldexp(1.0, -sq);
+  M3d A;
 #pragma unroll
-  for (int w = 0; w < 9; ++w) A.e[w] = cscale(A.e[w], sc);
-  // Taylor order: the smallest n with nrm^(n+1) / (n+1)! below 2^-56 (n <= 16 as nrm <= 1/2)
+  for (int w = 0; w < 9; ++w) A.e[w] = {df64(p[w].x * sc), df64(p[w].y * sc)};
+  // Taylor order: the smallest n with nrm^(n+1) / (n+1)! below 2^-50 (n <= 16 as nrm <= 1/2)
   int order = 1;
   for (double term = nrm; order < 16; ++order) {
     term *= nrm / (order + 1);
-    if (term < 0x1.0p-56) break;
+    if (term < 0x1.0p-50) break;
   }
-  M3 E;  // Horner: E = 1 + A (1 + A/2 (1 + ... (1 + A/n)))
+  M3d E;  // Horner: E = 1 + A (1 + A/2 (1 + ... (1 + A/n)))
 #pragma unroll
-  for (int w = 0; w < 9; ++w) E.e[w] = {(w % 4 == 0) ? 1.0 : 0.0, 0.0};
+  for (int w = 0; w < 9; ++w) E.e[w] = {df64((w % 4 == 0) ? 1.0f : 0.0f, 0.0f), df64(0.0f, 0.0f)};
   for (int k = order; k >= 1; --k) {
-    M3 T = mul_nn(A, E);
+    const M3d T = mul_d<false, false>(A, E);
+    // 1/k in double-float: the rounded reciprocal and its residual (1 - k hi, exact by FMA)
+    const float kf = (float)k, rh = __frcp_rn(kf);
+    const df64 inv = df_norm(df64(rh, __fmul_rn(__fmaf_rn(-kf, rh, 1.0f), rh)));
 #pragma unroll
-    for (int w = 0; w < 9; ++w) E.e[w] = cadd({(w % 4 == 0) ? 1.0 : 0.0, 0.0}, cscale(T.e[w], 1.0 / k));
+    for (int w = 0; w < 9; ++w) {
+      const df64 one = df64((w % 4 == 0) ? 1.0f : 0.0f, 0.0f);
+      E.e[w] = {df_norm(df_add_u(one, T.e[w].re * inv)), T.e[w].im * inv};
+    }
   }
-  for (int k = 0; k < sq; ++k) E = mul_nn(E, E);
-  const M3 un = mul_nn(E, u);
+  for (int k = 0; k < sq; ++k) E = mul_d<false, false>(E, E);
+  M3d u;
 #pragma unroll
-  for (int w = 0; w < 9; ++w) U[base + (size_t)w * g.Vh] = make_double2(un.e[w].re, un.e[w].im);
+  for (int w = 0; w < 9; ++w) {
+    const float4 d = Ud[base + (size_t)w * g.Vh];
+    u.e[w] = {df64(d.x, d.y), df64(d.z, d.w)};
+  }
+  const M3d un = mul_d<false, false>(E, u);
+#pragma unroll
+  for (int w = 0; w < 9; ++w) {
+    Ud[base + (size_t)w * g.Vh] = make_float4(un.e[w].re.hi, un.e[w].re.lo, un.e[w].im.hi, un.e[w].im.lo);
+    U[base + (size_t)w * g.Vh] = make_double2((double)un.e[w].re, (double)un.e[w].im);
+  }
 }
 
 constexpr int RED_THREADS = 256;
@@ -254,15 +270,26 @@ int check_mom(const lqcd_gauge* g, const lqcd_mom* m) {
   return LQCD_OK;
 }
 
+// the gauge field's double-float copy (made when missing; kept current by every update here)
+int df_links(const lqcd_gauge* g, float4** out) {
+  const void* base;
+  int nr;
+  LQCD_TRY(gauge_links(g, P_DF64, &base, &nr));
+  *out = static_cast<float4*>(const_cast<void*>(base));
+  return LQCD_OK;
+}
+
 int gauge_force_impl(const lqcd_gauge* g, double beta, double coeff, lqcd_mom* m) {
   const double c = coeff * beta / 3.0;
   const double2* U = static_cast<const double2*>(g->copy[P_F64][0]);
+  float4* Ud = nullptr;
+  LQCD_TRY(df_links(g, &Ud));
   const unsigned nb = blocks(2LL * g->g.Vh, HMC_THREADS);
   cudaStream_t st = g->ctx->stream;
-  k_gauge_force<0><<<nb, HMC_THREADS, 0, st>>>(U, g->g, c, m->d);
-  k_gauge_force<1><<<nb, HMC_THREADS, 0, st>>>(U, g->g, c, m->d);
-  k_gauge_force<2><<<nb, HMC_THREADS, 0, st>>>(U, g->g, c, m->d);
-  k_gauge_force<3><<<nb, HMC_THREADS, 0, st>>>(U, g->g, c, m->d);
+  k_gauge_force<0><<<nb, HMC_THREADS, 0, st>>>(U, Ud, g->g, c, m->d);
+  k_gauge_force<1><<<nb, HMC_THREADS, 0, st>>>(U, Ud, g->g, c, m->d);
+  k_gauge_force<2><<<nb, HMC_THREADS, 0, st>>>(U, Ud, g->g, c, m->d);
+  k_gauge_force<3><<<nb, HMC_THREADS, 0, st>>>(U, Ud, g->g, c, m->d);
   g->ctx->launches += 4;
   LQCD_CK(cudaGetLastError());
   return LQCD_OK;
@@ -327,10 +354,13 @@ int solve_normal_with(lqcd_engine* e, const lqcd_gauge* g, const lqcd_field* phi
   return lqcd_engine_result(e, id, x, info);
 }
 
-// refresh: rebuild the derived link copies now (else the caller does before they are read)
+// refresh: rebuild the derived link copies now (else the caller does before they are read);
+// the FP64 master and the double-float copy are always both updated
 int update_links(lqcd_gauge* g, const lqcd_mom* m, double eps, bool refresh) {
+  float4* Ud = nullptr;
+  LQCD_TRY(df_links(g, &Ud));
   k_expm_update<<<blocks(8LL * g->g.Vh, 128), 128, 0, g->ctx->stream>>>(static_cast<double2*>(g->copy[P_F64][0]),
-                                                                          g->g, m->d, eps);
+                                                                          Ud, g->g, m->d, eps);
   g->ctx->launches++;
   LQCD_CK(cudaGetLastError());
   return refresh ? refresh_gauge_copies(g) : LQCD_OK;

@@ -6,7 +6,9 @@ Bars:
     with the oracle's CG within cond * tol (1e-8 here);
   * forces computed from the same solution X: 1e-12 of max|G| (FP64 both sides, the
     same arithmetic up to summation order);
-  * gauge force 1e-12; exp(eps P) U 1e-14; kinetic energy 1e-13 relative;
+  * gauge force 1e-12 (staples in double-float, unit roundoff 2^-48 = 3.6e-15);
+    exp(eps P) U 5e-14 (double-float Horner: about ten chained products of unit roundoff
+    3.6e-15); kinetic energy 1e-13 relative;
   * a short trajectory: links and momenta within 1e-8 of the oracle's (the force solves
     stop at 1e-12, so the forces differ by ~1e-10 and the trajectory inherits that),
     dH within 1e-7; reversibility on the GPU within 1e-8.
@@ -84,7 +86,7 @@ def test_gauge_force_update_kinetic(ctx):
     for eps in (0.05, 0.7):  # 0.7 |P| > 1/2: exercises the scaling and squaring
         g2 = ctx.gauge(dims, U)
         lqcd.gauge_update(g2, m, eps)
-        assert np.abs(g2.download() - ohmc.expm_update(U, P, eps)).max() < 1e-14
+        assert np.abs(g2.download() - ohmc.expm_update(U, P, eps)).max() < 5e-14
 
 
 @pytest.mark.parametrize("scheme", [lqcd.LEAPFROG, lqcd.TWO_MN])
