@@ -736,8 +736,10 @@ def run_e2e(ctx, lqcd, sets, args, world):
     from paper_1112_5280_gb300 import synth
     U, psi = sets[0]
     g = ctx.gauge(DIMS, U, prec="f32", compress=18, t_bc=-1)
-    fi = ctx.field(DIMS, "f32", lqcd.ODD)
-    fo = ctx.field(DIMS, "f32", lqcd.EVEN)
+    # full-lattice fields: the host arrays of a user's call; D_eo reads the odd half of fi
+    # and writes the even half of fo
+    fi = ctx.field(DIMS, "f32", lqcd.FULL)
+    fo = ctx.field(DIMS, "f32", lqcd.FULL)
     host_in = torch.from_numpy(psi).pin_memory().numpy()
     host_out = torch.zeros(psi.shape, dtype=torch.complex128).pin_memory().numpy()
     Vh = synth.volume(DIMS) // 2
@@ -773,7 +775,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (no autotuner)")
     ap.add_argument("--no-variants", action="store_true", help="skip the one-application-per-launch timings")
     ap.add_argument("--dslash-only", action="store_true", help="skip the solver, multi-RHS, multi-lattice and serving sections")
-    ap.add_argument("--section", choices=["heatbath", "hmc", "dslash32", "solve"],
+    ap.add_argument("--section", choices=["heatbath", "hmc", "dslash32", "solve", "mrhs"],
                     help="run one section alone and print its JSON (profiling); no contract line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -796,6 +798,10 @@ def run_one_section(args, world, rank, local):
         inputs = {"solve": (synth.random_links(SOLVE_DIMS, SOLVE_EPS, seed=synth.SEED_LINKS),
                             synth.gaussian_spinor(SOLVE_DIMS, seed=synth.SEED_SOURCE))}
         res = run_solve_section(ctx, lqcd, inputs, world)
+    elif args.section == "mrhs":
+        from paper_1112_5280_gb300 import synth
+        inputs = {"mrhs_U": synth.random_links(MRHS_DIMS, EPS, seed=synth.SEED_LINKS)}
+        res = run_mrhs_section(ctx, lqcd, inputs, world)
     else:
         fn = {"heatbath": run_heatbath_section, "hmc": run_hmc_section,
               "dslash32": run_dslash32_section}[args.section]
