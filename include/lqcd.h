@@ -100,6 +100,12 @@ LQCD_API void* lqcd_ctx_stream(const lqcd_ctx* ctx);
 LQCD_API int lqcd_ctx_sync(lqcd_ctx* ctx);
 /* Number of batched-kernel launches this context has issued (instrumentation). */
 LQCD_API long long lqcd_ctx_launch_count(const lqcd_ctx* ctx);
+/* The one-shot solves keep their device buffers on the context between calls
+ * (the Krylov engine of lqcd_solve*, lqcd_solve_normal and the HMC driver; the
+ * BiCGStab vectors; operator and upload temporaries), so repeated solves
+ * allocate nothing. This waits for the context's stream and frees them; the
+ * next call allocates again. Objects the caller created are untouched. */
+LQCD_API int lqcd_ctx_release_cache(lqcd_ctx* ctx);
 
 /* ---------------------------------------------------------------- gauge field (A1) */
 

@@ -91,9 +91,13 @@ int lqcd::bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kapp
   const void* U64 = g->copy[tp][0];
   const size_t h64 = a256(half_spinor_bytes(tp, Vh)), hs = a256(half_spinor_bytes(sp, Vh));
   BicgBufs b;
-  const size_t total = 6 * h64 + 8 * hs;
-  cudaError_t err = cudaMalloc(&b.block, total);
-  if (err != cudaSuccess) return set_error(LQCD_ENOMEM, "BiCGStab buffers: %s", cudaGetErrorString(err));
+  // the vectors live on the context between calls: repeated solves allocate nothing
+  if (ctx_work(c, 6 * h64 + 8 * hs) != LQCD_OK) {
+    const std::string why = lqcd_last_error();
+    return set_error(LQCD_ENOMEM, "BiCGStab buffers: %s", why.c_str());
+  }
+  cudaError_t err = cudaSuccess;
+  b.block = c->work;
   {
     char* p = static_cast<char*>(b.block);
     void** f64[] = {&b.be, &b.bo, &b.bhat, &b.x64, &b.u64, &b.t64};
@@ -296,7 +300,6 @@ int lqcd::bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kapp
     if (rc == LQCD_OK && status == LQCD_OK && !(true_res <= tol)) status = LQCD_ENOCONV;
   }
   cudaStreamSynchronize(st);
-  cudaFree(b.block);
   if (info) {
     info->status = rc != LQCD_OK ? rc : status;
     info->iters = iters;

@@ -65,6 +65,17 @@ int ctx_tmp(lqcd_ctx* c, size_t bytes) {
   return LQCD_OK;
 }
 
+int ctx_work(lqcd_ctx* c, size_t bytes) {
+  if (c->work_bytes >= bytes) return LQCD_OK;
+  LQCD_CK(cudaStreamSynchronize(c->stream));
+  if (c->work) cudaFree(c->work);
+  c->work = nullptr;
+  c->work_bytes = 0;
+  LQCD_CK(cudaMalloc(&c->work, bytes));
+  c->work_bytes = bytes;
+  return LQCD_OK;
+}
+
 int ctx_staging(lqcd_ctx* c, size_t bytes) {
   if (c->staging_bytes >= bytes) return LQCD_OK;
   LQCD_CK(cudaStreamSynchronize(c->stream));
@@ -194,6 +205,7 @@ void ctx_release(lqcd_ctx* c) {
   if (c->host_sc) cudaFreeHost(c->host_sc);
   if (c->tmp) cudaFree(c->tmp);
   if (c->staging) cudaFree(c->staging);
+  if (c->work) cudaFree(c->work);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
 }
@@ -222,6 +234,22 @@ int lqcd_ctx_sync(lqcd_ctx* c) {
 }
 
 long long lqcd_ctx_launch_count(const lqcd_ctx* c) { return c ? c->launches : 0; }
+
+int lqcd_ctx_release_cache(lqcd_ctx* c) {
+  clear_error();
+  if (!c) return set_error(LQCD_EINVAL, "NULL context");
+  LQCD_CK(cudaSetDevice(c->device));
+  LQCD_CK(cudaStreamSynchronize(c->stream));
+  ctx_drop_engine(c);
+  void** bufs[] = {&c->tmp, &c->work, reinterpret_cast<void**>(&c->staging)};
+  size_t* caps[] = {&c->tmp_bytes, &c->work_bytes, &c->staging_bytes};
+  for (int i = 0; i < 3; ++i) {
+    if (*bufs[i]) cudaFree(*bufs[i]);
+    *bufs[i] = nullptr;
+    *caps[i] = 0;
+  }
+  return LQCD_OK;
+}
 
 void lqcd_set_grid_multiplier(int family, int mult) { set_grid_multiplier(family, mult); }
 

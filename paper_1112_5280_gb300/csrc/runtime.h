@@ -22,6 +22,8 @@ struct lqcd_ctx {
   size_t tmp_bytes = 0;
   double* staging = nullptr;          // host-layout FP64 staging on the device
   size_t staging_bytes = 0;
+  void* work = nullptr;               // solver vectors of the one-shot BiCGStab
+  size_t work_bytes = 0;
   long long launches = 0;
   // engine reused by the one-shot solves (lqcd_solve*, the HMC driver) while their options
   // match; it holds no reference to the context and is destroyed with it
@@ -87,6 +89,7 @@ size_t gauge_copy_bytes(int prec, int nr, int Vh);
 // device buffers of the context, grown on demand (synchronises when growing)
 int ctx_partials(lqcd_ctx* c, size_t n);
 int ctx_tmp(lqcd_ctx* c, size_t bytes);
+int ctx_work(lqcd_ctx* c, size_t bytes);
 int ctx_staging(lqcd_ctx* c, size_t bytes);
 
 // link copy for fields of precision field_prec (created on first use)

@@ -104,6 +104,7 @@ def load(build_if_missing: bool = True):
     _sig(lib, "lqcd_ctx_destroy", None, [_VP])
     _sig(lib, "lqcd_ctx_set_stream", i, [_VP, _VP])
     _sig(lib, "lqcd_ctx_stream", _VP, [_VP])
+    _sig(lib, "lqcd_ctx_release_cache", i, [_VP])
     _sig(lib, "lqcd_ctx_sync", i, [_VP])
     _sig(lib, "lqcd_ctx_launch_count", ll, [_VP])
     _sig(lib, "lqcd_set_grid_multiplier", None, [i, i])
@@ -239,6 +240,10 @@ class Context:
 
     def sync(self):
         _check(self._lib.lqcd_ctx_sync(self.h))
+
+    def release_cache(self):
+        """Frees the buffers the one-shot solves keep between calls (lqcd_ctx_release_cache)."""
+        _check(self._lib.lqcd_ctx_release_cache(self.h))
 
     @property
     def launches(self) -> int:

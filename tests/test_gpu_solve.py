@@ -74,6 +74,28 @@ def test_bicgstab(ctx, prec):
     _solve_check(ctx, (4, 4, 4, 4), 0.3, 0.12, prec, 18, solver=lqcd.BICGSTAB)
 
 
+@pytest.mark.parametrize("solver", [lqcd.CG, lqcd.BICGSTAB])
+def test_cached_buffers_reuse_and_release(ctx, solver):
+    """One-shot solves keep their buffers on the context: a solve after a larger lattice
+    grew them, and a solve after lqcd_ctx_release_cache freed them, equal the first bit for bit."""
+    opts = lqcd.solve_opts(sloppy_prec="f32", sloppy_compress=12, solver=solver)
+    small, large = (4, 4, 4, 6), (6, 6, 4, 8)
+    gs = ctx.gauge(small, synth.random_links(small, 0.4, seed=1011))
+    gl = ctx.gauge(large, synth.random_links(large, 0.4, seed=1012))
+    bs = synth.gaussian_spinor(small, seed=1013)
+    bl = synth.gaussian_spinor(large, seed=1014)
+    x0, i0 = lqcd.solve(gs, bs, 0.13, 1e-10, opts)
+    assert i0["status"] == 0
+    _, il = lqcd.solve(gl, bl, 0.13, 1e-10, opts)
+    assert il["status"] == 0
+    x1, _ = lqcd.solve(gs, bs, 0.13, 1e-10, opts)
+    assert np.array_equal(x0, x1)
+    ctx.release_cache()
+    ctx.release_cache()  # nothing cached: a no-op
+    x2, _ = lqcd.solve(gs, bs, 0.13, 1e-10, opts)
+    assert np.array_equal(x0, x2)
+
+
 def test_free_field_fft(ctx):
     """U = 1 on 8^3 x 16: the GPU solution equals the exact Fourier solution."""
     dims = (8, 8, 8, 16)
