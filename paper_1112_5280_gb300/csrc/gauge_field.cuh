@@ -107,31 +107,32 @@ __device__ __forceinline__ M3 mul_dn(const M3& a, const M3& b) {  // a^dag b
   return c;
 }
 
-// W_mu(x) = sum_{nu != mu} U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag + U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu)
-template <int mu>
-__device__ __forceinline__ M3 staple(const double2* U, const Geom& g, const Site& x) {
-  M3 W;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) W.e[i] = {0.0, 0.0};
-  const Site xp = shifted(g, x, mu, 1);
-#pragma unroll
-  for (int nu = 0; nu < 4; ++nu) {
-    if (nu == mu) continue;
-    const Site xn = shifted(g, x, nu, 1), xm = shifted(g, x, nu, -1), xpm = shifted(g, xp, nu, -1);
-    const M3 up = mul_nd(mul_nd(load_link(U, g, xp, nu), load_link(U, g, xn, mu)), load_link(U, g, x, nu));
-    const M3 lo = mul_dn(mul_nn(load_link(U, g, xm, mu), load_link(U, g, xpm, nu)), load_link(U, g, xm, nu));
-#pragma unroll
-    for (int i = 0; i < 9; ++i) W.e[i] = cadd(W.e[i], cadd(up.e[i], lo.e[i]));
-  }
-  return W;
-}
-
 // ---------------------------------------------------------------- double-float matrices
 // The FP64 pipes of this part run at 1/64 of the FP32 rate, so the SU(3) products of the
 // gauge kernels run in double-float (pairs of FP32, 48-bit significand) on the FP32 pipes,
 // reading the gauge field's double-float copy (float4 = (re.hi, re.lo, im.hi, im.lo) per
 // complex entry, the same word layout as the FP64 master). Products accumulate unnormalised
 // and each entry is normalised once.
+
+// A double as an (unnormalised) double-float pair by integer operations on its bits, for
+// kernels where the conversion instructions would load the FP64 pipe (1/64 of the FP32
+// rate on this part): hi keeps the top 24 significant bits (truncated), lo the next 24 of
+// the remaining 29 (truncated), so hi + lo is within 2^-47 relative of x and |lo| < ulp(hi).
+// Exponents outside +-60 (including zero, subnormals, inf and NaN) take the FP64 path.
+__device__ __forceinline__ df64 df_split_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  const int E = (int)((hw >> 20) & 0x7ffu);
+  if (E < 1023 - 60 || E > 1023 + 60) return df64(x);
+  const unsigned sign = hw & 0x80000000u;
+  const float hi = __uint_as_float(sign | ((unsigned)(E - 896) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+  const unsigned rem = lw & 0x1fffffffu;  // weight 2^(E - 1075) per unit
+  if (rem == 0u) return df64(hi, 0.0f);
+  const int top = 31 - __clz((int)rem);  // leading bit, <= 28
+  const unsigned m = top >= 23 ? rem >> (top - 23) : rem << (23 - top);
+  const float lo = __uint_as_float(sign | ((unsigned)(top + E - 948) << 23) | (m & 0x7fffffu));
+  return df64(hi, lo);
+}
 
 struct C2d {
   df64 re, im;
@@ -193,29 +194,79 @@ __device__ __forceinline__ M3d mul_d(const M3d& a, const M3d& b) {
   return c;
 }
 
-// the staple sum of staple<mu>, in double-float from the double-float copy Ud
-template <int mu>
-__device__ __forceinline__ M3d staple_df(const float4* Ud, const Geom& g, const Site& x) {
+// w += a op(b) in double-float: each entry accumulates unnormalised over k and is
+// normalised once (the layout of mul_d, without the intermediate matrix)
+template <bool DAGA, bool DAGB>
+__device__ __forceinline__ void mac_d(M3d& w, const M3d& a, const M3d& b) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      df64 re = w.e[i * 3 + j].re, im = w.e[i * 3 + j].im;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const C2d x = DAGA ? a.e[k * 3 + i] : a.e[i * 3 + k];
+        const C2d y = DAGB ? b.e[j * 3 + k] : b.e[k * 3 + j];
+        const df64 xi = DAGA ? -x.im : x.im, yi = DAGB ? -y.im : y.im;
+        df_mac_u(re, x.re, y.re);
+        df_mac_u(re, -xi, yi);
+        df_mac_u(im, x.re, yi);
+        df_mac_u(im, xi, y.re);
+      }
+      w.e[i * 3 + j] = {df_norm(re), df_norm(im)};
+    }
+}
+
+// m or m^dag, chosen at run time (selects on registers)
+__device__ __forceinline__ M3d dagger_if(const M3d& m, bool dag) {
+  M3d r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const C2d a = m.e[i * 3 + j], b = m.e[j * 3 + i];
+      r.e[i * 3 + j] = dag ? C2d{b.re, -b.im} : a;
+    }
+  return r;
+}
+
+// coordinate nu of s and the site shifted by d in direction nu, for a direction known only
+// at run time (selects, so that the site stays in registers)
+__device__ __forceinline__ int coord(const Site& s, int nu) {
+  return nu == 0 ? s.c[0] : (nu == 1 ? s.c[1] : (nu == 2 ? s.c[2] : s.c[3]));
+}
+__device__ __forceinline__ Site shifted_rt(const Geom& g, Site s, int nu, int d) {
+  const int L = nu == 0 ? g.L[0] : (nu == 1 ? g.L[1] : (nu == 2 ? g.L[2] : g.L[3]));
+  int v = coord(s, nu) + d;
+  v = v < 0 ? v + L : (v >= L ? v - L : v);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s.c[k] = (nu == k) ? v : s.c[k];
+  return s;
+}
+
+// The staple sum W_mu(x) = sum_{nu != mu} U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+//                                         + U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu)
+// for a direction mu known at run time, in double-float from the copy Ud. The six staples
+// run through one loop body of two products
+//   up (nu):   T = U_nu(x+mu) U_mu(x+nu)^dag,          W += T U_nu(x)^dag
+//   down (nu): T = U_nu(x+mu-nu)^dag U_mu(x-nu)^dag,   W += T U_nu(x-nu)
+// so that the instructions of the loop stay in the instruction cache (fully unrolled, at
+// about 1400 instructions per double-float product, the staple sum did not).
+__device__ __forceinline__ M3d staple_df(const float4* Ud, const Geom& g, const Site& x, int mu) {
   M3d W;
 #pragma unroll
   for (int i = 0; i < 9; ++i) W.e[i] = {df64(0.0f, 0.0f), df64(0.0f, 0.0f)};
-  const Site xp = shifted(g, x, mu, 1);
-#pragma unroll
-  for (int nu = 0; nu < 4; ++nu) {
-    if (nu == mu) continue;
-    const Site xn = shifted(g, x, nu, 1), xm = shifted(g, x, nu, -1), xpm = shifted(g, xp, nu, -1);
-    const M3d up = mul_d<false, true>(mul_d<false, true>(load_link_df(Ud, g, xp, nu), load_link_df(Ud, g, xn, mu)),
-                                      load_link_df(Ud, g, x, nu));
-    const M3d lo = mul_d<true, false>(mul_d<false, false>(load_link_df(Ud, g, xm, mu), load_link_df(Ud, g, xpm, nu)),
-                                      load_link_df(Ud, g, xm, nu));
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      W.e[i].re = df_add_u(W.e[i].re, df_add_u(up.e[i].re, lo.e[i].re));
-      W.e[i].im = df_add_u(W.e[i].im, df_add_u(up.e[i].im, lo.e[i].im));
-    }
+  const Site xp = shifted_rt(g, x, mu, 1);
+#pragma unroll 1
+  for (int t = 0; t < 6; ++t) {
+    const int k = t >> 1, nu = k + (k >= mu ? 1 : 0);
+    const bool up = (t & 1) == 0;
+    const Site s0 = up ? xp : shifted_rt(g, xp, nu, -1);
+    const Site s1 = shifted_rt(g, x, nu, up ? 1 : -1);
+    const Site s2 = up ? x : s1;
+    const M3d T = mul_d<false, true>(dagger_if(load_link_df(Ud, g, s0, nu), !up), load_link_df(Ud, g, s1, mu));
+    mac_d<false, false>(W, T, dagger_if(load_link_df(Ud, g, s2, nu), up));
   }
-#pragma unroll
-  for (int i = 0; i < 9; ++i) W.e[i] = {df_norm(W.e[i].re), df_norm(W.e[i].im)};
   return W;
 }
 

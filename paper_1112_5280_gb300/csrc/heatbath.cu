@@ -1,5 +1,6 @@
 // Pure-gauge SU(3) heatbath and plaquette (paper Section 3: the pure-gauge side needs an
-// SU(3) heatbath, citing Creutz) on the FP64 master copy of a gauge field.
+// SU(3) heatbath, citing Creutz). The heatbath keeps the FP64 master copy of a gauge field
+// and its double-float copy equal: the matrix algebra runs in double-float, the draws in FP64.
 //
 // Wilson action S = beta sum_P (1 - Re Tr U_P / 3). A sweep updates the links class by
 // class, mu = 0..3 and parity even, odd: the links U_mu(x) of one class share no staple,
@@ -58,11 +59,12 @@ __device__ __forceinline__ double unit_open0(uint64_t r) { return ((double)(r >>
 
 // Creutz's SU(2) draw; false after HB_MAX_ATTEMPTS
 __device__ __noinline__ bool su2_draw(double alpha, uint64_t seed, uint64_t c0, uint64_t c1, uint64_t c2, double b[4]) {
+  const double span = -expm1(-2.0 * alpha);  // 1 - exp(-2 alpha), the same for every attempt
   for (int attempt = 0; attempt < HB_MAX_ATTEMPTS; ++attempt) {
     uint64_t r[4] = {c0, c1, c2, (uint64_t)attempt};
     philox4x64(r, seed, 0);
     const double u0 = unit_open0(r[0]), u1 = unit_open0(r[1]), u2 = unit_open0(r[2]), u3 = unit_open0(r[3]);
-    const double b0 = alpha < 1e-12 ? 1.0 - 2.0 * u0 : 1.0 + log1p(-u0 * (-expm1(-2.0 * alpha))) / alpha;
+    const double b0 = alpha < 1e-12 ? 1.0 - 2.0 * u0 : 1.0 + log1p(-u0 * span) / alpha;
     const double s2 = 1.0 - b0 * b0;
     if (u1 * u1 <= s2) {
       const double rr = sqrt(fmax(s2, 0.0));
@@ -80,17 +82,37 @@ __device__ __noinline__ bool su2_draw(double alpha, uint64_t seed, uint64_t c0, 
   return false;
 }
 
-// the staple sum in double-float from the copy Ud; the updated link goes to U and Ud
-template <int mu>
-__global__ void __launch_bounds__(HB_THREADS) k_heatbath(double2* U, float4* Ud, Geom g, int par, double beta,
-                                                         uint64_t seed, uint64_t sweep,
-                                                         unsigned long long* fails) {
+__device__ __forceinline__ C2 to_c2(const C2d& a) { return {(double)a.re, (double)a.im}; }
+
+// a x + b y in double-float
+__device__ __forceinline__ C2d cmix_d(const C2d& a, const C2d& x, const C2d& b, const C2d& y) {
+  df64 re(0.0f, 0.0f), im(0.0f, 0.0f);
+  df_mac_u(re, a.re, x.re);
+  df_mac_u(re, -a.im, x.im);
+  df_mac_u(re, b.re, y.re);
+  df_mac_u(re, -b.im, y.im);
+  df_mac_u(im, a.re, x.im);
+  df_mac_u(im, a.im, x.re);
+  df_mac_u(im, b.re, y.im);
+  df_mac_u(im, b.im, y.re);
+  return {df_norm(re), df_norm(im)};
+}
+
+// The SU(3) algebra (staple sum, V = U W, the subgroup rotations of U and V) in
+// double-float from the copy Ud on the FP32 pipes; each subgroup's draw (k, v, Creutz)
+// in FP64 from its 2 x 2 block of V. The updated link goes to U and Ud.
+#ifndef LQCD_HB_MIN_BLOCKS
+#define LQCD_HB_MIN_BLOCKS 2
+#endif
+__global__ void __launch_bounds__(HB_THREADS, LQCD_HB_MIN_BLOCKS) k_heatbath(double2* U, float4* Ud, Geom g, int mu,
+                                                                             int par, double beta, uint64_t seed,
+                                                                             uint64_t sweep,
+                                                                             unsigned long long* fails) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= g.Vh) return;
   const Site x = site_of(g, par, h);
-  const M3 W = to_double(staple_df<mu>(Ud, g, x));
-  M3 u = load_link(U, g, x, mu);
-  M3 V = mul_nn(u, W);
+  M3d u = load_link_df(Ud, g, x, mu);
+  M3d V = mul_d<false, false>(u, staple_df(Ud, g, x, mu));
   const uint64_t s = (uint64_t)x.c[0] + (uint64_t)g.L[0] * ((uint64_t)x.c[1] + (uint64_t)g.L[1] *
                      ((uint64_t)x.c[2] + (uint64_t)g.L[2] * (uint64_t)x.c[3]));
   const uint64_t link_id = 4 * s + (uint64_t)mu;
@@ -98,15 +120,17 @@ __global__ void __launch_bounds__(HB_THREADS) k_heatbath(double2* U, float4* Ud,
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const int i = k == 1 ? 1 : 0, j = k == 0 ? 1 : 2;  // (0,1), (1,2), (0,2)
-    const C2 x00 = V.e[i * 3 + i], x01 = V.e[i * 3 + j], x10 = V.e[j * 3 + i], x11 = V.e[j * 3 + j];
+    const C2 x00 = to_c2(V.e[i * 3 + i]), x01 = to_c2(V.e[i * 3 + j]), x10 = to_c2(V.e[j * 3 + i]),
+             x11 = to_c2(V.e[j * 3 + j]);
     const double c0 = x00.re + x11.re, c1 = -(x01.im + x10.im), c2 = x10.re - x01.re, c3 = -(x00.im - x11.im);
     const double kk = sqrt(c0 * c0 + c1 * c1 + c2 * c2 + c3 * c3);
     double v[4] = {1.0, 0.0, 0.0, 0.0};
     if (kk > 0.0) {
-      v[0] = c0 / kk;
-      v[1] = c1 / kk;
-      v[2] = c2 / kk;
-      v[3] = c3 / kk;
+      const double ik = 1.0 / kk;
+      v[0] = c0 * ik;
+      v[1] = c1 * ik;
+      v[2] = c2 * ik;
+      v[3] = c3 * ik;
     }
     double b[4];
     if (!su2_draw(beta * kk / 3.0, seed, link_id, sweep, (uint64_t)k, b)) {
@@ -116,25 +140,38 @@ __global__ void __launch_bounds__(HB_THREADS) k_heatbath(double2* U, float4* Ud,
     // a = b v with mat(q) = [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]]
     const C2 B[4] = {{b[0], b[3]}, {b[2], b[1]}, {-b[2], b[1]}, {b[0], -b[3]}};
     const C2 Vm[4] = {{v[0], v[3]}, {v[2], v[1]}, {-v[2], v[1]}, {v[0], -v[3]}};
-    C2 A[4];
+    C2d A[4];
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
-      for (int q = 0; q < 2; ++q) A[r * 2 + q] = cadd(cmul(B[r * 2], Vm[q]), cmul(B[r * 2 + 1], Vm[2 + q]));
-    // U <- R U and V <- R V (rows i, j)
+      for (int q = 0; q < 2; ++q) {
+        const C2 a = cadd(cmul(B[r * 2], Vm[q]), cmul(B[r * 2 + 1], Vm[2 + q]));
+        A[r * 2 + q] = {df64(a.re), df64(a.im)};
+      }
+    // U <- R U and V <- R V (rows i, j; V is not needed after the last subgroup)
 #pragma unroll
     for (int col = 0; col < 3; ++col) {
-      const C2 ui = u.e[i * 3 + col], uj = u.e[j * 3 + col];
-      u.e[i * 3 + col] = cadd(cmul(A[0], ui), cmul(A[1], uj));
-      u.e[j * 3 + col] = cadd(cmul(A[2], ui), cmul(A[3], uj));
-      const C2 vi = V.e[i * 3 + col], vj = V.e[j * 3 + col];
-      V.e[i * 3 + col] = cadd(cmul(A[0], vi), cmul(A[1], vj));
-      V.e[j * 3 + col] = cadd(cmul(A[2], vi), cmul(A[3], vj));
+      const C2d ui = u.e[i * 3 + col], uj = u.e[j * 3 + col];
+      u.e[i * 3 + col] = cmix_d(A[0], ui, A[1], uj);
+      u.e[j * 3 + col] = cmix_d(A[2], ui, A[3], uj);
+      if (k < 2) {
+        const C2d vi = V.e[i * 3 + col], vj = V.e[j * 3 + col];
+        V.e[i * 3 + col] = cmix_d(A[0], vi, A[1], vj);
+        V.e[j * 3 + col] = cmix_d(A[2], vi, A[3], vj);
+      }
     }
   }
-  store_link(U, g, x, mu, u);
-  store_link_df(Ud, g, x, mu, to_df(u));
+  store_link(U, g, x, mu, to_double(u));
+  store_link_df(Ud, g, x, mu, u);
   if (nfail) atomicAdd(fails, (unsigned long long)nfail);
+}
+
+// FP64 master words from the double-float copy (hi + lo, exact in FP64)
+__global__ void k_master_from_df(double2* U, const float4* Ud, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 d = Ud[i];
+  U[i] = make_double2((double)d.x + (double)d.y, (double)d.z + (double)d.w);
 }
 
 __global__ void k_reunitarise(double2* U, float4* Ud, Geom g) {
@@ -244,14 +281,27 @@ __global__ void k_gauge_to_aos(const double2* U, Geom g, double2* aos) {
 }  // namespace
 
 // derived link copies follow the master after an update
-int refresh_gauge_copies(lqcd_gauge* g) {
+// keep_df: the double-float copy is already current (the master was built from it)
+int refresh_gauge_copies(lqcd_gauge* g, bool keep_df) {
   for (int p = 0; p < NPREC; ++p)
     for (int c = 0; c < 2; ++c) {
       if (p == P_F64 && c == 0) continue;
+      if (keep_df && p == P_DF64 && c == 0) continue;
       if (!g->copy[p][c]) continue;
       LQCD_CK(gauge_convert(g->copy[P_F64][0], g->g, p, c ? 12 : 18, g->copy[p][c], g->ctx->stream));
     }
   return LQCD_OK;
+}
+
+int links_from_df(lqcd_gauge* g) {
+  const float4* Ud = static_cast<const float4*>(g->copy[P_DF64][0]);
+  if (!Ud) return set_error(LQCD_EINVAL, "the gauge field has no double-float copy");
+  const long long n = 2LL * 4 * 9 * g->g.Vh;
+  k_master_from_df<<<(unsigned)((n + 255) / 256), 256, 0, g->ctx->stream>>>(
+      static_cast<double2*>(g->copy[P_F64][0]), Ud, n);
+  g->ctx->launches++;
+  LQCD_CK(cudaGetLastError());
+  return refresh_gauge_copies(g, true);
 }
 
 cudaError_t links_to_aos(const double2* U, const Geom& g, double2* aos, cudaStream_t s) {
@@ -290,12 +340,7 @@ int lqcd_heatbath(lqcd_gauge* g, double beta, int nsweeps, unsigned long long se
     const uint64_t sweep = (uint64_t)(sweep0 + (unsigned long long)sw);
     for (int mu = 0; mu < 4; ++mu)
       for (int par = 0; par < 2; ++par) {
-        switch (mu) {
-          case 0: k_heatbath<0><<<grid, HB_THREADS, 0, st>>>(U, Ud, g->g, par, beta, seed, sweep, d_fails); break;
-          case 1: k_heatbath<1><<<grid, HB_THREADS, 0, st>>>(U, Ud, g->g, par, beta, seed, sweep, d_fails); break;
-          case 2: k_heatbath<2><<<grid, HB_THREADS, 0, st>>>(U, Ud, g->g, par, beta, seed, sweep, d_fails); break;
-          default: k_heatbath<3><<<grid, HB_THREADS, 0, st>>>(U, Ud, g->g, par, beta, seed, sweep, d_fails); break;
-        }
+        k_heatbath<<<grid, HB_THREADS, 0, st>>>(U, Ud, g->g, mu, par, beta, seed, sweep, d_fails);
         c->launches++;
       }
     if (reunit) {

@@ -95,15 +95,47 @@ __device__ __forceinline__ void add_mom(double2* P, const Geom& g, const Site& x
   }
 }
 
-// P_mu(x) += coeff (beta / 3) TA(U W); the staple sum in double-float from the copy Ud
-template <int MU>
-__global__ void __launch_bounds__(HMC_THREADS) k_gauge_force(const double2* U, const float4* Ud, Geom g, double c,
-                                                            double2* P) {
+// P_mu(x) += c TA(U W), c = coeff beta / 3: the staple sum, U W and the anti-Hermitian
+// part in double-float from the copy Ud (FP32 pipes), only the accumulation into the FP64
+// momenta in FP64. All four directions in one launch (blockIdx.y = mu), one thread per
+// link, mu a run-time value so that the four share one instruction stream.
+#ifndef LQCD_GF_MIN_BLOCKS
+#define LQCD_GF_MIN_BLOCKS 2
+#endif
+__global__ void __launch_bounds__(HMC_THREADS, LQCD_GF_MIN_BLOCKS) k_gauge_force(const float4* Ud, Geom g, double c, double2* P) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2LL * g.Vh) return;
+  const int mu = blockIdx.y;
   const Site x = site_of(g, (int)(i / g.Vh), (int)(i % g.Vh));
-  const M3 W = to_double(staple_df<MU>(Ud, g, x));
-  add_mom(P, g, x, MU, traceless_ah(mul_nn(load_link(U, g, x, MU), W), c));
+  const M3d V = mul_d<false, false>(load_link_df(Ud, g, x, mu), staple_df(Ud, g, x, mu));
+  const size_t b = link_base(g, x, mu);
+  const size_t vh = (size_t)g.Vh;
+  // TA(V)_ii = i (Im V_ii - Im tr V / 3); TA(V)_ij = (V_ij - conj V_ji) / 2, TA_ji = -conj TA_ij
+  double d[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) d[k] = (double)V.e[k * 4].im;
+  const double tr = (d[0] + d[1] + d[2]) / 3.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double2 q = P[b + (size_t)(k * 4) * vh];
+    q.y += c * (d[k] - tr);
+    P[b + (size_t)(k * 4) * vh] = q;
+  }
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int col = r + 1; col < 3; ++col) {
+      const C2d x1 = V.e[r * 3 + col], y1 = V.e[col * 3 + r];
+      const double re = 0.5 * (double)df_add_u(x1.re, -y1.re), im = 0.5 * (double)df_add_u(x1.im, y1.im);
+      double2 q = P[b + (size_t)(r * 3 + col) * vh];
+      q.x += c * re;
+      q.y += c * im;
+      P[b + (size_t)(r * 3 + col) * vh] = q;
+      q = P[b + (size_t)(col * 3 + r) * vh];
+      q.x -= c * re;
+      q.y += c * im;
+      P[b + (size_t)(col * 3 + r) * vh] = q;
+    }
 }
 
 // P_mu(x) += c eta TA(U B), B = ((1 - g_mu) Phi(x+mu))^T conj(Psi(x)) + Psi(x+mu)^T conj((1 + g_mu) Phi(x))
@@ -167,52 +199,107 @@ __global__ void __launch_bounds__(HMC_THREADS) k_fermion_force(const double2* U,
   add_mom(P, g, x, MU, traceless_ah(mul_nn(load_link(U, g, x, MU), Bm), c * eta));
 }
 
-// U <- exp(eps P) U in double-float: Taylor series after scaling |eps P| below 1/2 (order
-// from the norm, at most 16), then squaring; U read from the double-float copy Ud, the
-// product written to both the FP64 master U and Ud
-__global__ void k_expm_update(double2* U, float4* Ud, Geom g, const double2* P, double eps) {
+// 1/k! for the Taylor coefficients as double-float constants (k! is exact in FP64 for
+// k <= 22; the pair is the FP64 value split into two floats at compile time)
+struct DFConst {
+  float hi, lo;
+};
+constexpr DFConst dfc(double v) { return {(float)v, (float)(v - (double)(float)v)}; }
+__constant__ DFConst kInvFact[18] = {
+    dfc(1.0), dfc(1.0), dfc(1.0 / 2.0), dfc(1.0 / 6.0), dfc(1.0 / 24.0), dfc(1.0 / 120.0), dfc(1.0 / 720.0),
+    dfc(1.0 / 5040.0), dfc(1.0 / 40320.0), dfc(1.0 / 362880.0), dfc(1.0 / 3628800.0), dfc(1.0 / 39916800.0),
+    dfc(1.0 / 479001600.0), dfc(1.0 / 6227020800.0), dfc(1.0 / 87178291200.0), dfc(1.0 / 1307674368000.0),
+    dfc(1.0 / 20922789888000.0), dfc(1.0 / 355687428096000.0)};
+
+// complex double-float scalars
+__device__ __forceinline__ C2d cmul_d(const C2d& a, const C2d& b) {
+  df64 re(0.0f, 0.0f), im(0.0f, 0.0f);
+  df_mac_u(re, a.re, b.re);
+  df_mac_u(re, -a.im, b.im);
+  df_mac_u(im, a.re, b.im);
+  df_mac_u(im, a.im, b.re);
+  return {df_norm(re), df_norm(im)};
+}
+__device__ __forceinline__ C2d cadd_d(const C2d& a, const C2d& b) {
+  return {df_norm(df_add_u(a.re, b.re)), df_norm(df_add_u(a.im, b.im))};
+}
+__device__ __forceinline__ C2d csub_d(const C2d& a, const C2d& b) { return cadd_d(a, {-b.re, -b.im}); }
+__device__ __forceinline__ C2d cscale_d(df64 f, const C2d& a) { return {f * a.re, f * a.im}; }
+
+// U <- exp(eps P) U in double-float: the Taylor polynomial of degree n after scaling
+// |eps P| below 1/2 (n from the norm, at most 16), then squaring; U read from the
+// double-float copy Ud, the product written to Ud and, when write_master, to the FP64
+// master U (else the caller rebuilds the master from Ud before reading it).
+// The polynomial is reduced by Cayley-Hamilton: with c2 = tr X, c1 = (tr(X)^2 - tr X^2) / 2
+// and c0 = det X, X^3 = c2 X^2 - c1 X + c0 I, so every power X^k = a_k I + b_k X + g_k X^2
+// with the scalar recursion a_{k+1} = g_k c0, b_{k+1} = a_k - g_k c1, g_{k+1} = b_k + g_k c2,
+// and sum_k X^k / k! = (sum a_k / k!) I + (sum b_k / k!) X + (sum g_k / k!) X^2: one matrix
+// product (X^2) for any degree. Everything runs on the FP32 pipes: P is split into
+// double-float pairs by integer operations, and the norm and the degree, which only need
+// to bound the Taylor tail, are taken in FP32 with a margin.
+__global__ void k_expm_update(double2* U, float4* Ud, Geom g, const double2* P, double eps, bool write_master) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // (par, mu, h)
   if (i >= 8LL * g.Vh) return;
   const int h = (int)(i % g.Vh);
   const size_t base = (size_t)(i / g.Vh) * 9 * g.Vh + h;
-  double nrm = 0.0;  // Frobenius norm of eps P (submultiplicative, so it bounds the Taylor tail)
-  double2 p[9];
+  const df64 e_df = df_split_bits(eps);
+  M3d A;
+  float n2 = 0.0f;
 #pragma unroll
   for (int w = 0; w < 9; ++w) {
-    p[w] = P[base + (size_t)w * g.Vh];
-    p[w].x *= eps;
-    p[w].y *= eps;
-    nrm += p[w].x * p[w].x + p[w].y * p[w].y;
+    const double2 q = P[base + (size_t)w * g.Vh];
+    A.e[w] = {e_df * df_split_bits(q.x), e_df * df_split_bits(q.y)};
+    n2 = __fmaf_rn(A.e[w].re.hi, A.e[w].re.hi, __fmaf_rn(A.e[w].im.hi, A.e[w].im.hi, n2));
   }
-  nrm = sqrt(nrm);
+  // Frobenius norm of eps P (submultiplicative, so it bounds the Taylor tail), rounded up
+  float nrm = sqrtf(n2) * (1.0f + 0x1.0p-16f);
   int sq = 0;
-  while (nrm > 0.5 && sq < 60) {
-    nrm *= 0.5;
+  while (nrm > 0.5f && sq < 60) {
+    nrm *= 0.5f;
     ++sq;
   }
-  const double sc = ldexp(1.0, -sq);
-  M3d A;
-#pragma unroll
-  for (int w = 0; w < 9; ++w) A.e[w] = {df64(p[w].x * sc), df64(p[w].y * sc)};
-  // Taylor order: the smallest n with nrm^(n+1) / (n+1)! below 2^-50 (n <= 16 as nrm <= 1/2)
-  int order = 1;
-  for (double term = nrm; order < 16; ++order) {
-    term *= nrm / (order + 1);
-    if (term < 0x1.0p-50) break;
-  }
-  M3d E;  // Horner: E = 1 + A (1 + A/2 (1 + ... (1 + A/n)))
-#pragma unroll
-  for (int w = 0; w < 9; ++w) E.e[w] = {df64((w % 4 == 0) ? 1.0f : 0.0f, 0.0f), df64(0.0f, 0.0f)};
-  for (int k = order; k >= 1; --k) {
-    const M3d T = mul_d<false, false>(A, E);
-    // 1/k in double-float: the rounded reciprocal and its residual (1 - k hi, exact by FMA)
-    const float kf = (float)k, rh = __frcp_rn(kf);
-    const df64 inv = df_norm(df64(rh, __fmul_rn(__fmaf_rn(-kf, rh, 1.0f), rh)));
+  if (sq > 0) {
+    const float sc = __uint_as_float((unsigned)(127 - sq) << 23);  // 2^-sq, exact scaling
 #pragma unroll
     for (int w = 0; w < 9; ++w) {
-      const df64 one = df64((w % 4 == 0) ? 1.0f : 0.0f, 0.0f);
-      E.e[w] = {df_norm(df_add_u(one, T.e[w].re * inv)), T.e[w].im * inv};
+      A.e[w].re = df64(A.e[w].re.hi * sc, A.e[w].re.lo * sc);
+      A.e[w].im = df64(A.e[w].im.hi * sc, A.e[w].im.lo * sc);
     }
+  }
+  // degree: the smallest n with nrm^(n+1) / (n+1)! below 2^-50 (n <= 16 as nrm <= 1/2)
+  int order = 1;
+  for (float term = nrm; order < 16; ++order) {
+    term *= __fdividef(nrm, (float)(order + 1));
+    if (term < 0x1.0p-50f) break;
+  }
+  const M3d A2 = mul_d<false, false>(A, A);
+  const C2d t1 = cadd_d(cadd_d(A.e[0], A.e[4]), A.e[8]);
+  const C2d t2 = cadd_d(cadd_d(A2.e[0], A2.e[4]), A2.e[8]);
+  const C2d c2 = t1;
+  const C2d c1 = cscale_d(df64(0.5f, 0.0f), csub_d(cmul_d(t1, t1), t2));
+  const C2d m0 = csub_d(cmul_d(A.e[4], A.e[8]), cmul_d(A.e[5], A.e[7]));
+  const C2d m1 = csub_d(cmul_d(A.e[3], A.e[8]), cmul_d(A.e[5], A.e[6]));
+  const C2d m2 = csub_d(cmul_d(A.e[3], A.e[7]), cmul_d(A.e[4], A.e[6]));
+  const C2d c0 = cadd_d(csub_d(cmul_d(A.e[0], m0), cmul_d(A.e[1], m1)), cmul_d(A.e[2], m2));
+  const C2d zero = {df64(0.0f, 0.0f), df64(0.0f, 0.0f)};
+  C2d a = {df64(1.0f, 0.0f), df64(0.0f, 0.0f)}, b = zero, gm = zero;  // X^0 = I
+  C2d sa = a, sb = b, sg = gm;                                        // sums over k of X^k / k!
+  for (int k = 1; k <= order; ++k) {
+    const C2d na = cmul_d(gm, c0), nb = csub_d(a, cmul_d(gm, c1)), ng = cadd_d(b, cmul_d(gm, c2));
+    a = na;
+    b = nb;
+    gm = ng;
+    const df64 f(kInvFact[k].hi, kInvFact[k].lo);
+    sa = cadd_d(sa, cscale_d(f, a));
+    sb = cadd_d(sb, cscale_d(f, b));
+    sg = cadd_d(sg, cscale_d(f, gm));
+  }
+  M3d E;
+#pragma unroll
+  for (int w = 0; w < 9; ++w) {
+    C2d e = cadd_d(cmul_d(sb, A.e[w]), cmul_d(sg, A2.e[w]));
+    if (w % 4 == 0) e = cadd_d(e, sa);
+    E.e[w] = e;
   }
   for (int k = 0; k < sq; ++k) E = mul_d<false, false>(E, E);
   M3d u;
@@ -223,9 +310,12 @@ __global__ void k_expm_update(double2* U, float4* Ud, Geom g, const double2* P, 
   }
   const M3d un = mul_d<false, false>(E, u);
 #pragma unroll
-  for (int w = 0; w < 9; ++w) {
+  for (int w = 0; w < 9; ++w)
     Ud[base + (size_t)w * g.Vh] = make_float4(un.e[w].re.hi, un.e[w].re.lo, un.e[w].im.hi, un.e[w].im.lo);
-    U[base + (size_t)w * g.Vh] = make_double2((double)un.e[w].re, (double)un.e[w].im);
+  if (write_master) {
+#pragma unroll
+    for (int w = 0; w < 9; ++w)
+      U[base + (size_t)w * g.Vh] = make_double2((double)un.e[w].re, (double)un.e[w].im);
   }
 }
 
@@ -281,16 +371,12 @@ int df_links(const lqcd_gauge* g, float4** out) {
 
 int gauge_force_impl(const lqcd_gauge* g, double beta, double coeff, lqcd_mom* m) {
   const double c = coeff * beta / 3.0;
-  const double2* U = static_cast<const double2*>(g->copy[P_F64][0]);
   float4* Ud = nullptr;
   LQCD_TRY(df_links(g, &Ud));
   const unsigned nb = blocks(2LL * g->g.Vh, HMC_THREADS);
   cudaStream_t st = g->ctx->stream;
-  k_gauge_force<0><<<nb, HMC_THREADS, 0, st>>>(U, Ud, g->g, c, m->d);
-  k_gauge_force<1><<<nb, HMC_THREADS, 0, st>>>(U, Ud, g->g, c, m->d);
-  k_gauge_force<2><<<nb, HMC_THREADS, 0, st>>>(U, Ud, g->g, c, m->d);
-  k_gauge_force<3><<<nb, HMC_THREADS, 0, st>>>(U, Ud, g->g, c, m->d);
-  g->ctx->launches += 4;
+  k_gauge_force<<<dim3(nb, 4), HMC_THREADS, 0, st>>>(Ud, g->g, c, m->d);
+  g->ctx->launches++;
   LQCD_CK(cudaGetLastError());
   return LQCD_OK;
 }
@@ -354,16 +440,16 @@ int solve_normal_with(lqcd_engine* e, const lqcd_gauge* g, const lqcd_field* phi
   return lqcd_engine_result(e, id, x, info);
 }
 
-// refresh: rebuild the derived link copies now (else the caller does before they are read);
-// the FP64 master and the double-float copy are always both updated
-int update_links(lqcd_gauge* g, const lqcd_mom* m, double eps, bool refresh) {
+// master: also write the FP64 master and rebuild the other link copies now; else only the
+// double-float copy moves, and the caller runs links_from_df before anything else reads links
+int update_links(lqcd_gauge* g, const lqcd_mom* m, double eps, bool master) {
   float4* Ud = nullptr;
   LQCD_TRY(df_links(g, &Ud));
   k_expm_update<<<blocks(8LL * g->g.Vh, 128), 128, 0, g->ctx->stream>>>(static_cast<double2*>(g->copy[P_F64][0]),
-                                                                          Ud, g->g, m->d, eps);
+                                                                          Ud, g->g, m->d, eps, master);
   g->ctx->launches++;
   LQCD_CK(cudaGetLastError());
-  return refresh ? refresh_gauge_copies(g) : LQCD_OK;
+  return master ? refresh_gauge_copies(g, true) : LQCD_OK;
 }
 
 int kinetic_impl(const lqcd_mom* m, double* out) {
@@ -576,11 +662,13 @@ int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m, co
   // kicks at the current links are merged until the links move
   double pend_f = 0.0, pend_g = 0.0;
   int force_evals = 0, solves_iters = 0;
-  bool first_f = true, copies_stale = false;  // derived link copies are rebuilt only for the solves
+  // the drifts move only the double-float copy; the master and the solver's copies are
+  // rebuilt from it only where a fermion force, the plaquette or the caller reads them
+  bool first_f = true, copies_stale = false;
   auto flush = [&]() -> int {
     if (pend_g != 0.0) LQCD_TRY(gauge_force_impl(g, p->beta, -pend_g, m));
     if (pend_f != 0.0) {
-      if (copies_stale) LQCD_TRY(refresh_gauge_copies(g));
+      if (copies_stale) LQCD_TRY(links_from_df(g));
       copies_stale = false;
       lqcd_solve_info si{};
       LQCD_TRY(solve_normal_with(e, g, phi, p->kappa, p->mu, p->tol, x, &si));
@@ -635,7 +723,10 @@ int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m, co
     }
   }
   if (rc == LQCD_OK) rc = flush();
-  if (rc == LQCD_OK && copies_stale) rc = refresh_gauge_copies(g);
+  if (copies_stale) {  // also after a failure: the master must not stay behind the double-float copy
+    const int r2 = links_from_df(g);
+    if (rc == LQCD_OK) rc = r2;
+  }
   if (rc == LQCD_OK) rc = kinetic_impl(m, &kin1);
   if (rc == LQCD_OK) rc = lqcd_plaquette(g, &plaq1);
   const double V = 2.0 * g->g.Vh;

@@ -106,7 +106,9 @@ int dslash_tw(const lqcd_gauge* gauge, int prec, const void* in, void* out, cons
 
 // pure gauge (heatbath.cu): derived link copies rebuilt from the FP64 master; FP64
 // link layout -> host AoS layout on the device
-int refresh_gauge_copies(lqcd_gauge* g);
+int refresh_gauge_copies(lqcd_gauge* g, bool keep_df = false);
+// the FP64 master rebuilt from the double-float copy, then the other copies from the master
+int links_from_df(lqcd_gauge* g);
 cudaError_t links_to_aos(const double2* U, const Geom& g, double2* aos, cudaStream_t s);
 
 // the context's cached engine for options o and at least n slots (engine.cu)

@@ -7,8 +7,9 @@ Bars:
   * forces computed from the same solution X: 1e-12 of max|G| (FP64 both sides, the
     same arithmetic up to summation order);
   * gauge force 1e-12 (staples in double-float, unit roundoff 2^-48 = 3.6e-15);
-    exp(eps P) U 5e-14 (double-float Horner: about ten chained products of unit roundoff
-    3.6e-15); kinetic energy 1e-13 relative;
+    exp(eps P) U (2^s * 10 + 4) u per link, u = 2^-48, s the number of squarings (the
+    Taylor stage and the product with U leave a few u, each squaring doubles the error);
+    kinetic energy 1e-13 relative;
   * a short trajectory: links and momenta within 1e-8 of the oracle's (the force solves
     stop at 1e-12, so the forces differ by ~1e-10 and the trajectory inherits that),
     dH within 1e-7; reversibility on the GPU within 1e-8.
@@ -71,6 +72,16 @@ def test_fermion_force_matches_oracle(ctx, mu, t_bc):
     assert np.abs(m.download() - 0.5 * ref).max() < 1e-12 * np.abs(ref).max()
 
 
+def _expm_bar(P, eps):
+    """Per-link bar for exp(eps P) U in double-float (unit roundoff u = 2^-48): the Taylor
+    stage and the product with U each leave a few u; each of the s squarings (|eps P|_F
+    halved s times to reach 1/2) doubles the relative error and adds one product's
+    rounding, so the bound is (2^s * 10 + 4) u."""
+    nrm = eps * np.sqrt((np.abs(P) ** 2).sum(axis=(-1, -2)))
+    s = np.maximum(0, np.ceil(np.log2(np.maximum(nrm, 1e-300) / 0.5)))
+    return (2.0 ** s * 10 + 4) * 2.0 ** -48
+
+
 def test_gauge_force_update_kinetic(ctx):
     dims, beta = (6, 4, 4, 4), 5.7
     U = synth.random_links(dims, 0.7, seed=221)
@@ -86,7 +97,8 @@ def test_gauge_force_update_kinetic(ctx):
     for eps in (0.05, 0.7):  # 0.7 |P| > 1/2: exercises the scaling and squaring
         g2 = ctx.gauge(dims, U)
         lqcd.gauge_update(g2, m, eps)
-        assert np.abs(g2.download() - ohmc.expm_update(U, P, eps)).max() < 5e-14
+        err = np.abs(g2.download() - ohmc.expm_update(U, P, eps)).max(axis=(-1, -2))
+        assert (err <= _expm_bar(P, eps)).all(), (err / _expm_bar(P, eps)).max()
 
 
 @pytest.mark.parametrize("scheme", [lqcd.LEAPFROG, lqcd.TWO_MN])
