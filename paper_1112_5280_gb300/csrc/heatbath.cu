@@ -55,29 +55,79 @@ __device__ __forceinline__ void philox4x64(uint64_t c[4], uint64_t k0, uint64_t 
   }
 }
 
-__device__ __forceinline__ double unit_open0(uint64_t r) { return ((double)(r >> 11) + 1.0) * 0x1.0p-53; }
+// u = ((r >> 11) + 1) 2^-53 in (0, 1], built from its bits by integer operations (the same
+// value as the FP64 expression, which would convert a 64-bit integer on the FP64 pipe)
+__device__ __forceinline__ double unit_open0(uint64_t r) {
+  const uint64_t k = (r >> 11) + 1;  // 1 .. 2^53
+  const int p = 63 - __clzll((long long)k);
+  if (p == 53) return 1.0;
+  const uint64_t mant = (k << (52 - p)) & ((1ULL << 52) - 1);
+  return __longlong_as_double((long long)(((uint64_t)(p + 970) << 52) | mant));
+}
+// the same u rounded toward zero to 24 bits (relative error below 2^-23), for FP32 work
+__device__ __forceinline__ float unit_open0_f(uint64_t r) {
+  const uint64_t k = (r >> 11) + 1;
+  const int p = 63 - __clzll((long long)k);
+  const unsigned m = (unsigned)(p >= 23 ? k >> (p - 23) : k << (23 - p));
+  return __uint_as_float(((unsigned)(p + 74) << 23) | (m & 0x7fffffu));
+}
 
-// Creutz's SU(2) draw; false after HB_MAX_ATTEMPTS
+// Creutz's SU(2) draw; false after HB_MAX_ATTEMPTS. The accept test u1^2 <= 1 - b0^2 is an
+// FP64 decision; it is first evaluated in FP32 with t = 1 - b0 = -log1p(-u0 span) / alpha,
+// 1 - b0^2 = t (2 - t), and taken from there only when the FP32 margin is beyond the FP32
+// error (the bound: u's to 2^-23, span to ~2^-22, log1p conditioned by at most 150 while
+// u0 span <= 1 - 2^-10, so |error of 1 - b0^2| < 2.2e-4 against a margin of 2^-11); every
+// other attempt, and the accepted one's b, are computed in FP64 exactly as before.
 __device__ __noinline__ bool su2_draw(double alpha, uint64_t seed, uint64_t c0, uint64_t c1, uint64_t c2, double b[4]) {
-  const double span = -expm1(-2.0 * alpha);  // 1 - exp(-2 alpha), the same for every attempt
+  const bool flat = alpha < 1e-12;  // uniform b0 in the alpha -> 0 limit
+  const float af = (float)alpha;
+  const float span_f = flat ? 0.0f : -expm1f(-2.0f * af);
+  double span = -1.0;  // the FP64 1 - exp(-2 alpha), computed on first use
   for (int attempt = 0; attempt < HB_MAX_ATTEMPTS; ++attempt) {
     uint64_t r[4] = {c0, c1, c2, (uint64_t)attempt};
     philox4x64(r, seed, 0);
-    const double u0 = unit_open0(r[0]), u1 = unit_open0(r[1]), u2 = unit_open0(r[2]), u3 = unit_open0(r[3]);
-    const double b0 = alpha < 1e-12 ? 1.0 - 2.0 * u0 : 1.0 + log1p(-u0 * span) / alpha;
-    const double s2 = 1.0 - b0 * b0;
-    if (u1 * u1 <= s2) {
-      const double rr = sqrt(fmax(s2, 0.0));
-      const double ct = 2.0 * u2 - 1.0;
-      const double st = sqrt(fmax(1.0 - ct * ct, 0.0));
-      double sp, cp;
-      sincospi(2.0 * u3, &sp, &cp);
-      b[0] = b0;
-      b[1] = rr * st * cp;
-      b[2] = rr * st * sp;
-      b[3] = rr * ct;
-      return true;
+    int verdict = -1;  // 1 accept, 0 reject, -1 undecided in FP32
+    {
+      const float u0f = unit_open0_f(r[0]), u1f = unit_open0_f(r[1]);
+      float s2f;
+      bool ok = true;
+      if (flat) {
+        const float b0f = 1.0f - 2.0f * u0f;
+        s2f = 1.0f - b0f * b0f;
+      } else {
+        const float xf = u0f * span_f;
+        ok = xf <= 1.0f - 0x1.0p-10f;
+        const float tf = -log1pf(-xf) / af;
+        s2f = tf * (2.0f - tf);
+      }
+      const float d = u1f * u1f - s2f;
+      if (ok && isfinite(d) && fabsf(d) > 0x1.0p-11f) verdict = d < 0.0f ? 1 : 0;
     }
+    if (verdict == 0) continue;
+    const double u0 = unit_open0(r[0]);
+    double b0;
+    if (flat) {
+      b0 = 1.0 - 2.0 * u0;
+    } else {
+      if (span < 0.0) span = -expm1(-2.0 * alpha);
+      b0 = 1.0 + log1p(-u0 * span) / alpha;
+    }
+    const double s2 = 1.0 - b0 * b0;
+    if (verdict == -1) {
+      const double u1 = unit_open0(r[1]);
+      if (!(u1 * u1 <= s2)) continue;
+    }
+    const double u2 = unit_open0(r[2]), u3 = unit_open0(r[3]);
+    const double rr = sqrt(fmax(s2, 0.0));
+    const double ct = 2.0 * u2 - 1.0;
+    const double st = sqrt(fmax(1.0 - ct * ct, 0.0));
+    double sp, cp;
+    sincospi(2.0 * u3, &sp, &cp);
+    b[0] = b0;
+    b[1] = rr * st * cp;
+    b[2] = rr * st * sp;
+    b[3] = rr * ct;
+    return true;
   }
   return false;
 }

@@ -40,7 +40,7 @@ def _oracle_spread(dims, U0, beta, **kw):
 
 # ragged: V/2 = 720 is 5.6 CTAs of 128; 2^4: coinciding neighbours
 @pytest.mark.parametrize("dims", [(6, 6, 4, 10), (2, 2, 2, 2), (4, 4, 4, 8)])
-@pytest.mark.parametrize("beta", [0.0, 2.3, 6.0])
+@pytest.mark.parametrize("beta", [0.0, 2.3, 6.0, 40.0])  # 40: alpha up to ~40, span = 1 in FP32
 def test_heatbath_matches_oracle(ctx, dims, beta):
     U0 = synth.random_links(dims, 0.8, seed=1001)
     g = ctx.gauge(dims, U0, prec="f64")
