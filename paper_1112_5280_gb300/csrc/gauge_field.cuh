@@ -169,6 +169,47 @@ __device__ __forceinline__ M3 to_double(const M3d& a) {
   return m;
 }
 
+// complex double-float scalars
+__device__ __forceinline__ C2d cmul_d(const C2d& a, const C2d& b) {
+  df64 re(0.0f, 0.0f), im(0.0f, 0.0f);
+  df_mac_u(re, a.re, b.re);
+  df_mac_u(re, -a.im, b.im);
+  df_mac_u(im, a.re, b.im);
+  df_mac_u(im, a.im, b.re);
+  return {df_norm(re), df_norm(im)};
+}
+__device__ __forceinline__ C2d cadd_d(const C2d& a, const C2d& b) {
+  return {df_norm(df_add_u(a.re, b.re)), df_norm(df_add_u(a.im, b.im))};
+}
+__device__ __forceinline__ C2d csub_d(const C2d& a, const C2d& b) { return cadd_d(a, {-b.re, -b.im}); }
+__device__ __forceinline__ C2d cscale_d(df64 f, const C2d& a) { return {f * a.re, f * a.im}; }
+
+// a x + b y in double-float
+__device__ __forceinline__ C2d cmix_d(const C2d& a, const C2d& x, const C2d& b, const C2d& y) {
+  df64 re(0.0f, 0.0f), im(0.0f, 0.0f);
+  df_mac_u(re, a.re, x.re);
+  df_mac_u(re, -a.im, x.im);
+  df_mac_u(re, b.re, y.re);
+  df_mac_u(re, -b.im, y.im);
+  df_mac_u(im, a.re, x.im);
+  df_mac_u(im, a.im, x.re);
+  df_mac_u(im, b.re, y.im);
+  df_mac_u(im, b.im, y.re);
+  return {df_norm(re), df_norm(im)};
+}
+
+// 1/sqrt(n) for n > 0 in double-float: the FP32 estimate and two Newton-Raphson steps
+// y <- y + y (1 - n y^2) / 2, each of which squares the relative error
+__device__ __forceinline__ df64 df_rsqrt(df64 n) {
+  df64 y(rsqrtf(n.hi), 0.0f);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const df64 r = df64(1.0f, 0.0f) - n * (y * y);
+    y = y + y * r * df64(0.5f, 0.0f);
+  }
+  return y;
+}
+
 // c = a op(b) with op(b) = b (DAGB false) or b^dag; a^dag b when DAGA
 template <bool DAGA, bool DAGB>
 __device__ __forceinline__ M3d mul_d(const M3d& a, const M3d& b) {

@@ -1,6 +1,7 @@
 // Pure-gauge SU(3) heatbath and plaquette (paper Section 3: the pure-gauge side needs an
-// SU(3) heatbath, citing Creutz). The heatbath keeps the FP64 master copy of a gauge field
-// and its double-float copy equal: the matrix algebra runs in double-float, the draws in FP64.
+// SU(3) heatbath, citing Creutz). The sweeps run on the gauge field's double-float copy
+// (the matrix algebra in double-float on the FP32 pipes, the draws in FP64); the FP64 master
+// is rebuilt from it at the end of the call.
 //
 // Wilson action S = beta sum_P (1 - Re Tr U_P / 3). A sweep updates the links class by
 // class, mu = 0..3 and parity even, odd: the links U_mu(x) of one class share no staple,
@@ -132,29 +133,14 @@ __device__ __noinline__ bool su2_draw(double alpha, uint64_t seed, uint64_t c0, 
   return false;
 }
 
-__device__ __forceinline__ C2 to_c2(const C2d& a) { return {(double)a.re, (double)a.im}; }
-
-// a x + b y in double-float
-__device__ __forceinline__ C2d cmix_d(const C2d& a, const C2d& x, const C2d& b, const C2d& y) {
-  df64 re(0.0f, 0.0f), im(0.0f, 0.0f);
-  df_mac_u(re, a.re, x.re);
-  df_mac_u(re, -a.im, x.im);
-  df_mac_u(re, b.re, y.re);
-  df_mac_u(re, -b.im, y.im);
-  df_mac_u(im, a.re, x.im);
-  df_mac_u(im, a.im, x.re);
-  df_mac_u(im, b.re, y.im);
-  df_mac_u(im, b.im, y.re);
-  return {df_norm(re), df_norm(im)};
-}
-
-// The SU(3) algebra (staple sum, V = U W, the subgroup rotations of U and V) in
-// double-float from the copy Ud on the FP32 pipes; each subgroup's draw (k, v, Creutz)
-// in FP64 from its 2 x 2 block of V. The updated link goes to U and Ud.
+// The SU(3) and SU(2) algebra (staple sum, V = U W, the subgroup projection c and its
+// direction v = c / |c|, a = b v, the rotations of U and V) in double-float from the copy Ud
+// on the FP32 pipes; the draw of b (Creutz) and |c| in FP64. The updated link goes to Ud
+// only: the caller rebuilds the FP64 master from it.
 #ifndef LQCD_HB_MIN_BLOCKS
 #define LQCD_HB_MIN_BLOCKS 2
 #endif
-__global__ void __launch_bounds__(HB_THREADS, LQCD_HB_MIN_BLOCKS) k_heatbath(double2* U, float4* Ud, Geom g, int mu,
+__global__ void __launch_bounds__(HB_THREADS, LQCD_HB_MIN_BLOCKS) k_heatbath(float4* Ud, Geom g, int mu,
                                                                              int par, double beta, uint64_t seed,
                                                                              uint64_t sweep,
                                                                              unsigned long long* fails) {
@@ -170,34 +156,35 @@ __global__ void __launch_bounds__(HB_THREADS, LQCD_HB_MIN_BLOCKS) k_heatbath(dou
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const int i = k == 1 ? 1 : 0, j = k == 0 ? 1 : 2;  // (0,1), (1,2), (0,2)
-    const C2 x00 = to_c2(V.e[i * 3 + i]), x01 = to_c2(V.e[i * 3 + j]), x10 = to_c2(V.e[j * 3 + i]),
-             x11 = to_c2(V.e[j * 3 + j]);
-    const double c0 = x00.re + x11.re, c1 = -(x01.im + x10.im), c2 = x10.re - x01.re, c3 = -(x00.im - x11.im);
-    const double kk = sqrt(c0 * c0 + c1 * c1 + c2 * c2 + c3 * c3);
-    double v[4] = {1.0, 0.0, 0.0, 0.0};
+    // c (the SU(2) projection of the block) and |c|^2 in double-float; k = |c|, 1 / k and
+    // alpha = beta k / 3 in FP64 (the draw's input); v = c / k in double-float
+    const C2d x00 = V.e[i * 3 + i], x01 = V.e[i * 3 + j], x10 = V.e[j * 3 + i], x11 = V.e[j * 3 + j];
+    const df64 c[4] = {df_norm(df_add_u(x00.re, x11.re)), -df_norm(df_add_u(x01.im, x10.im)),
+                       df_norm(df_add_u(x10.re, -x01.re)), -df_norm(df_add_u(x00.im, -x11.im))};
+    df64 k2(0.0f, 0.0f);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) df_mac_u(k2, c[q], c[q]);
+    const double kk = sqrt((double)df_norm(k2));
+    df64 v[4] = {df64(1.0f, 0.0f), df64(0.0f, 0.0f), df64(0.0f, 0.0f), df64(0.0f, 0.0f)};
     if (kk > 0.0) {
-      const double ik = 1.0 / kk;
-      v[0] = c0 * ik;
-      v[1] = c1 * ik;
-      v[2] = c2 * ik;
-      v[3] = c3 * ik;
+      const df64 ik = df_split_bits(1.0 / kk);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = c[q] * ik;
     }
-    double b[4];
-    if (!su2_draw(beta * kk / 3.0, seed, link_id, sweep, (uint64_t)k, b)) {
+    double bd[4];
+    if (!su2_draw(beta * kk / 3.0, seed, link_id, sweep, (uint64_t)k, bd)) {
       ++nfail;
       continue;
     }
+    const df64 b[4] = {df_split_bits(bd[0]), df_split_bits(bd[1]), df_split_bits(bd[2]), df_split_bits(bd[3])};
     // a = b v with mat(q) = [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]]
-    const C2 B[4] = {{b[0], b[3]}, {b[2], b[1]}, {-b[2], b[1]}, {b[0], -b[3]}};
-    const C2 Vm[4] = {{v[0], v[3]}, {v[2], v[1]}, {-v[2], v[1]}, {v[0], -v[3]}};
+    const C2d B[4] = {{b[0], b[3]}, {b[2], b[1]}, {-b[2], b[1]}, {b[0], -b[3]}};
+    const C2d Vm[4] = {{v[0], v[3]}, {v[2], v[1]}, {-v[2], v[1]}, {v[0], -v[3]}};
     C2d A[4];
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const C2 a = cadd(cmul(B[r * 2], Vm[q]), cmul(B[r * 2 + 1], Vm[2 + q]));
-        A[r * 2 + q] = {df64(a.re), df64(a.im)};
-      }
+      for (int q = 0; q < 2; ++q) A[r * 2 + q] = cmix_d(B[r * 2], Vm[q], B[r * 2 + 1], Vm[2 + q]);
     // U <- R U and V <- R V (rows i, j; V is not needed after the last subgroup)
 #pragma unroll
     for (int col = 0; col < 3; ++col) {
@@ -211,7 +198,6 @@ __global__ void __launch_bounds__(HB_THREADS, LQCD_HB_MIN_BLOCKS) k_heatbath(dou
       }
     }
   }
-  store_link(U, g, x, mu, to_double(u));
   store_link_df(Ud, g, x, mu, u);
   if (nfail) atomicAdd(fails, (unsigned long long)nfail);
 }
@@ -224,51 +210,47 @@ __global__ void k_master_from_df(double2* U, const float4* Ud, long long n) {
   U[i] = make_double2((double)d.x + (double)d.y, (double)d.z + (double)d.w);
 }
 
-__global__ void k_reunitarise(double2* U, float4* Ud, Geom g) {
+// Gram-Schmidt of rows 0 and 1, row 2 = conj(row0 x row1), in double-float on the copy Ud
+__global__ void k_reunitarise(float4* Ud, Geom g) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // (par, mu, h)
   if (i >= 8LL * g.Vh) return;
   const int h = (int)(i % g.Vh);
   const size_t base = (size_t)(i / g.Vh) * 9 * g.Vh + h;
-  C2 r[9];
+  C2d r[9];
 #pragma unroll
-  for (int w = 0; w < 9; ++w) {
-    const double2 d = U[base + (size_t)w * g.Vh];
-    r[w] = {d.x, d.y};
+  for (int w = 0; w < 6; ++w) {
+    const float4 d = Ud[base + (size_t)w * g.Vh];
+    r[w] = {df64(d.x, d.y), df64(d.z, d.w)};
   }
-  double n0 = 0.0;
+  auto normalise_row = [&](int o) {
+    df64 n(0.0f, 0.0f);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) n0 += r[c].re * r[c].re + r[c].im * r[c].im;
-  n0 = 1.0 / sqrt(n0);
+    for (int c = 0; c < 3; ++c) {
+      df_mac_u(n, r[o + c].re, r[o + c].re);
+      df_mac_u(n, r[o + c].im, r[o + c].im);
+    }
+    const df64 s = df_rsqrt(df_norm(n));
 #pragma unroll
-  for (int c = 0; c < 3; ++c) r[c] = {r[c].re * n0, r[c].im * n0};
-  C2 p = {0.0, 0.0};  // <row0, row1>
+    for (int c = 0; c < 3; ++c) r[o + c] = cscale_d(s, r[o + c]);
+  };
+  normalise_row(0);
+  C2d p = {df64(0.0f, 0.0f), df64(0.0f, 0.0f)};  // <row0, row1> = sum row1 conj(row0)
 #pragma unroll
-  for (int c = 0; c < 3; ++c) p = cadd(p, cmulc(r[3 + c], r[c]));
+  for (int c = 0; c < 3; ++c) p = cadd_d(p, cmul_d(r[3 + c], {r[c].re, -r[c].im}));
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const C2 t = cmul(p, r[c]);
-    r[3 + c] = {r[3 + c].re - t.re, r[3 + c].im - t.im};
-  }
-  double n1 = 0.0;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) n1 += r[3 + c].re * r[3 + c].re + r[3 + c].im * r[3 + c].im;
-  n1 = 1.0 / sqrt(n1);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) r[3 + c] = {r[3 + c].re * n1, r[3 + c].im * n1};
+  for (int c = 0; c < 3; ++c) r[3 + c] = csub_d(r[3 + c], cmul_d(p, r[c]));
+  normalise_row(3);
   // row 2 = conj(row0 x row1)
   auto cr = [&](int a, int b, int c, int d) {
-    const C2 x = cmul(r[a], r[b]), y = cmul(r[c], r[d]);
-    return C2{x.re - y.re, -(x.im - y.im)};
+    const C2d x = csub_d(cmul_d(r[a], r[b]), cmul_d(r[c], r[d]));
+    return C2d{x.re, -x.im};
   };
   r[6] = cr(1, 5, 2, 4);
   r[7] = cr(2, 3, 0, 5);
   r[8] = cr(0, 4, 1, 3);
 #pragma unroll
-  for (int w = 0; w < 9; ++w) {
-    U[base + (size_t)w * g.Vh] = make_double2(r[w].re, r[w].im);
-    const df64 re(r[w].re), im(r[w].im);
-    Ud[base + (size_t)w * g.Vh] = make_float4(re.hi, re.lo, im.hi, im.lo);
-  }
+  for (int w = 0; w < 9; ++w)
+    Ud[base + (size_t)w * g.Vh] = make_float4(r[w].re.hi, r[w].re.lo, r[w].im.hi, r[w].im.lo);
 }
 
 // per-CTA partial of sum_{x, mu<nu} Re Tr U_munu(x) over the sites of both parities
@@ -378,7 +360,7 @@ int lqcd_heatbath(lqcd_gauge* g, double beta, int nsweeps, unsigned long long se
   unsigned long long* d_fails = reinterpret_cast<unsigned long long*>(c->partials);
   LQCD_CK(cudaMemsetAsync(d_fails, 0, sizeof(unsigned long long), st));
   double2* U = static_cast<double2*>(g->copy[P_F64][0]);
-  // the double-float copy the staples read, rebuilt from the master at the start
+  // the double-float copy the sweeps work on, rebuilt from the master at the start
   const void* dfbase;
   int dfnr;
   LQCD_TRY(gauge_links(g, P_DF64, &dfbase, &dfnr));
@@ -390,16 +372,16 @@ int lqcd_heatbath(lqcd_gauge* g, double beta, int nsweeps, unsigned long long se
     const uint64_t sweep = (uint64_t)(sweep0 + (unsigned long long)sw);
     for (int mu = 0; mu < 4; ++mu)
       for (int par = 0; par < 2; ++par) {
-        k_heatbath<<<grid, HB_THREADS, 0, st>>>(U, Ud, g->g, mu, par, beta, seed, sweep, d_fails);
+        k_heatbath<<<grid, HB_THREADS, 0, st>>>(Ud, g->g, mu, par, beta, seed, sweep, d_fails);
         c->launches++;
       }
     if (reunit) {
-      k_reunitarise<<<rgrid, 256, 0, st>>>(U, Ud, g->g);
+      k_reunitarise<<<rgrid, 256, 0, st>>>(Ud, g->g);
       c->launches++;
     }
     LQCD_CK(cudaGetLastError());
   }
-  LQCD_TRY(refresh_gauge_copies(g));
+  LQCD_TRY(links_from_df(g));  // the sweeps moved the double-float copy only
   unsigned long long fails = 0;
   LQCD_CK(cudaMemcpyAsync(&fails, d_fails, sizeof fails, cudaMemcpyDeviceToHost, st));
   LQCD_CK(cudaStreamSynchronize(st));

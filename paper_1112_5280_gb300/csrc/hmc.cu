@@ -211,21 +211,6 @@ __constant__ DFConst kInvFact[18] = {
     dfc(1.0 / 479001600.0), dfc(1.0 / 6227020800.0), dfc(1.0 / 87178291200.0), dfc(1.0 / 1307674368000.0),
     dfc(1.0 / 20922789888000.0), dfc(1.0 / 355687428096000.0)};
 
-// complex double-float scalars
-__device__ __forceinline__ C2d cmul_d(const C2d& a, const C2d& b) {
-  df64 re(0.0f, 0.0f), im(0.0f, 0.0f);
-  df_mac_u(re, a.re, b.re);
-  df_mac_u(re, -a.im, b.im);
-  df_mac_u(im, a.re, b.im);
-  df_mac_u(im, a.im, b.re);
-  return {df_norm(re), df_norm(im)};
-}
-__device__ __forceinline__ C2d cadd_d(const C2d& a, const C2d& b) {
-  return {df_norm(df_add_u(a.re, b.re)), df_norm(df_add_u(a.im, b.im))};
-}
-__device__ __forceinline__ C2d csub_d(const C2d& a, const C2d& b) { return cadd_d(a, {-b.re, -b.im}); }
-__device__ __forceinline__ C2d cscale_d(df64 f, const C2d& a) { return {f * a.re, f * a.im}; }
-
 // U <- exp(eps P) U in double-float: the Taylor polynomial of degree n after scaling
 // |eps P| below 1/2 (n from the norm, at most 16), then squaring; U read from the
 // double-float copy Ud, the product written to Ud and, when write_master, to the FP64
