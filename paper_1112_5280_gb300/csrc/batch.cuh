@@ -5,10 +5,13 @@
 // Work is cut into tiles of TILE consecutive half-lattice sites of one slot.
 // A launch walks its tile list with a persistent grid (CTAs per SM chosen by
 // the tuner). Norm reductions are deterministic and batch independent: every
-// tile writes one FP64 partial at partial[slot.tile0 + tile_in_slot]; the last
-// tile of a slot to finish (atomic ticket) sums that slot's partials in tile
-// order and runs the slot's scalar program (the "finisher"). So the result of
-// a slot depends only on its own geometry, never on what else is in the batch.
+// tile writes one FP64 partial at partial[slot.tile0 + tile_in_slot]; a second,
+// small launch right after (k_finish, one CTA per slot) sums each slot's partials
+// in tile order and runs the slot's scalar program (the "finisher"). So the
+// result of a slot depends only on its own geometry, never on what else is in
+// the batch or on the grid. (The kernel boundary orders the partials; a ticket
+// inside the main kernel cost a fence and an atomic per tile and left one CTA
+// summing all partials, about 90 us per launch at 16 k tiles.)
 #pragma once
 
 #include "dslash.cuh"
@@ -59,8 +62,7 @@ struct Scalars {
   double cres[8];   // complex scalars (BiCGStab): re, im pairs
   int state, status, iter, maxiter, last, n_updates, restart_p;
   int normal;       // 1: solve Mhat^dag Mhat x = phi; converged on |phi - Mhat^dag Mhat x|
-  unsigned counter;
-  unsigned pad2[3];
+  unsigned pad2[4];
 };
 
 // One slot's operands for one batched kernel.
@@ -101,6 +103,7 @@ struct Launch {
   int ntiles;              // total tiles
   int interleave;          // 1: tile t -> (slot t % nslots, block t / nslots), equal Vh
   double* partials;
+  int finish;              // 1: the slots' Works reduce or finish; k_finish follows the launch
 };
 
 __device__ __forceinline__ const Work& work_of(const Launch& L, int slot) {
@@ -352,14 +355,12 @@ __device__ __noinline__ static void run_fin_bicg(const Work& w, const double* v)
   }
 }
 
-// Called by all threads of the CTA after its tile: records the partial sums, and
-// the slot's last tile sums all partials of the slot (in tile order) and runs
-// the finisher. Partials are strided by 3 (up to three sums per reduction).
+// Called by all threads of the CTA after its tile: records the tile's partial sums
+// (strided by 3: up to three sums per reduction) for k_finish.
 template <int NT>
-__device__ __forceinline__ void tile_finish(const Work& w, int tile_in_slot, double v0, double v1,
-                                            double v2, double* partials) {
+__device__ __forceinline__ void tile_partial(const Work& w, int tile_in_slot, double v0, double v1,
+                                             double v2, double* partials) {
   __shared__ double sh[NT / 32];
-  __shared__ int am_last;
   if (!w.red && w.fin == FIN_NONE) return;
   const int ns = (w.red >= 2) ? 3 : 1;
   double s[3];
@@ -371,27 +372,43 @@ __device__ __forceinline__ void tile_finish(const Work& w, int tile_in_slot, dou
   if (threadIdx.x == 0) {
     double* dst = partials + 3 * (size_t)(w.tile0 + tile_in_slot);
     for (int k = 0; k < ns; ++k) dst[k] = s[k];
-    __threadfence();
-    const unsigned ticket = atomicAdd(&w.sc->counter, 1u);
-    am_last = (ticket == (unsigned)w.ntiles - 1);
   }
-  __syncthreads();
-  if (am_last) {
-    __threadfence();
-    double acc[3] = {0, 0, 0};
-    for (int i = threadIdx.x; i < w.ntiles; i += NT) {
-      const double* src = partials + 3 * (size_t)(w.tile0 + i);
-      for (int k = 0; k < ns; ++k) acc[k] += __ldcg(src + k);
+}
+
+constexpr int FINISH_THREADS = 256;
+
+// Body of k_finish: CTA blockIdx.x sums the partials of slot blockIdx.x in a fixed order
+// (thread t adds tiles t, t + 256, t + 512, ... in that order, 4 loads in flight; then
+// block_sum) and runs the slot's finisher. Slots that did not run the step are skipped,
+// exactly as the main kernel skipped them.
+__device__ __forceinline__ void finish_slot(const Launch& L) {
+  __shared__ double sh[FINISH_THREADS / 32];
+  const int slot = blockIdx.x;
+  if (slot >= L.nslots) return;
+  const Work& w = work_of(L, slot);
+  if ((!w.red && w.fin == FIN_NONE) || !slot_runs(w)) return;
+  const int ns = (w.red >= 2) ? 3 : 1;
+  constexpr int UNR = 4;
+  double acc[3] = {0, 0, 0};
+  for (int i0 = threadIdx.x; i0 < w.ntiles; i0 += UNR * FINISH_THREADS) {
+    double x[UNR][3];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const int i = i0 + u * FINISH_THREADS;
+      const double* src = L.partials + 3 * (size_t)(w.tile0 + (i < w.ntiles ? i : 0));
+#pragma unroll
+      for (int k = 0; k < 3; ++k) x[u][k] = (k < ns) ? src[k] : 0.0;
     }
-    double tot[3] = {0, 0, 0};
-    for (int k = 0; k < ns; ++k) tot[k] = block_sum<NT>(acc[k], sh);
-    if (threadIdx.x == 0) {
-      w.sc->counter = 0;
-      run_fin(w, tot);
-      __threadfence();
-    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u)
+      if (i0 + u * FINISH_THREADS < w.ntiles)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          if (k < ns) acc[k] += x[u][k];
   }
-  __syncthreads();
+  double tot[3] = {0, 0, 0};
+  for (int k = 0; k < ns; ++k) tot[k] = block_sum<FINISH_THREADS>(acc[k], sh);
+  if (threadIdx.x == 0) run_fin(w, tot);
 }
 
 }  // namespace lqcd

@@ -35,7 +35,6 @@ __global__ void k_bicg_init(Scalars* s, double delta2, int maxiter) {
   s->maxiter = maxiter;
   s->state = S_RUNNING;
   s->status = ST_OK;
-  s->counter = 0;
 }
 
 }  // namespace lqcd

@@ -123,6 +123,7 @@ Launch single_launch(const Work& w, double* partials) {
   L.nslots = 1;
   L.ntiles = w.ntiles;
   L.partials = partials;
+  L.finish = (partials && (w.red || w.fin != FIN_NONE)) ? 1 : 0;
   return L;
 }
 

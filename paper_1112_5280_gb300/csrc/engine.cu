@@ -64,7 +64,6 @@ __global__ void k_slot_init(Scalars* s, double tol2, double nreal, int maxiter, 
   s->alpha = s->beta = 0.0;
   s->rr_max = 0.0;
   s->stop_rr = 0.0;
-  s->counter = 0;
 }
 
 __global__ void k_slot_cancel(Scalars* s, int status) {
@@ -292,7 +291,7 @@ StepKind kind_of(int s) {
 // untwisted slots carry the identity twist there and give the same bits)
 cudaError_t issue(lqcd_engine* e, int s, const Launch& L, bool tw) {
   const StepKind k = kind_of(s);
-  e->ctx->launches++;
+  e->ctx->launches += L.finish ? 2 : 1;
   if (k.dslash) {
     const int epi = k.epi_or_op + (tw ? EPI_LIN_TW - EPI_LIN : 0);
     if (k.f64) return launch_dslash(e->tp, 18, k.dag, epi, L, 0, e->ctx->stream);
@@ -311,6 +310,11 @@ Launch batch_launch(const lqcd_engine* e, int s) {
   L.ntiles = e->ntiles_total;
   L.interleave = e->interleave;
   L.partials = e->d_partials;
+  // k_finish follows when any active slot's Work of this step reduces or runs a finisher
+  for (int i = 0; i < L.nslots && !L.finish; ++i) {
+    const Work& w = e->h_works[(size_t)s * e->max_slots + i];
+    L.finish = ((w.red || w.fin != FIN_NONE) && w.run_if != S_NEVER) ? 1 : 0;
+  }
   return L;
 }
 

@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(TILE, DslashMinBlocks<SP>::value) k_dslash(con
         SpinorIO<XSloppy<SP>::P>::store(w.z, w.g.Vh, h, x);
       }
     }
-    tile_finish<TILE>(w, start / TILE, v0, v1, v2, L.partials);
+    tile_partial<TILE>(w, start / TILE, v0, v1, v2, L.partials);
   }
 }
 
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(3 * TILE, LQCD_DSLASH3_MIN_BLOCKS) k_dslash3(c
         SpinorIO<XSloppy<SP>::P>::store_colour(w.z, Vh, h, col, x);
       }
     }
-    tile_finish<3 * TILE>(w, start / TILE, v0, v1, v2, L.partials);
+    tile_partial<3 * TILE>(w, start / TILE, v0, v1, v2, L.partials);
   }
 }
 
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(TILE) k_blas(const Launch L) {
         v2 = site_norm2(r);
       }
     }
-    tile_finish<TILE>(w, start / TILE, v0, v1, v2, L.partials);
+    tile_partial<TILE>(w, start / TILE, v0, v1, v2, L.partials);
   }
 }
 

@@ -252,14 +252,23 @@ cudaError_t spinor_convert(const void* in, int pin, void* out, int pout, int Vh,
 
 // ------------------------------------------------------------------ dispatch
 
+// the slots' reduction totals and scalar finishers of the launch just issued on s
+__global__ void __launch_bounds__(FINISH_THREADS) k_finish(const Launch L) { finish_slot(L); }
+
+static cudaError_t then_finish(cudaError_t err, const Launch& L, cudaStream_t s) {
+  if (err != cudaSuccess || !L.finish) return err;
+  k_finish<<<L.nslots, FINISH_THREADS, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_dslash(int sp, int nr, bool dag, int epi, const Launch& L, int grid,
                           cudaStream_t s, int form) {
   switch (sp) {
-    case P_F64: return launch_dslash_f64(nr, dag, epi, L, grid, s, form);
-    case P_F32: return launch_dslash_f32(nr, dag, epi, L, grid, s, form);
-    case P_F16: return launch_dslash_f16(nr, dag, epi, L, grid, s, form);
-    case P_BF16: return launch_dslash_bf16(nr, dag, epi, L, grid, s, form);
-    case P_DF64: return launch_dslash_df64(nr, dag, epi, L, grid, s, form);
+    case P_F64: return then_finish(launch_dslash_f64(nr, dag, epi, L, grid, s, form), L, s);
+    case P_F32: return then_finish(launch_dslash_f32(nr, dag, epi, L, grid, s, form), L, s);
+    case P_F16: return then_finish(launch_dslash_f16(nr, dag, epi, L, grid, s, form), L, s);
+    case P_BF16: return then_finish(launch_dslash_bf16(nr, dag, epi, L, grid, s, form), L, s);
+    case P_DF64: return then_finish(launch_dslash_df64(nr, dag, epi, L, grid, s, form), L, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -277,11 +286,11 @@ int dslash_occupancy(int sp, int nr, int form) {
 
 cudaError_t launch_blas(int sp, int op, const Launch& L, int grid, cudaStream_t s, int tp) {
   switch (sp) {
-    case P_F64: return launch_blas_f64(op, tp, L, grid, s);
-    case P_F32: return launch_blas_f32(op, tp, L, grid, s);
-    case P_F16: return launch_blas_f16(op, tp, L, grid, s);
-    case P_BF16: return launch_blas_bf16(op, tp, L, grid, s);
-    case P_DF64: return launch_blas_df64(op, tp, L, grid, s);
+    case P_F64: return then_finish(launch_blas_f64(op, tp, L, grid, s), L, s);
+    case P_F32: return then_finish(launch_blas_f32(op, tp, L, grid, s), L, s);
+    case P_F16: return then_finish(launch_blas_f16(op, tp, L, grid, s), L, s);
+    case P_BF16: return then_finish(launch_blas_bf16(op, tp, L, grid, s), L, s);
+    case P_DF64: return then_finish(launch_blas_df64(op, tp, L, grid, s), L, s);
   }
   return cudaErrorInvalidValue;
 }
