@@ -24,6 +24,10 @@ namespace lqcd {
 constexpr int TILE = LQCD_TILE;   // sites per tile (one tile per CTA pass of a batched kernel)
 constexpr int MAX_SLOTS = 1024;   // slots in one launch
 
+// Dslash epilogues. EPI_PLAIN: EPI_LIN for launches in which no slot reduces or runs a
+// finisher (chosen by launch_dslash), compiled without the reduction code.
+enum Epi { EPI_LIN = 0, EPI_CG = 1, EPI_LIN_TW = 2, EPI_CG_TW = 3, EPI_PLAIN = 4 };
+
 // Slot state machine of the Krylov engine.
 enum SlotState { S_RUNNING = 0, S_UPDATE = 1, S_DONE = 2, S_FAILED = 3, S_IDLE = 4 };
 // run_if of a step that a slot never takes (the other reliable-update path)

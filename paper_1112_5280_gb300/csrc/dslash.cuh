@@ -416,4 +416,118 @@ __device__ __forceinline__ void dslash_site3(const Geom& g, int h, int out_par, 
   }
 }
 
+// ---------------------------------------------------------------- colour split, shared
+// projections (double-float)
+//
+// The three threads of a site (colour col = 0, 1, 2, in different warps of the CTA) each
+// need the projected half spinor h of all three colours of a neighbour. Each thread loads
+// and projects only its own colour and publishes it in shared memory; after a barrier it
+// reads the other two. Per hop that is one third of the spinor loads and projections of
+// the unshared form, at the cost of one CTA barrier per hop (two buffers alternate, so one
+// barrier per hop suffices). Every thread of the CTA must run all 8 hops: threads past
+// the end of the lattice pass a clamped site and discard the result.
+
+// one buffer: [colour][h0 | h1][tile site] of (re.hi, re.lo, im.hi, im.lo)
+template <int NT>
+struct ProjShare {
+  float4 h[2][3][2][NT];
+};
+
+__device__ __forceinline__ float4 pack_c(const Cx<df64>& a) { return make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
+__device__ __forceinline__ Cx<df64> unpack_c(const float4& d) { return {df64(d.x, d.y), df64(d.z, d.w)}; }
+
+template <int K, int LP, bool DAG, int NT>
+__device__ __forceinline__ void hop3s_df(const Geom& g, int h, const int nf[4], const int nb[4], int t,
+                                         const void* in, const void* Uout, const void* Uin, int col, int j,
+                                         df64 acc[8], ProjShare<NT>& sh) {
+  constexpr int MU = K / 2;
+  constexpr bool FWD = (K % 2) == 0;
+  constexpr int S = FWD ? (DAG ? 1 : -1) : (DAG ? -1 : 1);
+  const int n = FWD ? nf[MU] : nb[MU];
+  df64 v[8];
+  SpinorIO<P_DF64>::load_colour(in, g.Vh, n, col, v);
+  const Cx<df64> p0{v[0], v[1]}, p1{v[2], v[3]}, p2{v[4], v[5]}, p3{v[6], v[7]};
+  Cx<df64> h0, h1;
+  if (MU == 0) {
+    h0 = {df_add_u(p0.re, S * p3.im), df_add_u(p0.im, S * -p3.re)};
+    h1 = {df_add_u(p1.re, S * p2.im), df_add_u(p1.im, S * -p2.re)};
+  } else if (MU == 1) {
+    h0 = {df_add_u(p0.re, S * -p3.re), df_add_u(p0.im, S * -p3.im)};
+    h1 = {df_add_u(p1.re, S * p2.re), df_add_u(p1.im, S * p2.im)};
+  } else if (MU == 2) {
+    h0 = {df_add_u(p0.re, S * p2.im), df_add_u(p0.im, S * -p2.re)};
+    h1 = {df_add_u(p1.re, S * -p3.im), df_add_u(p1.im, S * p3.re)};
+  } else {
+    h0 = {df_add_u(p0.re, S * p2.re), df_add_u(p0.im, S * p2.im)};
+    h1 = {df_add_u(p1.re, S * p3.re), df_add_u(p1.im, S * p3.im)};
+  }
+  float4 (&buf)[3][2][NT] = sh.h[K & 1];
+  buf[col][0][j] = pack_c(h0);
+  buf[col][1][j] = pack_c(h1);
+  // row col of U (forward) or of U(x - mu)^dag (backward)
+  df64 r[6];
+  {
+    const char* base = link_dir<LP, 18>(FWD ? Uout : Uin, g.Vh, MU);
+    const int hl = FWD ? h : n;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int word = FWD ? (3 * col + b) : (3 * b + col);
+      const float4 d = ld_stream(reinterpret_cast<const float4*>(base) + hl + (size_t)word * g.Vh);
+      r[2 * b] = df64(d.x, d.y);
+      r[2 * b + 1] = FWD ? df64(d.z, d.w) : df64(-d.z, -d.w);
+    }
+  }
+  __syncthreads();
+  Cx<df64> w0{df64(0.0f, 0.0f), df64(0.0f, 0.0f)}, w1 = w0;
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const Cx<df64> hb0 = unpack_c(buf[b][0][j]), hb1 = unpack_c(buf[b][1][j]);
+    const df64 rr = r[2 * b], ri = r[2 * b + 1];
+    df_mac_u(w0.re, rr, hb0.re);
+    df_mac_u(w0.re, -ri, hb0.im);
+    df_mac_u(w0.im, rr, hb0.im);
+    df_mac_u(w0.im, ri, hb0.re);
+    df_mac_u(w1.re, rr, hb1.re);
+    df_mac_u(w1.re, -ri, hb1.im);
+    df_mac_u(w1.im, rr, hb1.im);
+    df_mac_u(w1.im, ri, hb1.re);
+  }
+  const int eta = (MU == 3 && t == (FWD ? g.L[3] - 1 : 0)) ? g.t_bc : 1;
+  if (MU == 3 && eta < 0) {
+    w0 = sgn<-1>(w0);
+    w1 = sgn<-1>(w1);
+  }
+  acc[0] = df_add_u(acc[0], w0.re); acc[1] = df_add_u(acc[1], w0.im);
+  acc[2] = df_add_u(acc[2], w1.re); acc[3] = df_add_u(acc[3], w1.im);
+  Cx<df64> l2, l3;
+  if (MU == 0) { l2 = sgn<S>(mul_i(w1)); l3 = sgn<S>(mul_i(w0)); }
+  else if (MU == 1) { l2 = sgn<S>(w1); l3 = sgn<-S>(w0); }
+  else if (MU == 2) { l2 = sgn<S>(mul_i(w0)); l3 = sgn<-S>(mul_i(w1)); }
+  else { l2 = sgn<S>(w0); l3 = sgn<S>(w1); }
+  acc[4] = df_add_u(acc[4], l2.re); acc[5] = df_add_u(acc[5], l2.im);
+  acc[6] = df_add_u(acc[6], l3.re); acc[7] = df_add_u(acc[7], l3.im);
+}
+
+// acc = colour col of (D_{p,1-p} in)(h) in double-float, 18-real double-float links; all
+// 3 NT threads of the CTA call it together (thread j of colour col: site h)
+template <int LP, bool DAG, int NT>
+__device__ __forceinline__ void dslash_site3s_df(const Geom& g, int h, int out_par, const void* in,
+                                                 const void* Uout, const void* Uin, int col, int j,
+                                                 df64 acc[8], ProjShare<NT>& sh) {
+  int nf[4], nb[4], t;
+  neighbours(g, h, out_par, nf, nb, t);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc[i] = df64(0.0f, 0.0f);
+  hop3s_df<0, LP, DAG, NT>(g, h, nf, nb, t, in, Uout, Uin, col, j, acc, sh);
+  hop3s_df<1, LP, DAG, NT>(g, h, nf, nb, t, in, Uout, Uin, col, j, acc, sh);
+  hop3s_df<2, LP, DAG, NT>(g, h, nf, nb, t, in, Uout, Uin, col, j, acc, sh);
+  hop3s_df<3, LP, DAG, NT>(g, h, nf, nb, t, in, Uout, Uin, col, j, acc, sh);
+  hop3s_df<4, LP, DAG, NT>(g, h, nf, nb, t, in, Uout, Uin, col, j, acc, sh);
+  hop3s_df<5, LP, DAG, NT>(g, h, nf, nb, t, in, Uout, Uin, col, j, acc, sh);
+  hop3s_df<6, LP, DAG, NT>(g, h, nf, nb, t, in, Uout, Uin, col, j, acc, sh);
+  hop3s_df<7, LP, DAG, NT>(g, h, nf, nb, t, in, Uout, Uin, col, j, acc, sh);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc[i] = df_norm(acc[i]);
+}
+
 }  // namespace lqcd

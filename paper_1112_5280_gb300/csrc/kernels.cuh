@@ -9,11 +9,11 @@ namespace lqcd {
 // EPI_*_TW: the same epilogues with the twisted-mass factors of the Work (site-diagonal
 // s (1 + i t g5) on the hopping term and on the operand vector); separate instantiations
 // keep the Wilson kernels free of the twist code.
-enum Epi { EPI_LIN = 0, EPI_CG = 1, EPI_LIN_TW = 2, EPI_CG_TW = 3 };
 template <int EPI>
 struct EpiTraits {
-  static constexpr bool lin = (EPI == EPI_LIN || EPI == EPI_LIN_TW);
+  static constexpr bool lin = (EPI == EPI_LIN || EPI == EPI_LIN_TW || EPI == EPI_PLAIN);
   static constexpr bool tw = (EPI == EPI_LIN_TW || EPI == EPI_CG_TW);
+  static constexpr bool red = (EPI != EPI_PLAIN);
 };
 
 // Occupancy target (CTAs of TILE threads per SM) of the Dslash: 6 leaves 168
@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(TILE, DslashMinBlocks<SP>::value) k_dslash(con
           for (int i = 0; i < 24; ++i) acc[i] += c * y2[i];
         }
         SpinorIO<SP>::store(w.out, w.g.Vh, h, acc);
-        if (w.red == 1) {
+        if (!EpiTraits<EPI>::red) {
+        } else if (w.red == 1) {
           v0 = site_norm2(acc);
         } else if (w.red == 2) {
           R z[24];
@@ -178,13 +179,14 @@ __global__ void __launch_bounds__(TILE, DslashMinBlocks<SP>::value) k_dslash(con
         SpinorIO<XSloppy<SP>::P>::store(w.z, w.g.Vh, h, x);
       }
     }
-    tile_partial<TILE>(w, start / TILE, v0, v1, v2, L.partials);
+    if constexpr (EpiTraits<EPI>::red) tile_partial<TILE>(w, start / TILE, v0, v1, v2, L.partials);
   }
 }
 
-// Colour-split batched Dslash for 18-real links: 3 * TILE threads per CTA, threads
-// [c * TILE, (c + 1) * TILE) compute colour c of the tile's TILE sites. Same epilogues,
-// reductions and finishers as k_dslash (colour-local pieces of each site).
+// Colour-split batched Dslash for 18-real double-float links: 3 * TILE threads per CTA,
+// threads [c * TILE, (c + 1) * TILE) compute colour c of the tile's TILE sites, sharing
+// each hop's projected half spinors through shared memory. Same epilogues, reductions
+// and finishers as k_dslash (colour-local pieces of each site).
 template <typename R>
 __device__ __forceinline__ double colour_norm2(const R v[8]) {
   R s = 0;
@@ -210,6 +212,8 @@ __device__ __forceinline__ void colour_dot(const R a[8], const R b[8], double& r
 template <int SP, int LP, bool DAG, int EPI>
 __global__ void __launch_bounds__(3 * TILE, LQCD_DSLASH3_MIN_BLOCKS) k_dslash3(const Launch L) {
   using R = typename SpinorIO<SP>::Real;
+  static_assert(SP == P_DF64 && LP == P_DF64, "the colour-split form is built for double-float");
+  __shared__ ProjShare<TILE> sh;
   if (single_slot_idle(L)) return;
   const int col = threadIdx.x / TILE;
   const int j = threadIdx.x - col * TILE;
@@ -221,11 +225,11 @@ __global__ void __launch_bounds__(3 * TILE, LQCD_DSLASH3_MIN_BLOCKS) k_dslash3(c
     const int h = start + j;
     const int Vh = w.g.Vh;
     double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+    // every thread runs the hops (they share projections through barriers); a thread
+    // past the end of the lattice takes the last site and drops the result
+    R acc[8];
+    dslash_site3s_df<LP, DAG, TILE>(w.g, h < Vh ? h : Vh - 1, w.out_par, w.in, w.Uout, w.Uin, col, j, acc, sh);
     if (h < Vh) {
-      R acc[8];
-      if (col == 0) dslash_site3<SP, LP, DAG, 0>(w.g, h, w.out_par, w.in, w.Uout, w.Uin, acc);
-      else if (col == 1) dslash_site3<SP, LP, DAG, 1>(w.g, h, w.out_par, w.in, w.Uout, w.Uin, acc);
-      else dslash_site3<SP, LP, DAG, 2>(w.g, h, w.out_par, w.in, w.Uout, w.Uin, acc);
       const R a = (R)w.a;
       if constexpr (EpiTraits<EPI>::lin) {
 #pragma unroll
@@ -247,7 +251,8 @@ __global__ void __launch_bounds__(3 * TILE, LQCD_DSLASH3_MIN_BLOCKS) k_dslash3(c
           for (int i = 0; i < 8; ++i) acc[i] += c * y2[i];
         }
         SpinorIO<SP>::store_colour(w.out, Vh, h, col, acc);
-        if (w.red == 1) {
+        if (!EpiTraits<EPI>::red) {
+        } else if (w.red == 1) {
           v0 = colour_norm2(acc);
         } else if (w.red == 2) {
           R z[8];
@@ -280,7 +285,7 @@ __global__ void __launch_bounds__(3 * TILE, LQCD_DSLASH3_MIN_BLOCKS) k_dslash3(c
         SpinorIO<XSloppy<SP>::P>::store_colour(w.z, Vh, h, col, x);
       }
     }
-    tile_partial<3 * TILE>(w, start / TILE, v0, v1, v2, L.partials);
+    if constexpr (EpiTraits<EPI>::red) tile_partial<3 * TILE>(w, start / TILE, v0, v1, v2, L.partials);
   }
 }
 

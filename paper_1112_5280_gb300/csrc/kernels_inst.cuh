@@ -90,6 +90,8 @@ cudaError_t dispatch_nr(bool dag, int epi, const Launch& L, int grid, cudaStream
   switch (epi) {
     case EPI_LIN: return dag ? go_dslash<NR, true, EPI_LIN>(L, grid, s, form)
                              : go_dslash<NR, false, EPI_LIN>(L, grid, s, form);
+    case EPI_PLAIN: return dag ? go_dslash<NR, true, EPI_PLAIN>(L, grid, s, form)
+                               : go_dslash<NR, false, EPI_PLAIN>(L, grid, s, form);
     case EPI_CG: if (dag) return go_dslash<NR, true, EPI_CG>(L, grid, s, form); break;
     case EPI_LIN_TW:
     case EPI_CG_TW:

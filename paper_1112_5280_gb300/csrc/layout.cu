@@ -263,6 +263,11 @@ static cudaError_t then_finish(cudaError_t err, const Launch& L, cudaStream_t s)
 
 cudaError_t launch_dslash(int sp, int nr, bool dag, int epi, const Launch& L, int grid,
                           cudaStream_t s, int form) {
+  // no slot reduces or finishes: the instantiation without the reduction code (a batched
+  // launch's finish flag covers its running slots; an inline Work says so itself)
+  if (epi == EPI_LIN && !L.finish &&
+      (L.works || (!L.inline_work.red && L.inline_work.fin == FIN_NONE)))
+    epi = EPI_PLAIN;
   switch (sp) {
     case P_F64: return then_finish(launch_dslash_f64(nr, dag, epi, L, grid, s, form), L, s);
     case P_F32: return then_finish(launch_dslash_f32(nr, dag, epi, L, grid, s, form), L, s);
