@@ -6,8 +6,8 @@
 // A launch walks its tile list with a persistent grid (CTAs per SM chosen by
 // the tuner). Norm reductions are deterministic and batch independent: every
 // tile writes one FP64 partial at partial[slot.tile0 + tile_in_slot]; a second,
-// small launch right after (k_finish, one CTA per slot) sums each slot's partials
-// in tile order and runs the slot's scalar program (the "finisher"). So the
+// small launch right after (k_finish in finish.cu) sums each slot's partials in
+// tile order and runs the slot's scalar program (the "finisher"). So the
 // result of a slot depends only on its own geometry, never on what else is in
 // the batch or on the grid. (The kernel boundary orders the partials; a ticket
 // inside the main kernel cost a fence and an atomic per tile and left one CTA
@@ -66,7 +66,8 @@ struct Scalars {
   double cres[8];   // complex scalars (BiCGStab): re, im pairs
   int state, status, iter, maxiter, last, n_updates, restart_p;
   int normal;       // 1: solve Mhat^dag Mhat x = phi; converged on |phi - Mhat^dag Mhat x|
-  unsigned pad2[4];
+  unsigned ticket;  // k_finish groups done (reset by the last)
+  unsigned pad2[3];
 };
 
 // One slot's operands for one batched kernel.
@@ -359,60 +360,45 @@ __device__ __noinline__ static void run_fin_bicg(const Work& w, const double* v)
   }
 }
 
-// Called by all threads of the CTA after its tile: records the tile's partial sums
-// (strided by 3: up to three sums per reduction) for k_finish.
+// The same for site values that are FP32 numbers (sloppy precisions): the warp stage adds
+// in FP32 (FP64 runs at 1/64 of the FP32 rate here), the warps' sums are added in FP64.
 template <int NT>
+__device__ __forceinline__ double block_sum_f32(double v, double* sh) {
+  float x = (float)v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = (double)x;
+  __syncthreads();
+  double s = 0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) s += sh[i];
+  }
+  __syncthreads();
+  return s;
+}
+
+// Called by all threads of the CTA after its tile: records the tile's partial sums
+// (strided by 3: up to three sums per reduction) for k_finish. F32: the site values
+// are FP32 sums (sloppy kernels).
+template <int NT, bool F32 = false>
 __device__ __forceinline__ void tile_partial(const Work& w, int tile_in_slot, double v0, double v1,
                                              double v2, double* partials) {
   __shared__ double sh[NT / 32];
   if (!w.red && w.fin == FIN_NONE) return;
   const int ns = (w.red >= 2) ? 3 : 1;
+  auto bsum = [&](double v) { return F32 ? block_sum_f32<NT>(v, sh) : block_sum<NT>(v, sh); };
   double s[3];
-  s[0] = block_sum<NT>(v0, sh);
+  s[0] = bsum(v0);
   if (ns == 3) {
-    s[1] = block_sum<NT>(v1, sh);
-    s[2] = block_sum<NT>(v2, sh);
+    s[1] = bsum(v1);
+    s[2] = bsum(v2);
   }
   if (threadIdx.x == 0) {
     double* dst = partials + 3 * (size_t)(w.tile0 + tile_in_slot);
     for (int k = 0; k < ns; ++k) dst[k] = s[k];
   }
-}
-
-constexpr int FINISH_THREADS = 256;
-
-// Body of k_finish: CTA blockIdx.x sums the partials of slot blockIdx.x in a fixed order
-// (thread t adds tiles t, t + 256, t + 512, ... in that order, 4 loads in flight; then
-// block_sum) and runs the slot's finisher. Slots that did not run the step are skipped,
-// exactly as the main kernel skipped them.
-__device__ __forceinline__ void finish_slot(const Launch& L) {
-  __shared__ double sh[FINISH_THREADS / 32];
-  const int slot = blockIdx.x;
-  if (slot >= L.nslots) return;
-  const Work& w = work_of(L, slot);
-  if ((!w.red && w.fin == FIN_NONE) || !slot_runs(w)) return;
-  const int ns = (w.red >= 2) ? 3 : 1;
-  constexpr int UNR = 4;
-  double acc[3] = {0, 0, 0};
-  for (int i0 = threadIdx.x; i0 < w.ntiles; i0 += UNR * FINISH_THREADS) {
-    double x[UNR][3];
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      const int i = i0 + u * FINISH_THREADS;
-      const double* src = L.partials + 3 * (size_t)(w.tile0 + (i < w.ntiles ? i : 0));
-#pragma unroll
-      for (int k = 0; k < 3; ++k) x[u][k] = (k < ns) ? src[k] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < UNR; ++u)
-      if (i0 + u * FINISH_THREADS < w.ntiles)
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-          if (k < ns) acc[k] += x[u][k];
-  }
-  double tot[3] = {0, 0, 0};
-  for (int k = 0; k < ns; ++k) tot[k] = block_sum<FINISH_THREADS>(acc[k], sh);
-  if (threadIdx.x == 0) run_fin(w, tot);
 }
 
 }  // namespace lqcd

@@ -35,6 +35,7 @@ __global__ void k_bicg_init(Scalars* s, double delta2, int maxiter) {
   s->maxiter = maxiter;
   s->state = S_RUNNING;
   s->status = ST_OK;
+  s->ticket = 0;
 }
 
 }  // namespace lqcd

@@ -64,6 +64,7 @@ __global__ void k_slot_init(Scalars* s, double tol2, double nreal, int maxiter, 
   s->alpha = s->beta = 0.0;
   s->rr_max = 0.0;
   s->stop_rr = 0.0;
+  s->ticket = 0;
 }
 
 __global__ void k_slot_cancel(Scalars* s, int status) {

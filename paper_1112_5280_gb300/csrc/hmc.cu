@@ -384,13 +384,27 @@ int half_norm2(lqcd_ctx* c, const void* half, const Geom& g, double* out, const 
 }
 
 // From X (even half of x, FP64): Y = Mhat X, the odd halves of Phi and Psi, S_f and
-// P += coeff G_f. x and y are FULL FP64 fields (their odd halves are overwritten).
+// P += coeff G_f. x and y are FULL FP64 fields (their odd halves are overwritten); xd and yd
+// are FULL double-float work fields: the four Dslash applications (Mhat X, D_oe X and
+// D^dag_oe Y) run in double-float (FP64 runs at 1/64 of the FP32 rate here), and Y, Phi_o
+// and Psi_o return to FP64 for the force kernel.
 // S_f: with phi, the variational 2 Re <phi, X> - |Y|^2, whose error is quadratic in the
 // solve's (X = X* - e gives S* - |Mhat e|^2); without, |Y|^2 = phi^dag X (linear error).
 int fermion_force_from_x(const lqcd_gauge* g, double kappa, double mu, lqcd_field* x, lqcd_field* y,
-                         double coeff, lqcd_mom* m, double* s_f, const lqcd_field* phi = nullptr) {
+                         lqcd_field* xd, lqcd_field* yd, double coeff, lqcd_mom* m, double* s_f,
+                         const lqcd_field* phi = nullptr) {
   const double a = 2.0 * kappa * mu, s = 1.0 / (1.0 + a * a);
-  LQCD_TRY(lqcd_apply_Mhat_tm(g, kappa, mu, x, y, 0));
+  const int Vh = g->g.Vh;
+  cudaStream_t st = g->ctx->stream;
+  LQCD_CK(spinor_convert(x->half[0], P_F64, xd->half[0], P_DF64, Vh, 1.0, st));
+  LQCD_TRY(lqcd_apply_Mhat_tm(g, kappa, mu, xd, yd, 0));
+  // Phi_o = A^-1 D_oe X_e, Psi_o = A^-dag (D^dag)_oe Y_e
+  LQCD_TRY(dslash_tw(g, P_DF64, xd->half[0], xd->half[1], nullptr, nullptr, 1.0, 0.0, 0.0, 1, false, s, -a, 0.0));
+  LQCD_TRY(dslash_tw(g, P_DF64, yd->half[0], yd->half[1], nullptr, nullptr, 1.0, 0.0, 0.0, 1, true, s, a, 0.0));
+  LQCD_CK(spinor_convert(yd->half[0], P_DF64, y->half[0], P_F64, Vh, 1.0, st));
+  LQCD_CK(spinor_convert(xd->half[1], P_DF64, x->half[1], P_F64, Vh, 1.0, st));
+  LQCD_CK(spinor_convert(yd->half[1], P_DF64, y->half[1], P_F64, Vh, 1.0, st));
+  g->ctx->launches += 4;
   double yy = 0.0;
   LQCD_TRY(half_norm2(g->ctx, y->half[0], g->g, &yy));
   if (phi) {
@@ -399,13 +413,9 @@ int fermion_force_from_x(const lqcd_gauge* g, double kappa, double mu, lqcd_fiel
     yy = 2.0 * px - yy;
   }
   if (s_f) *s_f = yy;
-  // Phi_o = A^-1 D_oe X_e, Psi_o = A^-dag (D^dag)_oe Y_e
-  LQCD_TRY(dslash_tw(g, P_F64, x->half[0], x->half[1], nullptr, nullptr, 1.0, 0.0, 0.0, 1, false, s, -a, 0.0));
-  LQCD_TRY(dslash_tw(g, P_F64, y->half[0], y->half[1], nullptr, nullptr, 1.0, 0.0, 0.0, 1, true, s, a, 0.0));
   const double c = -2.0 * kappa * kappa * coeff;
   const double2* U = static_cast<const double2*>(g->copy[P_F64][0]);
   const unsigned nb = blocks(2LL * g->g.Vh, HMC_THREADS);
-  cudaStream_t st = g->ctx->stream;
   const void *pe = x->half[0], *po = x->half[1], *se = y->half[0], *so = y->half[1];
   k_fermion_force<0><<<nb, HMC_THREADS, 0, st>>>(U, g->g, pe, po, se, so, c, m->d);
   k_fermion_force<1><<<nb, HMC_THREADS, 0, st>>>(U, g->g, pe, po, se, so, c, m->d);
@@ -556,13 +566,14 @@ int lqcd_fermion_force(const lqcd_gauge* g, double kappa, double mu, const lqcd_
   lqcd_ctx* c = g->ctx;
   LQCD_CK(cudaSetDevice(c->device));
   int dims[4] = {g->g.L[0], g->g.L[1], g->g.L[2], g->g.L[3]};
-  lqcd_field *xx = nullptr, *y = nullptr;
+  lqcd_field *xx = nullptr, *y = nullptr, *xd = nullptr, *yd = nullptr;
   int rc = lqcd_field_create(c, dims, LQCD_F64, LQCD_FULL, &xx);
   if (rc == LQCD_OK) rc = lqcd_field_create(c, dims, LQCD_F64, LQCD_FULL, &y);
+  if (rc == LQCD_OK) rc = lqcd_field_create(c, dims, LQCD_DF64, LQCD_FULL, &xd);
+  if (rc == LQCD_OK) rc = lqcd_field_create(c, dims, LQCD_DF64, LQCD_FULL, &yd);
   if (rc == LQCD_OK) rc = lqcd_field_copy(xx, x, 1.0);
-  if (rc == LQCD_OK) rc = fermion_force_from_x(g, kappa, mu, xx, y, coeff, m, s_f);
-  lqcd_field_destroy(xx);
-  lqcd_field_destroy(y);
+  if (rc == LQCD_OK) rc = fermion_force_from_x(g, kappa, mu, xx, y, xd, yd, coeff, m, s_f);
+  for (lqcd_field* f : {xx, y, xd, yd}) lqcd_field_destroy(f);
   return rc;
 }
 
@@ -625,12 +636,14 @@ int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m, co
   o.solver = LQCD_CG;
   o.mu = p->mu;
   int dims[4] = {g->g.L[0], g->g.L[1], g->g.L[2], g->g.L[3]};
-  lqcd_field *x = nullptr, *y = nullptr;
+  lqcd_field *x = nullptr, *y = nullptr, *xd = nullptr, *yd = nullptr;
   lqcd_engine* e = nullptr;
   void* backup = nullptr;
   const size_t ubytes = gauge_copy_bytes(P_F64, 18, g->g.Vh);
   int rc = lqcd_field_create(c, dims, LQCD_F64, LQCD_FULL, &x);
   if (rc == LQCD_OK) rc = lqcd_field_create(c, dims, LQCD_F64, LQCD_FULL, &y);
+  if (rc == LQCD_OK) rc = lqcd_field_create(c, dims, LQCD_DF64, LQCD_FULL, &xd);
+  if (rc == LQCD_OK) rc = lqcd_field_create(c, dims, LQCD_DF64, LQCD_FULL, &yd);
   if (rc == LQCD_OK) rc = ctx_engine(c, o, 1, &e);
   if (rc == LQCD_OK && p->accept_u > 0.0) {
     if (cudaMalloc(&backup, ubytes) != cudaSuccess) {
@@ -659,7 +672,7 @@ int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m, co
       LQCD_TRY(solve_normal_with(e, g, phi, p->kappa, p->mu, p->tol, x, &si));
       solves_iters += si.iters;
       double s = 0.0;
-      LQCD_TRY(fermion_force_from_x(g, p->kappa, p->mu, x, y, -pend_f, m, &s, phi));
+      LQCD_TRY(fermion_force_from_x(g, p->kappa, p->mu, x, y, xd, yd, -pend_f, m, &s, phi));
       if (first_f) sf0 = s;
       first_f = false;
       sf1 = s;
@@ -732,8 +745,7 @@ int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m, co
     cudaFree(backup);
   }
   if (rc != LQCD_OK && e) ctx_drop_engine(c);  // a failure may leave a request in the engine
-  lqcd_field_destroy(x);
-  lqcd_field_destroy(y);
+  for (lqcd_field* f : {x, y, xd, yd}) lqcd_field_destroy(f);
   if (info) {
     info->dH = h1 - h0;
     info->H0 = h0;

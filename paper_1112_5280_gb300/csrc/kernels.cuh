@@ -179,7 +179,8 @@ __global__ void __launch_bounds__(TILE, DslashMinBlocks<SP>::value) k_dslash(con
         SpinorIO<XSloppy<SP>::P>::store(w.z, w.g.Vh, h, x);
       }
     }
-    if constexpr (EpiTraits<EPI>::red) tile_partial<TILE>(w, start / TILE, v0, v1, v2, L.partials);
+    if constexpr (EpiTraits<EPI>::red)
+      tile_partial<TILE, std::is_same<R, float>::value>(w, start / TILE, v0, v1, v2, L.partials);
   }
 }
 

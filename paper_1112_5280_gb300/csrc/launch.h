@@ -17,6 +17,9 @@ cudaError_t launch_dslash(int sp, int nr, bool dag, int epi, const Launch& L, in
                           cudaStream_t s, int form = -1);
 // tp: precision of the FP64-class operand of the mixed ops (P_F64 or P_DF64)
 cudaError_t launch_blas(int sp, int op, const Launch& L, int grid, cudaStream_t s, int tp = P_F64);
+// k_finish for a launch whose slots reduce or finish (finish.cu); launch_dslash and
+// launch_blas issue it themselves when L.finish is set
+cudaError_t launch_finish(const Launch& L, cudaStream_t s);
 
 // per precision
 #define LQCD_DECL(SFX)                                                                     \

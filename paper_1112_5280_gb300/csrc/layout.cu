@@ -253,12 +253,9 @@ cudaError_t spinor_convert(const void* in, int pin, void* out, int pout, int Vh,
 // ------------------------------------------------------------------ dispatch
 
 // the slots' reduction totals and scalar finishers of the launch just issued on s
-__global__ void __launch_bounds__(FINISH_THREADS) k_finish(const Launch L) { finish_slot(L); }
-
 static cudaError_t then_finish(cudaError_t err, const Launch& L, cudaStream_t s) {
   if (err != cudaSuccess || !L.finish) return err;
-  k_finish<<<L.nslots, FINISH_THREADS, 0, s>>>(L);
-  return cudaGetLastError();
+  return launch_finish(L, s);
 }
 
 cudaError_t launch_dslash(int sp, int nr, bool dag, int epi, const Launch& L, int grid,
