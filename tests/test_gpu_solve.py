@@ -179,6 +179,31 @@ def test_engine_uneven_lattices_same_alone_and_in_mix(ctx):
     eng.close()
 
 
+def test_multi_group_reduction_alone_and_in_mix(ctx):
+    """A slot of more than 1024 tiles has its reductions summed by several CTAs (a count
+    fixed by its own tiles); in a batch with a small lattice it still gives its solo
+    result bit for bit, and so does the small one."""
+    big, small = (20, 20, 20, 40), (4, 4, 4, 8)  # V/2 = 160000 sites: 2500 tiles, 3 groups
+    opts = lqcd.solve_opts(sloppy_prec="f32", sloppy_compress=12)
+    fields = []
+    for dims, seed in ((big, 31), (small, 32)):
+        g = ctx.gauge(dims, synth.random_links(dims, 0.4, seed=seed), prec="f64")
+        src = ctx.field(dims, "f64", lqcd.FULL, data=synth.gaussian_spinor(dims, seed=seed + 1))
+        fields.append((dims, g, src))
+    eng = lqcd.Engine(ctx, opts, max_slots=4)
+    ids = [eng.submit(g, src, 0.13, 1e-10) for _, g, src in fields]
+    while eng.step() > 0:
+        pass
+    for rid, (dims, g, src) in zip(ids, fields):
+        x = ctx.field(dims, "f64", lqcd.FULL)
+        info = eng.result(rid, x)
+        assert info["status"] == 0 and info["true_resid"] <= 1e-10, info
+        solo = ctx.field(dims, "f64", lqcd.FULL)
+        lqcd.solve_fields(g, src, 0.13, 1e-10, solo, opts)
+        assert np.array_equal(solo.download(), x.download()), dims
+    eng.close()
+
+
 def test_nonconvergence_reports_status(ctx):
     dims = (4, 4, 4, 4)
     U = synth.random_links(dims, 0.5, seed=3)
