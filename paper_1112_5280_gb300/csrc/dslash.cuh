@@ -245,180 +245,12 @@ __device__ __forceinline__ void dslash_site(const Geom& g, int h, int out_par, c
 }
 
 // ---------------------------------------------------------------- colour-split form
-// Three threads per output site, thread COL computing output colour COL for all
-// four spins: each hop projects the whole neighbour spinor (the colour sum needs
-// every colour of h) but multiplies by one row only, row COL of U (forward) or
-// of U^dag = conj(column COL of U(x - mu)) (backward). The accumulator and the
-// link data per thread shrink three-fold; this pays where the per-site work is
-// latency bound at low occupancy (double-float), not where it is memory bound.
+// Three threads per output site, thread col computing output colour col for all
+// four spins, multiplying by one row only: row col of U (forward) or of
+// U^dag = conj(column col of U(x - mu)) (backward). The accumulator and the link
+// data per thread shrink three-fold; this pays where the per-site work is latency
+// bound at low occupancy (double-float), not where it is memory bound.
 
-// Row COL of U (ADJ false) or of U^dag (ADJ true), 18-real links with one
-// complex per word (element (i, j) is word 3 i + j).
-template <int LP, bool ADJ, int COL, typename R>
-__device__ __forceinline__ void link_row18(const void* base_mu, int Vh, int h, R r[6]) {
-#pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    const int word = ADJ ? (3 * b + COL) : (3 * COL + b);
-    R re, im;
-    if constexpr (LP == P_DF64) {
-      const float4 d = ld_stream(reinterpret_cast<const float4*>(base_mu) + h + (size_t)word * Vh);
-      re = R(df64(d.x, d.y));
-      im = R(df64(d.z, d.w));
-    } else if constexpr (LP == P_F64) {
-      const double2 d = ld_stream(reinterpret_cast<const double2*>(base_mu) + h + (size_t)word * Vh);
-      re = R(d.x);
-      im = R(d.y);
-    } else {
-      const float2 d = ld_stream(reinterpret_cast<const float2*>(base_mu) + h + (size_t)word * Vh);
-      re = R(d.x);
-      im = R(d.y);
-    }
-    r[2 * b] = re;
-    r[2 * b + 1] = ADJ ? -im : im;
-  }
-}
-
-// Double-float form of hop3 below: projections and the row products summed with the
-// unnormalised double-float operations (df_add_u, df_mac_u); acc stays unnormalised
-// across the hops and is normalised once by dslash_site3.
-template <int MU, int S>
-__device__ __forceinline__ void hop3_df(const df64 psi[24], const df64 r[6], int eta, df64 acc[8]) {
-  Cx<df64> h0[3], h1[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const Cx<df64> p0 = sp(psi, 0, c), p1 = sp(psi, 1, c), p2 = sp(psi, 2, c), p3 = sp(psi, 3, c);
-    if (MU == 0) {
-      h0[c] = {df_add_u(p0.re, S * p3.im), df_add_u(p0.im, S * -p3.re)};
-      h1[c] = {df_add_u(p1.re, S * p2.im), df_add_u(p1.im, S * -p2.re)};
-    } else if (MU == 1) {
-      h0[c] = {df_add_u(p0.re, S * -p3.re), df_add_u(p0.im, S * -p3.im)};
-      h1[c] = {df_add_u(p1.re, S * p2.re), df_add_u(p1.im, S * p2.im)};
-    } else if (MU == 2) {
-      h0[c] = {df_add_u(p0.re, S * p2.im), df_add_u(p0.im, S * -p2.re)};
-      h1[c] = {df_add_u(p1.re, S * -p3.im), df_add_u(p1.im, S * p3.re)};
-    } else {
-      h0[c] = {df_add_u(p0.re, S * p2.re), df_add_u(p0.im, S * p2.im)};
-      h1[c] = {df_add_u(p1.re, S * p3.re), df_add_u(p1.im, S * p3.im)};
-    }
-  }
-  // w = row . h: re = sum (r.re h.re - r.im h.im), im = sum (r.re h.im + r.im h.re)
-  Cx<df64> w0{df64(0.0f, 0.0f), df64(0.0f, 0.0f)}, w1 = w0;
-#pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    const df64 rr = r[2 * b], ri = r[2 * b + 1];
-    df_mac_u(w0.re, rr, h0[b].re);
-    df_mac_u(w0.re, -ri, h0[b].im);
-    df_mac_u(w0.im, rr, h0[b].im);
-    df_mac_u(w0.im, ri, h0[b].re);
-    df_mac_u(w1.re, rr, h1[b].re);
-    df_mac_u(w1.re, -ri, h1[b].im);
-    df_mac_u(w1.im, rr, h1[b].im);
-    df_mac_u(w1.im, ri, h1[b].re);
-  }
-  if (MU == 3 && eta < 0) {
-    w0 = sgn<-1>(w0);
-    w1 = sgn<-1>(w1);
-  }
-  acc[0] = df_add_u(acc[0], w0.re); acc[1] = df_add_u(acc[1], w0.im);
-  acc[2] = df_add_u(acc[2], w1.re); acc[3] = df_add_u(acc[3], w1.im);
-  Cx<df64> l2, l3;
-  if (MU == 0) { l2 = sgn<S>(mul_i(w1)); l3 = sgn<S>(mul_i(w0)); }
-  else if (MU == 1) { l2 = sgn<S>(w1); l3 = sgn<-S>(w0); }
-  else if (MU == 2) { l2 = sgn<S>(mul_i(w0)); l3 = sgn<-S>(mul_i(w1)); }
-  else { l2 = sgn<S>(w0); l3 = sgn<S>(w1); }
-  acc[4] = df_add_u(acc[4], l2.re); acc[5] = df_add_u(acc[5], l2.im);
-  acc[6] = df_add_u(acc[6], l3.re); acc[7] = df_add_u(acc[7], l3.im);
-}
-
-// acc (spin s: acc[2 s], acc[2 s + 1]) += eta (1 + S g_MU) x (row) h for one colour
-template <int MU, int S, typename R>
-__device__ __forceinline__ void hop3(const R psi[24], const R r[6], int eta, R acc[8]) {
-  if constexpr (std::is_same<R, df64>::value) {
-    hop3_df<MU, S>(psi, r, eta, acc);
-  } else {
-    Cx<R> h0[3], h1[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const Cx<R> p0 = sp(psi, 0, c), p1 = sp(psi, 1, c), p2 = sp(psi, 2, c), p3 = sp(psi, 3, c);
-      if (MU == 0) {
-        h0[c] = {p0.re + S * p3.im, p0.im - S * p3.re};
-        h1[c] = {p1.re + S * p2.im, p1.im - S * p2.re};
-      } else if (MU == 1) {
-        h0[c] = {p0.re - S * p3.re, p0.im - S * p3.im};
-        h1[c] = {p1.re + S * p2.re, p1.im + S * p2.im};
-      } else if (MU == 2) {
-        h0[c] = {p0.re + S * p2.im, p0.im - S * p2.re};
-        h1[c] = {p1.re - S * p3.im, p1.im + S * p3.re};
-      } else {
-        h0[c] = {p0.re + S * p2.re, p0.im + S * p2.im};
-        h1[c] = {p1.re + S * p3.re, p1.im + S * p3.im};
-      }
-    }
-    Cx<R> w0 = cmul(Cx<R>{r[0], r[1]}, h0[0]), w1 = cmul(Cx<R>{r[0], r[1]}, h1[0]);
-#pragma unroll
-    for (int b = 1; b < 3; ++b) {
-      const Cx<R> rb{r[2 * b], r[2 * b + 1]};
-      const Cx<R> m0 = cmul(rb, h0[b]), m1 = cmul(rb, h1[b]);
-      w0.re += m0.re; w0.im += m0.im;
-      w1.re += m1.re; w1.im += m1.im;
-    }
-    if (MU == 3 && eta < 0) {
-      w0 = sgn<-1>(w0);
-      w1 = sgn<-1>(w1);
-    }
-    acc[0] += w0.re; acc[1] += w0.im;
-    acc[2] += w1.re; acc[3] += w1.im;
-    Cx<R> l2, l3;
-    if (MU == 0) { l2 = sgn<S>(mul_i(w1)); l3 = sgn<S>(mul_i(w0)); }
-    else if (MU == 1) { l2 = sgn<S>(w1); l3 = sgn<-S>(w0); }
-    else if (MU == 2) { l2 = sgn<S>(mul_i(w0)); l3 = sgn<-S>(mul_i(w1)); }
-    else { l2 = sgn<S>(w0); l3 = sgn<S>(w1); }
-    acc[4] += l2.re; acc[5] += l2.im;
-    acc[6] += l3.re; acc[7] += l3.im;
-  }
-}
-
-template <int K, int SP, int LP, bool DAG, int COL>
-__device__ __forceinline__ void hop3_k(const Geom& g, int h, const int nf[4], const int nb[4], int t,
-                                       const void* in, const void* Uout, const void* Uin,
-                                       typename SpinorIO<SP>::Real acc[8]) {
-  using R = typename SpinorIO<SP>::Real;
-  constexpr int MU = K / 2;
-  constexpr bool FWD = (K % 2) == 0;
-  R psi[24], r[6];
-  SpinorIO<SP>::load(in, g.Vh, FWD ? nf[MU] : nb[MU], psi);
-  link_row18<LP, !FWD, COL>(link_dir<LP, 18>(FWD ? Uout : Uin, g.Vh, MU), g.Vh, FWD ? h : nb[MU], r);
-  const int eta = (MU == 3 && t == (FWD ? g.L[3] - 1 : 0)) ? g.t_bc : 1;
-  constexpr int S = FWD ? (DAG ? 1 : -1) : (DAG ? -1 : 1);
-  hop3<MU, S>(psi, r, eta, acc);
-}
-
-// acc = colour COL of (D_{p,1-p} in)(h), spin pairs (acc[2 s], acc[2 s + 1]); 18-real links.
-template <int SP, int LP, bool DAG, int COL>
-__device__ __forceinline__ void dslash_site3(const Geom& g, int h, int out_par, const void* in,
-                                             const void* Uout, const void* Uin,
-                                             typename SpinorIO<SP>::Real acc[8]) {
-  int nf[4], nb[4], t;
-  neighbours(g, h, out_par, nf, nb, t);
-#pragma unroll
-  for (int i = 0; i < 8; ++i) acc[i] = 0;
-  hop3_k<0, SP, LP, DAG, COL>(g, h, nf, nb, t, in, Uout, Uin, acc);
-  hop3_k<1, SP, LP, DAG, COL>(g, h, nf, nb, t, in, Uout, Uin, acc);
-  hop3_k<2, SP, LP, DAG, COL>(g, h, nf, nb, t, in, Uout, Uin, acc);
-  hop3_k<3, SP, LP, DAG, COL>(g, h, nf, nb, t, in, Uout, Uin, acc);
-  hop3_k<4, SP, LP, DAG, COL>(g, h, nf, nb, t, in, Uout, Uin, acc);
-  hop3_k<5, SP, LP, DAG, COL>(g, h, nf, nb, t, in, Uout, Uin, acc);
-  hop3_k<6, SP, LP, DAG, COL>(g, h, nf, nb, t, in, Uout, Uin, acc);
-  hop3_k<7, SP, LP, DAG, COL>(g, h, nf, nb, t, in, Uout, Uin, acc);
-  if constexpr (std::is_same<typename SpinorIO<SP>::Real, df64>::value) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i] = df_norm(acc[i]);
-  }
-}
-
-// ---------------------------------------------------------------- colour split, shared
-// projections (double-float)
-//
 // The three threads of a site (colour col = 0, 1, 2, in different warps of the CTA) each
 // need the projected half spinor h of all three colours of a neighbour. Each thread loads
 // and projects only its own colour and publishes it in shared memory; after a barrier it
