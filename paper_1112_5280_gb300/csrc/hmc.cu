@@ -34,83 +34,16 @@ using namespace gf;
 
 constexpr int HMC_THREADS = 128;
 
-__device__ __forceinline__ C2 times_i(C2 a) { return {-a.im, a.re}; }
-__device__ __forceinline__ C2 times_mi(C2 a) { return {a.im, -a.re}; }
-__device__ __forceinline__ C2 neg(C2 a) { return {-a.re, -a.im}; }
-__device__ __forceinline__ C2 csub(C2 a, C2 b) { return {a.re - b.re, a.im - b.im}; }
-
-// gamma_mu v on one colour's four spin components (chiral basis: g_k = [[0, -i s_k],
-// [i s_k, 0]] for mu = 0, 1, 2, g_t = [[0, 1], [1, 0]])
-template <int MU>
-__device__ __forceinline__ void gamma_mul(const C2 v[4], C2 o[4]) {
-  if (MU == 0) {
-    o[0] = times_mi(v[3]); o[1] = times_mi(v[2]); o[2] = times_i(v[1]); o[3] = times_i(v[0]);
-  } else if (MU == 1) {
-    o[0] = neg(v[3]); o[1] = v[2]; o[2] = v[1]; o[3] = neg(v[0]);
-  } else if (MU == 2) {
-    o[0] = times_mi(v[2]); o[1] = times_i(v[3]); o[2] = times_i(v[0]); o[3] = times_mi(v[1]);
-  } else {
-    o[0] = v[2]; o[1] = v[3]; o[2] = v[0]; o[3] = v[1];
-  }
-}
-
 __device__ __forceinline__ int eo_index(const Geom& g, const Site& s) {
   return (s.c[0] >> 1) + g.Lxh * (s.c[1] + g.L[1] * (s.c[2] + g.L[2] * s.c[3]));
 }
 
-// psi[spin][colour] of an FP64 half field (colour-major device layout)
-__device__ __forceinline__ void load_spinor(const void* half, int Vh, int h, C2 psi[4][3]) {
-  double v[24];
-  SpinorIO<P_F64>::load(half, Vh, h, v);
-#pragma unroll
-  for (int s = 0; s < 4; ++s)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) psi[s][c] = {v[sidx(s, c)], v[sidx(s, c) + 1]};
-}
-
-__device__ __forceinline__ M3 traceless_ah(const M3& m, double scale) {
-  M3 a;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const C2 x = m.e[i * 3 + j], y = m.e[j * 3 + i];
-      a.e[i * 3 + j] = {0.5 * (x.re - y.re) * scale, 0.5 * (x.im + y.im) * scale};
-    }
-  const double tr = (a.e[0].im + a.e[4].im + a.e[8].im) / 3.0;
-  a.e[0].im -= tr;
-  a.e[4].im -= tr;
-  a.e[8].im -= tr;
-  return a;
-}
-
-__device__ __forceinline__ void add_mom(double2* P, const Geom& g, const Site& x, int mu, const M3& f) {
-  const size_t b = link_base(g, x, mu);
-#pragma unroll
-  for (int w = 0; w < 9; ++w) {
-    double2 d = P[b + (size_t)w * g.Vh];
-    d.x += f.e[w].re;
-    d.y += f.e[w].im;
-    P[b + (size_t)w * g.Vh] = d;
-  }
-}
-
-// P_mu(x) += c TA(U W), c = coeff beta / 3: the staple sum, U W and the anti-Hermitian
-// part in double-float from the copy Ud (FP32 pipes), only the accumulation into the FP64
-// momenta in FP64. All four directions in one launch (blockIdx.y = mu), one thread per
-// link, mu a run-time value so that the four share one instruction stream.
-#ifndef LQCD_GF_MIN_BLOCKS
-#define LQCD_GF_MIN_BLOCKS 2
-#endif
-__global__ void __launch_bounds__(HMC_THREADS, LQCD_GF_MIN_BLOCKS) k_gauge_force(const float4* Ud, Geom g, double c, double2* P) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2LL * g.Vh) return;
-  const int mu = blockIdx.y;
-  const Site x = site_of(g, (int)(i / g.Vh), (int)(i % g.Vh));
-  const M3d V = mul_d<false, false>(load_link_df(Ud, g, x, mu), staple_df(Ud, g, x, mu));
+// P_mu(x) += c TA(V) for a double-float V: TA(V)_ii = i (Im V_ii - Im tr V / 3),
+// TA(V)_ij = (V_ij - conj V_ji) / 2, TA_ji = -conj TA_ij; only the accumulation into the FP64
+// momenta runs in FP64
+__device__ __forceinline__ void add_ta(double2* P, const Geom& g, const Site& x, int mu, const M3d& V, double c) {
   const size_t b = link_base(g, x, mu);
   const size_t vh = (size_t)g.Vh;
-  // TA(V)_ii = i (Im V_ii - Im tr V / 3); TA(V)_ij = (V_ij - conj V_ji) / 2, TA_ji = -conj TA_ij
   double d[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) d[k] = (double)V.e[k * 4].im;
@@ -138,9 +71,52 @@ __global__ void __launch_bounds__(HMC_THREADS, LQCD_GF_MIN_BLOCKS) k_gauge_force
     }
 }
 
-// P_mu(x) += c eta TA(U B), B = ((1 - g_mu) Phi(x+mu))^T conj(Psi(x)) + Psi(x+mu)^T conj((1 + g_mu) Phi(x))
+// P_mu(x) += c TA(U W), c = coeff beta / 3: the staple sum, U W and the anti-Hermitian
+// part in double-float from the copy Ud (FP32 pipes), only the accumulation into the FP64
+// momenta in FP64. All four directions in one launch (blockIdx.y = mu), one thread per
+// link, mu a run-time value so that the four share one instruction stream.
+#ifndef LQCD_GF_MIN_BLOCKS
+#define LQCD_GF_MIN_BLOCKS 2
+#endif
+__global__ void __launch_bounds__(HMC_THREADS, LQCD_GF_MIN_BLOCKS) k_gauge_force(const float4* Ud, Geom g, double c, double2* P) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2LL * g.Vh) return;
+  const int mu = blockIdx.y;
+  const Site x = site_of(g, (int)(i / g.Vh), (int)(i % g.Vh));
+  add_ta(P, g, x, mu, mul_d<false, false>(load_link_df(Ud, g, x, mu), staple_df(Ud, g, x, mu)), c);
+}
+
+// gamma_mu v on one colour's four spins in double-float (chiral basis, as in the Dslash:
+// g_k = [[0, -i s_k], [i s_k, 0]] for mu = 0, 1, 2, g_t = [[0, 1], [1, 0]])
+__device__ __forceinline__ C2d ti_d(const C2d& a) { return {-a.im, a.re}; }
+__device__ __forceinline__ C2d tmi_d(const C2d& a) { return {a.im, -a.re}; }
+__device__ __forceinline__ C2d neg_d(const C2d& a) { return {-a.re, -a.im}; }
 template <int MU>
-__global__ void __launch_bounds__(HMC_THREADS) k_fermion_force(const double2* U, Geom g, const void* phi_e,
+__device__ __forceinline__ void gamma_mul_d(const C2d v[4], C2d o[4]) {
+  if (MU == 0) {
+    o[0] = tmi_d(v[3]); o[1] = tmi_d(v[2]); o[2] = ti_d(v[1]); o[3] = ti_d(v[0]);
+  } else if (MU == 1) {
+    o[0] = neg_d(v[3]); o[1] = v[2]; o[2] = v[1]; o[3] = neg_d(v[0]);
+  } else if (MU == 2) {
+    o[0] = tmi_d(v[2]); o[1] = ti_d(v[3]); o[2] = ti_d(v[0]); o[3] = tmi_d(v[1]);
+  } else {
+    o[0] = v[2]; o[1] = v[3]; o[2] = v[0]; o[3] = v[1];
+  }
+}
+
+// acc += a conj(b), unnormalised double-float
+__device__ __forceinline__ void cmacc_d(C2d& acc, const C2d& a, const C2d& b) {
+  df_mac_u(acc.re, a.re, b.re);
+  df_mac_u(acc.re, a.im, b.im);
+  df_mac_u(acc.im, a.im, b.re);
+  df_mac_u(acc.im, -a.re, b.im);
+}
+
+// P_mu(x) += c eta TA(U B), B = ((1 - g_mu) Phi(x+mu))^T conj(Psi(x)) + Psi(x+mu)^T conj((1 + g_mu) Phi(x)),
+// all in double-float from the double-float fields Phi, Psi and links Ud; one thread per link
+// of direction MU. B's entries accumulate unnormalised and are normalised once.
+template <int MU>
+__global__ void __launch_bounds__(HMC_THREADS) k_fermion_force(const float4* Ud, Geom g, const void* phi_e,
                                                               const void* phi_o, const void* psi_e,
                                                               const void* psi_o, double c, double2* P) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -153,50 +129,54 @@ __global__ void __launch_bounds__(HMC_THREADS) k_fermion_force(const double2* U,
   const void* psi_x = par ? psi_o : psi_e;
   const void* phi_n = par ? phi_e : phi_o;
   const void* psi_n = par ? psi_e : psi_o;
-  C2 B[9];
+  M3d Bm;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) B[k] = {0.0, 0.0};
+  for (int k = 0; k < 9; ++k) Bm.e[k] = {df64(0.0f, 0.0f), df64(0.0f, 0.0f)};
   {
-    C2 f[4][3], s[4][3];
-    load_spinor(phi_n, g.Vh, hp, f);  // Phi(x + mu)
-    load_spinor(psi_x, g.Vh, h, s);   // Psi(x)
+    df64 s[24];  // Psi(x)
+    SpinorIO<P_DF64>::load(psi_x, g.Vh, h, s);
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      C2 v[4], gv[4];
+      df64 f[8];  // colour b of Phi(x + mu)
+      SpinorIO<P_DF64>::load_colour(phi_n, g.Vh, hp, b, f);
+      C2d v[4], gv[4];
 #pragma unroll
-      for (int sp = 0; sp < 4; ++sp) v[sp] = f[sp][b];
-      gamma_mul<MU>(v, gv);
+      for (int sp = 0; sp < 4; ++sp) v[sp] = {f[2 * sp], f[2 * sp + 1]};
+      gamma_mul_d<MU>(v, gv);
 #pragma unroll
-      for (int sp = 0; sp < 4; ++sp) v[sp] = csub(v[sp], gv[sp]);  // (1 - g_mu) Phi(x+mu), colour b
+      for (int sp = 0; sp < 4; ++sp) v[sp] = {df_add_u(v[sp].re, -gv[sp].re), df_add_u(v[sp].im, -gv[sp].im)};
 #pragma unroll
       for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int sp = 0; sp < 4; ++sp) B[b * 3 + a] = cadd(B[b * 3 + a], cmulc(v[sp], s[sp][a]));
+        for (int sp = 0; sp < 4; ++sp)
+          cmacc_d(Bm.e[b * 3 + a], v[sp], C2d{s[sidx(sp, a)], s[sidx(sp, a) + 1]});
     }
   }
   {
-    C2 f[4][3], s[4][3];
-    load_spinor(phi_x, g.Vh, h, f);   // Phi(x)
-    load_spinor(psi_n, g.Vh, hp, s);  // Psi(x + mu)
+    df64 f[24];  // Phi(x)
+    SpinorIO<P_DF64>::load(phi_x, g.Vh, h, f);
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      C2 v[4], gv[4];
+    for (int a = 0; a < 3; ++a) {
+      df64 t[8];  // colour a of Psi(x + mu)
+      SpinorIO<P_DF64>::load_colour(psi_n, g.Vh, hp, a, t);
 #pragma unroll
-      for (int sp = 0; sp < 4; ++sp) v[sp] = f[sp][b];
-      gamma_mul<MU>(v, gv);
+      for (int b = 0; b < 3; ++b) {
+        C2d v[4], gv[4];
 #pragma unroll
-      for (int sp = 0; sp < 4; ++sp) v[sp] = cadd(v[sp], gv[sp]);  // (1 + g_mu) Phi(x), colour b
+        for (int sp = 0; sp < 4; ++sp) v[sp] = {f[sidx(sp, b)], f[sidx(sp, b) + 1]};
+        gamma_mul_d<MU>(v, gv);
 #pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int sp = 0; sp < 4; ++sp) B[a * 3 + b] = cadd(B[a * 3 + b], cmulc(s[sp][a], v[sp]));
+        for (int sp = 0; sp < 4; ++sp) {
+          const C2d w{df_add_u(v[sp].re, gv[sp].re), df_add_u(v[sp].im, gv[sp].im)};  // (1 + g_mu) Phi(x)
+          cmacc_d(Bm.e[a * 3 + b], C2d{t[2 * sp], t[2 * sp + 1]}, w);
+        }
+      }
     }
   }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Bm.e[k] = {df_norm(Bm.e[k].re), df_norm(Bm.e[k].im)};
   const double eta = (MU == 3 && x.c[3] == g.L[3] - 1) ? (double)g.t_bc : 1.0;
-  M3 Bm;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) Bm.e[k] = B[k];
-  add_mom(P, g, x, MU, traceless_ah(mul_nn(load_link(U, g, x, MU), Bm), c * eta));
+  add_ta(P, g, x, MU, mul_d<false, false>(load_link_df(Ud, g, x, MU), Bm), c * eta);
 }
 
 // 1/k! for the Taylor coefficients as double-float constants (k! is exact in FP64 for
@@ -384,10 +364,10 @@ int half_norm2(lqcd_ctx* c, const void* half, const Geom& g, double* out, const 
 }
 
 // From X (even half of x, FP64): Y = Mhat X, the odd halves of Phi and Psi, S_f and
-// P += coeff G_f. x and y are FULL FP64 fields (their odd halves are overwritten); xd and yd
-// are FULL double-float work fields: the four Dslash applications (Mhat X, D_oe X and
-// D^dag_oe Y) run in double-float (FP64 runs at 1/64 of the FP32 rate here), and Y, Phi_o
-// and Psi_o return to FP64 for the force kernel.
+// P += coeff G_f. x and y are FULL FP64 fields (y's even half receives Y); xd and yd are
+// FULL double-float work fields that end up holding Phi = (X_e, A^-1 D_oe X_e) and
+// Psi = (Y_e, A^-dag (D^dag)_oe Y_e). The Dslash applications and the force kernel run
+// in double-float (FP64 runs at 1/64 of the FP32 rate here).
 // S_f: with phi, the variational 2 Re <phi, X> - |Y|^2, whose error is quadratic in the
 // solve's (X = X* - e gives S* - |Mhat e|^2); without, |Y|^2 = phi^dag X (linear error).
 int fermion_force_from_x(const lqcd_gauge* g, double kappa, double mu, lqcd_field* x, lqcd_field* y,
@@ -396,15 +376,15 @@ int fermion_force_from_x(const lqcd_gauge* g, double kappa, double mu, lqcd_fiel
   const double a = 2.0 * kappa * mu, s = 1.0 / (1.0 + a * a);
   const int Vh = g->g.Vh;
   cudaStream_t st = g->ctx->stream;
+  float4* Ud = nullptr;
+  LQCD_TRY(df_links(g, &Ud));
   LQCD_CK(spinor_convert(x->half[0], P_F64, xd->half[0], P_DF64, Vh, 1.0, st));
   LQCD_TRY(lqcd_apply_Mhat_tm(g, kappa, mu, xd, yd, 0));
   // Phi_o = A^-1 D_oe X_e, Psi_o = A^-dag (D^dag)_oe Y_e
   LQCD_TRY(dslash_tw(g, P_DF64, xd->half[0], xd->half[1], nullptr, nullptr, 1.0, 0.0, 0.0, 1, false, s, -a, 0.0));
   LQCD_TRY(dslash_tw(g, P_DF64, yd->half[0], yd->half[1], nullptr, nullptr, 1.0, 0.0, 0.0, 1, true, s, a, 0.0));
   LQCD_CK(spinor_convert(yd->half[0], P_DF64, y->half[0], P_F64, Vh, 1.0, st));
-  LQCD_CK(spinor_convert(xd->half[1], P_DF64, x->half[1], P_F64, Vh, 1.0, st));
-  LQCD_CK(spinor_convert(yd->half[1], P_DF64, y->half[1], P_F64, Vh, 1.0, st));
-  g->ctx->launches += 4;
+  g->ctx->launches += 2;
   double yy = 0.0;
   LQCD_TRY(half_norm2(g->ctx, y->half[0], g->g, &yy));
   if (phi) {
@@ -414,13 +394,12 @@ int fermion_force_from_x(const lqcd_gauge* g, double kappa, double mu, lqcd_fiel
   }
   if (s_f) *s_f = yy;
   const double c = -2.0 * kappa * kappa * coeff;
-  const double2* U = static_cast<const double2*>(g->copy[P_F64][0]);
   const unsigned nb = blocks(2LL * g->g.Vh, HMC_THREADS);
-  const void *pe = x->half[0], *po = x->half[1], *se = y->half[0], *so = y->half[1];
-  k_fermion_force<0><<<nb, HMC_THREADS, 0, st>>>(U, g->g, pe, po, se, so, c, m->d);
-  k_fermion_force<1><<<nb, HMC_THREADS, 0, st>>>(U, g->g, pe, po, se, so, c, m->d);
-  k_fermion_force<2><<<nb, HMC_THREADS, 0, st>>>(U, g->g, pe, po, se, so, c, m->d);
-  k_fermion_force<3><<<nb, HMC_THREADS, 0, st>>>(U, g->g, pe, po, se, so, c, m->d);
+  const void *pe = xd->half[0], *po = xd->half[1], *se = yd->half[0], *so = yd->half[1];
+  k_fermion_force<0><<<nb, HMC_THREADS, 0, st>>>(Ud, g->g, pe, po, se, so, c, m->d);
+  k_fermion_force<1><<<nb, HMC_THREADS, 0, st>>>(Ud, g->g, pe, po, se, so, c, m->d);
+  k_fermion_force<2><<<nb, HMC_THREADS, 0, st>>>(Ud, g->g, pe, po, se, so, c, m->d);
+  k_fermion_force<3><<<nb, HMC_THREADS, 0, st>>>(Ud, g->g, pe, po, se, so, c, m->d);
   g->ctx->launches += 4;
   LQCD_CK(cudaGetLastError());
   return LQCD_OK;
