@@ -258,6 +258,18 @@ LQCD_API int lqcd_solve_fields(const lqcd_gauge* g, const lqcd_field* src, doubl
 LQCD_API int lqcd_solve_multi(const lqcd_gauge* g, int n, const lqcd_field* const* srcs, double kappa,
                      double tol, const lqcd_solve_opts* opts, lqcd_field* const* xs,
                      lqcd_solve_info* infos);
+/* Batched one-shot solve (A10, A11): n independent systems M(kappas[i], mu) x_i = b_i,
+ * each on its own gauge field gauges[i] (any lattice sizes; all of one context), to its
+ * own tolerance tols[i], advanced together in the batched engine's launches. Gauges that
+ * are the same object share their link reads (multi-RHS); different ones form a
+ * multi-lattice batch. srcs[i], xs[i]: FULL FP64 fields of gauges[i]'s lattice. Each
+ * result equals the solve of that system alone, bit for bit. opts->solver LQCD_BICGSTAB
+ * runs the systems one after another. infos: n entries (may be NULL). Returns LQCD_OK if
+ * every solve converged, else the first failing status; LQCD_EINVAL for n outside
+ * 1..1024, a NULL entry, or gauges of different contexts. */
+LQCD_API int lqcd_solve_batch(int n, const lqcd_gauge* const* gauges, const lqcd_field* const* srcs,
+                              const double* kappas, const double* tols, const lqcd_solve_opts* opts,
+                              lqcd_field* const* xs, lqcd_solve_info* infos);
 
 /* ---------------------------------------------------------------- pure gauge */
 

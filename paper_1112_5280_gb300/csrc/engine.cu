@@ -987,6 +987,45 @@ int lqcd_solve_multi(const lqcd_gauge* g, int n, const lqcd_field* const* srcs, 
   return rc;
 }
 
+int lqcd_solve_batch(int n, const lqcd_gauge* const* gauges, const lqcd_field* const* srcs,
+                     const double* kappas, const double* tols, const lqcd_solve_opts* opts,
+                     lqcd_field* const* xs, lqcd_solve_info* infos) {
+  clear_error();
+  if (n < 1 || n > MAX_SLOTS || !gauges || !srcs || !kappas || !tols || !xs)
+    return set_error(LQCD_EINVAL, "bad arguments");
+  for (int i = 0; i < n; ++i) {
+    if (!gauges[i] || !srcs[i] || !xs[i]) return set_error(LQCD_EINVAL, "NULL entry %d", i);
+    if (gauges[i]->ctx != gauges[0]->ctx) return set_error(LQCD_EINVAL, "gauges of different contexts");
+  }
+  lqcd_solve_opts o;
+  lqcd_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.solver == LQCD_BICGSTAB) {
+    int first_bad = LQCD_OK;
+    for (int i = 0; i < n; ++i) {
+      lqcd_solve_info inf{};
+      int rc = bicgstab_solve(gauges[i], srcs[i], kappas[i], tols[i], &o, xs[i], &inf);
+      if (infos) infos[i] = inf;
+      if (rc != LQCD_OK && first_bad == LQCD_OK) first_bad = rc;
+    }
+    return first_bad;
+  }
+  lqcd_ctx* c = gauges[0]->ctx;
+  lqcd_engine* e = nullptr;
+  int rc = ctx_engine(c, o, n, &e);
+  if (rc != LQCD_OK) return rc;
+  std::vector<long long> ids(n);
+  for (int i = 0; i < n && rc == LQCD_OK; ++i)
+    rc = lqcd_engine_submit_tm(e, gauges[i], srcs[i], kappas[i], o.mu, tols[i], &ids[i]);
+  if (rc == LQCD_OK) rc = run_engine(e, n, ids.data(), xs, infos);
+  if (rc != LQCD_OK && !(rc == LQCD_ENOCONV || rc == LQCD_EBREAKDOWN || rc == LQCD_ENONFINITE)) {
+    ctx_drop_engine(c);  // a failed submit or launch may leave requests behind
+  } else {
+    engine_trim_pool(e, (size_t)8 << 30);
+  }
+  return rc;
+}
+
 int lqcd_solve(const lqcd_gauge* g, const double* host_src, double kappa, double tol,
                const lqcd_solve_opts* opts, double* host_x, lqcd_solve_info* info) {
   clear_error();

@@ -163,6 +163,8 @@ def load(build_if_missing: bool = True):
                                            C.POINTER(SolveInfo)])
         _sig(lib, "lqcd_solve_multi", i, [_VP, i, C.POINTER(_VP), d, d, C.POINTER(SolveOpts),
                                           C.POINTER(_VP), C.POINTER(SolveInfo)])
+        _sig(lib, "lqcd_solve_batch", i, [i, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(d), C.POINTER(d),
+                                          C.POINTER(SolveOpts), C.POINTER(_VP), C.POINTER(SolveInfo)])
         _sig(lib, "lqcd_engine_create", i, [_VP, C.POINTER(SolveOpts), sz, i, C.POINTER(_VP)])
         _sig(lib, "lqcd_engine_request_bytes", sz, [_VP, _IP])
         _sig(lib, "lqcd_engine_submit", i, [_VP, _VP, _VP, d, d, C.POINTER(ll)])
@@ -636,6 +638,32 @@ def solve_multi(gauge: Gauge, srcs, kappa, tol, xs, opts: SolveOpts | None = Non
     infos = (SolveInfo * n)()
     o = opts if opts is not None else solve_opts()
     rc = gauge._lib.lqcd_solve_multi(gauge.h, n, sp, float(kappa), float(tol), C.byref(o), xp, infos)
+    if rc not in (OK, ENOCONV, EBREAKDOWN, ENONFINITE):
+        _check(rc)
+    return [infos[i].as_dict() for i in range(n)]
+
+
+def solve_batch(gauges, srcs, kappas, tols, xs, opts: SolveOpts | None = None):
+    """lqcd_solve_batch: n independent systems, each on its own gauge field (any lattice
+    sizes), kappa and tolerance, solved together; returns the n info dicts."""
+    n = len(gauges)
+    if not (len(srcs) == len(xs) == n):
+        raise ValueError("gauges, srcs and xs must have the same length")
+    if isinstance(kappas, (int, float)):
+        kappas = [kappas] * n
+    if isinstance(tols, (int, float)):
+        tols = [tols] * n
+    if not (len(kappas) == len(tols) == n):
+        raise ValueError("kappas and tols must have one entry per system")
+    lib = gauges[0]._lib
+    gp = (_VP * n)(*[g.h for g in gauges])
+    sp = (_VP * n)(*[s.h for s in srcs])
+    xp = (_VP * n)(*[x.h for x in xs])
+    kp = (C.c_double * n)(*[float(k) for k in kappas])
+    tp = (C.c_double * n)(*[float(t) for t in tols])
+    infos = (SolveInfo * n)()
+    o = opts if opts is not None else solve_opts()
+    rc = lib.lqcd_solve_batch(n, gp, sp, kp, tp, C.byref(o), xp, infos)
     if rc not in (OK, ENOCONV, EBREAKDOWN, ENONFINITE):
         _check(rc)
     return [infos[i].as_dict() for i in range(n)]

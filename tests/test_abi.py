@@ -57,3 +57,12 @@ def test_no_oracle_in_product():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "wilson_oracle" not in txt, f
+
+
+def test_solve_batch_argument_checks_without_gpu():
+    """The binding refuses mismatched lists before it reaches the library."""
+    from paper_1112_5280_gb300 import lqcd
+    with pytest.raises(ValueError):
+        lqcd.solve_batch([object(), object()], [object()], 0.15, 1e-10, [object(), object()])
+    with pytest.raises(ValueError):
+        lqcd.solve_batch([object()], [object()], [0.1, 0.2], 1e-10, [object()])

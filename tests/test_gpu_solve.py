@@ -204,6 +204,43 @@ def test_multi_group_reduction_alone_and_in_mix(ctx):
     eng.close()
 
 
+def test_solve_batch_matches_solo(ctx):
+    """lqcd_solve_batch: systems on different lattices, gauges, kappas and tolerances (two
+    sharing one gauge field) give each its solo result bit for bit; BiCGStab runs them in
+    turn; bad arguments are refused."""
+    opts = lqcd.solve_opts(sloppy_prec="f16", sloppy_compress=12)
+    specs = [((6, 4, 4, 6), 0.15, 1e-10, 41), ((4, 4, 4, 8), 0.13, 1e-9, 42), ((8, 4, 4, 4), 0.14, 1e-10, 43)]
+    gauges, srcs, kappas, tols = [], [], [], []
+    for dims, kappa, tol, seed in specs:
+        g = ctx.gauge(dims, synth.random_links(dims, 0.5, seed=seed), prec="f64")
+        gauges.append(g)
+        srcs.append(ctx.field(dims, "f64", lqcd.FULL, data=synth.gaussian_spinor(dims, seed=seed + 1)))
+        kappas.append(kappa)
+        tols.append(tol)
+    # a second source on the first gauge field (multi-RHS inside the batch)
+    gauges.append(gauges[0])
+    srcs.append(ctx.field(specs[0][0], "f64", lqcd.FULL, data=synth.gaussian_spinor(specs[0][0], seed=49)))
+    kappas.append(specs[0][1])
+    tols.append(specs[0][2])
+    for o in (opts, lqcd.solve_opts(sloppy_prec="f32", sloppy_compress=12, solver=lqcd.BICGSTAB)):
+        xs = [ctx.field(g.dims, "f64", lqcd.FULL) for g in gauges]
+        infos = lqcd.solve_batch(gauges, srcs, kappas, tols, xs, o)
+        for g, src, kappa, tol, x, info in zip(gauges, srcs, kappas, tols, xs, infos):
+            assert info["status"] == 0 and info["true_resid"] <= tol, info
+            solo = ctx.field(g.dims, "f64", lqcd.FULL)
+            lqcd.solve_fields(g, src, kappa, tol, solo, o)
+            assert np.array_equal(solo.download(), x.download()), g.dims
+    with pytest.raises(ValueError):
+        lqcd.solve_batch(gauges, srcs[:2], kappas, tols, xs, opts)
+    other = lqcd.Context(0)
+    try:
+        g2 = other.gauge(specs[1][0], synth.unit_links(specs[1][0]))
+        with pytest.raises(lqcd.LqcdError):
+            lqcd.solve_batch([gauges[0], g2], srcs[:2], kappas[:2], tols[:2], xs[:2], opts)
+    finally:
+        other.close()
+
+
 def test_nonconvergence_reports_status(ctx):
     dims = (4, 4, 4, 4)
     U = synth.random_links(dims, 0.5, seed=3)
