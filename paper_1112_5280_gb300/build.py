@@ -89,10 +89,17 @@ DSLASH_KERNEL_FILES = ("field.cuh", "dslash.cuh", "batch.cuh", "kernels.cuh", "k
 
 
 def source_hash(files=DSLASH_KERNEL_FILES) -> str:
-    """Hash of kernel sources (ties profile counters to the code they were taken on)."""
+    """Hash of the kernel sources' code (ties profile counters to the code they were taken
+    on). Comments and blank lines are left out, so that editing a comment keeps the
+    counters; any change to the code itself changes the hash."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in sorted(files):
+        txt = open(os.path.join(CSRC, name)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        txt = re.sub(r"//[^\n]*", "", txt)
+        txt = "\n".join(line.rstrip() for line in txt.split("\n") if line.strip())
         h.update(name.encode())
-        h.update(open(os.path.join(CSRC, name), "rb").read())
+        h.update(txt.encode())
     return h.hexdigest()[:16]

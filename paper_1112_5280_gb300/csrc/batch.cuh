@@ -35,7 +35,7 @@ constexpr int S_NEVER = 99;
 // Status codes written into Scalars::status (mirrors the public LQCD_* codes).
 enum SlotStatus { ST_OK = 0, ST_MAXITER = -3, ST_BREAKDOWN = -4, ST_NONFINITE = -5 };
 
-// Scalar programs run by the last tile of a slot after a reduction.
+// Scalar programs run by k_finish for a slot after a reduction.
 enum Fin {
   FIN_NONE = 0,
   FIN_STORE0,    // res[0] = sum
@@ -156,7 +156,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return s;
 }
 
-// The scalar programs. Run by one thread of the slot's last tile.
+// The scalar programs. Run by one thread of k_finish for the slot.
 __device__ __noinline__ static void run_fin_bicg(const Work& w, const double* v);
 
 __device__ __noinline__ static void run_fin(const Work& w, const double* v) {
