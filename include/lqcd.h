@@ -275,8 +275,9 @@ LQCD_API int lqcd_solve_batch(int n, const lqcd_gauge* const* gauges, const lqcd
 
 /* SU(3) heatbath of the Wilson plaquette action S = beta sum_P (1 - Re Tr U_P / 3)
  * (paper Section 3: the pure-gauge side needs an SU(3) heatbath, citing Creutz), in
- * place on the gauge field's FP64 master copy; every other copy of g is refreshed
- * afterwards. nsweeps sweeps, numbered sweep0, sweep0 + 1, ...; a sweep updates the
+ * place. The sweeps run on the gauge field's double-float copy (matrix algebra in
+ * double-float, the draws in FP64); the FP64 master and every other copy of g are
+ * rebuilt from it afterwards, so the links carry a 48-bit significand. nsweeps sweeps, numbered sweep0, sweep0 + 1, ...; a sweep updates the
  * links class by class (mu = 0..3, parity even then odd), each link by Cabibbo-Marinari
  * over the SU(2) subgroups (0,1), (1,2), (0,2) with Creutz's SU(2) draw. Random numbers
  * are Philox4x64-10 with key (seed, 0) and counter (4 s + mu, sweep, subgroup, attempt),
@@ -314,12 +315,14 @@ LQCD_API int lqcd_gauge_force(const lqcd_gauge* g, double beta, double coeff, lq
 /* m += coeff G_f for the solution x = (Mhat^dag Mhat)^-1 phi (FULL FP64 field, even half
  * used): with Y = Mhat x, Phi = x_e + A^-1 D_oe x_e, Psi = Y + A^-dag (D^dag)_oe Y,
  * G_f = -2 kappa^2 eta TA(U [((1 - g_mu) Phi(x+mu))^T conj(Psi(x)) + Psi(x+mu)^T
- * conj((1 + g_mu) Phi(x))]) (spin summed; eta the t-boundary sign). *s_f (may be NULL)
- * receives S_f = |Y|^2 = phi^dag x. Synchronous. */
+ * conj((1 + g_mu) Phi(x))]) (spin summed; eta the t-boundary sign), computed in
+ * double-float. x is not modified. *s_f (may be NULL) receives S_f = |Y|^2 = phi^dag x.
+ * Synchronous. */
 LQCD_API int lqcd_fermion_force(const lqcd_gauge* g, double kappa, double mu, const lqcd_field* x,
                                 double coeff, lqcd_mom* m, double* s_f);
-/* U_mu(x) <- exp(eps P_mu(x)) U_mu(x) on the FP64 master (Taylor series of order 16 after
- * scaling |eps P| below 1/2, then squaring); derived link copies are rebuilt. */
+/* U_mu(x) <- exp(eps P_mu(x)) U_mu(x) in double-float (the Taylor polynomial, to a tail
+ * below 2^-50, after scaling |eps P| below 1/2, reduced by Cayley-Hamilton to one matrix
+ * product; then squaring). The FP64 master and the derived link copies are rebuilt. */
 LQCD_API int lqcd_gauge_update(lqcd_gauge* g, const lqcd_mom* m, double eps);
 /* Solves (Mhat^dag Mhat) x_e = src_e by the CG engine (mixed precision with reliable
  * updates as lqcd_solve; opts->mu the twisted mass; CG only) to
