@@ -46,6 +46,16 @@ MUTANTS = {
                                            "    twist(&g, 1.0, 0.0, tmp, tmp, 1);"),
     "t_neighbour_off_by_one": ("n[mu] = (c[mu] + 1) % g->L[mu];",
                                "n[mu] = (c[mu] + 1 + (mu == 3)) % g->L[mu];"),
+    # the true residual ||b - M x|| / ||b||, the judge of every GPU solve
+    "true_residual_uses_Mhat": ("oracle_apply_M(dims, t_bc, U, kappa, mu, x, (double*)y, 0);",
+                                "oracle_apply_Mhat(dims, t_bc, U, kappa, mu, x, (double*)y, 0);"),
+    "true_residual_uses_dagger": ("oracle_apply_M(dims, t_bc, U, kappa, mu, x, (double*)y, 0);",
+                                  "oracle_apply_M(dims, t_bc, U, kappa, mu, x, (double*)y, 1);"),
+    "true_residual_no_sqrt": ("double res = sqrt(vnorm2(y, n)) / sqrt(vnorm2(bb, n));",
+                              "double res = vnorm2(y, n) / sqrt(vnorm2(bb, n));"),
+    "true_residual_wrong_denominator": ("double res = sqrt(vnorm2(y, n)) / sqrt(vnorm2(bb, n));",
+                                        "double res = sqrt(vnorm2(y, n)) / sqrt(vnorm2((const cplx*)x, n));"),
+    "true_residual_sign": ("y[i] = bb[i] - y[i];", "y[i] = bb[i] + y[i];"),
 }
 
 
@@ -140,7 +150,17 @@ def _pin_checks():
             cols.append(oracle.apply_M(dims, U, 0.12, e.reshape(V, 4, 3), mu=0.25).reshape(-1))
         return bool(np.abs(M - np.stack(cols, axis=1)).max() < 1e-14)
 
-    checks.update(plane_wave=plane_wave, hermiticity=hermiticity, covariance=covariance,
+    def true_residual_dense():
+        ok = True
+        for dims, mu in (((2, 2, 2, 4), 0.0), ((2, 2, 2, 2), 0.3)):
+            U = synth.random_links(dims, 0.5, seed=16)
+            b, x = synth.gaussian_spinor(dims, 17), 0.7 * synth.gaussian_spinor(dims, 18)
+            M = dense.dense_wilson(dims, U, 0.13, mu=mu)
+            ref = np.linalg.norm(b.reshape(-1) - M @ x.reshape(-1)) / np.linalg.norm(b.reshape(-1))
+            ok &= abs(oracle.true_residual(dims, U, 0.13, b, x, mu=mu) - ref) <= 1e-13 * ref
+        return bool(ok)
+
+    checks.update(plane_wave=plane_wave, true_residual_dense=true_residual_dense, hermiticity=hermiticity, covariance=covariance,
                   brute_force=brute_force, eo_solve_vs_lapack=eo_solve_vs_lapack,
                   tm_hermiticity=tm_hermiticity, tm_solve_vs_lapack=tm_solve_vs_lapack,
                   tm_brute_force=tm_brute_force)
