@@ -197,12 +197,14 @@ LQCD_API int lqcd_apply_Mhat_tm(const lqcd_gauge* g, double kappa, double mu, co
  * The odd-parity temporary lives in a fixed 16 MiB device array that is part of
  * the library image (every GPU that loads the library holds it until the process
  * exits). Lattices whose half spinor exceeds it (FP32 beyond V/2 = 174762 sites,
- * FP64 beyond V/2 = 87381) are rejected with LQCD_EINVAL, and so is a gauge field
- * without a resident link copy for the fields' precision (make one first with
- * lqcd_gauge_add_copy). The call never calls cudaMalloc, cudaFree or an allocating
- * routine. Its first call on a device looks the array's device address up with
- * cudaGetSymbolAddress while that device is current; make that first call before
- * any stream capture. Every call uses the same array: calls whose GPU work can
+ * FP64 and double-float beyond V/2 = 87381) are rejected with LQCD_EINVAL, and so are
+ * a non-finite kappa and a gauge field without the resident link copy that
+ * lqcd_apply_Mhat would use for the fields' precision (the gauge's compression; 18
+ * reals for LQCD_DF64): make it first with lqcd_gauge_add_copy. The call never calls
+ * cudaMalloc, cudaFree or an allocating routine. Its first call on a device looks the
+ * array's device address up with cudaGetSymbolAddress while that device is current
+ * (and again after the device's context was destroyed and made anew, e.g. by
+ * cudaDeviceReset); make that first call before any stream capture. Every call uses the same array: calls whose GPU work can
  * overlap (different streams or contexts on one device without ordering between
  * them) race on it. The temporary is fully written before it is read, so a call
  * never sees what an earlier call left there. */

@@ -11,6 +11,9 @@
 // entry point keeps the temporary in a fixed-size array that is part of the
 // library image instead, so it never calls cudaMalloc, cudaFree or an
 // allocating library routine.
+#include <cuda.h>
+
+#include <cmath>
 #include <mutex>
 
 #include "kernels.cuh"
@@ -27,22 +30,47 @@ __device__ __align__(256) unsigned char g_mhat_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 void* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // context the address belongs to
 
 // Device address of the scratch array on `device` (which must be current).
-// Looked up once per device with cudaGetSymbolAddress: in host code the name
-// g_mhat_scratch is only a host-side stand-in and must never reach a kernel.
+// Looked up with cudaGetSymbolAddress at the first call on each device: in host
+// code the name g_mhat_scratch is only a host-side stand-in and must never
+// reach a kernel. The address belongs to the device's current context; if that
+// context was destroyed and made again (cudaDeviceReset), the context's unique
+// id changes and the address is looked up once more instead of reusing a dead one.
 int scratch_address(int device, void** out) {
   if (device < 0 || device >= kMaxDevices)
     return lqcd::set_error(LQCD_EINVAL, "device %d beyond the %d supported by the scratch table",
                            device, kMaxDevices);
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_addr[device]) {
+  // the two driver calls are fetched through the runtime, so that the library does not
+  // need the driver library at load time (it loads on machines without a GPU)
+  using GetCurrentFn = CUresult (*)(CUcontext*);
+  using GetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f0 = nullptr;
+    void* f1 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault) != cudaSuccess ||
+        !f0 || !f1)
+      return lqcd::set_error(LQCD_ECUDA, "driver entry points cuCtxGetCurrent / cuCtxGetId not found");
+    get_current = reinterpret_cast<GetCurrentFn>(f0);
+    get_id = reinterpret_cast<GetIdFn>(f1);
+  }
+  CUcontext cu = nullptr;
+  unsigned long long ctx_id = 0;
+  if (get_current(&cu) != CUDA_SUCCESS || !cu || get_id(cu, &ctx_id) != CUDA_SUCCESS)
+    return lqcd::set_error(LQCD_ECUDA, "no current CUDA context on device %d", device);
+  if (!g_scratch_addr[device] || g_scratch_ctx[device] != ctx_id) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_mhat_scratch);
     if (e != cudaSuccess || !p)
       return lqcd::set_error(LQCD_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s",
                              cudaGetErrorString(e));
     g_scratch_addr[device] = p;
+    g_scratch_ctx[device] = ctx_id;
   }
   *out = g_scratch_addr[device];
   return LQCD_OK;
@@ -76,6 +104,7 @@ extern "C" int lqcd_apply_Mhat_noalloc(const lqcd_gauge* g, double kappa, const 
   using namespace lqcd;
   clear_error();
   if (!g || !in || !out) return set_error(LQCD_EINVAL, "NULL argument");
+  if (!std::isfinite(kappa)) return set_error(LQCD_EINVAL, "kappa must be finite");
   if (in->prec != out->prec) return set_error(LQCD_EINVAL, "fields differ in precision");
   if (in->ctx != g->ctx || out->ctx != g->ctx) return set_error(LQCD_EINVAL, "objects of different contexts");
   for (int mu = 0; mu < 4; ++mu)
@@ -90,13 +119,15 @@ extern "C" int lqcd_apply_Mhat_noalloc(const lqcd_gauge* g, double kappa, const 
                      "fixed scratch of %zu bytes (use lqcd_apply_Mhat for this lattice)",
                      need, kScratchBytes);
   const int lp = link_prec_for(in->prec);
-  const int nr = g->compress;
+  // the copy lqcd_apply_Mhat would use: the gauge's compression, except double-float
+  // links, which always keep 18 reals
+  const int nr = (lp == P_DF64) ? 18 : g->compress;
   const void* links = g->copy[lp][nr == 12];
   if (!links)
     return set_error(LQCD_EINVAL,
                      "lqcd_apply_Mhat_noalloc: no resident %d-real link copy for this precision; "
-                     "create it first with lqcd_gauge_add_copy",
-                     nr);
+                     "create it first with lqcd_gauge_add_copy(g, prec, %d)",
+                     nr, nr);
   LQCD_CK(cudaSetDevice(g->ctx->device));
   void* tmp = nullptr;
   int rc = scratch_address(g->ctx->device, &tmp);
