@@ -267,6 +267,24 @@ def test_zero_source(ctx):
     assert info["status"] == 0 and np.all(x == 0)
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_bicgstab_breakdown_on_singular_system(ctx, prec):
+    """A singular system makes BiCGStab break down, reported as LQCD_EBREAKDOWN. With unit
+    links, periodic t and kappa = 1/8, D_eo D_oe maps a constant spinor to 64 times itself,
+    so Mhat = 1 - D_eo D_oe / 64 annihilates it. One real component equal to 1 on each of
+    the 256 even sites of 4x4x4x8 gives |bhat| = 16, so the restart vector r = bhat / 16 and
+    every hop sum are small integers over 16: the first <r0, Mhat p> is exactly zero."""
+    dims = (4, 4, 4, 8)
+    g = ctx.gauge(dims, synth.unit_links(dims), t_bc=+1)
+    even = synth.parity_of_sites(dims) == 0
+    b = np.zeros((synth.volume(dims), 4, 3), complex)
+    b[even, 0, 0] = 1.0
+    x, info = lqcd.solve(g, b, 0.125, 1e-10, lqcd.solve_opts(sloppy_prec=prec, solver=lqcd.BICGSTAB))
+    assert info["status"] == lqcd.EBREAKDOWN, info
+    assert info["iters"] == 0, info
+    g.close()
+
+
 def test_engine_budget_and_cancel(ctx):
     dims = (4, 4, 4, 4)
     g = ctx.gauge(dims, synth.random_links(dims, 0.3, seed=7))
@@ -310,13 +328,19 @@ def test_near_critical_16x32_mixed_f16(ctx):
 def test_full_size_solves_32x64(ctx):
     """The bench's solve workload at full size (32^3x64, kappa 0.155, eps 0.8, seeds 1001 /
     2002): mixed FP16-12 CG, Wilson and twisted mass (mu 0.01), each meets 1e-10 on the full
-    operator as measured by the oracle on the returned solution."""
+    operator as measured by the oracle on the returned solution. The Wilson solution is also
+    compared element by element with the oracle's own FP64 even-odd CG solution (to 1e-12,
+    computed once per machine): both solve the same system to a residual of 1e-10 or
+    below, so they differ by at most cond(M) times that; 1e-8 allows cond(M) up to 100."""
+    import oracle_cache
     dims, kappa, mu = (32, 32, 32, 64), 0.155, 0.01
-    U = synth.random_links(dims, 0.8, seed=synth.SEED_LINKS)
-    b = synth.gaussian_spinor(dims, seed=synth.SEED_SOURCE)
+    U, b, xo = oracle_cache.eo_solution(dims, 0.8, kappa, 0.0, synth.SEED_LINKS, synth.SEED_SOURCE, 1e-12)
     g = ctx.gauge(dims, U, prec="f64")
     for m in (0.0, mu):
         x, info = lqcd.solve(g, b, kappa, 1e-10, lqcd.solve_opts(sloppy_prec="f16", mu=m))
         assert info["status"] == 0, (m, info)
         assert oracle.true_residual(dims, U, kappa, b, x, mu=m) <= 1e-10, m
+        if m == 0.0:
+            err = np.linalg.norm(x - xo) / np.linalg.norm(xo)
+            assert err < 1e-8, err
     g.close()
