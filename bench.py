@@ -71,10 +71,9 @@ MRHS_DIMS = (24, 24, 24, 48)     # 12 point sources, kappa 0.15
 MRHS_KAPPA = 0.15
 MLAT_SIZES = ((8, 8, 8, 8), (12, 12, 12, 24), (16, 16, 16, 32))  # 64 uneven lattices
 MLAT_N = 64
-SERVE_POOL = 2                   # resident gauge fields / sources per serving lattice size
+SERVE_POOL = 4                   # resident gauge fields / sources per serving lattice size
+SERVE_N = 240                    # requests per serving run (after a separate warm-up stream)
 HB_DIMS, HB_BETA = (32, 32, 32, 64), 6.0  # pure-gauge SU(3) heatbath
-HB_FLOPS_PER_LINK = 3500         # FP64 flops of one link update (staple 2484, U W 198, 3 subgroups ~810)
-FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12  # SMs x max clock x FP64 FMA/clk/SM x 2 (1.26)
 
 
 def generate_inputs(full: bool):
@@ -114,9 +113,13 @@ def generate_inputs(full: bool):
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clock and throttle-reason samples, each stamped with nvidia-smi's own
+    timestamp (its output reaches the pipe in blocks, so the time a line is read says
+    nothing about when it was taken)."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 100
 
     def __init__(self, device: int):
         self.device = device
@@ -128,7 +131,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -138,7 +141,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append((time.perf_counter(), line.strip()))
+            self.lines.append(line.strip())
 
     def stop(self):
         if self.proc:
@@ -150,27 +153,41 @@ class ClockSampler:
         if self.t:
             self.t.join(timeout=2)
 
+    @staticmethod
+    def _stamp(text):
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(text.strip(), fmt).timestamp()
+            except ValueError:
+                pass
+        return None
+
     def summary(self, t0, t1):
-        sm, smax, reasons = [], [], set()
-        for ts, line in self.lines:
-            if not (t0 <= ts <= t1):
-                continue
+        """Samples stamped within [t0, t1] (time.time() seconds)."""
+        sm, smax, power, reasons = [], [], [], set()
+        for line in list(self.lines):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 8:
+            if len(parts) < 9:
+                continue
+            ts = self._stamp(parts[0])
+            if ts is None or not (t0 <= ts <= t1):
                 continue
             try:
-                sm.append(float(parts[0]))
-                smax.append(float(parts[1]))
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
             except ValueError:
                 continue
             names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-            for n, v in zip(names, parts[4:8]):
+            for n, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(n)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": float(np.median(power))}
 
 
 # ------------------------------------------------------------------ helpers
@@ -194,6 +211,23 @@ def profile_traffic(kernel_key: str):
         ent = d.get(kernel_key)
         if ent and ent.get("source_hash") == libbuild.source_hash():
             return ent.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+    return None
+
+
+def profile_counts(key: str):
+    """A per-unit count (instructions per site, ...) from an ncu capture, as committed in
+    profiles/counts.json, if it was taken on the current sources of the files it names."""
+    p = os.path.join(ROOT, "profiles", "counts.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        from paper_1112_5280_gb300 import build as libbuild
+        ent = d.get(key)
+        if ent and ent.get("source_hash") == libbuild.source_hash(tuple(ent["files"])):
+            return ent.get("value")
     except Exception:
         return None
     return None
@@ -265,27 +299,63 @@ def run_reference(args, world, rank):
     return 0
 
 
-def cpu_baseline_oracle(budget_s=12.0):
+def _time_oracle(fn, budget_s, min_n=1):
+    fn()
+    n, t0 = 0, time.perf_counter()
+    while n < min_n or time.perf_counter() - t0 < budget_s:
+        fn()
+        n += 1
+    return n, time.perf_counter() - t0
+
+
+def cpu_baseline_oracle(solve_inputs=None, budget_s=12.0):
+    """The FP64 oracle timed on the host cores (a reported baseline): the headline's D_eo at
+    16^3x32 on all cores for about budget_s, plus the oracle at one thread, the 32^3x64
+    D_eo and the 4^4 CG on M^dag M (the small workload), each bounded to a few seconds."""
     import oracle
     from paper_1112_5280_gb300 import synth
     U = synth.random_links(DIMS, EPS, seed=synth.SEED_LINKS)
     psi = synth.gaussian_spinor(DIMS, seed=synth.SEED_SOURCE)
     Vh = synth.volume(DIMS) // 2
-    oracle.hop_eo(DIMS, U, psi, 0)
-    n, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < budget_s:
-        oracle.hop_eo(DIMS, U, psi, 0)
-        n += 1
-    dt = time.perf_counter() - t0
-    return {"value": algorithmic_bytes_per_site(8, 18) * Vh * n / dt / 1e9, "unit": "GB/s",
-            "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": f"{n} FP64 oracle D_eo applications at 16^3x32 in {dt:.1f} s "
-                      "(FP64 operator, bytes counted at 1536 B/site)"}
+    b64 = algorithmic_bytes_per_site(8, 18)
+    cores = oracle.get_threads()
+    n, dt = _time_oracle(lambda: oracle.hop_eo(DIMS, U, psi, 0), budget_s)
+    out = {"value": b64 * Vh * n / dt / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+           "sample": f"{n} FP64 oracle D_eo applications at 16^3x32 in {dt:.1f} s "
+                     "(FP64 operator, bytes counted at 1536 B/site)"}
+    plan = {}
+    oracle.set_threads(1)
+    try:
+        n1, dt1 = _time_oracle(lambda: oracle.hop_eo(DIMS, U, psi, 0), 3.0)
+    finally:
+        oracle.set_threads(cores)
+    plan["deo_16x32_1thread"] = {"GBps": b64 * Vh * n1 / dt1 / 1e9, "ms_per_application": dt1 / n1 * 1e3,
+                                 "gflops": 1320 * Vh * n1 / dt1 / 1e9, "threads": 1}
+    plan["deo_16x32_all_cores"] = {"GBps": out["value"], "ms_per_application": dt / n * 1e3,
+                                   "gflops": 1320 * Vh * n / dt / 1e9, "threads": cores}
+    if solve_inputs is not None:
+        U2, b2 = solve_inputs
+        Vh2 = synth.volume(SOLVE_DIMS) // 2
+        n2, dt2 = _time_oracle(lambda: oracle.hop_eo(SOLVE_DIMS, U2, b2, 0), 3.0)
+        plan["deo_32x64_all_cores"] = {"GBps": b64 * Vh2 * n2 / dt2 / 1e9, "ms_per_application": dt2 / n2 * 1e3,
+                                       "gflops": 1320 * Vh2 * n2 / dt2 / 1e9, "threads": cores}
+    d0 = (4, 4, 4, 4)
+    U0 = synth.random_links(d0, 0.3, seed=synth.SEED_LINKS)
+    s0 = synth.gaussian_spinor(d0, seed=synth.SEED_SOURCE)
+    t0 = time.perf_counter()
+    _, st0, it0, r0 = oracle.solve(d0, U0, 0.12, s0, tol=1e-10, method=oracle.METHOD_CG_FULL)
+    plan["solve_4x4_cg_full_MdagM"] = {"ms": (time.perf_counter() - t0) * 1e3, "iters": it0,
+                                       "true_resid": r0, "converged": st0 == 0, "threads": cores}
+    out["plan"] = plan
+    return out
 
 
 # ------------------------------------------------------------------ GPU arm
 
 TUNE = True  # autotune launch shapes before timing (off with --no-autotune)
+
+
+CLOCK_WINDOW_S = 2.0  # the sampler needs load of at least this length around a timed region
 
 
 def run_ours(args, world, rank, local):
@@ -301,6 +371,10 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.Stream(device=dev)
     ctx = lqcd.Context(dev, stream)
     Vh = synth.volume(DIMS) // 2
+    # FMA rates of this GPU (the FP64 and double-float rooflines), measured before any
+    # sampled region
+    alu = {"f64_fma_tflops": ctx.alu_peak("f64"), "f32_fma_tflops": ctx.alu_peak("f32"),
+           "f32x2_fma_tflops": ctx.alu_peak("f32x2")}
 
     def make(prec):
         gs, fi, fo = [], [], []
@@ -322,7 +396,10 @@ def run_ours(args, world, rank, local):
     tuned = {}
 
     def timed(prec, steps, warmup, batched=True):
-        """One step = 100 applications captured once as a CUDA graph, replayed `steps` times."""
+        """One step = 100 applications captured once as a CUDA graph, replayed `steps` times.
+        Returns the event time of the timed replays, the launches in them and the clock
+        window: the timed region, extended by further (untimed) replays of the same graph
+        to CLOCK_WINDOW_S when it is shorter than the sampling period allows."""
         gs, fi, fo = make(prec)
         if not args.no_autotune:  # launch shape of this precision and slot count, measured
             tuned[f"{prec}_x{NSETS if batched else 1}"] = lqcd.autotune_dslash(
@@ -339,29 +416,39 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         barrier(world)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t0 = time.perf_counter()
+        t0 = time.time()
         with torch.cuda.stream(stream):
             e0.record(stream)
             for _ in range(steps):
                 graph.replay()
             e1.record(stream)
         torch.cuda.synchronize()
-        t1 = time.perf_counter()
+        t1 = time.time()
         barrier(world)
         ms = e0.elapsed_time(e1)
+        if t1 - t0 < CLOCK_WINDOW_S:
+            with torch.cuda.stream(stream):
+                while time.time() - t0 < CLOCK_WINDOW_S:
+                    for _ in range(20):
+                        graph.replay()
+                    torch.cuda.synchronize()
+        t2 = time.time()
         del graph
         if batch:
             batch.close()
         for o in gs + fi + fo:
             o.close()
         launches = steps * (APPS_PER_STEP // NSETS if batched else APPS_PER_STEP)
-        return ms, launches, (t0, t1)
+        return ms, launches, (t0, t1, t2)
 
     sampler = ClockSampler(dev)
     sampler.start()
-    time.sleep(0.3)
-    ms32, launches, (t0, t1) = timed("f32", args.steps, args.warmup)
-    clocks = sampler.summary(t0, t1)
+    time.sleep(0.5)
+    ms32, launches, (t0, t1, t2) = timed("f32", args.steps, args.warmup)
+    clocks = sampler.summary(t0 - 0.05, t2 + 0.05)
+    clocks["window"] = (f"timed region {t1 - t0:.3f} s" + (
+        f", extended to {t2 - t0:.2f} s by replaying the same graph (untimed)" if t2 > t1 else ""))
+    clocks["samples_in_timed_region"] = sampler.summary(t0 - 0.05, t1 + 0.05)["samples"]
     steps64 = max(3, args.steps // 8)
     ms64, _, _ = timed("f64", steps64, args.warmup)
     msdf, _, _ = timed("df64", steps64, args.warmup)
@@ -385,12 +472,16 @@ def run_ours(args, world, rank, local):
     apps64 = steps64 * APPS_PER_STEP
     gbs64 = b64 * apps64 / (ms64 * 1e-3) / 1e9
     flops_site = 1320
+    f64_tflops = flops_site * Vh * apps64 / (ms64 * 1e-3) / 1e12
+    df_tflops = flops_site * Vh * apps64 / (msdf * 1e-3) / 1e12
 
-    # end to end through the C ABI with host buffers: upload, 100 applications, download
-    e2e = run_e2e(ctx, lqcd, sets, args, world)
+    # end to end through the C ABI with host buffers: the headline workload (10 sets, 10-slot
+    # launches) with every set's input uploaded and output downloaded in every step
+    e2e = run_e2e(ctx, lqcd, sets, args, world, stream)
 
     peak, peak_kind = measured_peaks()
-    kname = f"k_dslash<F32,F32,18,nodag,LIN> x{NSETS} slots"
+    kname = f"k_dslash<F32,F32,18,nodag,EPI_PLAIN> x{NSETS} slots"
+    df_ops = profile_counts("dslash_df64_16x32_fp32_ops_per_site")
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -407,6 +498,26 @@ def run_ours(args, world, rank, local):
                      "traffic": profile_traffic("dslash_f32_18_16x32"),
                      "kernel": kname, "us_per_launch": us_per_launch,
                      "us_per_application": ms32 * 1e3 / apps},
+        # the paper's precision (Section 3: FP64): bound by the FP64 pipe on this part
+        "roofline_f64": {"bound": "alu", "achieved": f64_tflops, "peak": alu["f64_fma_tflops"],
+                         "unit": "TFLOP/s", "frac": f64_tflops / alu["f64_fma_tflops"],
+                         "peak_kind": "measured FP64 FMA rate of this GPU (lqcd_alu_peak, same run)",
+                         "flops_per_site": flops_site,
+                         "kernel": f"k_dslash<F64,F64,18,nodag,EPI_PLAIN> x{NSETS} slots",
+                         "us_per_application": ms64 * 1e3 / apps64,
+                         "hbm_frac": gbs64 / peak},
+        # FP64-class storage, arithmetic in double-float on the FP32 pipes
+        "roofline_df64": {"bound": "alu",
+                          "achieved": None if df_ops is None else df_ops * Vh * apps64 / (msdf * 1e-3) / 1e12,
+                          "peak": alu["f32_fma_tflops"] / 2, "unit": "T FP32 instructions/s",
+                          "frac": None if df_ops is None else
+                          df_ops * Vh * apps64 / (msdf * 1e-3) / 1e12 / (alu["f32_fma_tflops"] / 2),
+                          "peak_kind": "measured FP32 FMA rate / 2 (one FP32 instruction per lane and cycle)",
+                          "fp32_instructions_per_site": df_ops,
+                          "kernel": f"k_dslash3<DF64,DF64,nodag,EPI_PLAIN> x{NSETS} slots",
+                          "us_per_application": msdf * 1e3 / apps64,
+                          "hbm_frac": b64 * apps64 / (msdf * 1e-3) / 1e9 / peak},
+        "alu_peaks": alu,
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -416,7 +527,8 @@ def run_ours(args, world, rank, local):
             "dslash_f64_GBps": gbs64, "dslash_f64_us_per_application": ms64 * 1e3 / apps64,
             "dslash_df64_GBps": b64 * apps64 / (msdf * 1e-3) / 1e9,
             "dslash_df64_us_per_application": msdf * 1e3 / apps64,
-            "dslash_f64_gflops": flops_site * Vh * apps64 / (ms64 * 1e-3) / 1e9,
+            "dslash_f64_gflops": f64_tflops * 1e3,
+            "dslash_df64_gflops_double_float": df_tflops * 1e3,
             "one_application_per_launch": single,
         },
     }
@@ -426,10 +538,10 @@ def run_ours(args, world, rank, local):
         line["multi_rhs"] = run_mrhs_section(ctx, lqcd, inputs, world)
         line["multi_lattice"] = run_mlat_section(ctx, lqcd, inputs, world)
         line["serve"] = run_serve_section(ctx, lqcd, inputs, world, rank)
-        line["heatbath"] = run_heatbath_section(ctx, lqcd, world)
+        line["heatbath"] = run_heatbath_section(ctx, lqcd, world, alu)
         line["hmc"] = run_hmc_section(ctx, lqcd, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_oracle()
+        line["cpu_baseline"] = cpu_baseline_oracle(inputs.get("solve"))
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
@@ -484,10 +596,16 @@ def run_solve_section(ctx, lqcd, inputs, world):
                   true_resid=max(i["true_resid"] for i in infos),
                   converged=all(i["status"] == 0 for i in infos))
         out[name] = st
+    # the FP64-class comparator on this part is the double-float CG (FP64-class storage and
+    # arithmetic on the FP32 pipes); plain FP64 CG is bound by GB300's narrow FP64 pipe
+    base_df = out["cg_df64"]["solves_per_s"]
     base = out["cg_fp64"]["solves_per_s"]
     for name in list(out):
         if isinstance(out[name], dict) and "solves_per_s" in out[name]:
+            out[name]["speedup_vs_cg_df64"] = out[name]["solves_per_s"] / base_df
             out[name]["speedup_vs_cg_fp64"] = out[name]["solves_per_s"] / base
+    out["comparators"] = ("speedup_vs_cg_df64: against the double-float CG, the fair FP64-class "
+                          "comparator on GB300; speedup_vs_cg_fp64: against plain FP64 CG (FP64 pipe bound)")
     for o_ in (g, src, x):
         o_.close()
     return out
@@ -578,9 +696,11 @@ def run_mlat_section(ctx, lqcd, inputs, world):
     return res
 
 
-def run_heatbath_section(ctx, lqcd, world):
+def run_heatbath_section(ctx, lqcd, world, alu=None):
     """SU(3) heatbath sweeps at 32^3x64, beta 6.0, from a cold start (unit links): link
-    updates/s, FP64 ALU roofline, plaquette."""
+    updates/s and the FP64 pipe's share. The update's arithmetic is partly double-float on
+    the FP32 pipes and partly FP64 (Creutz's draw, the accept test); its FP64 roofline takes
+    the FP64 operations one link update executes, counted by ncu on the current sources."""
     import torch
     from paper_1112_5280_gb300 import synth
     g = ctx.gauge(HB_DIMS, synth.unit_links(HB_DIMS), prec="f64")
@@ -593,15 +713,19 @@ def run_heatbath_section(ctx, lqcd, world):
     dt = max_over_ranks(time.perf_counter() - t0, world)
     links = 4 * synth.volume(HB_DIMS)
     rate = links * n / dt
-    achieved = rate * HB_FLOPS_PER_LINK / 1e12
     res = {"workload": f"{'x'.join(map(str, HB_DIMS))} Wilson gauge action beta={HB_BETA}, cold start, "
                        "Cabibbo-Marinari + Creutz, reunitarised every sweep",
            "sweeps": n, "ms_per_sweep": dt / n * 1e3, "link_updates_per_s": rate * world,
-           "plaquette_after": g.plaquette(), "attempt_limit_hits": fails,
-           "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                        "frac": achieved / FP64_PEAK_TFLOPS,
-                        "peak_kind": "derived FP64: 152 SMs x 2.07 GHz x 2 FMA/clk/SM x 2 flop",
-                        "flops_per_link_update": HB_FLOPS_PER_LINK}}
+           "plaquette_after": g.plaquette(), "attempt_limit_hits": fails}
+    f64_ops = profile_counts("heatbath_32x64_fp64_flop_per_link")
+    if f64_ops and alu:
+        ach = rate * f64_ops / 1e12
+        res["roofline"] = {"bound": "alu", "achieved": ach, "peak": alu["f64_fma_tflops"],
+                           "unit": "TFLOP/s", "frac": ach / alu["f64_fma_tflops"],
+                           "peak_kind": "measured FP64 FMA rate of this GPU (lqcd_alu_peak, same run)",
+                           "fp64_flop_per_link_update": f64_ops,
+                           "note": "FP64 flop executed per link update (2 per DFMA), from an ncu capture "
+                                   "of k_heatbath on the current sources; the rest runs on the FP32 pipes"}
     g.close()
     return res
 
@@ -653,10 +777,14 @@ def run_dslash32_section(ctx, lqcd, world, U=None):
     return out
 
 
+HMC_NSTEPS, HMC_NGAUGE, HMC_TRAJ = 20, 4, 4
+
+
 def run_hmc_section(ctx, lqcd, world):
-    """One N_f = 2 twisted-mass HMC trajectory (2MN, tau 1, 8 outer x 4 gauge steps, force
-    solves to 1e-10 with FP16-12 sloppy CG) at 16^3x32 on links thermalised by 20 heatbath
-    sweeps at beta 5.6."""
+    """N_f = 2 twisted-mass HMC (2MN, tau 1, 20 outer x 4 gauge steps, force solves to 1e-10
+    with FP16-12 sloppy CG) at 16^3x32 on links thermalised by 20 heatbath sweeps at beta
+    5.6 and 2 HMC trajectories; then 4 timed trajectories with the Metropolis test. The step
+    count keeps |dH| near or below 1 (8 steps gave dH ~ 4)."""
     import torch
     from paper_1112_5280_gb300 import synth
     d = HMC_DIMS
@@ -665,6 +793,7 @@ def run_hmc_section(ctx, lqcd, world):
     ev = (synth.parity_of_sites(d) == 0)[:, None, None]
     eta = ctx.field(d, "f64", lqcd.FULL)
     phi = ctx.field(d, "f64", lqcd.FULL)
+    m = ctx.mom(d)
 
     def refresh(k):
         """Momentum and pseudofermion heatbath of trajectory k: phi = Mhat^dag eta at the current links."""
@@ -672,52 +801,61 @@ def run_hmc_section(ctx, lqcd, world):
         lqcd.apply_Mhat(g, HMC_KAPPA, eta, phi, dagger=True, mu=HMC_MU)
         m.upload(synth.gaussian_momenta(d, seed=synth.SEED_SOURCE + 20 + k))
 
-    m = ctx.mom(d)
-    p = lqcd.hmc_params(beta=HMC_BETA, kappa=HMC_KAPPA, mu=HMC_MU, tau=1.0, nsteps=8, ngauge=4,
-                        scheme=lqcd.TWO_MN, tol=1e-10)
+    kw = dict(beta=HMC_BETA, kappa=HMC_KAPPA, mu=HMC_MU, tau=1.0, nsteps=HMC_NSTEPS, ngauge=HMC_NGAUGE,
+              scheme=lqcd.TWO_MN, tol=1e-10)
     opts = lqcd.solve_opts(sloppy_prec="f16", sloppy_compress=12)
     warm = []
     for k in range(2):  # towards the dynamical ensemble (accepted unconditionally)
         refresh(k)
-        warm.append(lqcd.hmc_trajectory(g, p, m, phi, opts)["dH"])
-    refresh(2)
-    torch.cuda.synchronize()
-    barrier(world)
-    t0 = time.perf_counter()
-    info = lqcd.hmc_trajectory(g, p, m, phi, opts)
-    dt = max_over_ranks(time.perf_counter() - t0, world)
+        warm.append(lqcd.hmc_trajectory(g, lqcd.hmc_params(**kw), m, phi, opts)["dH"])
+    rng = np.random.default_rng(synth.SEED_ARRIVALS + 7)
+    ms, infos = [], []
+    for k in range(HMC_TRAJ):
+        refresh(2 + k)
+        p = lqcd.hmc_params(accept_u=float(1.0 - rng.random()), **kw)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        infos.append(lqcd.hmc_trajectory(g, p, m, phi, opts))
+        ms.append(max_over_ranks(time.perf_counter() - t0, world) * 1e3)
+    dH = [i["dH"] for i in infos]
     res = {"workload": f"{'x'.join(map(str, d))} N_f=2 twisted mass kappa={HMC_KAPPA} mu={HMC_MU}, "
-                       f"beta={HMC_BETA} (links: 20 heatbath sweeps, then 2 HMC trajectories), 2MN tau=1 8x4 steps, "
-                       "force solves 1e-10 (FP16-12 sloppy CG, double-float updates)",
-           "ms_per_trajectory": dt * 1e3, "trajectories_per_s": world / dt,
-           "dH": info["dH"], "dH_warmup": warm, "force_evals": info["force_evals"],
-           "solver_iters": info["solver_iters"],
-           "plaquette": info["plaquette"], "fermion_action_start": info["fermion0"]}
+                       f"beta={HMC_BETA} (links: 20 heatbath sweeps, then 2 HMC trajectories), 2MN tau=1 "
+                       f"{HMC_NSTEPS}x{HMC_NGAUGE} steps, force solves 1e-10 (FP16-12 sloppy CG, "
+                       f"double-float updates), {HMC_TRAJ} timed trajectories with the Metropolis test",
+           "ms_per_trajectory": float(np.mean(ms)), "ms_each": [round(v, 1) for v in ms],
+           "trajectories_per_s": world * 1e3 / float(np.mean(ms)),
+           "dH": dH, "dH_warmup": warm, "acceptance": float(np.mean([i["accepted"] for i in infos])),
+           "exp_minus_dH_mean": float(np.mean(np.exp(-np.asarray(dH)))),
+           "force_evals": infos[-1]["force_evals"], "solver_iters": infos[-1]["solver_iters"],
+           "plaquette": infos[-1]["plaquette"]}
     for o_ in (g, m, eta, phi):
         o_.close()
     return res
 
 
 def run_serve_section(ctx, lqcd, inputs, world, rank):
-    """Poisson stream over {8^4, 16^3x32, 24^3x48, 32^3x64} (0.4/0.3/0.2/0.1), resident gauge
-    fields, admission by HBM budget, continuous batching; closed-loop capacity, then open loop
-    at 0.5x and 0.9x of it."""
+    """Poisson stream over {8^4, 16^3x32, 24^3x48, 32^3x64} (0.4/0.3/0.2/0.1), 4 resident gauge
+    fields and sources per size, admission by HBM budget, continuous batching; closed-loop
+    capacity, then open loop at 0.5x and 0.9x of it, 240 requests each after a warm-up stream,
+    with p50/p99 per lattice size."""
     from paper_1112_5280_gb300 import serve, synth
     gpools, spools = inputs["serve"]
     opts = lqcd.solve_opts(sloppy_prec="f16", sloppy_compress=12, chunk=16)
     budget = 64 << 30
     srv = serve.GpuServer(ctx, serve.LATTICES, gpools, spools, opts=opts, hbm_budget=budget,
                           max_slots=64)
-    n = 120
+    n = SERVE_N
     mk = lambda rate, seed: serve.shard(serve.poisson_stream(
         n, rate, seed=seed, gauge_pool=SERVE_POOL, source_pool=SERVE_POOL), rank, world)  # noqa: E731
-    warm = serve.poisson_stream(8, 0, seed=1, gauge_pool=SERVE_POOL, source_pool=SERVE_POOL)
+    warm = serve.poisson_stream(16, 0, seed=1, gauge_pool=SERVE_POOL, source_pool=SERVE_POOL)
     srv.scheduler().run(warm, realtime=False)
     res, wall = srv.scheduler().run(mk(0, synth.SEED_ARRIVALS), realtime=False)
     cap = serve.summarize(res, wall)
     out = {"workload": "Poisson stream, lattices 8^4/16^3x32/24^3x48/32^3x64 weights 0.4/0.3/0.2/0.1, "
-                       "kappa U[0.12,0.155], tol 1e-10, FP16-12 sloppy CG + FP64 reliable updates, "
-                       f"budget {budget >> 30} GiB, up to 64 concurrent requests",
+                       f"kappa U[0.12,0.155], tol 1e-10, {SERVE_POOL} resident gauge fields and sources per "
+                       "size, FP16-12 sloppy CG + FP64-class reliable updates, "
+                       f"budget {budget >> 30} GiB, up to 64 concurrent requests, {n} requests per run",
            "closed_loop": cap}
     for frac in (0.5, 0.9):
         rate = frac * cap["solves_per_s"] * world
@@ -731,38 +869,57 @@ def run_serve_section(ctx, lqcd, inputs, world, rank):
     return out
 
 
-def run_e2e(ctx, lqcd, sets, args, world):
+def run_e2e(ctx, lqcd, sets, args, world, stream):
+    """The headline workload through the C ABI with host buffers: every step uploads each
+    set's input spinor from pinned host memory (full-lattice FP64, the host layout), runs the
+    10 batched launches of 10 applications and downloads each set's output. CUDA events on
+    the context stream around the steps; the downloads synchronise the host."""
     import torch
     from paper_1112_5280_gb300 import synth
-    U, psi = sets[0]
-    g = ctx.gauge(DIMS, U, prec="f32", compress=18, t_bc=-1)
+    gs = [ctx.gauge(DIMS, U, prec="f32", compress=18, t_bc=-1) for U, _ in sets]
     # full-lattice fields: the host arrays of a user's call; D_eo reads the odd half of fi
     # and writes the even half of fo
-    fi = ctx.field(DIMS, "f32", lqcd.FULL)
-    fo = ctx.field(DIMS, "f32", lqcd.FULL)
-    host_in = torch.from_numpy(psi).pin_memory().numpy()
-    host_out = torch.zeros(psi.shape, dtype=torch.complex128).pin_memory().numpy()
+    fi = [ctx.field(DIMS, "f32", lqcd.FULL) for _ in sets]
+    fo = [ctx.field(DIMS, "f32", lqcd.FULL) for _ in sets]
+    host_in = [torch.from_numpy(psi).pin_memory().numpy() for _, psi in sets]
+    host_out = [torch.zeros(psi.shape, dtype=torch.complex128).pin_memory().numpy() for _, psi in sets]
+    batch = lqcd.DslashBatch(gs, fi, fo, 0)
     Vh = synth.volume(DIMS) // 2
-    steps = max(3, args.steps // 10)
-    for _ in range(2):
-        fi.upload(host_in)
-        for _ in range(APPS_PER_STEP):
-            lqcd.dslash_eo(g, fi, fo, 0)
-        fo.download(host_out)
+
+    def step():
+        for f, h in zip(fi, host_in):
+            f.upload(h)
+        for _ in range(APPS_PER_STEP // NSETS):
+            batch.apply()
+        for f, h in zip(fo, host_out):
+            f.download(h)
+
+    steps = max(3, args.steps // 20)
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
     barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
-    for _ in range(steps):
-        fi.upload(host_in)
-        for _ in range(APPS_PER_STEP):
-            lqcd.dslash_eo(g, fi, fo, 0)
-        fo.download(host_out)
-    dt = max_over_ranks(time.perf_counter() - t0, world)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
     bytes_step = algorithmic_bytes_per_site(4, 18) * Vh * APPS_PER_STEP
-    for o in (g, fi, fo):
+    nbytes = sum(h.nbytes for h in host_in)
+    batch.close()
+    for o in gs + fi + fo:
         o.close()
-    return {"value": bytes_step * steps * world / dt / 1e9, "unit": "GB/s",
-            "h2d_bytes_per_step": int(psi.nbytes), "d2h_bytes_per_step": int(psi.nbytes),
-            "steps": steps, "note": "host FP64 spinor upload + 100 applications + download"}
+    return {"value": bytes_step * steps * world / (ms * 1e-3) / 1e9, "unit": "GB/s",
+            "h2d_bytes_per_step": int(nbytes), "d2h_bytes_per_step": int(nbytes),
+            "steps": steps, "ms_per_step": ms / steps, "wall_ms_per_step": wall * 1e3 / steps,
+            "note": f"headline workload: {NSETS} host FP64 spinors uploaded, {APPS_PER_STEP} "
+                    f"applications in {APPS_PER_STEP // NSETS} batched launches, {NSETS} outputs "
+                    "downloaded per step (CUDA events on the context stream)"}
 
 
 def main():
@@ -775,7 +932,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (no autotuner)")
     ap.add_argument("--no-variants", action="store_true", help="skip the one-application-per-launch timings")
     ap.add_argument("--dslash-only", action="store_true", help="skip the solver, multi-RHS, multi-lattice and serving sections")
-    ap.add_argument("--section", choices=["heatbath", "hmc", "dslash32", "solve", "mrhs"],
+    ap.add_argument("--section", choices=["heatbath", "hmc", "dslash32", "solve", "mrhs", "cpu"],
                     help="run one section alone and print its JSON (profiling); no contract line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -787,7 +944,29 @@ def main():
     return run_ours(args, world, rank, local)
 
 
+def run_cpu_plan():
+    """The oracle's CPU baseline in full (no GPU): the bounded figures of the bench line, and
+    the plain FP64 solves of the small (4^4) and the 32^3x64 kappa 0.155 workloads to 1e-10
+    on all host cores, with the oracle's own even-odd CG."""
+    import oracle
+    from paper_1112_5280_gb300 import synth
+    U = synth.random_links(SOLVE_DIMS, SOLVE_EPS, seed=synth.SEED_LINKS)
+    b = synth.gaussian_spinor(SOLVE_DIMS, seed=synth.SEED_SOURCE)
+    out = cpu_baseline_oracle((U, b))
+    t0 = time.perf_counter()
+    _, st, it, res = oracle.solve(SOLVE_DIMS, U, SOLVE_KAPPA, b, tol=1e-10, method=oracle.METHOD_CG_EO)
+    dt = time.perf_counter() - t0
+    out["plan"]["solve_32x64_cg_eo"] = {"ms": dt * 1e3, "solves_per_s": 1.0 / dt, "iters": it,
+                                        "true_resid": res, "converged": st == 0,
+                                        "threads": oracle.get_threads()}
+    return out
+
+
 def run_one_section(args, world, rank, local):
+    if args.section == "cpu":
+        if rank == 0:
+            print(json.dumps({"section": "cpu", **run_cpu_plan()}))
+        return 0
     import torch
     from paper_1112_5280_gb300 import lqcd
     dev = local if world > 1 else 0

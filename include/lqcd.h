@@ -422,6 +422,18 @@ LQCD_API int lqcd_engine_cancel(lqcd_engine* e, long long request_id, int status
 LQCD_API int lqcd_engine_stats(const lqcd_engine* e, int* active, size_t* bytes_in_use);
 LQCD_API void lqcd_engine_destroy(lqcd_engine* e);
 
+/* ---------------------------------------------------------------- instrumentation */
+
+/* Measured fused multiply-add throughput of the context's device in TFLOP/s (2 flop per
+ * FMA): kind 0 FP64, kind 1 FP32, kind 2 FP32 issued as packed pairs (fma.rn.f32x2, two
+ * FMAs per lane and instruction). The FP64 Dslash and the double-float kernels are bound
+ * by these rates rather than by HBM on GB300, whose FP64 pipe runs at a small fraction of
+ * its FP32 rate; the paper has no counterpart (it reports FP64 GFLOP/s on an AMD GPU).
+ * Runs a probe kernel of independent FMA chains on every SM six times on the context
+ * stream (the first as warm-up) and reports the fastest; about 0.1 s. Synchronous;
+ * allocates and frees a few bytes. LQCD_EINVAL for another kind. */
+LQCD_API int lqcd_alu_peak(lqcd_ctx* ctx, int kind, double* tflops);
+
 /* ---------------------------------------------------------------- tuning */
 
 /* Caps the persistent grid of batched kernel family (0 Dslash, 1 BLAS) at

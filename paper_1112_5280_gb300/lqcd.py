@@ -107,6 +107,7 @@ def load(build_if_missing: bool = True):
     _sig(lib, "lqcd_ctx_release_cache", i, [_VP])
     _sig(lib, "lqcd_ctx_sync", i, [_VP])
     _sig(lib, "lqcd_ctx_launch_count", ll, [_VP])
+    _sig(lib, "lqcd_alu_peak", i, [_VP, i, C.POINTER(d)])
     _sig(lib, "lqcd_set_grid_multiplier", None, [i, i])
     _sig(lib, "lqcd_set_dslash_form", i, [i, i])
     _sig(lib, "lqcd_gauge_upload", i, [_VP, _IP, _VP, i, i, i, C.POINTER(_VP)])
@@ -250,6 +251,13 @@ class Context:
     @property
     def launches(self) -> int:
         return int(self._lib.lqcd_ctx_launch_count(self.h))
+
+    def alu_peak(self, kind: str) -> float:
+        """Measured FMA throughput of the device in TFLOP/s: kind "f64", "f32" or "f32x2" (packed
+        FP32 pairs) (lqcd_alu_peak)."""
+        out = C.c_double(0.0)
+        _check(self._lib.lqcd_alu_peak(self.h, {"f64": 0, "f32": 1, "f32x2": 2}[kind], C.byref(out)))
+        return float(out.value)
 
     def gauge(self, dims, U, prec="f64", compress=18, t_bc=-1):
         return Gauge(self, dims, U, prec, compress, t_bc)

@@ -46,6 +46,7 @@ class Result:
     status: int
     iters: int
     true_resid: float
+    lattice: int = -1
 
     @property
     def latency(self) -> float:
@@ -89,7 +90,18 @@ def summarize(results: Sequence[Result], wall: float) -> dict:
         "mean_ms": None if not lat else 1e3 * float(np.mean(lat)),
         "max_resid": max((r.true_resid for r in ok), default=None),
         "wall_s": wall,
+        "by_lattice": by_lattice(results),
     }
+
+
+def by_lattice(results: Sequence[Result], lattices=LATTICES) -> dict:
+    """Request count, p50 and p99 latency per lattice size ("LxLyLzLt")."""
+    out = {}
+    for li in sorted({r.lattice for r in results if r.lattice >= 0}):
+        lat = [r.latency for r in results if r.lattice == li]
+        name = "x".join(map(str, lattices[li])) if li < len(lattices) else str(li)
+        out[name] = {"n": len(lat), "p50_ms": 1e3 * percentile(lat, 50), "p99_ms": 1e3 * percentile(lat, 99)}
+    return out
 
 
 class Scheduler:
@@ -125,7 +137,7 @@ class Scheduler:
             still = []
             for r in waiting:
                 if r.deadline is not None and now - r.arrival > r.deadline:
-                    results.append(Result(r.rid, r.arrival, now, now, -6, 0, float("nan")))
+                    results.append(Result(r.rid, r.arrival, now, now, -6, 0, float("nan"), r.lattice))
                 else:
                     still.append(r)
             waiting = still
@@ -147,7 +159,7 @@ class Scheduler:
                 for eid in self.engine.completed():
                     r, adm = active.pop(eid)
                     status, iters, resid = self.collect_fn(eid)
-                    results.append(Result(r.rid, r.arrival, adm, now, status, iters, resid))
+                    results.append(Result(r.rid, r.arrival, adm, now, status, iters, resid, r.lattice))
             elif i < len(pending):
                 # idle until the next arrival
                 if realtime:
