@@ -227,7 +227,10 @@ typedef struct lqcd_solve_opts {
   int true_prec;        /* FP64-class true residual, solution and outer correction: LQCD_F64
                            (native) or LQCD_DF64 (double-float); -1 (default): LQCD_F64 for an
                            FP64 solve, LQCD_DF64 otherwise */
-  int pad;
+  int multi_rhs_links;  /* solves that share one gauge field in a batch (lqcd_solve_multi,
+                           lqcd_solve_batch, engines): 0 (default) the sloppy Dslash loads each
+                           site block's links once for a group of those solves; -1 each solve
+                           loads its own (the results are the same bit for bit) */
   double mu;            /* twisted mass (paper Section 3: M = 1 - kappa D + 2 i kappa mu g5,
                            one flavour of the N_f = 2 doublet; the other is -mu). 0 (default):
                            the Wilson operator. Any finite value. */
@@ -451,25 +454,38 @@ LQCD_API int lqcd_set_dslash_form(int prec, int form);
  * fastest. The default (occupancy limit, default form) is kept unless another choice is
  * more than 2% faster. The record applies to every later Dslash launch (lqcd_dslash_eo,
  * batches, operators, solves, engines) of the same precision and link reals whose tile
- * count (64 output sites a tile) has the same floor(log2). Synchronous; not to be run
- * while another thread launches on the same device. The table is process-wide. */
+ * count (64 output sites a tile) has the same floor(log2).
+ * When all n > 1 slots are on the same gauge field (n right-hand sides, as in
+ * lqcd_solve_multi) and prec is LQCD_F32, LQCD_F16 or LQCD_BF16, it also times the
+ * shared-link form, in which a CTA loads a site block's links once and applies them to a
+ * group of slots, for every group size ceil(n / d) >= 2 and every grid, and records, under
+ * (prec, link reals, n, floor(log2) of the site blocks), the group size of the fastest
+ * (kept only when more than 2% faster than the slots loading their own links; else 0).
+ * Engines with n slots on one gauge field take that group size in their sloppy steps.
+ * Synchronous; not to be run while another thread launches on the same device. The table
+ * is process-wide. */
 typedef struct lqcd_tune_result {
   int prec;         /* spinor precision of the key */
   int nr;           /* link reals of the key (12 or 18) */
   int ntiles;       /* tiles of the tuned launch */
   int ctas_per_sm;  /* chosen persistent grid, CTAs per SM (0: occupancy limit) */
-  int form;         /* chosen kernel form: 0 one thread per site, 1 colour split (DF64) */
+  int form;         /* chosen kernel form: 0 one thread per site, 1 colour split (DF64),
+                       2 shared-link multi-RHS */
   int candidates;   /* configurations timed */
   double us_best;   /* per launch, chosen configuration */
-  double us_default;/* per launch, untuned default */
+  double us_default;/* per launch, untuned default (shared-link entries: the own-link launch) */
+  int nrhs;         /* 0: launch-shape entry; n >= 2: shared-link entry for n slots on one gauge */
+  int group;        /* shared-link entries: slots per group (0: own links faster) */
 } lqcd_tune_result;
 LQCD_API int lqcd_autotune_dslash(int n, const lqcd_gauge* const* g, int prec, int compress,
                                   lqcd_tune_result* out);
 /* Copies up to max table entries into out; *n = entries in the table. */
 LQCD_API int lqcd_tune_entries(lqcd_tune_result* out, int max, int* n);
 LQCD_API void lqcd_tune_clear(void);
-/* Text file of the table, tagged with the device name and SM count; loading a file
- * made on another device model, or a malformed file, gives LQCD_EINVAL and loads nothing. */
+/* JSON file of the table ({"format": "lqcd-tune", "version": 2, "device": name_smN,
+ * "entries": [{prec, nr, nrhs, bucket, ntiles, ctas_per_sm, form, group, candidates,
+ * us_best, us_default}, ...]}); loading a file made on another device model, or a malformed
+ * file or entry, gives LQCD_EINVAL and loads nothing. */
 LQCD_API int lqcd_tune_save(const char* path);
 LQCD_API int lqcd_tune_load(const char* path);
 

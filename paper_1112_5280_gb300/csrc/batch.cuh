@@ -106,9 +106,13 @@ struct Launch {
   Work inline_work;
   int nslots;
   int ntiles;              // total tiles
-  int interleave;          // 1: tile t -> (slot t % nslots, block t / nslots), equal Vh
+  int interleave;          // 1: tile t -> (slot t % nslots, block t / nslots), equal Vh;
+                           // 2: shared-link multi-RHS Dslash (all slots on one gauge field):
+                           //    tile t -> (slot group t % mrhs_groups, block t / mrhs_groups)
   double* partials;
   int finish;              // 1: the slots' Works reduce or finish; k_finish follows the launch
+  int mrhs_group;          // interleave 2: slots per group (group g holds [g G, (g + 1) G))
+  int mrhs_groups;         // interleave 2: number of slot groups
 };
 
 __device__ __forceinline__ const Work& work_of(const Launch& L, int slot) {

@@ -37,6 +37,16 @@ int make_geom(const int dims[4], int t_bc, Geom& g) {
   g.Lxh = dims[0] / 2;
   g.Vh = (int)(V / 2);
   g.t_bc = t_bc;
+  const int radix[3] = {g.Lxh, g.L[1], g.L[2]};
+  for (int k = 0; k < 3; ++k) {
+    geom_set_divisor(g, k, (unsigned)radix[k]);
+    // the method is exact for every 32-bit numerator; check the ends of the used range
+    const unsigned d = (unsigned)radix[k];
+    for (unsigned n : {0u, 1u, d - 1, d, d + 1, (unsigned)g.Vh - 1, (unsigned)g.Vh, 0x7fffffffu}) {
+      const unsigned q = geom_div(g, k, n);
+      if (q != n / d) return set_error(LQCD_EINVAL, "division constants for %u failed at %u", d, n);
+    }
+  }
   return LQCD_OK;
 }
 

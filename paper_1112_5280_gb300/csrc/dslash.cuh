@@ -26,17 +26,43 @@ struct Geom {
   int Lxh;   // Lx / 2
   int Vh;    // V / 2 sites per parity
   int t_bc;  // +1 periodic, -1 antiperiodic in t
+  // Division by the radices Lxh, Ly, Lz of the half-lattice index without a divide
+  // instruction (Granlund and Montgomery, "Division by invariant integers using
+  // multiplication", PLDI 1994, Figure 4.1): for divisor d with l = ceil(log2 d),
+  // m = floor(2^32 (2^l - d) / d) + 1, and every 32-bit n,
+  //   n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0),  t = (m n) >> 32.
+  unsigned dm[3];  // m for Lxh, Ly, Lz
+  int dsh[3];      // min(l, 1) | max(l - 1, 0) << 8
 };
+
+// n / d for radix k (0: Lxh, 1: Ly, 2: Lz) of the geometry
+__host__ __device__ __forceinline__ unsigned geom_div(const Geom& g, int k, unsigned n) {
+#ifdef __CUDA_ARCH__
+  const unsigned t = __umulhi(g.dm[k], n);
+#else
+  const unsigned t = (unsigned)(((unsigned long long)g.dm[k] * n) >> 32);
+#endif
+  return (t + ((n - t) >> (g.dsh[k] & 0xff))) >> (g.dsh[k] >> 8);
+}
+
+// the constants of geom_div for divisor d >= 1
+inline void geom_set_divisor(Geom& g, int k, unsigned d) {
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  g.dm[k] = (unsigned)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+  g.dsh[k] = (l < 1 ? l : 1) | ((l > 1 ? l - 1 : 0) << 8);
+}
 
 // Half-lattice index h = xh + Lxh*(y + Ly*(z + Lz*t)) with x = 2 xh + ((p+y+z+t) & 1).
 __device__ __forceinline__ void neighbours(const Geom& g, int h, int par, int nf[4], int nb[4],
                                            int& t) {
-  const int xh = h % g.Lxh;
-  int r = h / g.Lxh;
-  const int y = r % g.L[1];
-  r /= g.L[1];
-  const int z = r % g.L[2];
-  t = r / g.L[2];
+  const unsigned r0 = geom_div(g, 0, (unsigned)h);
+  const int xh = h - (int)r0 * g.Lxh;
+  const unsigned r1 = geom_div(g, 1, r0);
+  const int y = (int)r0 - (int)r1 * g.L[1];
+  const unsigned r2 = geom_div(g, 2, r1);
+  const int z = (int)r1 - (int)r2 * g.L[2];
+  t = (int)r2;
   const int x = 2 * xh + ((par + y + z + t) & 1);
   const int rest = h - xh;
   const int xp = (x + 1 == g.L[0]) ? 0 : x + 1;
@@ -60,8 +86,8 @@ __device__ __forceinline__ Cx<R> sp(const R* v, int spin, int col) {
 }
 template <typename R>
 __device__ __forceinline__ void acc_add(R* a, int spin, int col, Cx<R> w) {
-  a[sidx(spin, col)] += w.re;
-  a[sidx(spin, col) + 1] += w.im;
+  a[sidx(spin, col)] = f_add(a[sidx(spin, col)], w.re);
+  a[sidx(spin, col) + 1] = f_add(a[sidx(spin, col) + 1], w.im);
 }
 // i * w
 template <typename R>
@@ -75,42 +101,100 @@ __device__ __forceinline__ Cx<R> sgn(Cx<R> w) {
   return {-w.re, -w.im};
 }
 
-// One hop: acc += eta * (1 + S g_MU) (U or U^dag) psi, eta = +-1.
-template <int MU, int S, bool ADJ, typename R>
-__device__ __forceinline__ void hop(const R psi[24], const R u[18], int eta, R acc[24]) {
-  Cx<R> h0[3], h1[3];
+// Spin projection of one hop: h = psi_up + S A psi_dn (the rows of (1 + S g_MU) that carry
+// information), times eta = +-1 (the t-boundary sign).
+// a + S b for a compile-time sign S = +-1 (an add or a subtract, no product)
+template <int S, typename R>
+__device__ __forceinline__ R pm(R a, R b) {
+  return S > 0 ? f_add(a, b) : f_sub(a, b);
+}
+
+template <int MU, int S, typename R>
+__device__ __forceinline__ void project(const R psi[24], int eta, Cx<R> h0[3], Cx<R> h1[3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const Cx<R> p0 = sp(psi, 0, c), p1 = sp(psi, 1, c), p2 = sp(psi, 2, c), p3 = sp(psi, 3, c);
     if (MU == 0) {  // h = psi_up + S (-i sigma_1) psi_dn
-      h0[c] = {p0.re + S * p3.im, p0.im - S * p3.re};
-      h1[c] = {p1.re + S * p2.im, p1.im - S * p2.re};
+      h0[c] = {pm<S>(p0.re, p3.im), pm<-S>(p0.im, p3.re)};
+      h1[c] = {pm<S>(p1.re, p2.im), pm<-S>(p1.im, p2.re)};
     } else if (MU == 1) {  // -i sigma_2 = [[0,-1],[1,0]]
-      h0[c] = {p0.re - S * p3.re, p0.im - S * p3.im};
-      h1[c] = {p1.re + S * p2.re, p1.im + S * p2.im};
+      h0[c] = {pm<-S>(p0.re, p3.re), pm<-S>(p0.im, p3.im)};
+      h1[c] = {pm<S>(p1.re, p2.re), pm<S>(p1.im, p2.im)};
     } else if (MU == 2) {  // -i sigma_3 = diag(-i, i)
-      h0[c] = {p0.re + S * p2.im, p0.im - S * p2.re};
-      h1[c] = {p1.re - S * p3.im, p1.im + S * p3.re};
+      h0[c] = {pm<S>(p0.re, p2.im), pm<-S>(p0.im, p2.re)};
+      h1[c] = {pm<-S>(p1.re, p3.im), pm<S>(p1.im, p3.re)};
     } else {  // identity
-      h0[c] = {p0.re + S * p2.re, p0.im + S * p2.im};
-      h1[c] = {p1.re + S * p3.re, p1.im + S * p3.im};
+      h0[c] = {pm<S>(p0.re, p2.re), pm<S>(p0.im, p2.im)};
+      h1[c] = {pm<S>(p1.re, p3.re), pm<S>(p1.im, p3.im)};
     }
     if (MU == 3 && eta < 0) {
       h0[c] = sgn<-1>(h0[c]);
       h1[c] = sgn<-1>(h1[c]);
     }
   }
+}
+
+// The same projection on FP16 storage words, in packed half2 arithmetic: word c of a site
+// holds colour c as (spin 0, 1, 2, 3) x (re, im) half2 pairs. One FP16 rounding per
+// component of h; only the 6 complex numbers of h are then converted to FP32 (instead of
+// the 12 of psi).
+template <int MU, int S>
+__device__ __forceinline__ void project_h2(const uint4 w[3], int eta, Cx<float> h0[3], Cx<float> h1[3]) {
+  // (S, -S): multiplies the swapped pair (im, re) into S * (-i) * (re + i im) = S (im, -re)
+  const __half2 mi = __floats2half2_rn(float(S), float(-S));
+  const __half2 pi = __floats2half2_rn(float(-S), float(S));  // S * i * p = S (-im, re)
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const __half2 p0 = *reinterpret_cast<const __half2*>(&w[c].x);
+    const __half2 p1 = *reinterpret_cast<const __half2*>(&w[c].y);
+    const __half2 p2 = *reinterpret_cast<const __half2*>(&w[c].z);
+    const __half2 p3 = *reinterpret_cast<const __half2*>(&w[c].w);
+    __half2 a, b;
+    if (MU == 0) {
+      a = __hfma2(__lowhigh2highlow(p3), mi, p0);
+      b = __hfma2(__lowhigh2highlow(p2), mi, p1);
+    } else if (MU == 1) {
+      a = S > 0 ? __hsub2(p0, p3) : __hadd2(p0, p3);
+      b = S > 0 ? __hadd2(p1, p2) : __hsub2(p1, p2);
+    } else if (MU == 2) {
+      a = __hfma2(__lowhigh2highlow(p2), mi, p0);
+      b = __hfma2(__lowhigh2highlow(p3), pi, p1);
+    } else {
+      a = S > 0 ? __hadd2(p0, p2) : __hsub2(p0, p2);
+      b = S > 0 ? __hadd2(p1, p3) : __hsub2(p1, p3);
+    }
+    if (MU == 3 && eta < 0) {
+      a = __hneg2(a);
+      b = __hneg2(b);
+    }
+    const float2 fa = __half22float2(a), fb = __half22float2(b);
+    h0[c] = {fa.x, fa.y};
+    h1[c] = {fb.x, fb.y};
+  }
+}
+
+// The rest of a hop: acc += (U or U^dag) h, lifted back to four spins by (1 + S g_MU).
+template <int MU, int S, bool ADJ, typename R>
+__device__ __forceinline__ void hop_half(const Cx<R> h0[3], const Cx<R> h1[3], const R u[18], R acc[24]) {
+  // w = U h (or U^dag h) per spin row: for each product u h, re += u.re h.re - u.im h.im and
+  // im += u.re h.im + u.im h.re, as four multiply-adds in this order
   Cx<R> w0[3], w1[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    Cx<R> s0{R(0), R(0)}, s1{R(0), R(0)};
+    Cx<R> s0, s1;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
       const Cx<R> uab = ADJ ? Cx<R>{u[(b * 3 + a) * 2], -u[(b * 3 + a) * 2 + 1]}
                             : Cx<R>{u[(a * 3 + b) * 2], u[(a * 3 + b) * 2 + 1]};
-      const Cx<R> m0 = cmul(uab, h0[b]), m1 = cmul(uab, h1[b]);
-      s0.re += m0.re; s0.im += m0.im;
-      s1.re += m1.re; s1.im += m1.im;
+      if (b == 0) {
+        s0 = {f_mul(uab.re, h0[b].re), f_mul(uab.re, h0[b].im)};
+        s1 = {f_mul(uab.re, h1[b].re), f_mul(uab.re, h1[b].im)};
+      } else {
+        s0 = {f_fma(uab.re, h0[b].re, s0.re), f_fma(uab.re, h0[b].im, s0.im)};
+        s1 = {f_fma(uab.re, h1[b].re, s1.re), f_fma(uab.re, h1[b].im, s1.im)};
+      }
+      s0 = {f_fma(-uab.im, h0[b].im, s0.re), f_fma(uab.im, h0[b].re, s0.im)};
+      s1 = {f_fma(-uab.im, h1[b].im, s1.re), f_fma(uab.im, h1[b].re, s1.im)};
     }
     w0[a] = s0;
     w1[a] = s1;
@@ -132,6 +216,32 @@ __device__ __forceinline__ void hop(const R psi[24], const R u[18], int eta, R a
       acc_add(acc, 2, a, sgn<S>(w0[a]));
       acc_add(acc, 3, a, sgn<S>(w1[a]));
     }
+  }
+}
+
+// One hop: acc += eta * (1 + S g_MU) (U or U^dag) psi, eta = +-1.
+template <int MU, int S, bool ADJ, typename R>
+__device__ __forceinline__ void hop(const R psi[24], const R u[18], int eta, R acc[24]) {
+  Cx<R> h0[3], h1[3];
+  project<MU, S>(psi, eta, h0, h1);
+  hop_half<MU, S, ADJ>(h0, h1, u, acc);
+}
+
+// One hop from the raw storage words of the neighbour spinor: FP16 spinors are projected in
+// half2 before conversion, every other precision is unpacked and projected in its arithmetic
+// type. Every Dslash form calls this, so a site's arithmetic is the same in all of them.
+template <int MU, int S, bool ADJ, int SP>
+__device__ __forceinline__ void hop_words(const typename SpinorIO<SP>::Word w[SpinorIO<SP>::NW],
+                                          const typename SpinorIO<SP>::Real u[18], int eta,
+                                          typename SpinorIO<SP>::Real acc[24]) {
+  if constexpr (SP == P_F16) {
+    Cx<float> h0[3], h1[3];
+    project_h2<MU, S>(w, eta, h0, h1);
+    hop_half<MU, S, ADJ>(h0, h1, u, acc);
+  } else {
+    typename SpinorIO<SP>::Real psi[24];
+    SpinorIO<SP>::unpack(w, psi);
+    hop<MU, S, ADJ>(psi, u, eta, acc);
   }
 }
 
@@ -184,15 +294,14 @@ __device__ __forceinline__ void compute_hop(const Geom& g, int t, const HopBuf<S
   using R = typename SpinorIO<SP>::Real;
   constexpr int MU = K / 2;
   constexpr bool FWD = (K % 2) == 0;
-  R psi[24], u[18];
-  SpinorIO<SP>::unpack(b.s, psi);
+  R u[18];
   LinkIO<LP, NR>::unpack(b.u, u);
   if (NR == 12) reconstruct_row2(u);
   // forward: U_mu(x) psi(x + mu), projector (1 - g) for D, (1 + g) for D^dag
   // backward: U_mu(x - mu)^dag psi(x - mu), projector (1 + g) for D, (1 - g) for D^dag
   const int eta = (MU == 3 && t == (FWD ? g.L[3] - 1 : 0)) ? g.t_bc : 1;
   constexpr int S = FWD ? (DAG ? 1 : -1) : (DAG ? -1 : 1);
-  hop<MU, S, !FWD>(psi, u, eta, acc);
+  hop_words<MU, S, !FWD, SP>(b.s, u, eta, acc);
 }
 
 template <int K, int D, int SP, int LP, int NR, bool DAG>

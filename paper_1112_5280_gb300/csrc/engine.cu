@@ -126,6 +126,9 @@ struct lqcd_engine {
   bool dirty = true;
   int ntiles_total = 0;
   int interleave = 0;
+  // shared-link multi-RHS Dslash for the sloppy steps (interleave mode 2): slots per group,
+  // groups, and tiles (site blocks x groups); mrhs_groups == 0: not used
+  int mrhs_group = 0, mrhs_groups = 0, mrhs_tiles = 0;
   bool any_twist = false;  // some active request has mu != 0
   bool any_normal = false, any_plain = false;  // active normal-equation / M x = b requests
   cudaGraphExec_t exec = nullptr;
@@ -311,6 +314,13 @@ Launch batch_launch(const lqcd_engine* e, int s) {
   L.ntiles = e->ntiles_total;
   L.interleave = e->interleave;
   L.partials = e->d_partials;
+  const StepKind k = kind_of(s);
+  if (e->mrhs_groups > 0 && k.dslash && !k.f64) {
+    L.interleave = 2;
+    L.ntiles = e->mrhs_tiles;
+    L.mrhs_group = e->mrhs_group;
+    L.mrhs_groups = e->mrhs_groups;
+  }
   // k_finish follows when any active slot's Work of this step reduces or runs a finisher
   for (int i = 0; i < L.nslots && !L.finish; ++i) {
     const Work& w = e->h_works[(size_t)s * e->max_slots + i];
@@ -360,6 +370,29 @@ int rebuild(lqcd_engine* e) {
     else e->any_plain = true;
   }
   e->interleave = (same && n > 1) ? 1 : 0;
+  // Slots on one gauge field share each site block's link loads in the sloppy Dslash steps
+  // (k_dslash_mrhs): a CTA applies the block's links to a group of slots. The group size is
+  // the autotuner's for this key if it tuned one (0: own links); else groups are as large
+  // as the lattice allows while the launch keeps at least 8 tiles per SM. One slot per
+  // group gains nothing over the interleaved order.
+  e->mrhs_group = e->mrhs_groups = e->mrhs_tiles = 0;
+  if (e->interleave && !e->any_twist && e->opts.multi_rhs_links >= 0 &&
+      (e->sp == P_F32 || e->sp == P_F16 || e->sp == P_BF16)) {
+    const int blocks = e->reqs[e->active[0]].ntiles;
+    int gsize = tune_shared_links(e->sp, e->nr, n, blocks, nullptr);
+    if (gsize < 0) {
+      const int want = 8 * device_sm_count();
+      const int groups = std::min(n, std::max(1, (want + blocks - 1) / blocks));
+      gsize = (n + groups - 1) / groups;
+    }
+    gsize = std::min(gsize, n);
+    const int groups = gsize > 0 ? (n + gsize - 1) / gsize : 0;
+    if (gsize > 1) {
+      e->mrhs_group = gsize;
+      e->mrhs_groups = groups;
+      e->mrhs_tiles = blocks * groups;
+    }
+  }
   std::vector<int> prefix(n + 1, 0);
   e->h_works.assign((size_t)NSTEP * e->max_slots, Work{});
   for (int i = 0; i < n; ++i) {
@@ -880,7 +913,8 @@ namespace lqcd {
 static bool same_opts(const lqcd_solve_opts& a, const lqcd_solve_opts& b) {
   return a.solver == b.solver && a.sloppy_prec == b.sloppy_prec && a.sloppy_compress == b.sloppy_compress &&
          a.maxiter == b.maxiter && a.delta == b.delta && a.chunk == b.chunk && a.use_graph == b.use_graph &&
-         a.ru_interval == b.ru_interval && a.true_prec == b.true_prec;  // mu is per request
+         a.ru_interval == b.ru_interval && a.true_prec == b.true_prec &&
+         a.multi_rhs_links == b.multi_rhs_links;  // mu is per request
 }
 
 void ctx_drop_engine(lqcd_ctx* c) {

@@ -109,6 +109,38 @@ __device__ __forceinline__ df64 df_norm(df64 a) {
   return df64(s, __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(a.lo, v)));
 }
 
+// Arithmetic with a fixed rounding sequence. nvcc fuses a * b + c into one FMA where it
+// sees fit, and the same source inlined into two different kernels may be fused in two
+// different ways, which round differently. The site arithmetic of the Dslash, which must
+// give the same bits in every kernel form (one launch per slot, interleaved slots,
+// shared-link multi-RHS), spells every product and multiply-add out with these: float and
+// double map to the round-to-nearest intrinsics, which are never contracted or reordered;
+// double-float keeps its own operators.
+template <typename R>
+__device__ __forceinline__ R f_fma(R a, R b, R c) { return a * b + c; }
+template <>
+__device__ __forceinline__ float f_fma<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <>
+__device__ __forceinline__ double f_fma<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <typename R>
+__device__ __forceinline__ R f_mul(R a, R b) { return a * b; }
+template <>
+__device__ __forceinline__ float f_mul<float>(float a, float b) { return __fmul_rn(a, b); }
+template <>
+__device__ __forceinline__ double f_mul<double>(double a, double b) { return __dmul_rn(a, b); }
+template <typename R>
+__device__ __forceinline__ R f_add(R a, R b) { return a + b; }
+template <>
+__device__ __forceinline__ float f_add<float>(float a, float b) { return __fadd_rn(a, b); }
+template <>
+__device__ __forceinline__ double f_add<double>(double a, double b) { return __dadd_rn(a, b); }
+template <typename R>
+__device__ __forceinline__ R f_sub(R a, R b) { return a - b; }
+template <>
+__device__ __forceinline__ float f_sub<float>(float a, float b) { return __fsub_rn(a, b); }
+template <>
+__device__ __forceinline__ double f_sub<double>(double a, double b) { return __dsub_rn(a, b); }
+
 // Device order of the 24 reals of a spinor: colour-major, so that the 8 reals
 // (4 spin x re/im) of one colour are contiguous words:
 //   real(spin, colour, re/im) = (colour * 4 + spin) * 2 + re/im
@@ -563,18 +595,32 @@ struct LinkIO<P_F16, 12> {
   }
 };
 
+// a_i b_j - a_j b_i for complex a_i, b_j, a_j, b_i, in a fixed order of products and sums
+template <typename R>
+__device__ __forceinline__ Cx<R> cross_term(Cx<R> ai, Cx<R> bj, Cx<R> aj, Cx<R> bi) {
+  R re = f_mul(ai.re, bj.re);
+  re = f_fma(-ai.im, bj.im, re);
+  re = f_fma(-aj.re, bi.re, re);
+  re = f_fma(aj.im, bi.im, re);
+  R im = f_mul(ai.re, bj.im);
+  im = f_fma(ai.im, bj.re, im);
+  im = f_fma(-aj.re, bi.im, im);
+  im = f_fma(-aj.im, bi.re, im);
+  return {re, im};
+}
+
 // row 2 = conj(row0 x row1)
 template <typename R>
 __device__ __forceinline__ void reconstruct_row2(R u[18]) {
   const Cx<R> a0{u[0], u[1]}, a1{u[2], u[3]}, a2{u[4], u[5]};
   const Cx<R> b0{u[6], u[7]}, b1{u[8], u[9]}, b2{u[10], u[11]};
-  // c_k = a_i b_j - a_j b_i ; row2_k = conj(c_k)
-  Cx<R> c0 = cmul(a1, b2), d0 = cmul(a2, b1);
-  Cx<R> c1 = cmul(a2, b0), d1 = cmul(a0, b2);
-  Cx<R> c2 = cmul(a0, b1), d2 = cmul(a1, b0);
-  u[12] = c0.re - d0.re; u[13] = -(c0.im - d0.im);
-  u[14] = c1.re - d1.re; u[15] = -(c1.im - d1.im);
-  u[16] = c2.re - d2.re; u[17] = -(c2.im - d2.im);
+  // c_k = a_i b_j - a_j b_i (k, i, j cyclic); row2_k = conj(c_k)
+  const Cx<R> c0 = cross_term(a1, b2, a2, b1);
+  const Cx<R> c1 = cross_term(a2, b0, a0, b2);
+  const Cx<R> c2 = cross_term(a0, b1, a1, b0);
+  u[12] = c0.re; u[13] = -c0.im;
+  u[14] = c1.re; u[15] = -c1.im;
+  u[16] = c2.re; u[17] = -c2.im;
 }
 
 template <int LP, int NR>

@@ -30,12 +30,13 @@ struct Site {
 
 __device__ __forceinline__ Site site_of(const Geom& g, int par, int h) {
   Site s;
-  const int xh = h % g.Lxh;
-  int r = h / g.Lxh;
-  s.c[1] = r % g.L[1];
-  r /= g.L[1];
-  s.c[2] = r % g.L[2];
-  s.c[3] = r / g.L[2];
+  const unsigned r0 = geom_div(g, 0, (unsigned)h);
+  const int xh = h - (int)r0 * g.Lxh;
+  const unsigned r1 = geom_div(g, 1, r0);
+  s.c[1] = (int)r0 - (int)r1 * g.L[1];
+  const unsigned r2 = geom_div(g, 2, r1);
+  s.c[2] = (int)r1 - (int)r2 * g.L[2];
+  s.c[3] = (int)r2;
   s.c[0] = 2 * xh + ((par + s.c[1] + s.c[2] + s.c[3]) & 1);
   return s;
 }

@@ -34,22 +34,25 @@ struct DslashMinBlocks {
       (SP == P_DF64) ? 4 : ((SP == P_F16 || SP == P_BF16) ? LQCD_DSLASH_MIN_BLOCKS_HALF : LQCD_DSLASH_MIN_BLOCKS);
 };
 
+// Site sums with a fixed rounding sequence (f_fma; see field.cuh), as the Dslash forms share them.
 template <typename R>
 __device__ __forceinline__ double site_norm2(const R v[24]) {
-  R s = 0;
+  R s = f_mul(v[0], v[0]);
 #pragma unroll
-  for (int i = 0; i < 24; ++i) s += v[i] * v[i];
+  for (int i = 1; i < 24; ++i) s = f_fma(v[i], v[i], s);
   return (double)s;
 }
 
 // <a, b> = sum conj(a) b over one site, (re, im)
 template <typename R>
 __device__ __forceinline__ void site_dot(const R a[24], const R b[24], double& re, double& im) {
-  R sr = 0, si = 0;
+  R sr = R(0), si = R(0);
 #pragma unroll
   for (int i = 0; i < 12; ++i) {
-    sr += a[2 * i] * b[2 * i] + a[2 * i + 1] * b[2 * i + 1];
-    si += a[2 * i] * b[2 * i + 1] - a[2 * i + 1] * b[2 * i];
+    sr = f_fma(a[2 * i], b[2 * i], sr);
+    sr = f_fma(a[2 * i + 1], b[2 * i + 1], sr);
+    si = f_fma(a[2 * i], b[2 * i + 1], si);
+    si = f_fma(-a[2 * i + 1], b[2 * i], si);
   }
   re = (double)sr;
   im = (double)si;
@@ -84,8 +87,8 @@ __device__ __forceinline__ void twist24(R v[24], double sd, double td) {
   for (int c = 0; c < 12; ++c) {
     const R re = v[2 * c], im = v[2 * c + 1];
     const R tt = (c % 4) < 2 ? t : -t;
-    v[2 * c] = s * (re - tt * im);
-    v[2 * c + 1] = s * (im + tt * re);
+    v[2 * c] = f_mul(s, f_fma(-tt, im, re));
+    v[2 * c + 1] = f_mul(s, f_fma(tt, re, im));
   }
 }
 // the same for the 4 spins of one colour (v[2 spin], v[2 spin + 1])
@@ -106,6 +109,73 @@ __device__ __forceinline__ bool single_slot_idle(const Launch& L) {
   return L.nslots == 1 && !slot_runs(work_of(L, 0));
 }
 
+// Epilogue of the one-thread-per-site Dslash at site h of slot w, acc = D_{p,1-p} in at h:
+//   out = a * acc + c1 * y1 + c2 * y2                                 (EPI_LIN, EPI_PLAIN)
+//   r -= alpha (y1 + a * acc); x += alpha p                           (EPI_CG, CG step)
+// (twisted: out = T(a acc) + c1 y1 + c2 T_y y2 and r -= alpha (T_y y1 + T(a acc)))
+// and the site's contributions v0..v2 to the slot's reduction.
+template <int SP, int EPI>
+__device__ __forceinline__ void dslash_epilogue(const Work& w, int h, typename SpinorIO<SP>::Real acc[24],
+                                                double& v0, double& v1, double& v2) {
+  using R = typename SpinorIO<SP>::Real;
+  const R a = (R)w.a;
+  if constexpr (EpiTraits<EPI>::lin) {
+    if (w.a != 1.0) {  // a plain hopping term (a = 1) keeps acc as it is, bit for bit
+#pragma unroll
+      for (int i = 0; i < 24; ++i) acc[i] = f_mul(acc[i], a);
+    }
+    if constexpr (EpiTraits<EPI>::tw) twist24(acc, w.tw_s, w.tw_t);
+    R y[24];
+    if (w.y1) {
+      SpinorIO<SP>::load(w.y1, w.g.Vh, h, y);
+      const R c = (R)w.c1;
+#pragma unroll
+      for (int i = 0; i < 24; ++i) acc[i] = f_fma(c, y[i], acc[i]);
+    }
+    if (w.y2) {
+      R y2[24];
+      SpinorIO<SP>::load(w.y2, w.g.Vh, h, y2);
+      if constexpr (EpiTraits<EPI>::tw) twist24(y2, 1.0, w.ty_t);
+      const R c = (R)w.c2;
+#pragma unroll
+      for (int i = 0; i < 24; ++i) acc[i] = f_fma(c, y2[i], acc[i]);
+    }
+    SpinorIO<SP>::store(w.out, w.g.Vh, h, acc);
+    if (!EpiTraits<EPI>::red) {
+    } else if (w.red == 1) {
+      v0 = site_norm2(acc);
+    } else if (w.red == 2) {
+      R z[24];
+      SpinorIO<SP>::load(w.zin, w.g.Vh, h, z);
+      site_dot(z, acc, v0, v1);
+    } else if (w.red == 3) {  // <out, y1>, |out|^2
+      site_dot(acc, y, v0, v1);
+      v2 = site_norm2(acc);
+    }
+  } else {
+    const R alpha = (R)w.sc->alpha;
+    R y[24], r[24];
+    SpinorIO<SP>::load(w.y1, w.g.Vh, h, y);
+    SpinorIO<SP>::load(w.out, w.g.Vh, h, r);
+    if constexpr (EpiTraits<EPI>::tw) {
+      twist24(acc, w.tw_s, w.tw_t);
+      twist24(y, 1.0, w.ty_t);
+    }
+#pragma unroll
+    for (int i = 0; i < 24; ++i) r[i] = f_fma(-alpha, f_fma(a, acc[i], y[i]), r[i]);
+    SpinorIO<SP>::store(w.out, w.g.Vh, h, r);
+    v0 = site_norm2(r);
+    using XR = typename SpinorIO<XSloppy<SP>::P>::Real;
+    R p[24];
+    XR x[24];
+    SpinorIO<SP>::load(w.zin, w.g.Vh, h, p);
+    SpinorIO<XSloppy<SP>::P>::load(w.z, w.g.Vh, h, x);
+#pragma unroll
+    for (int i = 0; i < 24; ++i) x[i] = f_fma((XR)alpha, (XR)p[i], x[i]);
+    SpinorIO<XSloppy<SP>::P>::store(w.z, w.g.Vh, h, x);
+  }
+}
+
 // Batched Dslash: out = a * D_{p,1-p} in + c1 * y1 + c2 * y2      (EPI_LIN)
 //                 r -= alpha (y1 + a * D in); x += alpha p      (EPI_CG, CG step)
 // (twisted: out = T(a D in) + c1 y1 + c2 T_y y2 and r -= alpha (T_y y1 + T(a D in)))
@@ -124,63 +194,130 @@ __global__ void __launch_bounds__(TILE, DslashMinBlocks<SP>::value) k_dslash(con
     if (h < w.g.Vh) {
       R acc[24];
       dslash_site<SP, LP, NR, DAG>(w.g, h, w.out_par, w.in, w.Uout, w.Uin, acc);
-      const R a = (R)w.a;
-      if constexpr (EpiTraits<EPI>::lin) {
-#pragma unroll
-        for (int i = 0; i < 24; ++i) acc[i] *= a;
-        if constexpr (EpiTraits<EPI>::tw) twist24(acc, w.tw_s, w.tw_t);
-        R y[24];
-        if (w.y1) {
-          SpinorIO<SP>::load(w.y1, w.g.Vh, h, y);
-          const R c = (R)w.c1;
-#pragma unroll
-          for (int i = 0; i < 24; ++i) acc[i] += c * y[i];
-        }
-        if (w.y2) {
-          R y2[24];
-          SpinorIO<SP>::load(w.y2, w.g.Vh, h, y2);
-          if constexpr (EpiTraits<EPI>::tw) twist24(y2, 1.0, w.ty_t);
-          const R c = (R)w.c2;
-#pragma unroll
-          for (int i = 0; i < 24; ++i) acc[i] += c * y2[i];
-        }
-        SpinorIO<SP>::store(w.out, w.g.Vh, h, acc);
-        if (!EpiTraits<EPI>::red) {
-        } else if (w.red == 1) {
-          v0 = site_norm2(acc);
-        } else if (w.red == 2) {
-          R z[24];
-          SpinorIO<SP>::load(w.zin, w.g.Vh, h, z);
-          site_dot(z, acc, v0, v1);
-        } else if (w.red == 3) {  // <out, y1>, |out|^2
-          site_dot(acc, y, v0, v1);
-          v2 = site_norm2(acc);
-        }
-      } else {
-        const R alpha = (R)w.sc->alpha;
-        R y[24], r[24];
-        SpinorIO<SP>::load(w.y1, w.g.Vh, h, y);
-        SpinorIO<SP>::load(w.out, w.g.Vh, h, r);
-        if constexpr (EpiTraits<EPI>::tw) {
-          twist24(acc, w.tw_s, w.tw_t);
-          twist24(y, 1.0, w.ty_t);
-        }
-#pragma unroll
-        for (int i = 0; i < 24; ++i) r[i] -= alpha * (y[i] + a * acc[i]);
-        SpinorIO<SP>::store(w.out, w.g.Vh, h, r);
-        v0 = site_norm2(r);
-        using XR = typename SpinorIO<XSloppy<SP>::P>::Real;
-        R p[24];
-        XR x[24];
-        SpinorIO<SP>::load(w.zin, w.g.Vh, h, p);
-        SpinorIO<XSloppy<SP>::P>::load(w.z, w.g.Vh, h, x);
-#pragma unroll
-        for (int i = 0; i < 24; ++i) x[i] += (XR)alpha * (XR)p[i];
-        SpinorIO<XSloppy<SP>::P>::store(w.z, w.g.Vh, h, x);
-      }
+      dslash_epilogue<SP, EPI>(w, h, acc, v0, v1, v2);
     }
     if constexpr (EpiTraits<EPI>::red)
       tile_partial<TILE, std::is_same<R, float>::value>(w, start / TILE, v0, v1, v2, L.partials);
+  }
+}
+
+// ------------------------------------------------------------------ multi-right-hand-side form
+// Every slot of the launch solves on the same gauge field (one lattice, one link copy): the
+// 12 spin-colour point sources of a propagator (paper Section 4) or any set of solves on one
+// configuration. A CTA takes one block of TILE sites and one group of slots. Each thread
+// loads the 8 links of its site once (row 2 of 12-real links rebuilt in registers, exactly as
+// k_dslash does), keeps them in shared memory, and then computes its site for every running
+// slot of the group, in slot order, with k_dslash's hop arithmetic, epilogue and per-slot
+// partial sums. So the links cross HBM once per site block for all slots instead of once per
+// slot, and each slot's result is the same as in a launch of its own.
+constexpr int MRHS_W = 5;  // float4 words per link in shared memory: 18 reals padded to 20
+#ifndef LQCD_DSLASH_MRHS_MIN_BLOCKS
+#define LQCD_DSLASH_MRHS_MIN_BLOCKS 5  // 40 KB of links per CTA: 5 CTAs per SM
+#endif
+
+// the links of a thread's site: word w of hop k at s[(k * MRHS_W + w) * TILE + thread]
+__device__ __forceinline__ void mrhs_store_link(float4* s, int k, const float u[18]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    s[(k * MRHS_W + q) * TILE] = make_float4(u[4 * q], u[4 * q + 1], u[4 * q + 2], u[4 * q + 3]);
+  s[(k * MRHS_W + 4) * TILE] = make_float4(u[16], u[17], 0.0f, 0.0f);
+}
+__device__ __forceinline__ void mrhs_load_link(const float4* s, int k, float u[18]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float4 d = s[(k * MRHS_W + q) * TILE];
+    u[4 * q] = d.x; u[4 * q + 1] = d.y; u[4 * q + 2] = d.z; u[4 * q + 3] = d.w;
+  }
+  const float4 d = s[(k * MRHS_W + 4) * TILE];
+  u[16] = d.x; u[17] = d.y;
+}
+
+template <int K, int LP, int NR>
+__device__ __forceinline__ void mrhs_fetch_link(const Geom& g, int h, const int nb[4], const void* Uout,
+                                                const void* Uin, float4* s) {
+  constexpr int MU = K / 2;
+  constexpr bool FWD = (K % 2) == 0;
+  float u[18];
+  load_link<LP, NR>(link_dir<LP, NR>(FWD ? Uout : Uin, g.Vh, MU), g.Vh, FWD ? h : nb[MU], u);
+  mrhs_store_link(s, K, u);
+}
+
+// Hop K of D in at site h with the staged links; the spinor words of hop K + D are issued
+// while hop K is computed (depth D), as in HopPipe.
+template <int K, int D, int SP, bool DAG>
+struct MrhsPipe {
+  using IO = SpinorIO<SP>;
+  __device__ __forceinline__ static void run(const Geom& g, int t, const int nf[4], const int nb[4],
+                                             const void* in, const float4* s,
+                                             typename IO::Word (&b)[D][IO::NW], float acc[24]) {
+    constexpr int MU = K / 2;
+    constexpr bool FWD = (K % 2) == 0;
+    float u[18];
+    mrhs_load_link(s, K, u);
+    const int eta = (MU == 3 && t == (FWD ? g.L[3] - 1 : 0)) ? g.t_bc : 1;
+    constexpr int S = FWD ? (DAG ? 1 : -1) : (DAG ? -1 : 1);
+    hop_words<MU, S, !FWD, SP>(b[K % D], u, eta, acc);
+    if (K + D < 8) {
+      constexpr int KN = (K + D < 8) ? K + D : 0;
+      IO::load_raw(in, g.Vh, (KN % 2 == 0) ? nf[KN / 2] : nb[KN / 2], b[K % D]);
+    }
+    MrhsPipe<K + 1, D, SP, DAG>::run(g, t, nf, nb, in, s, b, acc);
+  }
+};
+template <int D, int SP, bool DAG>
+struct MrhsPipe<8, D, SP, DAG> {
+  __device__ __forceinline__ static void run(const Geom&, int, const int*, const int*, const void*,
+                                             const float4*, typename SpinorIO<SP>::Word (&)[D][SpinorIO<SP>::NW],
+                                             float*) {}
+};
+
+template <int SP, int LP, int NR, bool DAG, int EPI>
+__global__ void __launch_bounds__(TILE, LQCD_DSLASH_MRHS_MIN_BLOCKS) k_dslash_mrhs(const Launch L) {
+  static_assert(SP == P_F32 || SP == P_F16 || SP == P_BF16, "multi-RHS form: FP32 arithmetic");
+  using IO = SpinorIO<SP>;
+  constexpr int D = DslashDepth<SP>::value;
+  __shared__ float4 su[8 * MRHS_W * TILE];
+  float4* s = su + threadIdx.x;
+  for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
+    const int group = tile % L.mrhs_groups;
+    const int block = tile / L.mrhs_groups;
+    const int s0 = group * L.mrhs_group;
+    const int s1 = min(L.nslots, s0 + L.mrhs_group);
+    bool any = false;
+    for (int si = s0; si < s1; ++si) any = any || slot_runs(work_of(L, si));
+    if (!any) continue;
+    const Work& w0 = work_of(L, s0);  // lattice, parity and links are those of every slot
+    const Geom& g = w0.g;
+    const int h = block * TILE + threadIdx.x;
+    const bool live = h < g.Vh;
+    int nf[4], nb[4], t = 0;
+    if (live) {
+      neighbours(g, h, w0.out_par, nf, nb, t);
+      mrhs_fetch_link<0, LP, NR>(g, h, nb, w0.Uout, w0.Uin, s);
+      mrhs_fetch_link<1, LP, NR>(g, h, nb, w0.Uout, w0.Uin, s);
+      mrhs_fetch_link<2, LP, NR>(g, h, nb, w0.Uout, w0.Uin, s);
+      mrhs_fetch_link<3, LP, NR>(g, h, nb, w0.Uout, w0.Uin, s);
+      mrhs_fetch_link<4, LP, NR>(g, h, nb, w0.Uout, w0.Uin, s);
+      mrhs_fetch_link<5, LP, NR>(g, h, nb, w0.Uout, w0.Uin, s);
+      mrhs_fetch_link<6, LP, NR>(g, h, nb, w0.Uout, w0.Uin, s);
+      mrhs_fetch_link<7, LP, NR>(g, h, nb, w0.Uout, w0.Uin, s);
+    }
+    for (int si = s0; si < s1; ++si) {
+      const Work& w = work_of(L, si);
+      if (!slot_runs(w)) continue;  // uniform over the CTA
+      double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+      if (live) {
+        typename IO::Word b[D][IO::NW];
+#pragma unroll
+        for (int k = 0; k < D; ++k) IO::load_raw(w.in, g.Vh, (k % 2 == 0) ? nf[k / 2] : nb[k / 2], b[k]);
+        float acc[24];
+#pragma unroll
+        for (int i = 0; i < 24; ++i) acc[i] = 0.0f;
+        MrhsPipe<0, D, SP, DAG>::run(g, t, nf, nb, w.in, s, b, acc);
+        dslash_epilogue<SP, EPI>(w, h, acc, v0, v1, v2);
+      }
+      if constexpr (EpiTraits<EPI>::red) tile_partial<TILE, true>(w, block, v0, v1, v2, L.partials);
+    }
   }
 }
 

@@ -26,6 +26,22 @@ cudaError_t go_dslash(const Launch& L, int grid, cudaStream_t s, int form) {
     if (form < 0) form = t.form;
     cps = t.ctas_per_sm;
   }
+  // shared-link multi-RHS launches (every slot on one gauge field): FP32-arithmetic
+  // precisions, Wilson epilogues
+  if (L.interleave == 2) {
+    if constexpr ((SPX == P_F32 || SPX == P_F16 || SPX == P_BF16) && !EpiTraits<EPI>::tw) {
+      auto fm = k_dslash_mrhs<SPX, LPX, NR, DAG, EPI>;
+      if (grid <= 0) {
+        int scps = 0;
+        tune_shared_links(SPX, NR, L.nslots, L.ntiles / L.mrhs_groups, &scps);
+        grid = grid_for((const void*)fm, L.ntiles, 0, TILE, scps);
+      }
+      fm<<<grid, TILE, 0, s>>>(L);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
   // twisted double-float runs the colour-split form alone (the one-thread-per-site form
   // is slower there and its twisted instantiations dominate the build)
   constexpr bool split_only = (SPX == P_DF64 && EpiTraits<EPI>::tw);
@@ -144,8 +160,18 @@ int site_occupancy_12() {
 }
 }  // namespace
 
+template <int P>
+int shared_link_occupancy(int nr) {
+  if constexpr (P == P_F32 || P == P_F16 || P == P_BF16) {
+    if (nr == 18) return kernel_occupancy((const void*)k_dslash_mrhs<P, LPX, 18, false, EPI_LIN>, TILE);
+    if (nr == 12) return kernel_occupancy((const void*)k_dslash_mrhs<P, LPX, 12, false, EPI_LIN>, TILE);
+  }
+  return 0;
+}
+
 int LQCD_CAT(dslash_occupancy_, LQCD_SFX)(int nr, int form) {
   if (form == 1) return colour_split_occupancy<SPX>(nr);
+  if (form == 2) return shared_link_occupancy<SPX>(nr);
   if (form != 0) return 0;
   if (nr == 18) return kernel_occupancy((const void*)k_dslash<SPX, LPX, 18, false, EPI_LIN>, TILE);
   if (nr == 12) return site_occupancy_12<SPX>();

@@ -40,7 +40,8 @@ void set_grid_multiplier(int kernel_family, int mult);  // 0 = occupancy limit
 // ctas_per_sm > 0 caps the grid below the occupancy limit (autotuned choice)
 int grid_for(const void* kernel_fn, int ntiles, int family, int block, int ctas_per_sm = 0);
 int kernel_occupancy(const void* kernel_fn, int block);
-// resident CTAs per SM of the Dslash of this precision, link reals and form (0 if no such form)
+// resident CTAs per SM of the Dslash of this precision, link reals and form (0 if no such
+// form): 0 one thread per site, 1 colour split (double-float), 2 shared-link multi-RHS
 int dslash_occupancy(int sp, int nr, int form);
 
 // Autotuner table (tune.cu): the launch choice for Dslash launches of this precision and
@@ -50,6 +51,10 @@ struct TuneChoice {
   int form;         // 0 site, 1 colour split
 };
 TuneChoice tune_choice(int sp, int nr, int ntiles);
+// Shared-link choice for nrhs slots on one gauge field of `blocks` site blocks: the tuned
+// slots per group (0: every slot loads its own links), with *ctas_per_sm the tuned grid
+// (0: occupancy limit); -1 when nothing was tuned for the key.
+int tune_shared_links(int sp, int nr, int nrhs, int blocks, int* ctas_per_sm);
 
 // Whether the Dslash of spinor precision prec uses the colour-split form (double-float
 // only; a runtime switch for measurement).

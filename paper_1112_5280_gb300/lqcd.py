@@ -33,7 +33,7 @@ class SolveOpts(C.Structure):
     _fields_ = [("solver", C.c_int), ("sloppy_prec", C.c_int), ("sloppy_compress", C.c_int),
                 ("maxiter", C.c_int), ("delta", C.c_double), ("chunk", C.c_int),
                 ("use_graph", C.c_int), ("ru_interval", C.c_int), ("true_prec", C.c_int),
-                ("pad", C.c_int), ("mu", C.c_double)]
+                ("multi_rhs_links", C.c_int), ("mu", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -69,7 +69,7 @@ LEAPFROG, TWO_MN = 0, 1
 class TuneResult(C.Structure):
     _fields_ = [("prec", C.c_int), ("nr", C.c_int), ("ntiles", C.c_int), ("ctas_per_sm", C.c_int),
                 ("form", C.c_int), ("candidates", C.c_int), ("us_best", C.c_double),
-                ("us_default", C.c_double)]
+                ("us_default", C.c_double), ("nrhs", C.c_int), ("group", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -148,6 +148,38 @@ def test_multi_rhs_point_sources_match_single(ctx):
             assert np.array_equal(x1.download(), x), k
 
 
+@pytest.mark.parametrize("prec,compress", [("f32", 12), ("f16", 12), ("f32", 18), ("bf16", 12)])
+def test_multi_rhs_shared_links_match_single(ctx, prec, compress):
+    """Section 4's 12 point sources on 16^3x32, large enough for the shared-link multi-RHS
+    Dslash (each site block's links loaded once for a group of sources): every solution equals
+    the same solve alone and the same batch with per-source link loads
+    (multi_rhs_links = -1), bit for bit, and meets 1e-10 by the oracle's residual."""
+    dims = (16, 16, 16, 32)
+    U = synth.random_links(dims, 0.5, seed=83)
+    site = synth.point_site(dims)
+    srcs_h = _point_sources(dims, site)
+    g = ctx.gauge(dims, U, prec="f64")
+    srcs = [ctx.field(dims, "f64", lqcd.FULL, data=s) for s in srcs_h]
+    shared = [ctx.field(dims, "f64", lqcd.FULL) for _ in srcs_h]
+    own = [ctx.field(dims, "f64", lqcd.FULL) for _ in srcs_h]
+    o_sh = lqcd.solve_opts(sloppy_prec=prec, sloppy_compress=compress)
+    o_own = lqcd.solve_opts(sloppy_prec=prec, sloppy_compress=compress, multi_rhs_links=-1)
+    infos = lqcd.solve_multi(g, srcs, 0.15, 1e-10, shared, o_sh)
+    infos_own = lqcd.solve_multi(g, srcs, 0.15, 1e-10, own, o_own)
+    x1 = ctx.field(dims, "f64", lqcd.FULL)
+    for k, (inf, s) in enumerate(zip(infos, srcs_h)):
+        assert inf["status"] == 0 and inf["true_resid"] <= 1e-10, (k, inf)
+        assert infos_own[k]["iters"] == inf["iters"], k
+        x = shared[k].download()
+        assert np.array_equal(own[k].download(), x), k
+        if k in (0, 5, 11):
+            assert oracle.true_residual(dims, U, 0.15, s, x) <= 1e-10, k
+            lqcd.solve_fields(g, srcs[k], 0.15, 1e-10, x1, o_sh)
+            assert np.array_equal(x1.download(), x), k
+    for f_ in srcs + shared + own + [x1, g]:
+        f_.close()
+
+
 def test_engine_uneven_lattices_same_alone_and_in_mix(ctx):
     """Several lattices of different sizes and kappas in one engine: each result equals its
     solo solve bit for bit."""
