@@ -629,22 +629,33 @@ def run_mrhs_section(ctx, lqcd, inputs, world):
         tuned = {"f32_12_x12": lqcd.autotune_dslash([g] * 12, "f32", 12),
                  "df64_18_x12": lqcd.autotune_dslash([g] * 12, "df64", 18)}
 
-    def together(opts):
-        lqcd.solve_multi(g, srcs, MRHS_KAPPA, 1e-10, xs, opts)  # warm-up (engine, graph)
+    st = ctx._stream
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def timed_call(fn):
+        """wall and device (events on the context stream) time of one synchronous call, ms"""
+        e0, e1 = ev(), ev()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        inf = lqcd.solve_multi(g, srcs, MRHS_KAPPA, 1e-10, xs, opts)
-        return time.perf_counter() - t0, inf
+        e0.record(st)
+        out = fn()
+        e1.record(st)
+        e1.synchronize()
+        return (time.perf_counter() - t0) * 1e3, e0.elapsed_time(e1), out
 
-    t_own, _ = together(o_own)
-    t_multi, infos = together(o)
+    def together(opts):
+        lqcd.solve_multi(g, srcs, MRHS_KAPPA, 1e-10, xs, opts)  # warm-up (engine, graph)
+        return timed_call(lambda: lqcd.solve_multi(g, srcs, MRHS_KAPPA, 1e-10, xs, opts))
+
+    own_wall, own_dev, _ = together(o_own)
+    multi_wall, multi_dev, infos = together(o)
+    t_own, t_multi = own_wall * 1e-3, multi_wall * 1e-3
     lqcd.solve_fields(g, srcs[0], MRHS_KAPPA, 1e-10, xs[0], o)  # warm-up of the one-slot engine
-    torch.cuda.synchronize()
-    each = []
+    each, each_dev = [], []
     for s_, x_ in zip(srcs, xs):
-        t0 = time.perf_counter()
-        lqcd.solve_fields(g, s_, MRHS_KAPPA, 1e-10, x_, o)
-        each.append((time.perf_counter() - t0) * 1e3)
+        w_, d_, _ = timed_call(lambda: lqcd.solve_fields(g, s_, MRHS_KAPPA, 1e-10, x_, o))
+        each.append(w_)
+        each_dev.append(d_)
     t_seq = sum(each) * 1e-3
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -655,6 +666,8 @@ def run_mrhs_section(ctx, lqcd, inputs, world):
            "pion_correlator_t0_t1": [float(corr[1, 0].real), float(corr[1, 1].real)],
            "multi_ms": t_multi * 1e3, "multi_own_links_ms": t_own * 1e3, "sequential_ms": t_seq * 1e3,
            "sequential_ms_each": [round(v, 2) for v in each],
+           "sequential_device_ms_each": [round(v, 2) for v in each_dev],
+           "multi_device_ms": multi_dev, "multi_own_links_device_ms": own_dev,
            "solves_per_s": 12 / t_multi, "speedup_vs_sequential": t_seq / t_multi,
            "speedup_shared_vs_own_links": t_own / t_multi,
            "max_true_resid": max(i["true_resid"] for i in infos),
