@@ -327,11 +327,13 @@ static int gauge_upload_impl(lqcd_ctx* c, const int dims[4], const double* U, bo
 
 int lqcd_gauge_upload(lqcd_ctx* c, const int dims[4], const double* U, int prec, int compress,
                       int t_bc, lqcd_gauge** out) {
+  LQCD_TRACE("lqcd_gauge_upload");
   return gauge_upload_impl(c, dims, U, false, prec, compress, t_bc, out);
 }
 
 int lqcd_gauge_upload_dev(lqcd_ctx* c, const int dims[4], const double* U, int prec, int compress,
                           int t_bc, lqcd_gauge** out) {
+  LQCD_TRACE("lqcd_gauge_upload_dev");
   return gauge_upload_impl(c, dims, U, true, prec, compress, t_bc, out);
 }
 
@@ -434,10 +436,13 @@ static int field_upload_impl(lqcd_field* f, const double* psi, bool dev) {
   return LQCD_OK;
 }
 
-int lqcd_field_upload(lqcd_field* f, const double* psi) { return field_upload_impl(f, psi, false); }
-int lqcd_field_upload_dev(lqcd_field* f, const double* psi) { return field_upload_impl(f, psi, true); }
+int lqcd_field_upload(lqcd_field* f, const double* psi) {
+  LQCD_TRACE("lqcd_field_upload"); return field_upload_impl(f, psi, false); }
+int lqcd_field_upload_dev(lqcd_field* f, const double* psi) {
+  LQCD_TRACE("lqcd_field_upload_dev"); return field_upload_impl(f, psi, true); }
 
 int lqcd_field_download_dev(const lqcd_field* f, double* psi) {
+  LQCD_TRACE("lqcd_field_download_dev");
   clear_error();
   if (!f || !psi) return set_error(LQCD_EINVAL, "NULL argument");
   LQCD_TRY(ctx_set_device(f->ctx));
@@ -446,6 +451,7 @@ int lqcd_field_download_dev(const lqcd_field* f, double* psi) {
 }
 
 int lqcd_field_download(const lqcd_field* f, double* psi) {
+  LQCD_TRACE("lqcd_field_download");
   clear_error();
   if (!f || !psi) return set_error(LQCD_EINVAL, "NULL argument");
   lqcd_ctx* c = f->ctx;
@@ -579,6 +585,7 @@ static int dslash_lin(const lqcd_gauge* gauge, int prec, const void* in, void* o
 
 int lqcd_dslash_eo(const lqcd_gauge* g, const lqcd_field* in, lqcd_field* out, int out_parity,
                    int dagger) {
+  LQCD_TRACE("lqcd_dslash_eo");
   clear_error();
   LQCD_TRY(check_pair(g, in, out));
   if (out_parity != 0 && out_parity != 1) return set_error(LQCD_EINVAL, "parity %d", out_parity);
@@ -677,6 +684,7 @@ int lqcd_dslash_batch_create(int n, const lqcd_gauge* const* g, const lqcd_field
 }
 
 int lqcd_dslash_batch_apply(lqcd_dslash_batch* b) {
+  LQCD_TRACE("lqcd_dslash_batch_apply");
   clear_error();
   if (!b) return set_error(LQCD_EINVAL, "batch is NULL");
   LQCD_TRY(ctx_set_device(b->ctx));
@@ -708,6 +716,7 @@ int lqcd_apply_M(const lqcd_gauge* g, double kappa, const lqcd_field* in, lqcd_f
 
 int lqcd_apply_Mhat_tm(const lqcd_gauge* g, double kappa, double mu, const lqcd_field* in,
                        lqcd_field* out, int dagger) {
+  LQCD_TRACE("lqcd_apply_Mhat_tm");
   clear_error();
   if (!std::isfinite(kappa) || !std::isfinite(mu)) return set_error(LQCD_EINVAL, "kappa and mu must be finite");
   LQCD_TRY(check_pair(g, in, out));
@@ -731,6 +740,7 @@ int lqcd_apply_Mhat_tm(const lqcd_gauge* g, double kappa, double mu, const lqcd_
 
 int lqcd_apply_M_tm(const lqcd_gauge* g, double kappa, double mu, const lqcd_field* in,
                     lqcd_field* out, int dagger) {
+  LQCD_TRACE("lqcd_apply_M_tm");
   clear_error();
   if (!std::isfinite(kappa) || !std::isfinite(mu)) return set_error(LQCD_EINVAL, "kappa and mu must be finite");
   LQCD_TRY(check_pair(g, in, out));

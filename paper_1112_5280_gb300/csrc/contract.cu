@@ -207,6 +207,7 @@ using namespace lqcd;
 
 extern "C" int lqcd_meson_correlator(const lqcd_field* const* props, int ngamma, const int* gammas,
                                      double* host_corr) {
+  LQCD_TRACE("lqcd_meson_correlator");
   clear_error();
   if (!props || !gammas || !host_corr || ngamma < 1 || ngamma > MAXG)
     return set_error(LQCD_EINVAL, "bad arguments (ngamma = %d, at most %d)", ngamma, MAXG);

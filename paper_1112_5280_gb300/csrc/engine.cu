@@ -637,6 +637,7 @@ size_t lqcd_engine_request_bytes(const lqcd_engine* e, const int dims[4]) {
 
 int lqcd_engine_submit(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field* src, double kappa,
                        double tol, long long* request_id) {
+  LQCD_TRACE("lqcd_engine_submit");
   if (!e) {
     clear_error();
     return set_error(LQCD_EINVAL, "engine is NULL");
@@ -649,11 +650,13 @@ static int submit_impl(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field
 
 int lqcd_engine_submit_tm(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field* src, double kappa,
                           double mu, double tol, long long* request_id) {
+  LQCD_TRACE("lqcd_engine_submit_tm");
   return submit_impl(e, gauge, src, kappa, mu, tol, false, request_id);
 }
 
 int lqcd_engine_submit_normal(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field* src, double kappa,
                               double mu, double tol, long long* request_id) {
+  LQCD_TRACE("lqcd_engine_submit_normal");
   return submit_impl(e, gauge, src, kappa, mu, tol, true, request_id);
 }
 
@@ -785,6 +788,7 @@ static int submit_impl(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field
 }
 
 int lqcd_engine_step(lqcd_engine* e, int* n_active) {
+  LQCD_TRACE("lqcd_engine_step");
   clear_error();
   if (!e) return set_error(LQCD_EINVAL, "engine is NULL");
   lqcd_ctx* c = e->ctx;
@@ -859,6 +863,7 @@ int lqcd_engine_completed(lqcd_engine* e, long long* ids, int max, int* n) {
 }
 
 int lqcd_engine_result(lqcd_engine* e, long long id, lqcd_field* x, lqcd_solve_info* info) {
+  LQCD_TRACE("lqcd_engine_result");
   clear_error();
   if (!e) return set_error(LQCD_EINVAL, "engine is NULL");
   auto it = e->reqs.find(id);
@@ -974,6 +979,7 @@ static int run_engine(lqcd_engine* e, int n, const long long* ids, lqcd_field* c
 
 int lqcd_solve_fields(const lqcd_gauge* g, const lqcd_field* src, double kappa, double tol,
                       const lqcd_solve_opts* opts, lqcd_field* x, lqcd_solve_info* info) {
+  LQCD_TRACE("lqcd_solve_fields");
   const lqcd_field* s[1] = {src};
   lqcd_field* xx[1] = {x};
   return lqcd_solve_multi(g, 1, s, kappa, tol, opts, xx, info);
@@ -982,6 +988,7 @@ int lqcd_solve_fields(const lqcd_gauge* g, const lqcd_field* src, double kappa, 
 int lqcd_solve_multi(const lqcd_gauge* g, int n, const lqcd_field* const* srcs, double kappa,
                      double tol, const lqcd_solve_opts* opts, lqcd_field* const* xs,
                      lqcd_solve_info* infos) {
+  LQCD_TRACE("lqcd_solve_multi");
   clear_error();
   const auto t0 = std::chrono::steady_clock::now();
   if (!g || n < 1 || n > MAX_SLOTS || !srcs || !xs) return set_error(LQCD_EINVAL, "bad arguments");
@@ -1024,6 +1031,7 @@ int lqcd_solve_multi(const lqcd_gauge* g, int n, const lqcd_field* const* srcs, 
 int lqcd_solve_batch(int n, const lqcd_gauge* const* gauges, const lqcd_field* const* srcs,
                      const double* kappas, const double* tols, const lqcd_solve_opts* opts,
                      lqcd_field* const* xs, lqcd_solve_info* infos) {
+  LQCD_TRACE("lqcd_solve_batch");
   clear_error();
   if (n < 1 || n > MAX_SLOTS || !gauges || !srcs || !kappas || !tols || !xs)
     return set_error(LQCD_EINVAL, "bad arguments");
@@ -1062,6 +1070,7 @@ int lqcd_solve_batch(int n, const lqcd_gauge* const* gauges, const lqcd_field* c
 
 int lqcd_solve(const lqcd_gauge* g, const double* host_src, double kappa, double tol,
                const lqcd_solve_opts* opts, double* host_x, lqcd_solve_info* info) {
+  LQCD_TRACE("lqcd_solve");
   clear_error();
   const auto t0 = std::chrono::steady_clock::now();
   if (!g || !host_src || !host_x) return set_error(LQCD_EINVAL, "NULL argument");

@@ -349,6 +349,7 @@ extern "C" {
 
 int lqcd_heatbath(lqcd_gauge* g, double beta, int nsweeps, unsigned long long seed,
                   unsigned long long sweep0, int reunit, long long* fails_out) {
+  LQCD_TRACE("lqcd_heatbath");
   clear_error();
   if (!g) return set_error(LQCD_EINVAL, "gauge is NULL");
   if (!(beta >= 0.0) || !std::isfinite(beta)) return set_error(LQCD_EINVAL, "beta must be finite and >= 0");
@@ -390,6 +391,7 @@ int lqcd_heatbath(lqcd_gauge* g, double beta, int nsweeps, unsigned long long se
 }
 
 int lqcd_plaquette(const lqcd_gauge* g, double* plaq) {
+  LQCD_TRACE("lqcd_plaquette");
   clear_error();
   if (!g || !plaq) return set_error(LQCD_EINVAL, "NULL argument");
   lqcd_ctx* c = g->ctx;
@@ -409,6 +411,7 @@ int lqcd_plaquette(const lqcd_gauge* g, double* plaq) {
 }
 
 int lqcd_gauge_download(const lqcd_gauge* g, double* host_U) {
+  LQCD_TRACE("lqcd_gauge_download");
   clear_error();
   if (!g || !host_U) return set_error(LQCD_EINVAL, "NULL argument");
   lqcd_ctx* c = g->ctx;

@@ -520,6 +520,7 @@ int lqcd_mom_zero(lqcd_mom* m) {
 }
 
 int lqcd_mom_kinetic(const lqcd_mom* m, double* energy) {
+  LQCD_TRACE("lqcd_mom_kinetic");
   clear_error();
   if (!m || !energy) return set_error(LQCD_EINVAL, "NULL argument");
   LQCD_CK(cudaSetDevice(m->ctx->device));
@@ -527,6 +528,7 @@ int lqcd_mom_kinetic(const lqcd_mom* m, double* energy) {
 }
 
 int lqcd_gauge_force(const lqcd_gauge* g, double beta, double coeff, lqcd_mom* m) {
+  LQCD_TRACE("lqcd_gauge_force");
   clear_error();
   LQCD_TRY(check_mom(g, m));
   if (!std::isfinite(beta) || !std::isfinite(coeff)) return set_error(LQCD_EINVAL, "beta and coeff must be finite");
@@ -536,6 +538,7 @@ int lqcd_gauge_force(const lqcd_gauge* g, double beta, double coeff, lqcd_mom* m
 
 int lqcd_fermion_force(const lqcd_gauge* g, double kappa, double mu, const lqcd_field* x, double coeff,
                        lqcd_mom* m, double* s_f) {
+  LQCD_TRACE("lqcd_fermion_force");
   clear_error();
   LQCD_TRY(check_mom(g, m));
   if (!x || x->prec != LQCD_F64 || x->subset != LQCD_FULL || memcmp(x->g.L, g->g.L, sizeof g->g.L))
@@ -557,6 +560,7 @@ int lqcd_fermion_force(const lqcd_gauge* g, double kappa, double mu, const lqcd_
 }
 
 int lqcd_gauge_update(lqcd_gauge* g, const lqcd_mom* m, double eps) {
+  LQCD_TRACE("lqcd_gauge_update");
   clear_error();
   LQCD_TRY(check_mom(g, m));
   if (!std::isfinite(eps)) return set_error(LQCD_EINVAL, "eps must be finite");
@@ -566,6 +570,7 @@ int lqcd_gauge_update(lqcd_gauge* g, const lqcd_mom* m, double eps) {
 
 int lqcd_solve_normal(const lqcd_gauge* g, const lqcd_field* src, double kappa, double tol,
                       const lqcd_solve_opts* opts, lqcd_field* x, lqcd_solve_info* info) {
+  LQCD_TRACE("lqcd_solve_normal");
   clear_error();
   if (!g || !src || !x) return set_error(LQCD_EINVAL, "NULL argument");
   lqcd_solve_opts o;
@@ -596,6 +601,7 @@ void lqcd_hmc_params_default(lqcd_hmc_params* p) {
 
 int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m, const lqcd_field* phi,
                         const lqcd_solve_opts* opts, lqcd_hmc_info* info) {
+  LQCD_TRACE("lqcd_hmc_trajectory");
   clear_error();
   const auto t0 = std::chrono::steady_clock::now();
   if (info) memset(info, 0, sizeof *info);

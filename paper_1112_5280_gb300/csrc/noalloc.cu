@@ -101,6 +101,7 @@ int dslash_noalloc(const lqcd_gauge* gauge, int prec, const void* links, int nr,
 
 extern "C" int lqcd_apply_Mhat_noalloc(const lqcd_gauge* g, double kappa, const lqcd_field* in,
                                        lqcd_field* out, int dagger) {
+  LQCD_TRACE("lqcd_apply_Mhat_noalloc");
   using namespace lqcd;
   clear_error();
   if (!g || !in || !out) return set_error(LQCD_EINVAL, "NULL argument");

@@ -92,6 +92,7 @@ int measure(lqcd_ctx* c, int iters, double* tflops) {
 }  // namespace
 
 extern "C" int lqcd_alu_peak(lqcd_ctx* ctx, int kind, double* tflops) {
+  LQCD_TRACE("lqcd_alu_peak");
   using namespace lqcd;
   clear_error();
   if (!ctx || !tflops) return set_error(LQCD_EINVAL, "NULL argument");

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
 #include <cstdarg>
@@ -75,6 +76,17 @@ void clear_error();
     if (e_ != cudaSuccess)                                                                \
       return ::lqcd::set_error(LQCD_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
+
+// An NVTX range over a library call, named after the entry point: profilers (Nsight Systems,
+// ncu --nvtx) attribute kernels to the call that issued them. Without an attached tool the
+// push and pop return at once; the header-only NVTX needs no library at link time.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+#define LQCD_TRACE(name) ::lqcd::TraceRange lqcd_trace_range_(name)
 
 #define LQCD_TRY(x)                 \
   do {                              \

@@ -231,6 +231,7 @@ static void fill_result(lqcd_tune_result* r, const Key& k, const Entry& e) {
 extern "C" {
 
 int lqcd_autotune_dslash(int n, const lqcd_gauge* const* g, int prec, int compress, lqcd_tune_result* out) {
+  LQCD_TRACE("lqcd_autotune_dslash");
   clear_error();
   if (n < 1 || n > MAX_SLOTS || !g || !g[0]) return set_error(LQCD_EINVAL, "bad gauge list (n = %d)", n);
   if (prec < LQCD_F64 || prec > LQCD_DF64) return set_error(LQCD_EINVAL, "precision %d", prec);
