@@ -370,17 +370,20 @@ int rebuild(lqcd_engine* e) {
     else e->any_plain = true;
   }
   e->interleave = (same && n > 1) ? 1 : 0;
-  // Slots on one gauge field share each site block's link loads in the sloppy Dslash steps
-  // (k_dslash_mrhs): a CTA applies the block's links to a group of slots. The group size is
-  // the autotuner's for this key if it tuned one (0: own links); else groups are as large
-  // as the lattice allows while the launch keeps at least 8 tiles per SM. One slot per
-  // group gains nothing over the interleaved order.
+  // Slots on one gauge field may share each site block's link loads in the sloppy Dslash
+  // steps (k_dslash_mrhs): a CTA applies the block's links to a group of slots. The group
+  // size is the autotuner's measured choice for this key. Without one the slots load their
+  // own links: in the interleaved tile order consecutive CTAs read the same links, which L2
+  // then serves, and at 24^3x48 with FP32-12 links the shared form measured slower (its
+  // 40 KB of links per CTA cost one CTA per SM). multi_rhs_links > 0 asks for the shared
+  // form untuned, with groups as large as the lattice allows while the launch keeps at
+  // least 8 tiles per SM.
   e->mrhs_group = e->mrhs_groups = e->mrhs_tiles = 0;
   if (e->interleave && !e->any_twist && e->opts.multi_rhs_links >= 0 &&
       (e->sp == P_F32 || e->sp == P_F16 || e->sp == P_BF16)) {
     const int blocks = e->reqs[e->active[0]].ntiles;
     int gsize = tune_shared_links(e->sp, e->nr, n, blocks, nullptr);
-    if (gsize < 0) {
+    if (gsize < 0 && e->opts.multi_rhs_links > 0) {
       const int want = 8 * device_sm_count();
       const int groups = std::min(n, std::max(1, (want + blocks - 1) / blocks));
       gsize = (n + groups - 1) / groups;

@@ -162,7 +162,7 @@ def test_multi_rhs_shared_links_match_single(ctx, prec, compress):
     srcs = [ctx.field(dims, "f64", lqcd.FULL, data=s) for s in srcs_h]
     shared = [ctx.field(dims, "f64", lqcd.FULL) for _ in srcs_h]
     own = [ctx.field(dims, "f64", lqcd.FULL) for _ in srcs_h]
-    o_sh = lqcd.solve_opts(sloppy_prec=prec, sloppy_compress=compress)
+    o_sh = lqcd.solve_opts(sloppy_prec=prec, sloppy_compress=compress, multi_rhs_links=1)
     o_own = lqcd.solve_opts(sloppy_prec=prec, sloppy_compress=compress, multi_rhs_links=-1)
     infos = lqcd.solve_multi(g, srcs, 0.15, 1e-10, shared, o_sh)
     infos_own = lqcd.solve_multi(g, srcs, 0.15, 1e-10, own, o_own)
