@@ -115,6 +115,19 @@ struct Launch {
   int mrhs_groups;         // interleave 2: number of slot groups
 };
 
+// Programmatic dependent launch. The batched kernels are launched with programmatic stream
+// serialization (launch_k in launch.h), so the next kernel on the stream may be launched
+// while this one is still running. Each of them first waits for the grids before it to
+// complete and their memory to be visible (griddepcontrol.wait, before any access to global
+// memory, so any chain of dependent kernels stays ordered), then lets the next one launch
+// (griddepcontrol.launch_dependents). The next grid's CTAs are then resident and waiting
+// when this grid's last CTAs finish, instead of starting a launch only then. Without the
+// launch attribute both instructions return at once.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ const Work& work_of(const Launch& L, int slot) {
   return L.works ? L.works[slot] : L.inline_work;
 }

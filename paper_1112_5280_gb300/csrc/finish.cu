@@ -28,6 +28,7 @@ __device__ __forceinline__ int finish_groups(int ntiles) {
 __global__ void __launch_bounds__(FINISH_THREADS) k_finish(const Launch L) {
   __shared__ double sh[FINISH_THREADS / 32];
   __shared__ int am_last;
+  pdl_entry();
   const int slot = blockIdx.x, q = blockIdx.y;
   if (slot >= L.nslots) return;
   const Work& w = work_of(L, slot);
@@ -91,8 +92,7 @@ cudaError_t launch_finish(const Launch& L, cudaStream_t s) {
   // enough groups for the largest slot (no slot has more tiles than the launch)
   int gy = (L.ntiles + FINISH_TILES - 1) / FINISH_TILES;
   gy = gy < 1 ? 1 : (gy > FINISH_GROUPS ? FINISH_GROUPS : gy);
-  k_finish<<<dim3(L.nslots, gy), FINISH_THREADS, 0, s>>>(L);
-  return cudaGetLastError();
+  return launch_k(k_finish, dim3(L.nslots, gy), dim3(FINISH_THREADS), s, L);
 }
 
 }  // namespace lqcd

@@ -182,6 +182,7 @@ __device__ __forceinline__ void dslash_epilogue(const Work& w, int h, typename S
 // with the Work's reduction (norm / dots) and scalar finisher per slot.
 template <int SP, int LP, int NR, bool DAG, int EPI>
 __global__ void __launch_bounds__(TILE, DslashMinBlocks<SP>::value) k_dslash(const Launch L) {
+  pdl_entry();
   using R = typename SpinorIO<SP>::Real;
   if (single_slot_idle(L)) return;
   for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
@@ -273,6 +274,7 @@ struct MrhsPipe<8, D, SP, DAG> {
 
 template <int SP, int LP, int NR, bool DAG, int EPI>
 __global__ void __launch_bounds__(TILE, LQCD_DSLASH_MRHS_MIN_BLOCKS) k_dslash_mrhs(const Launch L) {
+  pdl_entry();
   static_assert(SP == P_F32 || SP == P_F16 || SP == P_BF16, "multi-RHS form: FP32 arithmetic");
   using IO = SpinorIO<SP>;
   constexpr int D = DslashDepth<SP>::value;
@@ -349,6 +351,7 @@ __device__ __forceinline__ void colour_dot(const R a[8], const R b[8], double& r
 #endif
 template <int SP, int LP, bool DAG, int EPI>
 __global__ void __launch_bounds__(3 * TILE, LQCD_DSLASH3_MIN_BLOCKS) k_dslash3(const Launch L) {
+  pdl_entry();
   using R = typename SpinorIO<SP>::Real;
   static_assert(SP == P_DF64 && LP == P_DF64, "the colour-split form is built for double-float");
   __shared__ ProjShare<TILE> sh;
@@ -461,6 +464,7 @@ __device__ __forceinline__ void caxpy(R* out, const R* x, R cr, R ci, const R* y
 // FP64-class vectors (true residual, solution accumulator) in the mixed ops.
 template <int SP, int OP, int TP = P_F64>
 __global__ void __launch_bounds__(TILE) k_blas(const Launch L) {
+  pdl_entry();
   using R = typename SpinorIO<SP>::Real;
   using TR = typename SpinorIO<TP>::Real;
   if (single_slot_idle(L)) return;

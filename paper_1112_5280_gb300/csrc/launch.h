@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "batch.cuh"
 
 namespace lqcd {
@@ -33,6 +35,26 @@ LQCD_DECL(f16)
 LQCD_DECL(bf16)
 LQCD_DECL(df64)
 #undef LQCD_DECL
+
+// Launches of the batched kernels, with programmatic stream serialization when the
+// environment variable LQCD_PDL=1 is set: the kernel may then be launched before the
+// previous kernel on the stream completes, and waits for it itself (pdl_entry in
+// batch.cuh). Plain launches by default (measured no faster with it).
+bool pdl_enabled();
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Number of SMs of the current device and the persistent-grid multiplier.
 int device_sm_count();

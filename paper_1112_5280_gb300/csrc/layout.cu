@@ -3,6 +3,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <cstdlib>
 #include <mutex>
 #include <unordered_map>
 
@@ -273,6 +274,18 @@ cudaError_t launch_dslash(int sp, int nr, bool dag, int epi, const Launch& L, in
     case P_DF64: return then_finish(launch_dslash_df64(nr, dag, epi, L, grid, s, form), L, s);
   }
   return cudaErrorInvalidValue;
+}
+
+// Off unless LQCD_PDL=1: measured on GB300, the parked grids gained nothing (every kernel
+// waits for its predecessor before its first memory access) and cost 1% on the batched
+// Dslash and 3% on the 32^3x64 mixed CG; without the attribute the entry instructions of
+// the kernels cost nothing measurable.
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("LQCD_PDL");
+    return v && v[0] == '1';
+  }();
+  return on;
 }
 
 int dslash_occupancy(int sp, int nr, int form) {
