@@ -348,7 +348,10 @@ typedef struct lqcd_hmc_params {
   int nsteps;              /* outer (fermion force) steps */
   int ngauge;              /* inner (gauge force) steps per outer step, >= 1 */
   int scheme;              /* LQCD_LEAPFROG or LQCD_2MN, on both levels */
-  int pad;
+  int chrono;              /* initial guess of each force solve after the first: 0 (default) x = 0;
+                              1 the last solution; 2 the linear extrapolation 2 X_last - X_before.
+                              The solves still converge to tol, so the trajectory changes only at
+                              the level of tol (and is reversible only to that level) */
   double tol;              /* residual of the force solves (normal equations) */
   double accept_u;         /* uniform in (0, 1] for the Metropolis test; <= 0: no test, links kept */
 } lqcd_hmc_params;

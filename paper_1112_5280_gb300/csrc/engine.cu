@@ -649,7 +649,8 @@ int lqcd_engine_submit(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field
 }
 
 static int submit_impl(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field* src, double kappa,
-                       double mu, double tol, bool normal, long long* request_id);
+                       double mu, double tol, bool normal, long long* request_id,
+                       const lqcd_field* x0 = nullptr);
 
 int lqcd_engine_submit_tm(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field* src, double kappa,
                           double mu, double tol, long long* request_id) {
@@ -663,10 +664,14 @@ int lqcd_engine_submit_normal(lqcd_engine* e, const lqcd_gauge* gauge, const lqc
   return submit_impl(e, gauge, src, kappa, mu, tol, true, request_id);
 }
 
+// x0 (may be NULL): the starting even half x_e (a FULL or EVEN FP64 field of the lattice);
+// NULL starts from x = 0
 static int submit_impl(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field* src, double kappa,
-                       double mu, double tol, bool normal, long long* request_id) {
+                       double mu, double tol, bool normal, long long* request_id, const lqcd_field* x0) {
   clear_error();
   if (!e || !gauge || !src || !request_id) return set_error(LQCD_EINVAL, "NULL argument");
+  if (x0 && (x0->prec != LQCD_F64 || !x0->half[0] || memcmp(x0->g.L, gauge->g.L, sizeof x0->g.L)))
+    return set_error(LQCD_EINVAL, "the initial guess must be an FP64 field of the lattice holding the even parity");
   if (!std::isfinite(mu) || !std::isfinite(kappa)) return set_error(LQCD_EINVAL, "kappa and mu must be finite");
   if (src->prec != LQCD_F64 || src->subset != LQCD_FULL)
     return set_error(LQCD_EINVAL, "source must be a FULL FP64 field");
@@ -718,7 +723,9 @@ static int submit_impl(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field
       if (normal) err = cudaMemsetAsync(R.buf.bo, 0, hb, st);  // only phi_e counts
       else err = spinor_convert(src->half[1], P_F64, R.buf.bo, e->tp, q.g.Vh, 1.0, st);
     }
-    if (err == cudaSuccess) err = cudaMemsetAsync(R.buf.x64, 0, hb, st);
+    if (err == cudaSuccess)
+      err = x0 ? spinor_convert(x0->half[0], P_F64, R.buf.x64, e->tp, q.g.Vh, 1.0, st)
+               : cudaMemsetAsync(R.buf.x64, 0, hb, st);
     if (err == cudaSuccess) err = cudaMemsetAsync(R.buf.xs, 0, half_spinor_bytes(e->xp, q.g.Vh), st);
     if (err == cudaSuccess) err = cudaMemsetAsync(sc, 0, sizeof(Scalars), st);
     if (err != cudaSuccess) rc = set_error(LQCD_ECUDA, "submit copies: %s", cudaGetErrorString(err));
@@ -766,11 +773,26 @@ static int submit_impl(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field
       err = launch_dslash(e->tp, 18, false, EPI_LIN, single_launch(d, e->d_partials), 0, st);
     }
     if (err == cudaSuccess) {
-      // first true residual and restart (state UPDATE, restart_p = 1)
+      // first true residual and restart (state UPDATE, restart_p = 1). With x = 0 the update's
+      // fold and its two FP64-class Dslash would compute u = bhat - Mhat 0 from zero fields:
+      // u = bhat exactly, so it is an exact copy (a = 1) with its norm and the same finisher,
+      // followed by the rest of the update.
+      // From an initial guess the whole update runs (u = bhat - Mhat x0).
       Work w2[NSTEP];
       step_works(e, R, w2);
+      if (!x0) {
+        Work cu = slot_work(e, R);
+        cu.in = R.buf.bhat;
+        cu.out = R.buf.u64;
+        cu.a = 1.0;
+        cu.red = 1;
+        cu.fin = FIN_TRUERES;
+        cu.run_if = S_UPDATE;
+        err = launch_blas(e->tp, B_AXPBY, single_launch(cu, e->d_partials), 0, st, e->tp);
+      }
       for (int s : ru_steps(normal, !normal)) {
         if (err != cudaSuccess) break;
+        if (!x0 && (s == RU_FOLD || s == RU_D1 || s == RU_RES)) continue;
         err = issue(e, s, single_launch(w2[s], e->d_partials), mu != 0.0);
       }
     }
@@ -945,6 +967,11 @@ int ctx_engine(lqcd_ctx* c, const lqcd_solve_opts& o, int n, lqcd_engine** out) 
   c->engine_opts = o;
   *out = e;
   return LQCD_OK;
+}
+
+int engine_submit_normal_guess(lqcd_engine* e, const lqcd_gauge* g, const lqcd_field* src,
+                               const lqcd_field* x0, double kappa, double mu, double tol, long long* id) {
+  return submit_impl(e, g, src, kappa, mu, tol, true, id, x0);
 }
 
 void engine_trim_pool(lqcd_engine* e, size_t keep_bytes) {

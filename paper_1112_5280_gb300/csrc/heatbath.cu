@@ -137,8 +137,11 @@ __device__ __noinline__ bool su2_draw(double alpha, uint64_t seed, uint64_t c0, 
 // direction v = c / |c|, a = b v, the rotations of U and V) in double-float from the copy Ud
 // on the FP32 pipes; the draw of b (Creutz) and |c| in FP64. The updated link goes to Ud
 // only: the caller rebuilds the FP64 master from it.
+// 3 CTAs of 128 threads per SM (168 registers, a 100-byte spill) against 2 (254 registers,
+// no spill): measured on GB300 at 32^3x64 beta 6, 39.7 against 43.2 ms per sweep with the
+// same chain; the update is latency bound, so the extra warps outweigh the spill.
 #ifndef LQCD_HB_MIN_BLOCKS
-#define LQCD_HB_MIN_BLOCKS 2
+#define LQCD_HB_MIN_BLOCKS 3
 #endif
 __global__ void __launch_bounds__(HB_THREADS, LQCD_HB_MIN_BLOCKS) k_heatbath(float4* Ud, Geom g, int mu,
                                                                              int par, double beta, uint64_t seed,

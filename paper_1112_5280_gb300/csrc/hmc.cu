@@ -75,6 +75,8 @@ __device__ __forceinline__ void add_ta(double2* P, const Geom& g, const Site& x,
 // part in double-float from the copy Ud (FP32 pipes), only the accumulation into the FP64
 // momenta in FP64. All four directions in one launch (blockIdx.y = mu), one thread per
 // link, mu a run-time value so that the four share one instruction stream.
+// 2 CTAs per SM (254 registers, no spill): 3 (168 registers, a 68-byte spill) measured 3%
+// slower over a 16^3x32 HMC trajectory on GB300.
 #ifndef LQCD_GF_MIN_BLOCKS
 #define LQCD_GF_MIN_BLOCKS 2
 #endif
@@ -405,10 +407,14 @@ int fermion_force_from_x(const lqcd_gauge* g, double kappa, double mu, lqcd_fiel
   return LQCD_OK;
 }
 
+// x0 (may be NULL): the starting even half of the solve (else x = 0)
 int solve_normal_with(lqcd_engine* e, const lqcd_gauge* g, const lqcd_field* phi, double kappa, double mu,
-                      double tol, lqcd_field* x, lqcd_solve_info* info) {
+                      double tol, lqcd_field* x, lqcd_solve_info* info, const lqcd_field* x0 = nullptr) {
   long long id = 0;
-  LQCD_TRY(lqcd_engine_submit_normal(e, g, phi, kappa, mu, tol, &id));
+  if (x0)
+    LQCD_TRY(engine_submit_normal_guess(e, g, phi, x0, kappa, mu, tol, &id));
+  else
+    LQCD_TRY(lqcd_engine_submit_normal(e, g, phi, kappa, mu, tol, &id));
   int active = 1;
   while (active > 0) LQCD_TRY(lqcd_engine_step(e, &active));
   return lqcd_engine_result(e, id, x, info);
@@ -611,7 +617,7 @@ int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m, co
     return set_error(LQCD_EINVAL, "phi must be a FULL FP64 field of the gauge's lattice (even half used)");
   if (p->nsteps < 1 || p->ngauge < 1 || !(p->tau > 0) || !std::isfinite(p->tau) || !(p->tol > 0) ||
       (p->scheme != LQCD_LEAPFROG && p->scheme != LQCD_2MN) || !std::isfinite(p->beta) ||
-      !std::isfinite(p->kappa) || !std::isfinite(p->mu))
+      !std::isfinite(p->kappa) || !std::isfinite(p->mu) || p->chrono < 0 || p->chrono > 2)
     return set_error(LQCD_EINVAL, "bad HMC parameters");
   lqcd_ctx* c = g->ctx;
   LQCD_CK(cudaSetDevice(c->device));
@@ -622,6 +628,7 @@ int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m, co
   o.mu = p->mu;
   int dims[4] = {g->g.L[0], g->g.L[1], g->g.L[2], g->g.L[3]};
   lqcd_field *x = nullptr, *y = nullptr, *xd = nullptr, *yd = nullptr;
+  lqcd_field *xprev = nullptr, *guess = nullptr;  // chronological initial guesses
   lqcd_engine* e = nullptr;
   void* backup = nullptr;
   const size_t ubytes = gauge_copy_bytes(P_F64, 18, g->g.Vh);
@@ -629,6 +636,8 @@ int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m, co
   if (rc == LQCD_OK) rc = lqcd_field_create(c, dims, LQCD_F64, LQCD_FULL, &y);
   if (rc == LQCD_OK) rc = lqcd_field_create(c, dims, LQCD_DF64, LQCD_FULL, &xd);
   if (rc == LQCD_OK) rc = lqcd_field_create(c, dims, LQCD_DF64, LQCD_FULL, &yd);
+  if (rc == LQCD_OK && p->chrono == 2) rc = lqcd_field_create(c, dims, LQCD_F64, LQCD_FULL, &xprev);
+  if (rc == LQCD_OK && p->chrono == 2) rc = lqcd_field_create(c, dims, LQCD_F64, LQCD_FULL, &guess);
   if (rc == LQCD_OK) rc = ctx_engine(c, o, 1, &e);
   if (rc == LQCD_OK && p->accept_u > 0.0) {
     if (cudaMalloc(&backup, ubytes) != cudaSuccess) {
@@ -654,7 +663,21 @@ int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m, co
       if (copies_stale) LQCD_TRY(links_from_df(g));
       copies_stale = false;
       lqcd_solve_info si{};
-      LQCD_TRY(solve_normal_with(e, g, phi, p->kappa, p->mu, p->tol, x, &si));
+      // initial guess: none, the last solution (chrono 1), or 2 X_last - X_before (chrono 2)
+      const lqcd_field* x0 = nullptr;
+      if (p->chrono >= 1 && force_evals >= 1) x0 = x;
+      if (p->chrono == 2 && force_evals >= 2) {
+        Work w = blank_work(g->g);
+        w.in = x->half[0];
+        w.y1 = xprev->half[0];
+        w.out = guess->half[0];
+        w.a = 2.0;
+        w.c1 = -1.0;
+        LQCD_CK(launch_blas(P_F64, B_AXPBY, single_launch(w, nullptr), 0, c->stream, P_F64));
+        x0 = guess;
+      }
+      if (p->chrono == 2 && force_evals >= 1) LQCD_TRY(lqcd_field_copy(xprev, x, 1.0));
+      LQCD_TRY(solve_normal_with(e, g, phi, p->kappa, p->mu, p->tol, x, &si, x0));
       solves_iters += si.iters;
       double s = 0.0;
       LQCD_TRY(fermion_force_from_x(g, p->kappa, p->mu, x, y, xd, yd, -pend_f, m, &s, phi));
@@ -730,7 +753,7 @@ int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m, co
     cudaFree(backup);
   }
   if (rc != LQCD_OK && e) ctx_drop_engine(c);  // a failure may leave a request in the engine
-  for (lqcd_field* f : {x, y, xd, yd}) lqcd_field_destroy(f);
+  for (lqcd_field* f : {x, y, xd, yd, xprev, guess}) lqcd_field_destroy(f);
   if (info) {
     info->dH = h1 - h0;
     info->H0 = h0;

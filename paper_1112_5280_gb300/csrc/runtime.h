@@ -129,6 +129,10 @@ void ctx_drop_engine(lqcd_ctx* c);
 // after a one-shot solve: free pooled slot blocks beyond keep_bytes
 void engine_trim_pool(lqcd_engine* e, size_t keep_bytes);
 
+// a normal-equation request of the engine starting from x0 (FP64, even half used; engine.cu)
+int engine_submit_normal_guess(lqcd_engine* e, const lqcd_gauge* g, const lqcd_field* src,
+                               const lqcd_field* x0, double kappa, double mu, double tol, long long* id);
+
 // BiCGStab on Mhat (bicgstab.cu)
 int bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kappa, double tol,
                    const lqcd_solve_opts* opts, lqcd_field* x, lqcd_solve_info* info);

@@ -48,7 +48,7 @@ class SolveInfo(C.Structure):
 
 class HmcParams(C.Structure):
     _fields_ = [("beta", C.c_double), ("kappa", C.c_double), ("mu", C.c_double), ("tau", C.c_double),
-                ("nsteps", C.c_int), ("ngauge", C.c_int), ("scheme", C.c_int), ("pad", C.c_int),
+                ("nsteps", C.c_int), ("ngauge", C.c_int), ("scheme", C.c_int), ("chrono", C.c_int),
                 ("tol", C.c_double), ("accept_u", C.c_double)]
 
 

@@ -223,6 +223,38 @@ def test_dslash_batch_matches_oracle(ctx, prec, same_size):
     b.close()
 
 
+@pytest.fixture(scope="module")
+def bench_sets():
+    """The benchmark's 10 field sets: 16^3x32 links exp(i 0.5 H) and Gaussian spinors, seeds
+    1001 + k and 2002 + k (bench.py's generator)."""
+    dims = (16, 16, 16, 32)
+    return dims, [(synth.random_links(dims, 0.5, seed=synth.SEED_LINKS + k),
+                   synth.gaussian_spinor(dims, seed=synth.SEED_SOURCE + k)) for k in range(10)]
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64", "df64"])
+def test_bench_launch_configuration(ctx, bench_sets, prec):
+    """The launch the benchmark times, at full size: one batch of the 10 field sets (10 slots
+    of 16^3x32, 18-real links, antiperiodic t, out parity 0) applied twice; 500 sampled even
+    output sites of every set against the oracle's hopping term at those sites."""
+    dims, sets = bench_sets
+    gs = [ctx.gauge(dims, U, prec=prec, compress=18, t_bc=-1) for U, _ in sets]
+    fins = [ctx.field(dims, prec, lqcd.ODD, data=psi) for _, psi in sets]
+    fouts = [ctx.field(dims, prec, lqcd.EVEN) for _ in sets]
+    b = lqcd.DslashBatch(gs, fins, fouts, 0)
+    b.apply()
+    b.apply()
+    even = np.flatnonzero(synth.parity_of_sites(dims) == 0)
+    rng = np.random.default_rng(11)
+    for k, ((U, psi), fo) in enumerate(zip(sets, fouts)):
+        sites = np.concatenate([rng.choice(even, 500, replace=False), even[[0, -1]]])
+        ref = oracle.hop_sites(dims, U, psi, sites)
+        assert _rel_err(fo.download()[sites], ref) < TOL[prec], k
+    b.close()
+    for o in gs + fins + fouts:
+        o.close()
+
+
 @pytest.mark.parametrize("form", [0, 1])
 def test_df64_both_forms(ctx, form):
     """Both Dslash forms of double-float (one thread per site, three per site) meet the FP64 bar."""

@@ -150,12 +150,43 @@ def test_trajectory_reversible_and_metropolis(ctx):
         assert np.array_equal(g2.download(), U)
 
 
+@pytest.mark.parametrize("chrono", [1, 2])
+def test_chronological_guess_keeps_the_trajectory(ctx, chrono):
+    """Force solves that start from the last solution (chrono 1) or from its linear
+    extrapolation (chrono 2) still converge to the same tolerance, so the trajectory matches
+    the oracle's to the same 1e-8 as the solves from zero, and dH to 1e-7; the solves take
+    fewer iterations in total."""
+    dims, beta, kappa, mu = (4, 4, 4, 4), 5.0, 0.12, 0.1
+    U = synth.random_links(dims, 0.5, seed=251)
+    P = synth.gaussian_momenta(dims, 252)
+    phi = ohmc.pseudofermion(dims, U, kappa, mu, synth.gaussian_spinor(dims, seed=253) * _even(dims))
+    U1, P1 = ohmc.integrate(dims, U, P, phi, beta, kappa, mu, 0.4, 4, scheme="2mn", ngauge=2)
+    H0 = ohmc.hamiltonian(dims, U, P, phi, beta, kappa, mu)
+    H1 = ohmc.hamiltonian(dims, U1, P1, phi, beta, kappa, mu)
+    iters = {}
+    for ch in (0, chrono):
+        g = ctx.gauge(dims, U)
+        m = ctx.mom(dims, P)
+        f = ctx.field(dims, "f64", lqcd.FULL, data=phi)
+        p = lqcd.hmc_params(beta=beta, kappa=kappa, mu=mu, tau=0.4, nsteps=4, ngauge=2,
+                            scheme=lqcd.TWO_MN, tol=1e-12, chrono=ch)
+        info = lqcd.hmc_trajectory(g, p, m, f, lqcd.solve_opts(sloppy_prec="f32"))
+        assert np.abs(g.download() - U1).max() < 1e-8, ch
+        assert np.abs(m.download() - P1).max() < 1e-8, ch
+        assert abs(info["dH"] - (H1 - H0)) < 1e-7, (ch, info["dH"], H1 - H0)
+        iters[ch] = info["solver_iters"]
+        assert info["force_evals"] == 9
+        for o in (g, m, f):
+            o.close()
+    assert iters[chrono] < iters[0], iters
+
+
 def test_bad_hmc_arguments(ctx):
     dims = (2, 2, 2, 2)
     g = ctx.gauge(dims, synth.unit_links(dims))
     m = ctx.mom(dims)
     f = ctx.field(dims, "f64", lqcd.FULL)
-    for kw in ({"nsteps": 0}, {"ngauge": 0}, {"tau": -1.0}, {"scheme": 7}, {"tol": 0.0}):
+    for kw in ({"nsteps": 0}, {"ngauge": 0}, {"tau": -1.0}, {"scheme": 7}, {"tol": 0.0}, {"chrono": 3}):
         with pytest.raises(lqcd.LqcdError):
             lqcd.hmc_trajectory(g, lqcd.hmc_params(**kw), m, f)
     with pytest.raises(lqcd.LqcdError):

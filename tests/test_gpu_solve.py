@@ -180,6 +180,25 @@ def test_multi_rhs_shared_links_match_single(ctx, prec, compress):
         f_.close()
 
 
+def test_multi_rhs_full_size_24x48(ctx):
+    """The benchmark's multi-RHS workload at full size: 24^3x48, kappa 0.15, eps 0.5 (seed
+    1001), Section 4's 12 point sources at the seeded site, FP32-12 inner and FP64-class
+    outer, solved together: every solution meets 1e-10 by the oracle's FP64 residual."""
+    dims = (24, 24, 24, 48)
+    U = synth.random_links(dims, 0.5, seed=synth.SEED_LINKS)
+    site = synth.point_site(dims)
+    g = ctx.gauge(dims, U, prec="f64")
+    srcs_h = _point_sources(dims, site)
+    srcs = [ctx.field(dims, "f64", lqcd.FULL, data=s_) for s_ in srcs_h]
+    xs = [ctx.field(dims, "f64", lqcd.FULL) for _ in srcs_h]
+    infos = lqcd.solve_multi(g, srcs, 0.15, 1e-10, xs, lqcd.solve_opts(sloppy_prec="f32", sloppy_compress=12))
+    for k, (inf, s_, x_) in enumerate(zip(infos, srcs_h, xs)):
+        assert inf["status"] == 0, (k, inf)
+        assert oracle.true_residual(dims, U, 0.15, s_, x_.download()) <= 1e-10, k
+    for o in srcs + xs + [g]:
+        o.close()
+
+
 def test_engine_uneven_lattices_same_alone_and_in_mix(ctx):
     """Several lattices of different sizes and kappas in one engine: each result equals its
     solo solve bit for bit."""
