@@ -806,6 +806,7 @@ def run_dslash32_section(ctx, lqcd, world, U=None):
 
 
 HMC_NSTEPS, HMC_NGAUGE, HMC_TRAJ = 20, 4, 4
+HMC_CHRONO = 2  # force solves start from the linear extrapolation of the last two solutions
 
 
 def run_hmc_section(ctx, lqcd, world):
@@ -830,7 +831,7 @@ def run_hmc_section(ctx, lqcd, world):
         m.upload(synth.gaussian_momenta(d, seed=synth.SEED_SOURCE + 20 + k))
 
     kw = dict(beta=HMC_BETA, kappa=HMC_KAPPA, mu=HMC_MU, tau=1.0, nsteps=HMC_NSTEPS, ngauge=HMC_NGAUGE,
-              scheme=lqcd.TWO_MN, tol=1e-10)
+              scheme=lqcd.TWO_MN, tol=1e-10, chrono=HMC_CHRONO)
     opts = lqcd.solve_opts(sloppy_prec="f16", sloppy_compress=12)
     warm = []
     for k in range(2):  # towards the dynamical ensemble (accepted unconditionally)
@@ -850,7 +851,8 @@ def run_hmc_section(ctx, lqcd, world):
     res = {"workload": f"{'x'.join(map(str, d))} N_f=2 twisted mass kappa={HMC_KAPPA} mu={HMC_MU}, "
                        f"beta={HMC_BETA} (links: 20 heatbath sweeps, then 2 HMC trajectories), 2MN tau=1 "
                        f"{HMC_NSTEPS}x{HMC_NGAUGE} steps, force solves 1e-10 (FP16-12 sloppy CG, "
-                       f"double-float updates), {HMC_TRAJ} timed trajectories with the Metropolis test",
+                       f"double-float updates, initial guess by linear extrapolation of the last two "
+                       f"solutions), {HMC_TRAJ} timed trajectories with the Metropolis test",
            "ms_per_trajectory": float(np.mean(ms)), "ms_each": [round(v, 1) for v in ms],
            "trajectories_per_s": world * 1e3 / float(np.mean(ms)),
            "dH": dH, "dH_warmup": warm, "acceptance": float(np.mean([i["accepted"] for i in infos])),

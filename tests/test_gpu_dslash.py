@@ -223,6 +223,49 @@ def test_dslash_batch_matches_oracle(ctx, prec, same_size):
     b.close()
 
 
+def _nan_spinor(dims):
+    return np.full((synth.volume(dims), 4, 3), complex(np.nan, np.nan))
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32", "f16", "bf16"])
+def test_outputs_fully_written(ctx, prec):
+    """Coverage check with poisoned outputs: every output field is filled with NaN before the
+    kernel, and every site of the parity the kernel writes must come back finite. Ragged
+    lattices (partial last tiles), single launches of both parities, a batch of mixed
+    sizes, Mhat into an even field, and a solve into a poisoned solution field."""
+    shapes = [(6, 6, 4, 10), (2, 4, 6, 4), (4, 4, 4, 4)]
+    nr = 12 if prec in ("f16", "bf16") else 18
+    gs, fins, fouts = [], [], []
+    for k, dims in enumerate(shapes):
+        gs.append(ctx.gauge(dims, synth.random_links(dims, 0.5, seed=500 + k), prec=prec, compress=nr))
+        fins.append(ctx.field(dims, prec, lqcd.FULL, data=synth.gaussian_spinor(dims, seed=600 + k)))
+        fouts.append(ctx.field(dims, prec, lqcd.FULL, data=_nan_spinor(dims)))
+    for g, fi, fo in zip(gs, fins, fouts):
+        for p in (0, 1):
+            lqcd.dslash_eo(g, fi, fo, p)
+        assert np.isfinite(fo.download()).all()
+    for fo, dims in zip(fouts, shapes):
+        fo.upload(_nan_spinor(dims))
+    b = lqcd.DslashBatch(gs, fins, fouts, 1, dagger=True)
+    b.apply()
+    for fo, dims in zip(fouts, shapes):
+        assert np.isfinite(fo.download()[_par(dims, 1)]).all(), dims
+    b.close()
+    for g, fi, fo, dims in zip(gs, fins, fouts, shapes):
+        fo.upload(_nan_spinor(dims))
+        lqcd.apply_Mhat(g, 0.13, fi, fo)
+        assert np.isfinite(fo.download()[_par(dims, 0)]).all(), dims
+    dims = shapes[0]
+    g64 = ctx.gauge(dims, synth.random_links(dims, 0.5, seed=500), prec="f64")
+    src = ctx.field(dims, "f64", lqcd.FULL, data=synth.gaussian_spinor(dims, seed=610))
+    x = ctx.field(dims, "f64", lqcd.FULL, data=_nan_spinor(dims))
+    sp = prec if prec != "f64" else "f64"
+    info = lqcd.solve_fields(g64, src, 0.13, 1e-10, x, lqcd.solve_opts(sloppy_prec=sp, sloppy_compress=nr))
+    assert info["status"] == 0 and np.isfinite(x.download()).all()
+    for o in gs + fins + fouts + [g64, src, x]:
+        o.close()
+
+
 @pytest.fixture(scope="module")
 def bench_sets():
     """The benchmark's 10 field sets: 16^3x32 links exp(i 0.5 H) and Gaussian spinors, seeds
