@@ -532,6 +532,13 @@ def run_ours(args, world, rank, local):
             "one_application_per_launch": single,
         },
     }
+    if "f32" in single:
+        # per-application cost inside a launch: t(10 sets) = 10 a + X and t(1 set) = a + X
+        a = (us_per_launch - single["f32"]["us_per_launch"]) / (NSETS - 1)
+        line["extra"]["dslash_f32_in_launch"] = {
+            "us_per_application": a, "us_per_launch_fixed": us_per_launch - NSETS * a,
+            "GBps": b32 / (a * 1e-6) / 1e9, "frac_of_measured_hbm": b32 / (a * 1e-6) / 1e9 / peak,
+            "note": "from the 10-set and 1-set launch timings: launch, ramp-up and tail excluded"}
     if not args.dslash_only:
         line["solve"] = run_solve_section(ctx, lqcd, inputs, world)
         line["dslash32"] = run_dslash32_section(ctx, lqcd, world, U=inputs["solve"][0])

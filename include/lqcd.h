@@ -443,6 +443,14 @@ LQCD_API void lqcd_engine_destroy(lqcd_engine* e);
  * allocates and frees a few bytes. LQCD_EINVAL for another kind. */
 LQCD_API int lqcd_alu_peak(lqcd_ctx* ctx, int kind, double* tflops);
 
+/* Debug build (compiled with -DLQCD_DEBUG_BOUNDS; lqcd.py loads it when the environment
+ * variable LQCD_DEBUG_BOUNDS=1): every spinor and link access of the batched kernels checks
+ * its site index against the field; the first index outside is recorded and replaced by 0,
+ * so that the kernel stays inside its buffers (no trap). This waits for the context's stream
+ * and returns in *word the first record since the last call, (1 << 63) | (Vh << 32) | index,
+ * or 0, and clears the records. LQCD_EINVAL in the normal build. */
+LQCD_API int lqcd_debug_bounds(lqcd_ctx* ctx, unsigned long long* word);
+
 /* ---------------------------------------------------------------- tuning */
 
 /* Caps the persistent grid of batched kernel family (0 Dslash, 1 BLAS) at

@@ -18,6 +18,13 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "liblqcd.so")
+# the debug build: device bounds checks on every field access (LQCD_DEBUG_BOUNDS)
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+LIB_DEBUG = os.path.join(BUILD_DEBUG, "liblqcd.so")
+
+
+def lib_path(debug: bool = False) -> str:
+    return LIB_DEBUG if debug else LIB
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "-Xcompiler", "-fvisibility=hidden",
@@ -38,15 +45,16 @@ def _deps():
         glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(debug: bool = False) -> bool:
+    lib = lib_path(debug)
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def _compile(src, extra):
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _compile(src, extra, outdir=BUILD):
+    obj = os.path.join(outdir, os.path.basename(src)[:-3] + ".o")
     # LQCD_NVCC_EXTRA: extra nvcc flags, e.g. -D values of the compile-time tunables
     env_extra = os.environ.get("LQCD_NVCC_EXTRA", "").split()
     cmd = [_nvcc()] + NVCC_FLAGS + extra + env_extra + ["-c", src, "-o", obj]
@@ -56,26 +64,31 @@ def _compile(src, extra):
     return obj, r.stderr
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False, debug: bool = False) -> str:
+    """Compile and link the library (debug=True: the bounds-checked build, in its own folder)."""
+    lib = lib_path(debug)
+    outdir = os.path.dirname(lib)
+    if not force and up_to_date(debug):
+        return lib
+    os.makedirs(outdir, exist_ok=True)
     extra = ["-Xptxas", "-v"] if ptxas_verbose else []
+    if debug:
+        extra = extra + ["-DLQCD_DEBUG_BOUNDS"]
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        results = list(ex.map(lambda s: _compile(s, extra), srcs))
+        results = list(ex.map(lambda s: _compile(s, extra, outdir), srcs))
     if verbose or ptxas_verbose:
         for _, err in results:
             if err:
                 print(err, file=sys.stderr)
     objs = [o for o, _ in results]
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [_nvcc(), "-shared"] + ARCH + ["-o", tmp] + objs + ["-lcuda"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -246,6 +246,24 @@ int lqcd_ctx_sync(lqcd_ctx* c) {
 
 long long lqcd_ctx_launch_count(const lqcd_ctx* c) { return c ? c->launches : 0; }
 
+int lqcd_debug_bounds(lqcd_ctx* c, unsigned long long* word) {
+  clear_error();
+  if (!c || !word) return set_error(LQCD_EINVAL, "NULL argument");
+  *word = 0;
+#ifdef LQCD_DEBUG_BOUNDS
+  LQCD_TRY(ctx_set_device(c));
+  LQCD_CK(cudaStreamSynchronize(c->stream));
+  for (auto read : bounds_word_readers()) {
+    unsigned long long v = 0;
+    if (read(&v) != 0) return set_error(LQCD_ECUDA, "reading a bounds-check word failed");
+    if (v && !*word) *word = v;
+  }
+  return LQCD_OK;
+#else
+  return set_error(LQCD_EINVAL, "the library was built without LQCD_DEBUG_BOUNDS");
+#endif
+}
+
 int lqcd_ctx_release_cache(lqcd_ctx* c) {
   clear_error();
   if (!c) return set_error(LQCD_EINVAL, "NULL context");

@@ -22,7 +22,15 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace lqcd {
+
+// Readers of the debug bounds-check words, one per translation unit (LQCD_DEBUG_BOUNDS).
+inline std::vector<int (*)(unsigned long long*)>& bounds_word_readers() {
+  static std::vector<int (*)(unsigned long long*)> readers;
+  return readers;
+}
 
 // Storage precisions. P_DF64 stores each real as an (hi, lo) pair of floats
 // (8 bytes, like FP64) and computes in double-float arithmetic (below).
@@ -161,6 +169,39 @@ __device__ __forceinline__ Cx<T> cmulc(Cx<T> a, Cx<T> b) {  // conj(a) * b
   return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
 }
 
+// ------------------------------------------------------------------ debug bounds checks
+// Built with -DLQCD_DEBUG_BOUNDS, every spinor and link access of the field IO below checks
+// its half-lattice site index against the field's size. The first index outside it is
+// recorded in an error word of the translation unit, (1 << 63) | (Vh << 32) | index, and
+// the access goes to site 0 instead, so a faulty index reads and writes only inside the
+// field (no trap, no fault). lqcd_debug_bounds() collects and clears the words of every
+// translation unit. Without the flag the check compiles to nothing.
+#ifdef LQCD_DEBUG_BOUNDS
+static __device__ unsigned long long lqcd_bounds_word;
+__device__ __forceinline__ int checked_site(int h, int Vh) {
+  if ((unsigned)h < (unsigned)Vh) return h;
+  atomicCAS(&lqcd_bounds_word, 0ull,
+            (1ull << 63) | ((unsigned long long)(unsigned)Vh << 32) | (unsigned long long)(unsigned)h);
+  return 0;
+}
+#define LQCD_SITE(h, Vh) ::lqcd::checked_site((h), (Vh))
+// host side: the word of this translation unit, read and cleared (registered at load)
+namespace {
+int read_bounds_word(unsigned long long* out) {
+  unsigned long long v = 0, z = 0;
+  if (cudaMemcpyFromSymbol(&v, lqcd_bounds_word, sizeof v) != cudaSuccess) return -1;
+  if (v && cudaMemcpyToSymbol(lqcd_bounds_word, &z, sizeof z) != cudaSuccess) return -1;
+  *out = v;
+  return 0;
+}
+struct BoundsWordRegistration {
+  BoundsWordRegistration() { bounds_word_readers().push_back(&read_bounds_word); }
+} bounds_word_registration;
+}  // namespace
+#else
+#define LQCD_SITE(h, Vh) (h)
+#endif
+
 // ------------------------------------------------------------------ raw loads
 // Read-only data is loaded through the non-coherent path. Links are read
 // exactly once per half-lattice sweep, so they bypass L1 allocation.
@@ -235,6 +276,7 @@ struct SpinorIO<P_F64> {
   using Word = double2;
   static constexpr int NW = 12;
   __device__ static void load_raw(const void* base, int Vh, int h, Word w[NW]) {
+    h = LQCD_SITE(h, Vh);
     const double2* p = reinterpret_cast<const double2*>(base) + h;
 #pragma unroll
     for (int c = 0; c < NW; ++c) w[c] = ld_ro(p + (size_t)c * Vh);
@@ -248,6 +290,7 @@ struct SpinorIO<P_F64> {
   }
   // the 8 reals of colour a: words 4a .. 4a+3
   __device__ static void load_colour(const void* base, int Vh, int h, int a, double v[8]) {
+    h = LQCD_SITE(h, Vh);
     const double2* p = reinterpret_cast<const double2*>(base) + h + (size_t)(4 * a) * Vh;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -257,11 +300,13 @@ struct SpinorIO<P_F64> {
     }
   }
   __device__ static void store_colour(void* base, int Vh, int h, int a, const double v[8]) {
+    h = LQCD_SITE(h, Vh);
     double2* p = reinterpret_cast<double2*>(base) + h + (size_t)(4 * a) * Vh;
 #pragma unroll
     for (int c = 0; c < 4; ++c) p[(size_t)c * Vh] = make_double2(v[2 * c], v[2 * c + 1]);
   }
   __device__ static void load(const void* base, int Vh, int h, double v[24]) {
+    h = LQCD_SITE(h, Vh);
     const double2* p = reinterpret_cast<const double2*>(base) + h;
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
@@ -271,6 +316,7 @@ struct SpinorIO<P_F64> {
     }
   }
   __device__ static void store(void* base, int Vh, int h, const double v[24]) {
+    h = LQCD_SITE(h, Vh);
     double2* p = reinterpret_cast<double2*>(base) + h;
 #pragma unroll
     for (int c = 0; c < 12; ++c) p[(size_t)c * Vh] = make_double2(v[2 * c], v[2 * c + 1]);
@@ -284,6 +330,7 @@ struct SpinorIO<P_F32> {
   using Word = float4;
   static constexpr int NW = 6;
   __device__ static void load_raw(const void* base, int Vh, int h, Word w[NW]) {
+    h = LQCD_SITE(h, Vh);
     const float4* p = reinterpret_cast<const float4*>(base) + h;
 #pragma unroll
     for (int c = 0; c < NW; ++c) w[c] = ld_ro(p + (size_t)c * Vh);
@@ -299,17 +346,20 @@ struct SpinorIO<P_F32> {
   }
   // the 8 reals of colour a: words 2a, 2a+1
   __device__ static void load_colour(const void* base, int Vh, int h, int a, float v[8]) {
+    h = LQCD_SITE(h, Vh);
     const float4* p = reinterpret_cast<const float4*>(base) + h + (size_t)(2 * a) * Vh;
     const float4 d0 = ld_ro(p), d1 = ld_ro(p + Vh);
     v[0] = d0.x; v[1] = d0.y; v[2] = d0.z; v[3] = d0.w;
     v[4] = d1.x; v[5] = d1.y; v[6] = d1.z; v[7] = d1.w;
   }
   __device__ static void store_colour(void* base, int Vh, int h, int a, const float v[8]) {
+    h = LQCD_SITE(h, Vh);
     float4* p = reinterpret_cast<float4*>(base) + h + (size_t)(2 * a) * Vh;
     p[0] = make_float4(v[0], v[1], v[2], v[3]);
     p[Vh] = make_float4(v[4], v[5], v[6], v[7]);
   }
   __device__ static void load(const void* base, int Vh, int h, float v[24]) {
+    h = LQCD_SITE(h, Vh);
     const float4* p = reinterpret_cast<const float4*>(base) + h;
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
@@ -321,6 +371,7 @@ struct SpinorIO<P_F32> {
     }
   }
   __device__ static void store(void* base, int Vh, int h, const float v[24]) {
+    h = LQCD_SITE(h, Vh);
     float4* p = reinterpret_cast<float4*>(base) + h;
 #pragma unroll
     for (int c = 0; c < 6; ++c)
@@ -336,6 +387,7 @@ struct SpinorIO<P_DF64> {
   static constexpr int NW = 12;
   // the 8 reals of colour a (colour-major order): words 4a .. 4a+3
   __device__ static void load_colour(const void* base, int Vh, int h, int a, df64 v[8]) {
+    h = LQCD_SITE(h, Vh);
     const float4* p = reinterpret_cast<const float4*>(base) + h + (size_t)(4 * a) * Vh;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -345,11 +397,13 @@ struct SpinorIO<P_DF64> {
     }
   }
   __device__ static void store_colour(void* base, int Vh, int h, int a, const df64 v[8]) {
+    h = LQCD_SITE(h, Vh);
     float4* p = reinterpret_cast<float4*>(base) + h + (size_t)(4 * a) * Vh;
 #pragma unroll
     for (int c = 0; c < 4; ++c) p[(size_t)c * Vh] = make_float4(v[2 * c].hi, v[2 * c].lo, v[2 * c + 1].hi, v[2 * c + 1].lo);
   }
   __device__ static void load_raw(const void* base, int Vh, int h, Word w[NW]) {
+    h = LQCD_SITE(h, Vh);
     const float4* p = reinterpret_cast<const float4*>(base) + h;
 #pragma unroll
     for (int c = 0; c < NW; ++c) w[c] = ld_ro(p + (size_t)c * Vh);
@@ -362,11 +416,13 @@ struct SpinorIO<P_DF64> {
     }
   }
   __device__ static void load(const void* base, int Vh, int h, df64 v[24]) {
+    h = LQCD_SITE(h, Vh);
     Word w[NW];
     load_raw(base, Vh, h, w);
     unpack(w, v);
   }
   __device__ static void store(void* base, int Vh, int h, const df64 v[24]) {
+    h = LQCD_SITE(h, Vh);
     float4* p = reinterpret_cast<float4*>(base) + h;
 #pragma unroll
     for (int c = 0; c < NW; ++c)
@@ -381,6 +437,7 @@ struct SpinorIO16 {
   using Word = uint4;
   static constexpr int NW = 3;
   __device__ static void load_raw(const void* base, int Vh, int h, Word w[NW]) {
+    h = LQCD_SITE(h, Vh);
     const uint4* p = reinterpret_cast<const uint4*>(base) + h;
 #pragma unroll
     for (int c = 0; c < NW; ++c) w[c] = ld_ro(p + (size_t)c * Vh);
@@ -397,11 +454,13 @@ struct SpinorIO16 {
   __device__ static unsigned pack(float a, float b) { return BF ? pack_b2(a, b) : pack_h2(a, b); }
   // the 8 reals of colour a: word a
   __device__ static void load_colour(const void* base, int Vh, int h, int a, float v[8]) {
+    h = LQCD_SITE(h, Vh);
     const uint4 d = ld_ro(reinterpret_cast<const uint4*>(base) + h + (size_t)a * Vh);
     const float2 x = unpack(d.x), y = unpack(d.y), z = unpack(d.z), w = unpack(d.w);
     v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y; v[4] = z.x; v[5] = z.y; v[6] = w.x; v[7] = w.y;
   }
   __device__ static void store_colour(void* base, int Vh, int h, int a, const float v[8]) {
+    h = LQCD_SITE(h, Vh);
     uint4 d;
     d.x = pack(v[0], v[1]);
     d.y = pack(v[2], v[3]);
@@ -410,6 +469,7 @@ struct SpinorIO16 {
     reinterpret_cast<uint4*>(base)[h + (size_t)a * Vh] = d;
   }
   __device__ static void load(const void* base, int Vh, int h, float v[24]) {
+    h = LQCD_SITE(h, Vh);
     const uint4* p = reinterpret_cast<const uint4*>(base) + h;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -420,6 +480,7 @@ struct SpinorIO16 {
     }
   }
   __device__ static void store(void* base, int Vh, int h, const float v[24]) {
+    h = LQCD_SITE(h, Vh);
     uint4* p = reinterpret_cast<uint4*>(base) + h;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -451,6 +512,7 @@ struct LinkIO<P_F64, NR> {
   using Word = double2;
   static constexpr int NW = NR / 2;
   __device__ static void load_raw(const void* base_mu, int Vh, int h, Word w[NW]) {
+    h = LQCD_SITE(h, Vh);
     const double2* p = reinterpret_cast<const double2*>(base_mu) + h;
 #pragma unroll
     for (int c = 0; c < NW; ++c) w[c] = ld_stream(p + (size_t)c * Vh);
@@ -463,6 +525,7 @@ struct LinkIO<P_F64, NR> {
     }
   }
   __device__ static void load(const void* base_mu, int Vh, int h, double u[18]) {
+    h = LQCD_SITE(h, Vh);
     Word w[NW];
     load_raw(base_mu, Vh, h, w);
     unpack(w, u);
@@ -475,6 +538,7 @@ struct LinkIO<P_DF64, NR> {
   using Word = float4;
   static constexpr int NW = NR / 2;
   __device__ static void load_raw(const void* base_mu, int Vh, int h, Word w[NW]) {
+    h = LQCD_SITE(h, Vh);
     const float4* p = reinterpret_cast<const float4*>(base_mu) + h;
 #pragma unroll
     for (int c = 0; c < NW; ++c) w[c] = ld_stream(p + (size_t)c * Vh);
@@ -487,6 +551,7 @@ struct LinkIO<P_DF64, NR> {
     }
   }
   __device__ static void load(const void* base_mu, int Vh, int h, df64 u[18]) {
+    h = LQCD_SITE(h, Vh);
     Word w[NW];
     load_raw(base_mu, Vh, h, w);
     unpack(w, u);
@@ -499,6 +564,7 @@ struct LinkIO<P_F32, 18> {
   using Word = float2;
   static constexpr int NW = 9;
   __device__ static void load_raw(const void* base_mu, int Vh, int h, Word w[NW]) {
+    h = LQCD_SITE(h, Vh);
     const float2* p = reinterpret_cast<const float2*>(base_mu) + h;
 #pragma unroll
     for (int c = 0; c < NW; ++c) w[c] = ld_stream(p + (size_t)c * Vh);
@@ -511,6 +577,7 @@ struct LinkIO<P_F32, 18> {
     }
   }
   __device__ static void load(const void* base_mu, int Vh, int h, float u[18]) {
+    h = LQCD_SITE(h, Vh);
     Word w[NW];
     load_raw(base_mu, Vh, h, w);
     unpack(w, u);
@@ -523,6 +590,7 @@ struct LinkIO<P_F32, 12> {
   using Word = float4;
   static constexpr int NW = 3;
   __device__ static void load_raw(const void* base_mu, int Vh, int h, Word w[NW]) {
+    h = LQCD_SITE(h, Vh);
     const float4* p = reinterpret_cast<const float4*>(base_mu) + h;
 #pragma unroll
     for (int c = 0; c < NW; ++c) w[c] = ld_stream(p + (size_t)c * Vh);
@@ -537,6 +605,7 @@ struct LinkIO<P_F32, 12> {
     }
   }
   __device__ static void load(const void* base_mu, int Vh, int h, float u[18]) {
+    h = LQCD_SITE(h, Vh);
     Word w[NW];
     load_raw(base_mu, Vh, h, w);
     unpack(w, u);
@@ -549,6 +618,7 @@ struct LinkIO<P_F16, 18> {
   using Word = unsigned;
   static constexpr int NW = 9;
   __device__ static void load_raw(const void* base_mu, int Vh, int h, Word w[NW]) {
+    h = LQCD_SITE(h, Vh);
     const unsigned* p = reinterpret_cast<const unsigned*>(base_mu) + h;
 #pragma unroll
     for (int c = 0; c < NW; ++c) w[c] = ld_stream(p + (size_t)c * Vh);
@@ -562,6 +632,7 @@ struct LinkIO<P_F16, 18> {
     }
   }
   __device__ static void load(const void* base_mu, int Vh, int h, float u[18]) {
+    h = LQCD_SITE(h, Vh);
     Word w[NW];
     load_raw(base_mu, Vh, h, w);
     unpack(w, u);
@@ -574,6 +645,7 @@ struct LinkIO<P_F16, 12> {
   using Word = uint2;
   static constexpr int NW = 3;
   __device__ static void load_raw(const void* base_mu, int Vh, int h, Word w[NW]) {
+    h = LQCD_SITE(h, Vh);
     const uint2* p = reinterpret_cast<const uint2*>(base_mu) + h;
 #pragma unroll
     for (int c = 0; c < NW; ++c) w[c] = ld_stream(p + (size_t)c * Vh);
@@ -589,6 +661,7 @@ struct LinkIO<P_F16, 12> {
     }
   }
   __device__ static void load(const void* base_mu, int Vh, int h, float u[18]) {
+    h = LQCD_SITE(h, Vh);
     Word w[NW];
     load_raw(base_mu, Vh, h, w);
     unpack(w, u);

@@ -87,15 +87,19 @@ def _sig(lib, name, res, args):
 
 
 def load(build_if_missing: bool = True):
-    """Load the library; builds it first when it is missing or stale and nvcc exists."""
+    """Load the library; builds it first when it is missing or stale and nvcc exists.
+    With the environment variable LQCD_DEBUG_BOUNDS=1 the bounds-checked debug build is
+    built and loaded instead (see lqcd_debug_bounds)."""
     global _lib
     if _lib is not None:
         return _lib
-    if build_if_missing and not _build.up_to_date():
-        _build.build()
-    if not os.path.exists(_build.LIB):
-        raise RuntimeError(f"liblqcd.so not built ({_build.LIB}); run __graft_entry__.build()")
-    lib = C.CDLL(_build.LIB)
+    debug = os.environ.get("LQCD_DEBUG_BOUNDS", "0") == "1"
+    path = _build.lib_path(debug)
+    if build_if_missing and not _build.up_to_date(debug):
+        _build.build(debug=debug)
+    if not os.path.exists(path):
+        raise RuntimeError(f"liblqcd.so not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
     i, d, sz, ll = C.c_int, C.c_double, C.c_size_t, C.c_longlong
     _sig(lib, "lqcd_status_string", C.c_char_p, [i])
     _sig(lib, "lqcd_last_error", C.c_char_p, [])
@@ -108,6 +112,7 @@ def load(build_if_missing: bool = True):
     _sig(lib, "lqcd_ctx_sync", i, [_VP])
     _sig(lib, "lqcd_ctx_launch_count", ll, [_VP])
     _sig(lib, "lqcd_alu_peak", i, [_VP, i, C.POINTER(d)])
+    _sig(lib, "lqcd_debug_bounds", i, [_VP, C.POINTER(C.c_ulonglong)])
     _sig(lib, "lqcd_set_grid_multiplier", None, [i, i])
     _sig(lib, "lqcd_set_dslash_form", i, [i, i])
     _sig(lib, "lqcd_gauge_upload", i, [_VP, _IP, _VP, i, i, i, C.POINTER(_VP)])
@@ -251,6 +256,15 @@ class Context:
     @property
     def launches(self) -> int:
         return int(self._lib.lqcd_ctx_launch_count(self.h))
+
+    def debug_bounds(self):
+        """(index, size) of the first out-of-range field access recorded since the last call by
+        the bounds-checked build (LQCD_DEBUG_BOUNDS=1), or None; raises in the normal build."""
+        w = C.c_ulonglong(0)
+        _check(self._lib.lqcd_debug_bounds(self.h, C.byref(w)))
+        if not w.value:
+            return None
+        return int(w.value & 0xFFFFFFFF), int((w.value >> 32) & 0x7FFFFFFF)
 
     def alu_peak(self, kind: str) -> float:
         """Measured FMA throughput of the device in TFLOP/s: kind "f64", "f32" or "f32x2" (packed
