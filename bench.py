@@ -186,8 +186,12 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
-                "reasons": sorted(reasons), "samples": len(sm),
+                "sm_mhz_min": float(min(sm)), "reasons": sorted(reasons), "samples": len(sm),
                 "power_w_median": float(np.median(power))}
+
+    def windows_min(self, windows):
+        """Lowest SM clock sampled inside each (t0, t1) window, None where no sample fell."""
+        return [self.summary(a, b).get("sm_mhz_min") for a, b in windows]
 
 
 # ------------------------------------------------------------------ helpers
@@ -460,7 +464,6 @@ def run_ours(args, world, rank, local):
             us = ms * 1e3 / n
             single[prec] = {"us_per_launch": us,
                             "GBps": algorithmic_bytes_per_site(nb, 18) * Vh / (us * 1e-6) / 1e9}
-    sampler.stop()
 
     apps = args.steps * APPS_PER_STEP
     b32 = algorithmic_bytes_per_site(4, 18) * Vh
@@ -540,13 +543,21 @@ def run_ours(args, world, rank, local):
             "GBps": b32 / (a * 1e-6) / 1e9, "frac_of_measured_hbm": b32 / (a * 1e-6) / 1e9 / peak,
             "note": "from the 10-set and 1-set launch timings: launch, ramp-up and tail excluded"}
     if not args.dslash_only:
-        line["solve"] = run_solve_section(ctx, lqcd, inputs, world)
-        line["dslash32"] = run_dslash32_section(ctx, lqcd, world, U=inputs["solve"][0])
-        line["multi_rhs"] = run_mrhs_section(ctx, lqcd, inputs, world)
-        line["multi_lattice"] = run_mlat_section(ctx, lqcd, inputs, world)
-        line["serve"] = run_serve_section(ctx, lqcd, inputs, world, rank)
-        line["heatbath"] = run_heatbath_section(ctx, lqcd, world, alu)
-        line["hmc"] = run_hmc_section(ctx, lqcd, world)
+        def section(name, fn):
+            """run one section; its clock samples (median, lowest) go with its results"""
+            t_a = time.time()
+            res = fn()
+            res["clocks"] = sampler.summary(t_a, time.time())
+            line[name] = res
+
+        section("solve", lambda: run_solve_section(ctx, lqcd, inputs, world))
+        section("dslash32", lambda: run_dslash32_section(ctx, lqcd, world, U=inputs["solve"][0]))
+        section("multi_rhs", lambda: run_mrhs_section(ctx, lqcd, inputs, world, sampler))
+        section("multi_lattice", lambda: run_mlat_section(ctx, lqcd, inputs, world))
+        section("serve", lambda: run_serve_section(ctx, lqcd, inputs, world, rank))
+        section("heatbath", lambda: run_heatbath_section(ctx, lqcd, world, alu))
+        section("hmc", lambda: run_hmc_section(ctx, lqcd, world))
+    sampler.stop()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(inputs.get("solve"))
     if rank == 0:
@@ -618,8 +629,9 @@ def run_solve_section(ctx, lqcd, inputs, world):
     return out
 
 
-def run_mrhs_section(ctx, lqcd, inputs, world):
-    """24^3x48, kappa 0.15: 12 point sources (spin x colour) solved together vs one by one."""
+def run_mrhs_section(ctx, lqcd, inputs, world, sampler=None):
+    """24^3x48, kappa 0.15: 12 point sources (spin x colour) solved together vs one by one.
+    With a running clock sampler, the lowest SM clock seen during each solve is reported."""
     import torch
     from paper_1112_5280_gb300 import synth
     U = inputs["mrhs_U"]
@@ -643,12 +655,16 @@ def run_mrhs_section(ctx, lqcd, inputs, world):
         """wall and device (events on the context stream) time of one synchronous call, ms"""
         e0, e1 = ev(), ev()
         torch.cuda.synchronize()
+        w0 = time.time()
         t0 = time.perf_counter()
         e0.record(st)
         out = fn()
         e1.record(st)
         e1.synchronize()
+        windows.append((w0, time.time()))
         return (time.perf_counter() - t0) * 1e3, e0.elapsed_time(e1), out
+
+    windows = []
 
     def together(opts):
         lqcd.solve_multi(g, srcs, MRHS_KAPPA, 1e-10, xs, opts)  # warm-up (engine, graph)
@@ -683,6 +699,12 @@ def run_mrhs_section(ctx, lqcd, inputs, world):
            "note": "multi: one batch with the default link sharing (the tuner's measured choice for "
                    "this key); multi_shared_links: one batch with each site block's links loaded once "
                    "for a group of sources (k_dslash_mrhs) regardless of tuning"}
+    if sampler is not None:  # windows: shared, default, then the 12 single solves
+        time.sleep(0.3)  # the last samples reach the pipe in blocks
+        lows = sampler.windows_min(windows)
+        res["sm_mhz_min_multi"] = lows[1]
+        res["sm_mhz_min_multi_shared_links"] = lows[0]
+        res["sm_mhz_min_sequential_each"] = lows[2:]
     for o_ in [g] + srcs + xs:
         o_.close()
     return res
