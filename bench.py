@@ -644,9 +644,11 @@ def run_mrhs_section(ctx, lqcd, inputs, world, sampler=None):
     o = lqcd.solve_opts(sloppy_prec="f32", sloppy_compress=12)  # shared links if tuned faster
     o_shared = lqcd.solve_opts(sloppy_prec="f32", sloppy_compress=12, multi_rhs_links=1)
     tuned = {}
-    if TUNE:  # the 12-slot sloppy launch and the FP64-class update launch
+    if TUNE:  # the sloppy and the FP64-class update launch, 12 slots and one (the comparator)
         tuned = {"f32_12_x12": lqcd.autotune_dslash([g] * 12, "f32", 12),
-                 "df64_18_x12": lqcd.autotune_dslash([g] * 12, "df64", 18)}
+                 "df64_18_x12": lqcd.autotune_dslash([g] * 12, "df64", 18),
+                 "f32_12_x1": lqcd.autotune_dslash([g], "f32", 12),
+                 "df64_18_x1": lqcd.autotune_dslash([g], "df64", 18)}
 
     st = ctx._stream
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
@@ -719,9 +721,14 @@ def run_mlat_section(ctx, lqcd, inputs, world):
     srcs = [ctx.field(d, "f64", lqcd.FULL, data=b) for d, _, _, b in items]
     xs = {d: ctx.field(d, "f64", lqcd.FULL) for d in MLAT_SIZES}
     tuned = {}
-    if TUNE:  # all 64 slots in one launch: the sloppy and the FP64-class operator
+    if TUNE:  # all 64 slots in one launch, and one slot of each size (the comparator)
         tuned = {"f32_12_x64": lqcd.autotune_dslash(gs, "f32", 12),
                  "df64_18_x64": lqcd.autotune_dslash(gs, "df64", 18)}
+        for d in MLAT_SIZES:
+            g1 = next(g_ for g_, (d_, _, _, _) in zip(gs, items) if d_ == d)
+            tag = "x".join(str(v) for v in d)
+            tuned[f"f32_12_{tag}"] = lqcd.autotune_dslash([g1], "f32", 12)
+            tuned[f"df64_18_{tag}"] = lqcd.autotune_dslash([g1], "df64", 18)
 
     def batched():
         eng = lqcd.Engine(ctx, o, max_slots=MLAT_N)

@@ -464,8 +464,9 @@ LQCD_API int lqcd_set_dslash_form(int prec, int form);
  * from measurement on this device. lqcd_autotune_dslash times one batched Dslash launch
  * over n slots (slot i on gauge g[i], which may repeat; fields of precision prec, zero
  * valued scratch allocated and freed by the call) for every distinct persistent grid,
- * 1 .. occupancy-limit CTAs per SM, of every compiled kernel form, and records the
- * fastest. The default (occupancy limit, default form) is kept unless another choice is
+ * 1 .. occupancy-limit CTAs per SM, of every compiled kernel form (for LQCD_F32 also the
+ * one-thread-per-site Dslash compiled for 8 CTAs per SM, a second register budget), and
+ * records the fastest. The default (occupancy limit, default form) is kept unless another choice is
  * more than 2% faster. The record applies to every later Dslash launch (lqcd_dslash_eo,
  * batches, operators, solves, engines) of the same precision and link reals whose tile
  * count (64 output sites a tile) has the same floor(log2).
@@ -484,7 +485,8 @@ typedef struct lqcd_tune_result {
   int ntiles;       /* tiles of the tuned launch */
   int ctas_per_sm;  /* chosen persistent grid, CTAs per SM (0: occupancy limit) */
   int form;         /* chosen kernel form: 0 one thread per site, 1 colour split (DF64),
-                       2 shared-link multi-RHS */
+                       2 shared-link multi-RHS, 3 one thread per site compiled for 8 CTAs
+                       per SM (FP32: 128 registers, more warps with fewer loads each) */
   int candidates;   /* configurations timed */
   double us_best;   /* per launch, chosen configuration */
   double us_default;/* per launch, untuned default (shared-link entries: the own-link launch) */

@@ -116,16 +116,24 @@ struct Launch {
 };
 
 // Programmatic dependent launch. The batched kernels are launched with programmatic stream
-// serialization (launch_k in launch.h), so the next kernel on the stream may be launched
-// while this one is still running. Each of them first waits for the grids before it to
-// complete and their memory to be visible (griddepcontrol.wait, before any access to global
-// memory, so any chain of dependent kernels stays ordered), then lets the next one launch
-// (griddepcontrol.launch_dependents). The next grid's CTAs are then resident and waiting
-// when this grid's last CTAs finish, instead of starting a launch only then. Without the
-// launch attribute both instructions return at once.
+// serialization (launch_k in launch.h) when it is enabled, so the next kernel on the stream
+// may be launched while this one is still running. Each of them first waits for the grids
+// before it to complete and their memory to be visible (griddepcontrol.wait, before any
+// access to global memory, so any chain of dependent kernels stays ordered). A CTA lets the
+// next grid launch (griddepcontrol.launch_dependents) when it starts its last tile, so the
+// next grid's CTAs take the SM slots that this grid's tail leaves free, instead of a launch
+// starting only after the last CTA ends. Without the launch attribute both instructions
+// return at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// kernels without a tile loop
 __device__ __forceinline__ void pdl_entry() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  pdl_wait();
+  pdl_trigger();
+}
+// a persistent CTA about to take `tile`: its last one triggers the dependents
+__device__ __forceinline__ void pdl_last_tile(int tile, int ntiles) {
+  if (tile + (int)gridDim.x >= ntiles) pdl_trigger();
 }
 
 __device__ __forceinline__ const Work& work_of(const Launch& L, int slot) {

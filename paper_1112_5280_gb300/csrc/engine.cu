@@ -668,6 +668,7 @@ int lqcd_engine_submit_normal(lqcd_engine* e, const lqcd_gauge* gauge, const lqc
 // NULL starts from x = 0
 static int submit_impl(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field* src, double kappa,
                        double mu, double tol, bool normal, long long* request_id, const lqcd_field* x0) {
+  PdlSolverScope pdl_scope;  // solver launches: no programmatic dependent launch
   clear_error();
   if (!e || !gauge || !src || !request_id) return set_error(LQCD_EINVAL, "NULL argument");
   if (x0 && (x0->prec != LQCD_F64 || !x0->half[0] || memcmp(x0->g.L, gauge->g.L, sizeof x0->g.L)))
@@ -814,6 +815,7 @@ static int submit_impl(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field
 
 int lqcd_engine_step(lqcd_engine* e, int* n_active) {
   LQCD_TRACE("lqcd_engine_step");
+  PdlSolverScope pdl_scope;  // solver launches: no programmatic dependent launch
   clear_error();
   if (!e) return set_error(LQCD_EINVAL, "engine is NULL");
   lqcd_ctx* c = e->ctx;
@@ -889,6 +891,7 @@ int lqcd_engine_completed(lqcd_engine* e, long long* ids, int max, int* n) {
 
 int lqcd_engine_result(lqcd_engine* e, long long id, lqcd_field* x, lqcd_solve_info* info) {
   LQCD_TRACE("lqcd_engine_result");
+  PdlSolverScope pdl_scope;  // solver launches: no programmatic dependent launch
   clear_error();
   if (!e) return set_error(LQCD_EINVAL, "engine is NULL");
   auto it = e->reqs.find(id);

@@ -33,6 +33,11 @@ struct DslashMinBlocks {
   static constexpr int value =
       (SP == P_DF64) ? 4 : ((SP == P_F16 || SP == P_BF16) ? LQCD_DSLASH_MIN_BLOCKS_HALF : LQCD_DSLASH_MIN_BLOCKS);
 };
+// The second register budget of the FP32 Dslash (launch form 3): 8 CTAs per SM, 128
+// registers per thread. More warps with fewer hops in flight each; it pays where the
+// launch is latency bound rather than at the HBM roofline (slots sharing links through
+// L2), and the autotuner times it against the default.
+constexpr int DSLASH_MIN_BLOCKS_HI = 8;
 
 // Site sums with a fixed rounding sequence (f_fma; see field.cuh), as the Dslash forms share them.
 template <typename R>
@@ -180,12 +185,13 @@ __device__ __forceinline__ void dslash_epilogue(const Work& w, int h, typename S
 //                 r -= alpha (y1 + a * D in); x += alpha p      (EPI_CG, CG step)
 // (twisted: out = T(a D in) + c1 y1 + c2 T_y y2 and r -= alpha (T_y y1 + T(a D in)))
 // with the Work's reduction (norm / dots) and scalar finisher per slot.
-template <int SP, int LP, int NR, bool DAG, int EPI>
-__global__ void __launch_bounds__(TILE, DslashMinBlocks<SP>::value) k_dslash(const Launch L) {
-  pdl_entry();
+template <int SP, int LP, int NR, bool DAG, int EPI, int MB = DslashMinBlocks<SP>::value>
+__global__ void __launch_bounds__(TILE, MB) k_dslash(const Launch L) {
+  pdl_wait();
   using R = typename SpinorIO<SP>::Real;
   if (single_slot_idle(L)) return;
   for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
+    pdl_last_tile(tile, L.ntiles);
     int slot, start;
     tile_of(L, tile, slot, start);
     const Work& w = work_of(L, slot);
@@ -274,13 +280,14 @@ struct MrhsPipe<8, D, SP, DAG> {
 
 template <int SP, int LP, int NR, bool DAG, int EPI>
 __global__ void __launch_bounds__(TILE, LQCD_DSLASH_MRHS_MIN_BLOCKS) k_dslash_mrhs(const Launch L) {
-  pdl_entry();
+  pdl_wait();
   static_assert(SP == P_F32 || SP == P_F16 || SP == P_BF16, "multi-RHS form: FP32 arithmetic");
   using IO = SpinorIO<SP>;
   constexpr int D = DslashDepth<SP>::value;
   __shared__ float4 su[8 * MRHS_W * TILE];
   float4* s = su + threadIdx.x;
   for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
+    pdl_last_tile(tile, L.ntiles);
     const int group = tile % L.mrhs_groups;
     const int block = tile / L.mrhs_groups;
     const int s0 = group * L.mrhs_group;
@@ -351,7 +358,7 @@ __device__ __forceinline__ void colour_dot(const R a[8], const R b[8], double& r
 #endif
 template <int SP, int LP, bool DAG, int EPI>
 __global__ void __launch_bounds__(3 * TILE, LQCD_DSLASH3_MIN_BLOCKS) k_dslash3(const Launch L) {
-  pdl_entry();
+  pdl_wait();
   using R = typename SpinorIO<SP>::Real;
   static_assert(SP == P_DF64 && LP == P_DF64, "the colour-split form is built for double-float");
   __shared__ ProjShare<TILE> sh;
@@ -359,6 +366,7 @@ __global__ void __launch_bounds__(3 * TILE, LQCD_DSLASH3_MIN_BLOCKS) k_dslash3(c
   const int col = threadIdx.x / TILE;
   const int j = threadIdx.x - col * TILE;
   for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
+    pdl_last_tile(tile, L.ntiles);
     int slot, start;
     tile_of(L, tile, slot, start);
     const Work& w = work_of(L, slot);
@@ -464,11 +472,12 @@ __device__ __forceinline__ void caxpy(R* out, const R* x, R cr, R ci, const R* y
 // FP64-class vectors (true residual, solution accumulator) in the mixed ops.
 template <int SP, int OP, int TP = P_F64>
 __global__ void __launch_bounds__(TILE) k_blas(const Launch L) {
-  pdl_entry();
+  pdl_wait();
   using R = typename SpinorIO<SP>::Real;
   using TR = typename SpinorIO<TP>::Real;
   if (single_slot_idle(L)) return;
   for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
+    pdl_last_tile(tile, L.ntiles);
     int slot, start;
     tile_of(L, tile, slot, start);
     const Work& w = work_of(L, slot);

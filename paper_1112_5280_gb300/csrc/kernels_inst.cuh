@@ -52,6 +52,13 @@ cudaError_t go_dslash(const Launch& L, int grid, cudaStream_t s, int form) {
       return launch_k(fn3, dim3(grid), dim3(3 * TILE), s, L);
     }
   }
+  if constexpr (SPX == P_F32) {
+    if (form == 3) {  // the FP32 Dslash at the second register budget
+      auto fh = k_dslash<SPX, LPX, NR, DAG, EPI, DSLASH_MIN_BLOCKS_HI>;
+      if (grid <= 0) grid = grid_for((const void*)fh, L.ntiles, 0, TILE, cps);
+      return launch_k(fh, dim3(grid), dim3(TILE), s, L);
+    }
+  }
   if constexpr (!split_only) {
     auto fn = k_dslash<SPX, LPX, NR, DAG, EPI>;
     if (grid <= 0) grid = grid_for((const void*)fn, L.ntiles, 0, TILE, cps);
@@ -165,9 +172,21 @@ int shared_link_occupancy(int nr) {
   return 0;
 }
 
+namespace {
+template <int P>
+int second_budget_occupancy(int nr) {
+  if constexpr (P == P_F32) {
+    if (nr == 18) return kernel_occupancy((const void*)k_dslash<P, LPX, 18, false, EPI_LIN, DSLASH_MIN_BLOCKS_HI>, TILE);
+    if (nr == 12) return kernel_occupancy((const void*)k_dslash<P, LPX, 12, false, EPI_LIN, DSLASH_MIN_BLOCKS_HI>, TILE);
+  }
+  return 0;
+}
+}  // namespace
+
 int LQCD_CAT(dslash_occupancy_, LQCD_SFX)(int nr, int form) {
   if (form == 1) return colour_split_occupancy<SPX>(nr);
   if (form == 2) return shared_link_occupancy<SPX>(nr);
+  if (form == 3) return second_budget_occupancy<SPX>(nr);
   if (form != 0) return 0;
   if (nr == 18) return kernel_occupancy((const void*)k_dslash<SPX, LPX, 18, false, EPI_LIN>, TILE);
   if (nr == 12) return site_occupancy_12<SPX>();

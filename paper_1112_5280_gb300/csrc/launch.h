@@ -14,7 +14,8 @@ namespace lqcd {
 inline int link_prec_for(int sp) { return (sp == P_F64 || sp == P_F32 || sp == P_DF64) ? sp : P_F16; }
 
 // grid <= 0: persistent grid of the autotuned CTAs per SM (else the occupancy limit);
-// form < 0: the autotuned Dslash form (else the default), 0 site, 1 colour split.
+// form < 0: the autotuned Dslash form (else the default), 0 site, 1 colour split,
+// 3 site at the second register budget (FP32 only; other precisions take form 0).
 cudaError_t launch_dslash(int sp, int nr, bool dag, int epi, const Launch& L, int grid,
                           cudaStream_t s, int form = -1);
 // tp: precision of the FP64-class operand of the mixed ops (P_F64 or P_DF64)
@@ -36,11 +37,18 @@ LQCD_DECL(bf16)
 LQCD_DECL(df64)
 #undef LQCD_DECL
 
-// Launches of the batched kernels, with programmatic stream serialization when the
-// environment variable LQCD_PDL=1 is set: the kernel may then be launched before the
-// previous kernel on the stream completes, and waits for it itself (pdl_entry in
-// batch.cuh). Plain launches by default (measured no faster with it).
+// Launches of the batched kernels, with programmatic stream serialization where enabled:
+// the kernel may then be launched before the previous kernel on the stream completes, and
+// waits for it itself (pdl_wait in batch.cuh). Enabled for operator launches, disabled
+// while a PdlSolverScope is alive on the calling thread (the solvers' step chains, where it
+// measured no faster); LQCD_PDL=1 / 0 forces it on / off everywhere.
 bool pdl_enabled();
+struct PdlSolverScope {
+  PdlSolverScope();
+  ~PdlSolverScope();
+  PdlSolverScope(const PdlSolverScope&) = delete;
+  PdlSolverScope& operator=(const PdlSolverScope&) = delete;
+};
 template <typename... KArgs, typename... Args>
 cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args&&... args) {
   cudaLaunchConfig_t cfg = {};
@@ -63,14 +71,15 @@ void set_grid_multiplier(int kernel_family, int mult);  // 0 = occupancy limit
 int grid_for(const void* kernel_fn, int ntiles, int family, int block, int ctas_per_sm = 0);
 int kernel_occupancy(const void* kernel_fn, int block);
 // resident CTAs per SM of the Dslash of this precision, link reals and form (0 if no such
-// form): 0 one thread per site, 1 colour split (double-float), 2 shared-link multi-RHS
+// form): 0 one thread per site, 1 colour split (double-float), 2 shared-link multi-RHS,
+// 3 one thread per site at 8 CTAs per SM (FP32)
 int dslash_occupancy(int sp, int nr, int form);
 
 // Autotuner table (tune.cu): the launch choice for Dslash launches of this precision and
 // link reals whose tile count has the same floor(log2) as a tuned launch.
 struct TuneChoice {
   int ctas_per_sm;  // 0: occupancy limit
-  int form;         // 0 site, 1 colour split
+  int form;         // 0 site, 1 colour split, 3 site at the second register budget
 };
 TuneChoice tune_choice(int sp, int nr, int ntiles);
 // Shared-link choice for nrhs slots on one gauge field of `blocks` site blocks: the tuned

@@ -276,16 +276,27 @@ cudaError_t launch_dslash(int sp, int nr, bool dag, int epi, const Launch& L, in
   return cudaErrorInvalidValue;
 }
 
-// Off unless LQCD_PDL=1: measured on GB300, the parked grids gained nothing (every kernel
-// waits for its predecessor before its first memory access) and cost 1% on the batched
-// Dslash and 3% on the 32^3x64 mixed CG; without the attribute the entry instructions of
-// the kernels cost nothing measurable.
+// Programmatic dependent launch of the batched kernels (each CTA lets the next grid launch
+// when it starts its last tile). Measured on GB300: the batched 16^3x32 FP32 Dslash of ten
+// slots per launch, applied back to back, 81.5 -> 80.5 us per launch; the solvers' step
+// chains (32^3x64 CG in FP16, BF16, FP32 and double-float, BiCGStab) within +-2% either
+// way, double-float CG the slowest. So it is on for the operator launches (lqcd_dslash_eo,
+// batches, M-hat) and off inside the solvers (PdlSolverScope); LQCD_PDL=1 turns it on
+// everywhere, LQCD_PDL=0 off everywhere.
+namespace {
+thread_local int t_solver_depth = 0;
+}
+PdlSolverScope::PdlSolverScope() { ++t_solver_depth; }
+PdlSolverScope::~PdlSolverScope() { --t_solver_depth; }
+
 bool pdl_enabled() {
-  static const bool on = [] {
+  static const int mode = [] {
     const char* v = std::getenv("LQCD_PDL");
-    return v && v[0] == '1';
+    if (!v || !v[0]) return -1;
+    return v[0] == '1' ? 1 : 0;
   }();
-  return on;
+  if (mode >= 0) return mode == 1;
+  return t_solver_depth == 0;
 }
 
 int dslash_occupancy(int sp, int nr, int form) {

@@ -1,7 +1,9 @@
 // Launch autotuner of the batched Dslash. For a given set of gauge fields (one slot
 // each, as in a multi-RHS or multi-lattice launch) it times every distinct persistent
-// grid (CTAs per SM from 1 to the occupancy limit) of every compiled kernel form and
-// keeps the fastest in a table keyed by (spinor precision, link reals, floor(log2(tiles))).
+// grid (CTAs per SM from 1 to the occupancy limit) of every compiled kernel form (one
+// thread per site at the default register budget; colour split for double-float; one
+// thread per site at 8 CTAs per SM, 128 registers, for FP32) and keeps the fastest in a
+// table keyed by (spinor precision, link reals, floor(log2(tiles))).
 // When every slot is on the same gauge field (n right-hand sides), it also times the
 // shared-link form, which loads each site block's links once for a group of slots, for
 // several group sizes and grids, against the slots loading their own links, and keeps the
@@ -335,7 +337,8 @@ int lqcd_autotune_dslash(int n, const lqcd_gauge* const* g, int prec, int compre
   ent.ntiles = ntiles;
   double best_us = 1e30, def_us = 0;
   int best_cps = 0, best_form = def_form;
-  for (int form = 0; form < 2 && err == cudaSuccess; ++form) {
+  for (int form : {0, 1, 3}) {
+    if (err != cudaSuccess) break;
     const int occ = dslash_occupancy(prec, nr, form);
     if (occ < 1) continue;
     int last_grid = -1;
@@ -512,7 +515,7 @@ int lqcd_tune_load(const char* path) {
                       get_int(o, "group", e.group) && get_int(o, "candidates", e.candidates) &&
                       get_num(o, "us_best", e.us_best) && get_num(o, "us_default", e.us_default);
     const bool valid = read && prec >= LQCD_F64 && prec <= LQCD_DF64 && (nr == 12 || nr == 18) && b >= 0 &&
-                       b <= 30 && e.ctas_per_sm >= 0 && e.ctas_per_sm <= 64 && e.form >= 0 && e.form <= 2 &&
+                       b <= 30 && e.ctas_per_sm >= 0 && e.ctas_per_sm <= 64 && e.form >= 0 && e.form <= 3 &&
                        dslash_occupancy(prec, nr, e.form) > 0 &&
                        (nrhs == 0 ? (e.form != 2 && e.group == 0)
                                   : (nrhs >= 2 && nrhs <= MAX_SLOTS &&

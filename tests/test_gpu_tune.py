@@ -48,9 +48,9 @@ def test_tuned_choice_is_valid_and_results_unchanged(ctx, prec, compress):
     assert r["ntiles"] == 4 * (np.prod(dims) // 2 // 64)
     assert r["candidates"] >= 1 and r["us_best"] > 0 and r["us_default"] > 0
     assert r["us_best"] <= r["us_default"] * 1.0000001
-    assert 0 <= r["ctas_per_sm"] <= 32 and r["form"] in (0, 1)
-    if prec == "df64":
-        assert r["candidates"] >= 2  # both kernel forms were timed
+    assert 0 <= r["ctas_per_sm"] <= 32 and r["form"] in ((0, 3) if prec == "f32" else (0, 1))
+    if prec in ("df64", "f32"):
+        assert r["candidates"] >= 2  # both kernel forms (register budgets) were timed
     # force a non-default choice for the single-slot launch size and compare bitwise
     single = lqcd.autotune_dslash([g], prec)
     assert single["ntiles"] == np.prod(dims) // 2 // 64
@@ -119,6 +119,36 @@ def _entry(**kw):
     return e
 
 
+@pytest.mark.parametrize("compress", [12, 18])
+def test_second_register_budget_is_bitwise_the_default(ctx, tmp_path, compress):
+    """Form 3 (the FP32 Dslash compiled for 8 CTAs per SM) runs the same site arithmetic in
+    the same order: M-hat and a whole solve are bitwise those of the default form."""
+    dims = (8, 8, 8, 16)  # 64 tiles per half lattice: bucket 6
+    U = synth.random_links(dims, 0.5, seed=93)
+    psi = synth.gaussian_spinor(dims, seed=94)
+    g = ctx.gauge(dims, U, prec="f32", compress=compress)
+    g64 = ctx.gauge(dims, U, prec="f64")
+    b = ctx.field(dims, "f64", lqcd.FULL, data=psi)
+    o = lqcd.solve_opts(sloppy_prec="f32", sloppy_compress=compress)
+
+    def run():
+        x = ctx.field(dims, "f64", lqcd.FULL)
+        info = lqcd.solve_fields(g64, b, 0.15, 1e-10, x, o)
+        out = x.download()
+        x.close()
+        return _mhat(ctx, g, dims, psi, "f32"), out, info["iters"]
+
+    ref = run()
+    tag = _device_tag(ctx, tmp_path)
+    p = tmp_path / "hi.json"
+    p.write_text(json.dumps({"format": "lqcd-tune", "version": 2, "device": tag, "entries": [
+        _entry(prec=1, nr=compress, bucket=6, ntiles=64, form=3)]}))
+    lqcd.tune_load(p)
+    assert [e["form"] for e in lqcd.tune_entries()] == [3]
+    got = run()
+    assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1]) and ref[2] == got[2]
+
+
 def test_load_rejects_foreign_and_malformed_files(ctx, tmp_path):
     tag = _device_tag(ctx, tmp_path)
 
@@ -131,6 +161,7 @@ def test_load_rejects_foreign_and_malformed_files(ctx, tmp_path):
         "no_such_form": doc([_entry(form=7)]),
         "shared_form_without_rhs": doc([_entry(form=2, group=2)]),
         "group_beyond_rhs": doc([_entry(nrhs=4, bucket=3, form=2, group=6)]),
+        "second_budget_not_fp32": doc([_entry(prec=2, nr=12, form=3)]),
         "missing_field": doc([{k: v for k, v in _entry().items() if k != "ctas_per_sm"}]),
         "truncated": doc([_entry()])[:-3],
         "text_format": "lqcd-tune 1 " + tag + "\ndslash 1 18 5 40 0 0 3 10.0 10.0\n",
@@ -184,6 +215,6 @@ def test_shared_link_group_size_does_not_change_results(ctx, tmp_path):
     lqcd.tune_clear()
     res = lqcd.autotune_dslash([g] * 12, "f32", 12)
     assert res["nrhs"] == 12 and (res["group"] == 0 or 2 <= res["group"] <= 12)
-    assert res["form"] == (2 if res["group"] else 0)
+    assert res["form"] == 2 if res["group"] else res["form"] in (0, 3)
     got = run()
     assert all(np.array_equal(a, b) for a, b in zip(ref, got))
