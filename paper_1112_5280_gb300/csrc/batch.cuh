@@ -113,6 +113,7 @@ struct Launch {
   int finish;              // 1: the slots' Works reduce or finish; k_finish follows the launch
   int mrhs_group;          // interleave 2: slots per group (group g holds [g G, (g + 1) G))
   int mrhs_groups;         // interleave 2: number of slot groups
+  int gated;               // 1: some slot runs only in a given solver state (Work::run_if >= 0)
 };
 
 // Programmatic dependent launch. The batched kernels are launched with programmatic stream
@@ -162,6 +163,54 @@ __device__ __forceinline__ void tile_of(const Launch& L, int tile, int& slot, in
 __device__ __forceinline__ bool slot_runs(const Work& w) {
   if (w.run_if < 0) return true;
   return *((volatile int*)&w.sc->state) == w.run_if;
+}
+
+// Per-CTA view of a solver launch (gated, 2..VIEW_SLOTS slots), staged in shared memory once
+// per CTA: whether each slot runs in this launch (a slot's state changes only in the
+// finisher kernels between launches, never during one) and the tile prefix of the
+// concatenated tile order. Each tile then finds its slot and run flag in shared memory
+// instead of reading the slot state from global memory (a dependent L2 round trip) and
+// binary-searching the prefix there. Ungated launches (operators: every slot runs) and
+// larger ones keep the plain path, without the prologue.
+constexpr int VIEW_SLOTS = 128;
+struct SlotView {
+  unsigned runs[VIEW_SLOTS / 32];
+  int prefix[VIEW_SLOTS + 1];
+};
+
+// Called by every thread of the CTA (it ends in a barrier); false when the launch has one
+// slot or more than VIEW_SLOTS.
+__device__ __forceinline__ bool view_load(const Launch& L, SlotView& v) {
+  if (!L.gated || L.nslots <= 1 || L.nslots > VIEW_SLOTS) return false;
+  for (int i = threadIdx.x; i < VIEW_SLOTS / 32; i += blockDim.x) v.runs[i] = 0u;
+  __syncthreads();
+  for (int i = threadIdx.x; i < L.nslots; i += blockDim.x) {
+    if (slot_runs(work_of(L, i))) atomicOr(&v.runs[i >> 5], 1u << (i & 31));
+    if (!L.interleave) v.prefix[i] = __ldg(L.tile_prefix + i);
+  }
+  if (threadIdx.x == 0 && !L.interleave) v.prefix[L.nslots] = __ldg(L.tile_prefix + L.nslots);
+  __syncthreads();
+  return true;
+}
+
+// tile_of with the prefix from the view when there is one
+__device__ __forceinline__ void tile_of_v(const Launch& L, const SlotView& v, bool view, int tile, int& slot,
+                                          int& start) {
+  if (!view || L.interleave) {
+    tile_of(L, tile, slot, start);
+    return;
+  }
+  int lo = 0, hi = L.nslots;  // largest slot with prefix[slot] <= tile
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (v.prefix[mid] <= tile) lo = mid; else hi = mid;
+  }
+  slot = lo;
+  start = (tile - v.prefix[lo]) * TILE;
+}
+
+__device__ __forceinline__ bool slot_runs_v(const SlotView& v, bool view, const Launch& L, int slot) {
+  return view ? ((v.runs[slot >> 5] >> (slot & 31)) & 1u) != 0u : slot_runs(work_of(L, slot));
 }
 
 // Block-wide FP64 sum in a fixed order (NT threads). Result valid in thread 0.

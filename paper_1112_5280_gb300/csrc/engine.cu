@@ -326,6 +326,8 @@ Launch batch_launch(const lqcd_engine* e, int s) {
     const Work& w = e->h_works[(size_t)s * e->max_slots + i];
     L.finish = ((w.red || w.fin != FIN_NONE) && w.run_if != S_NEVER) ? 1 : 0;
   }
+  for (int i = 0; i < L.nslots && !L.gated; ++i)
+    L.gated = e->h_works[(size_t)s * e->max_slots + i].run_if >= 0 ? 1 : 0;
   return L;
 }
 

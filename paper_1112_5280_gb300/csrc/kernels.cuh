@@ -190,12 +190,14 @@ __global__ void __launch_bounds__(TILE, MB) k_dslash(const Launch L) {
   pdl_wait();
   using R = typename SpinorIO<SP>::Real;
   if (single_slot_idle(L)) return;
+  __shared__ SlotView sv;
+  const bool view = view_load(L, sv);
   for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
     pdl_last_tile(tile, L.ntiles);
     int slot, start;
-    tile_of(L, tile, slot, start);
+    tile_of_v(L, sv, view, tile, slot, start);
+    if (!slot_runs_v(sv, view, L, slot)) continue;
     const Work& w = work_of(L, slot);
-    if (!slot_runs(w)) continue;
     const int h = start + threadIdx.x;
     double v0 = 0.0, v1 = 0.0, v2 = 0.0;
     if (h < w.g.Vh) {
@@ -212,31 +214,43 @@ __global__ void __launch_bounds__(TILE, MB) k_dslash(const Launch L) {
 // Every slot of the launch solves on the same gauge field (one lattice, one link copy): the
 // 12 spin-colour point sources of a propagator (paper Section 4) or any set of solves on one
 // configuration. A CTA takes one block of TILE sites and one group of slots. Each thread
-// loads the 8 links of its site once (row 2 of 12-real links rebuilt in registers, exactly as
-// k_dslash does), keeps them in shared memory, and then computes its site for every running
-// slot of the group, in slot order, with k_dslash's hop arithmetic, epilogue and per-slot
-// partial sums. So the links cross HBM once per site block for all slots instead of once per
-// slot, and each slot's result is the same as in a launch of its own.
-constexpr int MRHS_W = 5;  // float4 words per link in shared memory: 18 reals padded to 20
-#ifndef LQCD_DSLASH_MRHS_MIN_BLOCKS
-#define LQCD_DSLASH_MRHS_MIN_BLOCKS 5  // 40 KB of links per CTA: 5 CTAs per SM
-#endif
+// loads the 8 links of its site once and keeps them in shared memory, and then computes its
+// site for every running slot of the group, in slot order, with k_dslash's hop arithmetic,
+// epilogue and per-slot partial sums. So the links cross HBM once per site block for all
+// slots instead of once per slot, and each slot's result is the same as in a launch of its
+// own. 18-real links are kept whole (padded to 5 float4, 40 KB per CTA: 5 CTAs per SM);
+// 12-real links keep their 12 stored reals (3 float4, 24 KB per CTA, 8 CTAs per SM at 128
+// registers) and rebuild row 2 at each use, from the same reals and with the same
+// operations as k_dslash, so the bits agree.
+template <int NR>
+struct Mrhs {
+  static constexpr int W = NR == 12 ? 3 : 5;  // float4 words per link in shared memory
+  static constexpr int MIN_BLOCKS = NR == 12 ? 8 : 5;
+};
 
-// the links of a thread's site: word w of hop k at s[(k * MRHS_W + w) * TILE + thread]
+// the links of a thread's site: word q of hop k at s[(k * W + q) * TILE + thread]
+template <int NR>
 __device__ __forceinline__ void mrhs_store_link(float4* s, int k, const float u[18]) {
+  constexpr int W = Mrhs<NR>::W;
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
-    s[(k * MRHS_W + q) * TILE] = make_float4(u[4 * q], u[4 * q + 1], u[4 * q + 2], u[4 * q + 3]);
-  s[(k * MRHS_W + 4) * TILE] = make_float4(u[16], u[17], 0.0f, 0.0f);
+  for (int q = 0; q < (NR == 12 ? 3 : 4); ++q)
+    s[(k * W + q) * TILE] = make_float4(u[4 * q], u[4 * q + 1], u[4 * q + 2], u[4 * q + 3]);
+  if (NR == 18) s[(k * W + 4) * TILE] = make_float4(u[16], u[17], 0.0f, 0.0f);
 }
+template <int NR>
 __device__ __forceinline__ void mrhs_load_link(const float4* s, int k, float u[18]) {
+  constexpr int W = Mrhs<NR>::W;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const float4 d = s[(k * MRHS_W + q) * TILE];
+  for (int q = 0; q < (NR == 12 ? 3 : 4); ++q) {
+    const float4 d = s[(k * W + q) * TILE];
     u[4 * q] = d.x; u[4 * q + 1] = d.y; u[4 * q + 2] = d.z; u[4 * q + 3] = d.w;
   }
-  const float4 d = s[(k * MRHS_W + 4) * TILE];
-  u[16] = d.x; u[17] = d.y;
+  if (NR == 18) {
+    const float4 d = s[(k * W + 4) * TILE];
+    u[16] = d.x; u[17] = d.y;
+  } else {
+    reconstruct_row2(u);
+  }
 }
 
 template <int K, int LP, int NR>
@@ -245,13 +259,13 @@ __device__ __forceinline__ void mrhs_fetch_link(const Geom& g, int h, const int 
   constexpr int MU = K / 2;
   constexpr bool FWD = (K % 2) == 0;
   float u[18];
-  load_link<LP, NR>(link_dir<LP, NR>(FWD ? Uout : Uin, g.Vh, MU), g.Vh, FWD ? h : nb[MU], u);
-  mrhs_store_link(s, K, u);
+  LinkIO<LP, NR>::load(link_dir<LP, NR>(FWD ? Uout : Uin, g.Vh, MU), g.Vh, FWD ? h : nb[MU], u);
+  mrhs_store_link<NR>(s, K, u);
 }
 
 // Hop K of D in at site h with the staged links; the spinor words of hop K + D are issued
 // while hop K is computed (depth D), as in HopPipe.
-template <int K, int D, int SP, bool DAG>
+template <int K, int D, int SP, int NR, bool DAG>
 struct MrhsPipe {
   using IO = SpinorIO<SP>;
   __device__ __forceinline__ static void run(const Geom& g, int t, const int nf[4], const int nb[4],
@@ -260,7 +274,7 @@ struct MrhsPipe {
     constexpr int MU = K / 2;
     constexpr bool FWD = (K % 2) == 0;
     float u[18];
-    mrhs_load_link(s, K, u);
+    mrhs_load_link<NR>(s, K, u);
     const int eta = (MU == 3 && t == (FWD ? g.L[3] - 1 : 0)) ? g.t_bc : 1;
     constexpr int S = FWD ? (DAG ? 1 : -1) : (DAG ? -1 : 1);
     hop_words<MU, S, !FWD, SP>(b[K % D], u, eta, acc);
@@ -268,23 +282,25 @@ struct MrhsPipe {
       constexpr int KN = (K + D < 8) ? K + D : 0;
       IO::load_raw(in, g.Vh, (KN % 2 == 0) ? nf[KN / 2] : nb[KN / 2], b[K % D]);
     }
-    MrhsPipe<K + 1, D, SP, DAG>::run(g, t, nf, nb, in, s, b, acc);
+    MrhsPipe<K + 1, D, SP, NR, DAG>::run(g, t, nf, nb, in, s, b, acc);
   }
 };
-template <int D, int SP, bool DAG>
-struct MrhsPipe<8, D, SP, DAG> {
+template <int D, int SP, int NR, bool DAG>
+struct MrhsPipe<8, D, SP, NR, DAG> {
   __device__ __forceinline__ static void run(const Geom&, int, const int*, const int*, const void*,
                                              const float4*, typename SpinorIO<SP>::Word (&)[D][SpinorIO<SP>::NW],
                                              float*) {}
 };
 
 template <int SP, int LP, int NR, bool DAG, int EPI>
-__global__ void __launch_bounds__(TILE, LQCD_DSLASH_MRHS_MIN_BLOCKS) k_dslash_mrhs(const Launch L) {
+__global__ void __launch_bounds__(TILE, Mrhs<NR>::MIN_BLOCKS) k_dslash_mrhs(const Launch L) {
   pdl_wait();
   static_assert(SP == P_F32 || SP == P_F16 || SP == P_BF16, "multi-RHS form: FP32 arithmetic");
   using IO = SpinorIO<SP>;
   constexpr int D = DslashDepth<SP>::value;
-  __shared__ float4 su[8 * MRHS_W * TILE];
+  __shared__ float4 su[8 * Mrhs<NR>::W * TILE];
+  __shared__ SlotView sv;
+  const bool view = view_load(L, sv);
   float4* s = su + threadIdx.x;
   for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
     pdl_last_tile(tile, L.ntiles);
@@ -293,7 +309,7 @@ __global__ void __launch_bounds__(TILE, LQCD_DSLASH_MRHS_MIN_BLOCKS) k_dslash_mr
     const int s0 = group * L.mrhs_group;
     const int s1 = min(L.nslots, s0 + L.mrhs_group);
     bool any = false;
-    for (int si = s0; si < s1; ++si) any = any || slot_runs(work_of(L, si));
+    for (int si = s0; si < s1; ++si) any = any || slot_runs_v(sv, view, L, si);
     if (!any) continue;
     const Work& w0 = work_of(L, s0);  // lattice, parity and links are those of every slot
     const Geom& g = w0.g;
@@ -312,8 +328,8 @@ __global__ void __launch_bounds__(TILE, LQCD_DSLASH_MRHS_MIN_BLOCKS) k_dslash_mr
       mrhs_fetch_link<7, LP, NR>(g, h, nb, w0.Uout, w0.Uin, s);
     }
     for (int si = s0; si < s1; ++si) {
+      if (!slot_runs_v(sv, view, L, si)) continue;  // uniform over the CTA
       const Work& w = work_of(L, si);
-      if (!slot_runs(w)) continue;  // uniform over the CTA
       double v0 = 0.0, v1 = 0.0, v2 = 0.0;
       if (live) {
         typename IO::Word b[D][IO::NW];
@@ -322,7 +338,7 @@ __global__ void __launch_bounds__(TILE, LQCD_DSLASH_MRHS_MIN_BLOCKS) k_dslash_mr
         float acc[24];
 #pragma unroll
         for (int i = 0; i < 24; ++i) acc[i] = 0.0f;
-        MrhsPipe<0, D, SP, DAG>::run(g, t, nf, nb, w.in, s, b, acc);
+        MrhsPipe<0, D, SP, NR, DAG>::run(g, t, nf, nb, w.in, s, b, acc);
         dslash_epilogue<SP, EPI>(w, h, acc, v0, v1, v2);
       }
       if constexpr (EpiTraits<EPI>::red) tile_partial<TILE, true>(w, block, v0, v1, v2, L.partials);
@@ -363,14 +379,16 @@ __global__ void __launch_bounds__(3 * TILE, LQCD_DSLASH3_MIN_BLOCKS) k_dslash3(c
   static_assert(SP == P_DF64 && LP == P_DF64, "the colour-split form is built for double-float");
   __shared__ ProjShare<TILE> sh;
   if (single_slot_idle(L)) return;
+  __shared__ SlotView sv;
+  const bool view = view_load(L, sv);
   const int col = threadIdx.x / TILE;
   const int j = threadIdx.x - col * TILE;
   for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
     pdl_last_tile(tile, L.ntiles);
     int slot, start;
-    tile_of(L, tile, slot, start);
+    tile_of_v(L, sv, view, tile, slot, start);
+    if (!slot_runs_v(sv, view, L, slot)) continue;
     const Work& w = work_of(L, slot);
-    if (!slot_runs(w)) continue;
     const int h = start + j;
     const int Vh = w.g.Vh;
     double v0 = 0.0, v1 = 0.0, v2 = 0.0;
@@ -476,12 +494,14 @@ __global__ void __launch_bounds__(TILE) k_blas(const Launch L) {
   using R = typename SpinorIO<SP>::Real;
   using TR = typename SpinorIO<TP>::Real;
   if (single_slot_idle(L)) return;
+  __shared__ SlotView sv;
+  const bool view = view_load(L, sv);
   for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
     pdl_last_tile(tile, L.ntiles);
     int slot, start;
-    tile_of(L, tile, slot, start);
+    tile_of_v(L, sv, view, tile, slot, start);
+    if (!slot_runs_v(sv, view, L, slot)) continue;
     const Work& w = work_of(L, slot);
-    if (!slot_runs(w)) continue;
     const int h = start + threadIdx.x;
     const int Vh = w.g.Vh;
     double v0 = 0.0, v1 = 0.0, v2 = 0.0;
