@@ -166,47 +166,82 @@ __device__ __forceinline__ bool slot_runs(const Work& w) {
 }
 
 // Per-CTA view of a solver launch (gated, 2..VIEW_SLOTS slots), staged in shared memory once
-// per CTA: whether each slot runs in this launch (a slot's state changes only in the
-// finisher kernels between launches, never during one) and the tile prefix of the
-// concatenated tile order. Each tile then finds its slot and run flag in shared memory
-// instead of reading the slot state from global memory (a dependent L2 round trip) and
-// binary-searching the prefix there. Ungated launches (operators: every slot runs) and
+// per CTA: which slots run in this launch (a slot's state changes only in the finisher
+// kernels between launches, never during one), compacted in slot order, with the prefix of
+// their tile counts. The CTAs then stride over the running slots' tiles only, so a launch in
+// which a few slots run (a reliable update that some slots take, slots waiting for one) is
+// spread over every CTA; striding over all tiles and skipping idle slots' left the CTAs
+// whose tiles fell on idle slots without work (with interleaved tiles a CTA meets only
+// nslots / gcd(grid, nslots) slots). Each tile finds its slot in shared memory, instead of
+// reading the slot state from global memory (a dependent L2 round trip) and binary-searching
+// the tile prefix there. Which CTA computes a tile changes no result: each tile's partial
+// sum goes to the slot's own tile index. Ungated launches (operators: every slot runs) and
 // larger ones keep the plain path, without the prologue.
 constexpr int VIEW_SLOTS = 128;
 struct SlotView {
+  int nact;                    // running slots
+  int total;                   // their tiles
   unsigned runs[VIEW_SLOTS / 32];
-  int prefix[VIEW_SLOTS + 1];
+  short act[VIEW_SLOTS];       // the running slots, in slot order
+  int prefix[VIEW_SLOTS + 1];  // concatenated order: first tile of each running slot
 };
 
-// Called by every thread of the CTA (it ends in a barrier); false when the launch has one
-// slot or more than VIEW_SLOTS.
+// Called by every thread of the CTA (it ends in a barrier); false when the launch is not
+// gated, has one slot or more than VIEW_SLOTS. Warp 0 compacts the running slots.
 __device__ __forceinline__ bool view_load(const Launch& L, SlotView& v) {
   if (!L.gated || L.nslots <= 1 || L.nslots > VIEW_SLOTS) return false;
-  for (int i = threadIdx.x; i < VIEW_SLOTS / 32; i += blockDim.x) v.runs[i] = 0u;
-  __syncthreads();
-  for (int i = threadIdx.x; i < L.nslots; i += blockDim.x) {
-    if (slot_runs(work_of(L, i))) atomicOr(&v.runs[i >> 5], 1u << (i & 31));
-    if (!L.interleave) v.prefix[i] = __ldg(L.tile_prefix + i);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int base = 0, tiles = 0;
+    for (int c = 0; c < L.nslots; c += 32) {
+      const int i = c + lane;
+      bool run = false;
+      int cnt = 0;
+      if (i < L.nslots) {
+        run = slot_runs(work_of(L, i));
+        if (run && !L.interleave) cnt = __ldg(L.tile_prefix + i + 1) - __ldg(L.tile_prefix + i);
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, run);
+      int sc = cnt;  // inclusive scan of the running slots' tile counts
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, sc, o);
+        if (lane >= o) sc += y;
+      }
+      if (run) {
+        const int k = base + __popc(m & ((1u << lane) - 1u));
+        v.act[k] = (short)i;
+        v.prefix[k] = tiles + sc - cnt;
+      }
+      if (lane == 0) v.runs[c >> 5] = m;
+      tiles += __shfl_sync(0xffffffffu, sc, 31);
+      base += __popc(m);
+    }
+    if (lane == 0) {
+      v.nact = base;
+      v.prefix[base] = tiles;
+      v.total = L.interleave ? base * (L.ntiles / L.nslots) : tiles;
+    }
   }
-  if (threadIdx.x == 0 && !L.interleave) v.prefix[L.nslots] = __ldg(L.tile_prefix + L.nslots);
   __syncthreads();
   return true;
 }
 
-// tile_of with the prefix from the view when there is one
-__device__ __forceinline__ void tile_of_v(const Launch& L, const SlotView& v, bool view, int tile, int& slot,
-                                          int& start) {
-  if (!view || L.interleave) {
-    tile_of(L, tile, slot, start);
-    return;
+// running tile t (0 <= t < v.total) -> (slot, first site); interleave 1 or concatenated
+__device__ __forceinline__ void view_tile(const Launch& L, const SlotView& v, int t, int& slot, int& start) {
+  if (L.interleave) {
+    const int k = t % v.nact;
+    slot = v.act[k];
+    start = (t / v.nact) * TILE;
+  } else {
+    int lo = 0, hi = v.nact;  // largest k with prefix[k] <= t
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (v.prefix[mid] <= t) lo = mid; else hi = mid;
+    }
+    slot = v.act[lo];
+    start = (t - v.prefix[lo]) * TILE;
   }
-  int lo = 0, hi = L.nslots;  // largest slot with prefix[slot] <= tile
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (v.prefix[mid] <= tile) lo = mid; else hi = mid;
-  }
-  slot = lo;
-  start = (tile - v.prefix[lo]) * TILE;
 }
 
 __device__ __forceinline__ bool slot_runs_v(const SlotView& v, bool view, const Launch& L, int slot) {

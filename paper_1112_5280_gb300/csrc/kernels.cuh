@@ -192,11 +192,16 @@ __global__ void __launch_bounds__(TILE, MB) k_dslash(const Launch L) {
   if (single_slot_idle(L)) return;
   __shared__ SlotView sv;
   const bool view = view_load(L, sv);
-  for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
-    pdl_last_tile(tile, L.ntiles);
+  const int ntiles = view ? sv.total : L.ntiles;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    pdl_last_tile(tile, ntiles);
     int slot, start;
-    tile_of_v(L, sv, view, tile, slot, start);
-    if (!slot_runs_v(sv, view, L, slot)) continue;
+    if (view) {
+      view_tile(L, sv, tile, slot, start);
+    } else {
+      tile_of(L, tile, slot, start);
+      if (!slot_runs(work_of(L, slot))) continue;
+    }
     const Work& w = work_of(L, slot);
     const int h = start + threadIdx.x;
     double v0 = 0.0, v1 = 0.0, v2 = 0.0;
@@ -381,13 +386,18 @@ __global__ void __launch_bounds__(3 * TILE, LQCD_DSLASH3_MIN_BLOCKS) k_dslash3(c
   if (single_slot_idle(L)) return;
   __shared__ SlotView sv;
   const bool view = view_load(L, sv);
+  const int ntiles = view ? sv.total : L.ntiles;
   const int col = threadIdx.x / TILE;
   const int j = threadIdx.x - col * TILE;
-  for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
-    pdl_last_tile(tile, L.ntiles);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    pdl_last_tile(tile, ntiles);
     int slot, start;
-    tile_of_v(L, sv, view, tile, slot, start);
-    if (!slot_runs_v(sv, view, L, slot)) continue;
+    if (view) {
+      view_tile(L, sv, tile, slot, start);
+    } else {
+      tile_of(L, tile, slot, start);
+      if (!slot_runs(work_of(L, slot))) continue;
+    }
     const Work& w = work_of(L, slot);
     const int h = start + j;
     const int Vh = w.g.Vh;
@@ -496,11 +506,16 @@ __global__ void __launch_bounds__(TILE) k_blas(const Launch L) {
   if (single_slot_idle(L)) return;
   __shared__ SlotView sv;
   const bool view = view_load(L, sv);
-  for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
-    pdl_last_tile(tile, L.ntiles);
+  const int ntiles = view ? sv.total : L.ntiles;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    pdl_last_tile(tile, ntiles);
     int slot, start;
-    tile_of_v(L, sv, view, tile, slot, start);
-    if (!slot_runs_v(sv, view, L, slot)) continue;
+    if (view) {
+      view_tile(L, sv, tile, slot, start);
+    } else {
+      tile_of(L, tile, slot, start);
+      if (!slot_runs(work_of(L, slot))) continue;
+    }
     const Work& w = work_of(L, slot);
     const int h = start + threadIdx.x;
     const int Vh = w.g.Vh;
