@@ -980,12 +980,32 @@ def run_e2e(ctx, lqcd, sets, args, world, stream):
     batch.close()
     for o in gs + fi + fo:
         o.close()
+    # the copy bound of such a step: plain pinned-host <-> device copies of the same bytes
+    # (one buffer each way, CUDA events), plus the device-timed compute of the headline
+    hbuf = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    dbuf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    rates = {}
+    with torch.cuda.stream(stream):
+        for name, dst, src in (("h2d", dbuf, hbuf), ("d2h", hbuf, dbuf)):
+            dst.copy_(src, non_blocking=True)
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            for _ in range(3):
+                dst.copy_(src, non_blocking=True)
+            c1.record(stream)
+            c1.synchronize()
+            rates[name] = 3 * nbytes / (c0.elapsed_time(c1) * 1e-3) / 1e9
+    del hbuf, dbuf
+    copy_ms = (nbytes / rates["h2d"] + nbytes / rates["d2h"]) / 1e6
     return {"value": bytes_step * steps * world / (ms * 1e-3) / 1e9, "unit": "GB/s",
             "h2d_bytes_per_step": int(nbytes), "d2h_bytes_per_step": int(nbytes),
             "steps": steps, "ms_per_step": ms / steps, "wall_ms_per_step": wall * 1e3 / steps,
+            "copy_GBps": {"h2d": rates["h2d"], "d2h": rates["d2h"]},
+            "copy_ms_per_step": copy_ms,
             "note": f"headline workload: {NSETS} host FP64 spinors uploaded, {APPS_PER_STEP} "
                     f"applications in {APPS_PER_STEP // NSETS} batched launches, {NSETS} outputs "
-                    "downloaded per step (CUDA events on the context stream)"}
+                    "downloaded per step (CUDA events on the context stream); copy_GBps: plain "
+                    "pinned copies of the same bytes, the bound of the step's transfers"}
 
 
 def main():

@@ -231,9 +231,10 @@ typedef struct lqcd_solve_opts {
                            lqcd_solve_batch, engines), sloppy FP32 / FP16 / BF16 Wilson: 0
                            (default) the sloppy Dslash loads each site block's links once for
                            a group of those solves when the autotuner measured that faster
-                           (lqcd_autotune_dslash), else each solve loads its own; 1 shares
-                           them untuned as well; -1 never shares. The results are the same
-                           bit for bit in every case. */
+                           (lqcd_autotune_dslash), else each solve loads its own; 1 always
+                           shares them (the tuned group size if there is one, else groups as
+                           large as leave 8 tiles per SM); -1 never shares. The results are
+                           the same bit for bit in every case. */
   double mu;            /* twisted mass (paper Section 3: M = 1 - kappa D + 2 i kappa mu g5,
                            one flavour of the N_f = 2 doublet; the other is -mu). 0 (default):
                            the Wilson operator. Any finite value. */

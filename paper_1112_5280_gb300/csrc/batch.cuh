@@ -186,6 +186,13 @@ struct SlotView {
   int prefix[VIEW_SLOTS + 1];  // concatenated order: first tile of each running slot
 };
 
+// Dynamic shared memory of a one-thread-per-site Dslash launch: the slot view for gated
+// launches, nothing otherwise (operator launches then keep the L1 carve-out of a kernel
+// without shared memory).
+inline size_t view_smem(const Launch& L) {
+  return (L.gated && L.nslots > 1 && L.nslots <= VIEW_SLOTS) ? sizeof(SlotView) : 0;
+}
+
 // Called by every thread of the CTA (it ends in a barrier); false when the launch is not
 // gated, has one slot or more than VIEW_SLOTS. Warp 0 compacts the running slots.
 __device__ __forceinline__ bool view_load(const Launch& L, SlotView& v) {

@@ -376,16 +376,16 @@ int rebuild(lqcd_engine* e) {
   // steps (k_dslash_mrhs): a CTA applies the block's links to a group of slots. The group
   // size is the autotuner's measured choice for this key. Without one the slots load their
   // own links: in the interleaved tile order consecutive CTAs read the same links, which L2
-  // then serves, and at 24^3x48 with FP32-12 links the shared form measured slower (its
-  // 40 KB of links per CTA cost one CTA per SM). multi_rhs_links > 0 asks for the shared
-  // form untuned, with groups as large as the lattice allows while the launch keeps at
-  // least 8 tiles per SM.
+  // then serves, and at 24^3x48 with FP32-12 links the shared form measured no faster (the
+  // own-link launch at 8 CTAs per SM is as fast). multi_rhs_links > 0 asks for the shared
+  // form always: in the tuned group size when the tuner measured one, else in groups as
+  // large as the lattice allows while the launch keeps at least 8 tiles per SM.
   e->mrhs_group = e->mrhs_groups = e->mrhs_tiles = 0;
   if (e->interleave && !e->any_twist && e->opts.multi_rhs_links >= 0 &&
       (e->sp == P_F32 || e->sp == P_F16 || e->sp == P_BF16)) {
     const int blocks = e->reqs[e->active[0]].ntiles;
     int gsize = tune_shared_links(e->sp, e->nr, n, blocks, nullptr);
-    if (gsize < 0 && e->opts.multi_rhs_links > 0) {
+    if (gsize <= 0 && e->opts.multi_rhs_links > 0) {
       const int want = 8 * device_sm_count();
       const int groups = std::min(n, std::max(1, (want + blocks - 1) / blocks));
       gsize = (n + groups - 1) / groups;

@@ -92,7 +92,7 @@ cudaError_t launch_finish(const Launch& L, cudaStream_t s) {
   // enough groups for the largest slot (no slot has more tiles than the launch)
   int gy = (L.ntiles + FINISH_TILES - 1) / FINISH_TILES;
   gy = gy < 1 ? 1 : (gy > FINISH_GROUPS ? FINISH_GROUPS : gy);
-  return launch_k(k_finish, dim3(L.nslots, gy), dim3(FINISH_THREADS), s, L);
+  return launch_k(k_finish, dim3(L.nslots, gy), dim3(FINISH_THREADS), 0, s, L);
 }
 
 }  // namespace lqcd

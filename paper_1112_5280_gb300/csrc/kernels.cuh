@@ -185,33 +185,46 @@ __device__ __forceinline__ void dslash_epilogue(const Work& w, int h, typename S
 //                 r -= alpha (y1 + a * D in); x += alpha p      (EPI_CG, CG step)
 // (twisted: out = T(a D in) + c1 y1 + c2 T_y y2 and r -= alpha (T_y y1 + T(a D in)))
 // with the Work's reduction (norm / dots) and scalar finisher per slot.
+template <int SP, int LP, int NR, bool DAG, int EPI>
+__device__ __forceinline__ void dslash_tile(const Launch& L, int slot, int start) {
+  using R = typename SpinorIO<SP>::Real;
+  const Work& w = work_of(L, slot);
+  const int h = start + threadIdx.x;
+  double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+  if (h < w.g.Vh) {
+    R acc[24];
+    dslash_site<SP, LP, NR, DAG>(w.g, h, w.out_par, w.in, w.Uout, w.Uin, acc);
+    dslash_epilogue<SP, EPI>(w, h, acc, v0, v1, v2);
+  }
+  if constexpr (EpiTraits<EPI>::red)
+    tile_partial<TILE, std::is_same<R, float>::value>(w, start / TILE, v0, v1, v2, L.partials);
+}
+
+// The tile loop is written twice: over the running slots' tiles of a gated launch (slot
+// view), and over all tiles otherwise, so that operator launches run the plain loop without
+// the view's branches and without shared memory (measured: one loop with a static view cost
+// 1.3% more instructions and 2-3% of the headline launch).
 template <int SP, int LP, int NR, bool DAG, int EPI, int MB = DslashMinBlocks<SP>::value>
 __global__ void __launch_bounds__(TILE, MB) k_dslash(const Launch L) {
   pdl_wait();
-  using R = typename SpinorIO<SP>::Real;
   if (single_slot_idle(L)) return;
-  __shared__ SlotView sv;
-  const bool view = view_load(L, sv);
-  const int ntiles = view ? sv.total : L.ntiles;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    pdl_last_tile(tile, ntiles);
-    int slot, start;
-    if (view) {
+  extern __shared__ int4 dyn_smem[];  // the slot view, launched with view_smem(L) bytes
+  SlotView& sv = *reinterpret_cast<SlotView*>(dyn_smem);
+  if (view_load(L, sv)) {
+    for (int tile = blockIdx.x; tile < sv.total; tile += gridDim.x) {
+      pdl_last_tile(tile, sv.total);
+      int slot, start;
       view_tile(L, sv, tile, slot, start);
-    } else {
-      tile_of(L, tile, slot, start);
-      if (!slot_runs(work_of(L, slot))) continue;
+      dslash_tile<SP, LP, NR, DAG, EPI>(L, slot, start);
     }
-    const Work& w = work_of(L, slot);
-    const int h = start + threadIdx.x;
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
-    if (h < w.g.Vh) {
-      R acc[24];
-      dslash_site<SP, LP, NR, DAG>(w.g, h, w.out_par, w.in, w.Uout, w.Uin, acc);
-      dslash_epilogue<SP, EPI>(w, h, acc, v0, v1, v2);
-    }
-    if constexpr (EpiTraits<EPI>::red)
-      tile_partial<TILE, std::is_same<R, float>::value>(w, start / TILE, v0, v1, v2, L.partials);
+    return;
+  }
+  for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
+    pdl_last_tile(tile, L.ntiles);
+    int slot, start;
+    tile_of(L, tile, slot, start);
+    if (!slot_runs(work_of(L, slot))) continue;
+    dslash_tile<SP, LP, NR, DAG, EPI>(L, slot, start);
   }
 }
 

@@ -36,7 +36,7 @@ cudaError_t go_dslash(const Launch& L, int grid, cudaStream_t s, int form) {
         tune_shared_links(SPX, NR, L.nslots, L.ntiles / L.mrhs_groups, &scps);
         grid = grid_for((const void*)fm, L.ntiles, 0, TILE, scps);
       }
-      return launch_k(fm, dim3(grid), dim3(TILE), s, L);
+      return launch_k(fm, dim3(grid), dim3(TILE), 0, s, L);
     } else {
       return cudaErrorInvalidValue;
     }
@@ -49,20 +49,20 @@ cudaError_t go_dslash(const Launch& L, int grid, cudaStream_t s, int form) {
       // double-float: the colour-split form (latency bound at one thread per site)
       auto fn3 = k_dslash3<SPX, LPX, DAG, EPI>;
       if (grid <= 0) grid = grid_for((const void*)fn3, L.ntiles, 0, 3 * TILE, cps);
-      return launch_k(fn3, dim3(grid), dim3(3 * TILE), s, L);
+      return launch_k(fn3, dim3(grid), dim3(3 * TILE), 0, s, L);
     }
   }
   if constexpr (SPX == P_F32) {
     if (form == 3) {  // the FP32 Dslash at the second register budget
       auto fh = k_dslash<SPX, LPX, NR, DAG, EPI, DSLASH_MIN_BLOCKS_HI>;
       if (grid <= 0) grid = grid_for((const void*)fh, L.ntiles, 0, TILE, cps);
-      return launch_k(fh, dim3(grid), dim3(TILE), s, L);
+      return launch_k(fh, dim3(grid), dim3(TILE), view_smem(L), s, L);
     }
   }
   if constexpr (!split_only) {
     auto fn = k_dslash<SPX, LPX, NR, DAG, EPI>;
     if (grid <= 0) grid = grid_for((const void*)fn, L.ntiles, 0, TILE, cps);
-    return launch_k(fn, dim3(grid), dim3(TILE), s, L);
+    return launch_k(fn, dim3(grid), dim3(TILE), view_smem(L), s, L);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -83,7 +83,7 @@ cudaError_t go_blas(const Launch& L, int grid, cudaStream_t s) {
   auto fn = k_blas<P, OP, TP>;
   if (L.ntiles <= 0) return cudaSuccess;
   if (grid <= 0) grid = grid_for((const void*)fn, L.ntiles, 1, TILE);
-  return launch_k(fn, dim3(grid), dim3(TILE), s, L);
+  return launch_k(fn, dim3(grid), dim3(TILE), 0, s, L);
 }
 }  // namespace
 
