@@ -219,7 +219,8 @@ typedef struct lqcd_solve_opts {
                            LQCD_F32 / F16 / BF16: mixed precision */
   int sloppy_compress;  /* 18 or 12 reals per link of the sloppy operator */
   int maxiter;          /* iteration limit (default 50000) */
-  double delta;         /* reliable-update threshold on |r| (<= 0: 0.01 mixed, none for FP64) */
+  double delta;         /* reliable-update threshold on |r| (<= 0: 0.01 for FP16 / BF16 sloppy,
+                           0.001 for FP32 sloppy, none for FP64 and double-float) */
   int chunk;            /* iterations per CUDA-graph replay / host poll (default 32) */
   int use_graph;        /* 1: capture iteration chunks as CUDA graphs (default 1) */
   int ru_interval;      /* iterations between reliable-update blocks in a CUDA-graph chunk

@@ -593,10 +593,13 @@ int lqcd_engine_create(lqcd_ctx* c, const lqcd_solve_opts* opts, size_t budget, 
   e->xp = fp64_class ? o.sloppy_prec : P_F32;
   e->nr = fp64_class ? 18 : o.sloppy_compress;
   e->tp = (o.true_prec == -1) ? (o.sloppy_prec == LQCD_F64 ? P_F64 : P_DF64) : o.true_prec;
-  // delta = 0.01: measured on GB300 for FP16/BF16/FP32 sloppy storage, 32^3x64 at
-  // kappa 0.155, six FP64-class updates instead of eleven at 0.1 and 30% faster,
-  // with the same iteration count; the FP64-class true residual decides convergence.
-  const double delta = o.delta > 0 ? o.delta : (fp64_class ? 0.0 : 0.01);
+  // Default delta by sloppy storage, measured on GB300 (32^3x64 at kappa 0.155, tol 1e-10;
+  // smaller delta: fewer FP64-class updates, until the sloppy residual recurrence drifts):
+  // FP16 / BF16 0.01 (six updates, 39 / 45 iterations; at 0.003 BF16 took 944 iterations
+  // and at 0.0003 FP16 269), FP32 0.001 (five updates, 40 iterations, 3% faster than at
+  // 0.01; the 12-source 24^3x48 batch 4% faster). The FP64-class true residual decides
+  // convergence in every case.
+  const double delta = o.delta > 0 ? o.delta : (fp64_class ? 0.0 : (o.sloppy_prec == LQCD_F32 ? 0.001 : 0.01));
   e->delta2 = delta * delta;
   e->ru_every = o.ru_interval > 0 ? std::min(o.ru_interval, o.chunk) : 0;  // 0: per batch
   e->budget = budget;
