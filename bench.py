@@ -483,7 +483,11 @@ def run_ours(args, world, rank, local):
     e2e = run_e2e(ctx, lqcd, sets, args, world, stream)
 
     peak, peak_kind = measured_peaks()
-    kname = f"k_dslash<F32,F32,18,nodag,EPI_PLAIN> x{NSETS} slots"
+    # the timed kernel: the tuner's form for the 10-slot key (0: default register budget, 3: 8
+    # CTAs per SM); its ncu traffic is keyed by form in profiles/traffic.json
+    form32 = tuned.get(f"f32_x{NSETS}", {}).get("form", 0) if tuned else 0
+    kname = (f"k_dslash<F32,F32,18,nodag,EPI_PLAIN> x{NSETS} slots, form {form32} "
+             f"({'8 CTAs per SM, 128 registers' if form32 == 3 else '6 CTAs per SM'})")
     df_ops = profile_counts("dslash_df64_16x32_fp32_ops_per_site")
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -498,7 +502,7 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world} (independent lattices per GPU)"},
         "roofline": {"bound": "hbm", "achieved": gbs_rank, "peak": peak, "unit": "GB/s",
                      "frac": gbs_rank / peak, "peak_kind": f"{peak_kind} copy bandwidth (burst)",
-                     "traffic": profile_traffic("dslash_f32_18_16x32"),
+                     "traffic": profile_traffic("dslash_f32_18_16x32" + ("_form3" if form32 == 3 else "")),
                      "kernel": kname, "us_per_launch": us_per_launch,
                      "us_per_application": ms32 * 1e3 / apps},
         # the paper's precision (Section 3: FP64): bound by the FP64 pipe on this part
