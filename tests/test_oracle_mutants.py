@@ -46,7 +46,7 @@ MUTANTS = {
                                            "    twist(&g, 1.0, 0.0, tmp, tmp, 1);"),
     "t_neighbour_off_by_one": ("n[mu] = (c[mu] + 1) % g->L[mu];",
                                "n[mu] = (c[mu] + 1 + (mu == 3)) % g->L[mu];"),
-    # the true residual ||b - M x|| / ||b||, the judge of every GPU solve
+    # the true residual ||b - M x|| / ||b||, the arbiter of every GPU solve
     "true_residual_uses_Mhat": ("oracle_apply_M(dims, t_bc, U, kappa, mu, x, (double*)y, 0);",
                                 "oracle_apply_Mhat(dims, t_bc, U, kappa, mu, x, (double*)y, 0);"),
     "true_residual_uses_dagger": ("oracle_apply_M(dims, t_bc, U, kappa, mu, x, (double*)y, 0);",

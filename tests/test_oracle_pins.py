@@ -331,13 +331,13 @@ def test_tm_solvers_vs_lapack(method):
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
 
 
-# ---------------------------------------------------------------- true residual (the solves' judge)
+# ---------------------------------------------------------------- true residual (the solves' arbiter)
 
 @pytest.mark.parametrize("dims,t_bc,mu", [((2, 2, 2, 2), -1, 0.0), ((2, 2, 2, 4), -1, 0.0),
                                           ((2, 2, 2, 4), 1, 0.0), ((2, 2, 2, 4), -1, 0.3),
                                           ((2, 2, 2, 2), 1, -0.2)])
 def test_true_residual_against_dense(dims, t_bc, mu):
-    """oracle.true_residual is the judge of every GPU solve, so it is pinned on its own:
+    """oracle.true_residual is the arbiter of every GPU solve, so it is pinned on its own:
     ||b - M x|| / ||b|| with M the dense matrix built block by block (dense.py), for a random
     x where the value is O(1) (Wilson and twisted, both t boundaries). x = 0 gives 1,
     the LAPACK solution gives rounding level, and the value is invariant under a common
