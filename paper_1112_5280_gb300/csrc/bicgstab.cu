@@ -56,7 +56,7 @@ size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 int lqcd::bicgstab_solve(const lqcd_gauge* g, const lqcd_field* src, double kappa, double tol,
                               const lqcd_solve_opts* o, lqcd_field* x, lqcd_solve_info* info) {
-  PdlSolverScope pdl_scope;  // solver launches: no programmatic dependent launch
+  PdlSolverScope pdl_scope(g && pdl_solver_off((g->g.Vh + TILE - 1) / TILE));  // large: no PDL
   const auto t0 = std::chrono::steady_clock::now();
   if (info) memset(info, 0, sizeof *info);
   if (!g || !src || !x || !o) return set_error(LQCD_EINVAL, "NULL argument");

@@ -673,7 +673,7 @@ int lqcd_engine_submit_normal(lqcd_engine* e, const lqcd_gauge* gauge, const lqc
 // NULL starts from x = 0
 static int submit_impl(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field* src, double kappa,
                        double mu, double tol, bool normal, long long* request_id, const lqcd_field* x0) {
-  PdlSolverScope pdl_scope;  // solver launches: no programmatic dependent launch
+  PdlSolverScope pdl_scope(gauge && pdl_solver_off((gauge->g.Vh + TILE - 1) / TILE));  // large: no PDL
   clear_error();
   if (!e || !gauge || !src || !request_id) return set_error(LQCD_EINVAL, "NULL argument");
   if (x0 && (x0->prec != LQCD_F64 || !x0->half[0] || memcmp(x0->g.L, gauge->g.L, sizeof x0->g.L)))
@@ -818,9 +818,17 @@ static int submit_impl(lqcd_engine* e, const lqcd_gauge* gauge, const lqcd_field
   return LQCD_OK;
 }
 
+// tiles of the launches over the engine's active solves (the programmatic-launch rule)
+static long long engine_active_tiles(const lqcd_engine* e) {
+  long long t = 0;
+  if (e)
+    for (long long id : e->active) t += e->reqs.at(id).ntiles;
+  return t;
+}
+
 int lqcd_engine_step(lqcd_engine* e, int* n_active) {
   LQCD_TRACE("lqcd_engine_step");
-  PdlSolverScope pdl_scope;  // solver launches: no programmatic dependent launch
+  PdlSolverScope pdl_scope(pdl_solver_off(engine_active_tiles(e)));  // large launches: no PDL
   clear_error();
   if (!e) return set_error(LQCD_EINVAL, "engine is NULL");
   lqcd_ctx* c = e->ctx;
@@ -896,12 +904,12 @@ int lqcd_engine_completed(lqcd_engine* e, long long* ids, int max, int* n) {
 
 int lqcd_engine_result(lqcd_engine* e, long long id, lqcd_field* x, lqcd_solve_info* info) {
   LQCD_TRACE("lqcd_engine_result");
-  PdlSolverScope pdl_scope;  // solver launches: no programmatic dependent launch
   clear_error();
   if (!e) return set_error(LQCD_EINVAL, "engine is NULL");
   auto it = e->reqs.find(id);
   if (it == e->reqs.end()) return set_error(LQCD_EINVAL, "unknown request %lld", id);
   Request& q = it->second;
+  PdlSolverScope pdl_scope(pdl_solver_off(q.ntiles));  // large launches: no PDL
   if (!q.finished) return set_error(LQCD_EBUSY, "request %lld still running", id);
   LQCD_CK(cudaSetDevice(e->ctx->device));
   if (x) {

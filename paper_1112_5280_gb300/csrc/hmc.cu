@@ -545,7 +545,7 @@ int lqcd_gauge_force(const lqcd_gauge* g, double beta, double coeff, lqcd_mom* m
 int lqcd_fermion_force(const lqcd_gauge* g, double kappa, double mu, const lqcd_field* x, double coeff,
                        lqcd_mom* m, double* s_f) {
   LQCD_TRACE("lqcd_fermion_force");
-  PdlSolverScope pdl_scope;  // solver launches: no programmatic dependent launch
+  PdlSolverScope pdl_scope(g && pdl_solver_off((g->g.Vh + TILE - 1) / TILE));  // large: no PDL
   clear_error();
   LQCD_TRY(check_mom(g, m));
   if (!x || x->prec != LQCD_F64 || x->subset != LQCD_FULL || memcmp(x->g.L, g->g.L, sizeof g->g.L))
@@ -578,7 +578,7 @@ int lqcd_gauge_update(lqcd_gauge* g, const lqcd_mom* m, double eps) {
 int lqcd_solve_normal(const lqcd_gauge* g, const lqcd_field* src, double kappa, double tol,
                       const lqcd_solve_opts* opts, lqcd_field* x, lqcd_solve_info* info) {
   LQCD_TRACE("lqcd_solve_normal");
-  PdlSolverScope pdl_scope;  // solver launches: no programmatic dependent launch
+  PdlSolverScope pdl_scope(g && pdl_solver_off((g->g.Vh + TILE - 1) / TILE));  // large: no PDL
   clear_error();
   if (!g || !src || !x) return set_error(LQCD_EINVAL, "NULL argument");
   lqcd_solve_opts o;
@@ -610,7 +610,7 @@ void lqcd_hmc_params_default(lqcd_hmc_params* p) {
 int lqcd_hmc_trajectory(lqcd_gauge* g, const lqcd_hmc_params* p, lqcd_mom* m, const lqcd_field* phi,
                         const lqcd_solve_opts* opts, lqcd_hmc_info* info) {
   LQCD_TRACE("lqcd_hmc_trajectory");
-  PdlSolverScope pdl_scope;  // solver launches: no programmatic dependent launch
+  PdlSolverScope pdl_scope(g && pdl_solver_off((g->g.Vh + TILE - 1) / TILE));  // large: no PDL
   clear_error();
   const auto t0 = std::chrono::steady_clock::now();
   if (info) memset(info, 0, sizeof *info);

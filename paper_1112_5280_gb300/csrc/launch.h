@@ -39,16 +39,24 @@ LQCD_DECL(df64)
 
 // Launches of the batched kernels, with programmatic stream serialization where enabled:
 // the kernel may then be launched before the previous kernel on the stream completes, and
-// waits for it itself (pdl_wait in batch.cuh). Enabled for operator launches, disabled
-// while a PdlSolverScope is alive on the calling thread (the solvers' step chains, where it
-// measured no faster); LQCD_PDL=1 / 0 forces it on / off everywhere.
+// waits for it itself (pdl_wait in batch.cuh). Enabled for operator launches and for the
+// step chains of small solves; disabled while a PdlSolverScope(true) is alive on the calling
+// thread, which the solvers open when their launches hold more than PDL_SOLVER_MAX_TILES
+// tiles; LQCD_PDL=1 / 0 forces it on / off everywhere.
 bool pdl_enabled();
 struct PdlSolverScope {
-  PdlSolverScope();
+  explicit PdlSolverScope(bool off);
   ~PdlSolverScope();
   PdlSolverScope(const PdlSolverScope&) = delete;
   PdlSolverScope& operator=(const PdlSolverScope&) = delete;
+  bool off_;
 };
+// Measured on GB300: in solver step chains of up to about two tiles per resident CTA (8^4 to
+// 16^3x32 one slot at a time, the 16^3x32 HMC) the programmatic launch hides launch latency
+// (one-by-one small solves 9% faster, HMC 2%); in larger ones it costs up to 10% (the
+// 32^3x64 double-float CG, the 64-lattice engine 6%).
+constexpr long long PDL_SOLVER_MAX_TILES = 2048;
+inline bool pdl_solver_off(long long tiles) { return tiles > PDL_SOLVER_MAX_TILES; }
 template <typename... KArgs, typename... Args>
 cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t dyn_smem, cudaStream_t s,
                      Args&&... args) {

@@ -279,15 +279,19 @@ cudaError_t launch_dslash(int sp, int nr, bool dag, int epi, const Launch& L, in
 // Programmatic dependent launch of the batched kernels (each CTA lets the next grid launch
 // when it starts its last tile). Measured on GB300: the batched 16^3x32 FP32 Dslash of ten
 // slots per launch, applied back to back, 81.5 -> 80.5 us per launch; the solvers' step
-// chains (32^3x64 CG in FP16, BF16, FP32 and double-float, BiCGStab) within +-2% either
-// way, double-float CG the slowest. So it is on for the operator launches (lqcd_dslash_eo,
-// batches, M-hat) and off inside the solvers (PdlSolverScope); LQCD_PDL=1 turns it on
-// everywhere, LQCD_PDL=0 off everywhere.
+// chains gain where their launches are small (up to PDL_SOLVER_MAX_TILES tiles) and lose
+// where they are large (launch.h). So it is on for the operator launches (lqcd_dslash_eo,
+// batches, M-hat) and the small solvers, and off in the large ones (PdlSolverScope);
+// LQCD_PDL=1 turns it on everywhere, LQCD_PDL=0 off everywhere.
 namespace {
 thread_local int t_solver_depth = 0;
 }
-PdlSolverScope::PdlSolverScope() { ++t_solver_depth; }
-PdlSolverScope::~PdlSolverScope() { --t_solver_depth; }
+PdlSolverScope::PdlSolverScope(bool off) : off_(off) {
+  if (off_) ++t_solver_depth;
+}
+PdlSolverScope::~PdlSolverScope() {
+  if (off_) --t_solver_depth;
+}
 
 bool pdl_enabled() {
   static const int mode = [] {
