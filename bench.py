@@ -364,11 +364,16 @@ CLOCK_WINDOW_S = 2.0  # the sampler needs load of at least this length around a 
 
 def run_ours(args, world, rank, local):
     global TUNE
+    import torch
+    from paper_1112_5280_gb300 import lqcd, synth
+    loaded = []
+    if args.load_tune:  # a saved table stands in for the tuner (same choices, no tuning launches)
+        lqcd.tune_load(args.load_tune)
+        args.no_autotune = True
+        loaded = [e for e in lqcd.tune_entries() if e["nrhs"] == 0]
     TUNE = not args.no_autotune
     inputs = generate_inputs(full=not args.dslash_only)
     sets = inputs["sets"]
-    import torch
-    from paper_1112_5280_gb300 import lqcd, synth
 
     dev = local if world > 1 else 0
     torch.cuda.set_device(dev)
@@ -485,6 +490,11 @@ def run_ours(args, world, rank, local):
     peak, peak_kind = measured_peaks()
     # the timed kernel: the tuner's form for the 10-slot key (0: default register budget, 3: 8
     # CTAs per SM); its ncu traffic is keyed by form in profiles/traffic.json
+    if loaded:  # the loaded table's entry for this launch size (FP32, 18 reals)
+        ent = [e for e in loaded if e["prec"] == 1 and e["nr"] == 18 and
+               int(np.log2(e["ntiles"])) == int(np.log2(NSETS * (Vh // 64)))]
+        tuned = {f"f32_x{NSETS}": ent[0]} if ent else {}
+        tuned["loaded_from"] = args.load_tune
     form32 = tuned.get(f"f32_x{NSETS}", {}).get("form", 0) if tuned else 0
     kname = (f"k_dslash<F32,F32,18,nodag,EPI_PLAIN> x{NSETS} slots, form {form32} "
              f"({'8 CTAs per SM, 128 registers' if form32 == 3 else '6 CTAs per SM'})")
@@ -562,6 +572,8 @@ def run_ours(args, world, rank, local):
         section("heatbath", lambda: run_heatbath_section(ctx, lqcd, world, alu))
         section("hmc", lambda: run_hmc_section(ctx, lqcd, world))
     sampler.stop()
+    if args.save_tune and rank == 0:
+        lqcd.tune_save(args.save_tune)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(inputs.get("solve"))
     if rank == 0:
@@ -1022,6 +1034,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (no autotuner)")
+    ap.add_argument("--save-tune", metavar="PATH", help="save the autotuner's table (JSON) after the run")
+    ap.add_argument("--load-tune", metavar="PATH",
+                    help="launch shapes from a saved table instead of tuning (profiling the tuned launches)")
     ap.add_argument("--no-variants", action="store_true", help="skip the one-application-per-launch timings")
     ap.add_argument("--dslash-only", action="store_true", help="skip the solver, multi-RHS, multi-lattice and serving sections")
     ap.add_argument("--section", choices=["heatbath", "hmc", "dslash32", "solve", "mrhs", "cpu"],
