@@ -230,6 +230,43 @@ def test_engine_uneven_lattices_same_alone_and_in_mix(ctx):
     eng.close()
 
 
+@pytest.mark.parametrize("nslots", [100, 140])
+def test_engine_many_slots_same_alone_and_in_mix(ctx, nslots):
+    """An engine holding more slots than the per-CTA slot view takes (128: the launches then
+    stride over all tiles and read slot states from global memory) and one holding fewer
+    (the view compacts the running slots): slots that converge and update at different
+    iterations each give their solo result bit for bit."""
+    shapes = [(4, 4, 4, 4), (4, 4, 2, 4), (2, 4, 4, 4)]
+    opts = lqcd.solve_opts(sloppy_prec="f32")
+    eng = lqcd.Engine(ctx, opts, max_slots=nslots)
+    items = []
+    for k in range(nslots):
+        dims = shapes[k % 3]
+        kappa = 0.12 + 0.03 * (k % 7) / 6
+        U = synth.random_links(dims, 0.5, seed=3000 + k)
+        g = ctx.gauge(dims, U, prec="f64")
+        src = ctx.field(dims, "f64", lqcd.FULL, data=synth.gaussian_spinor(dims, seed=5000 + k))
+        items.append((eng.submit(g, src, kappa, 1e-10), dims, kappa, g, src))
+    while eng.step() > 0:
+        pass
+    iters = set()
+    for rid, dims, kappa, g, src in items:
+        x = ctx.field(dims, "f64", lqcd.FULL)
+        info = eng.result(rid, x)
+        assert info["status"] == 0 and info["true_resid"] <= 1e-10, info
+        iters.add(info["iters"])
+        xs = ctx.field(dims, "f64", lqcd.FULL)
+        lqcd.solve_fields(g, src, kappa, 1e-10, xs, opts)
+        assert np.array_equal(xs.download(), x.download()), (rid, dims, kappa)
+        x.close()
+        xs.close()
+    assert len(iters) > 1  # the slots ran different iteration counts
+    eng.close()
+    for _, _, _, g, src in items:
+        g.close()
+        src.close()
+
+
 def test_multi_group_reduction_alone_and_in_mix(ctx):
     """A slot of more than 1024 tiles has its reductions summed by several CTAs (a count
     fixed by its own tiles); in a batch with a small lattice it still gives its solo
