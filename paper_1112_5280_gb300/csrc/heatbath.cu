@@ -139,7 +139,8 @@ __device__ __noinline__ bool su2_draw(double alpha, uint64_t seed, uint64_t c0, 
 // only: the caller rebuilds the FP64 master from it.
 // 3 CTAs of 128 threads per SM (168 registers, a 100-byte spill) against 2 (254 registers,
 // no spill): measured on GB300 at 32^3x64 beta 6, 39.7 against 43.2 ms per sweep with the
-// same chain; the update is latency bound, so the extra warps outweigh the spill.
+// same chain; the update is latency bound, so the extra warps outweigh the spill. At 4 CTAs
+// (128 registers) the spill grows and the sweep takes 40.1 ms.
 #ifndef LQCD_HB_MIN_BLOCKS
 #define LQCD_HB_MIN_BLOCKS 3
 #endif
