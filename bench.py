@@ -925,7 +925,7 @@ def run_serve_section(ctx, lqcd, inputs, world, rank):
     queue the capacity was measured with."""
     from paper_1112_5280_gb300 import serve, synth
     gpools, spools = inputs["serve"]
-    opts = lqcd.solve_opts(sloppy_prec="f16", sloppy_compress=12, chunk=16)
+    opts = lqcd.solve_opts(sloppy_prec="f16", sloppy_compress=12)
     budget = 64 << 30
     srv = serve.GpuServer(ctx, serve.LATTICES, gpools, spools, opts=opts, hbm_budget=budget,
                           max_slots=64)

@@ -221,7 +221,7 @@ typedef struct lqcd_solve_opts {
   int maxiter;          /* iteration limit (default 50000) */
   double delta;         /* reliable-update threshold on |r| (<= 0: 0.01 for FP16 / BF16 sloppy,
                            0.001 for FP32 sloppy, none for FP64 and double-float) */
-  int chunk;            /* iterations per CUDA-graph replay / host poll (default 32) */
+  int chunk;            /* iterations per CUDA-graph replay / host poll (default 8) */
   int use_graph;        /* 1: capture iteration chunks as CUDA graphs (default 1) */
   int ru_interval;      /* iterations between reliable-update blocks in a CUDA-graph chunk
                            (0: default 4) */
